@@ -1,0 +1,245 @@
+"""ctypes front-end of the FP64 CPU oracle (oracle/bt_oracle.c).
+
+TEST INFRASTRUCTURE.  Only the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this package.  The product path (the
+CUDA library and its binding) never touches it.
+
+A "graph" here is anything with the attributes ``renders`` (objects with
+``depth`` float32 HxW, ``normals`` float32 HxWx3, ``mask`` uint8 HxW),
+``cams`` (objects with ``fx, fy, cx, cy, width, height``), ``matches``
+(list of ``(i, j, pts_i, pts_j)``), ``pose_init`` (N,4,4) and ``fixed`` (N,).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+
+
+class _Frame(C.Structure):
+    _fields_ = [("depth", C.POINTER(C.c_float)), ("normals", C.POINTER(C.c_float)),
+                ("mask", C.POINTER(C.c_uint8)), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class _MatchSet(C.Structure):
+    _fields_ = [("i", C.c_int32), ("j", C.c_int32), ("count", C.c_int32),
+                ("pts_i", C.POINTER(C.c_float)), ("pts_j", C.POINTER(C.c_float))]
+
+
+class _Params(C.Structure):
+    _fields_ = [("huber_sparse", C.c_double), ("huber_dense", C.c_double),
+                ("dense_max_dist", C.c_double), ("dense_max_normal_deg", C.c_double),
+                ("lambda_sparse", C.c_double), ("lambda_dense", C.c_double)]
+
+
+@dataclass
+class Params:
+    """Method constants.  Defaults: Huber thresholds 5 mm and normal gate
+    45 deg (the paper's only distance and angle constants, Sec. IV-B),
+    distance gate 2 cm, lambda_1 = lambda_2 = 1 (Sec. IV-D)."""
+    huber_sparse: float = 0.005
+    huber_dense: float = 0.005
+    dense_max_dist: float = 0.02
+    dense_max_normal_deg: float = 45.0
+    lambda_sparse: float = 1.0
+    lambda_dense: float = 1.0
+
+    def c(self) -> _Params:
+        return _Params(self.huber_sparse, self.huber_dense, self.dense_max_dist,
+                       self.dense_max_normal_deg, self.lambda_sparse, self.lambda_dense)
+
+
+_LIB = None
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        path = _build.build()
+        L = C.CDLL(str(path))
+        L.orc_huber_rho.restype = C.c_double
+        L.orc_huber_rho.argtypes = [C.c_double, C.c_double]
+        L.orc_huber_weight.restype = C.c_double
+        L.orc_huber_weight.argtypes = [C.c_double, C.c_double]
+        L.orc_se3_exp.argtypes = [_dp, _dp]
+        L.orc_se3_log.argtypes = [_dp, _dp]
+        L.orc_cholesky_solve.restype = C.c_int
+        L.orc_cholesky_solve.argtypes = [C.c_int, _dp, _dp]
+        L.orc_associate.restype = C.c_int
+        L.orc_associate.argtypes = [C.POINTER(_Frame), C.POINTER(_Frame), _dp, _dp,
+                                    C.POINTER(_Params), _ip, _ip, C.c_int]
+        L.orc_dense_terms.argtypes = [C.POINTER(_Frame), C.POINTER(_Frame), _dp, _dp, _ip, _ip,
+                                      C.c_int, _dp, _dp]
+        L.orc_sparse_terms.argtypes = [C.POINTER(_MatchSet), _dp, _dp, _dp, _dp]
+        L.orc_energy.argtypes = [C.POINTER(_Frame), C.c_int, _dp, C.POINTER(_MatchSet), C.c_int,
+                                 C.POINTER(_Params), C.c_int, _dp]
+        L.orc_normal_equations.restype = C.c_long
+        L.orc_normal_equations.argtypes = [C.POINTER(_Frame), C.c_int, _dp, C.POINTER(_MatchSet),
+                                           C.c_int, C.POINTER(_Params), C.c_int, _dp, _dp, _dp]
+        L.orc_solve.restype = C.c_int
+        L.orc_solve.argtypes = [C.POINTER(_Frame), C.c_int, _dp, _ip, C.POINTER(_MatchSet), C.c_int,
+                                C.POINTER(_Params), C.c_int, C.c_int, _dp, _dp]
+        _LIB = L
+    return _LIB
+
+
+def default_threads() -> int:
+    return max(1, os.cpu_count() or 1)
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+class Problem:
+    """Marshals a graph into the oracle's C structures (kept alive here)."""
+
+    def __init__(self, graph, nodes=None):
+        nodes = list(range(len(graph.renders))) if nodes is None else list(nodes)
+        pos = {f: k for k, f in enumerate(nodes)}
+        self.keep = []
+        self.frames = (_Frame * max(1, len(nodes)))()
+        for k, f in enumerate(nodes):
+            r, cam = graph.renders[f], graph.cams[f]
+            d = np.ascontiguousarray(r.depth, np.float32)
+            n = np.ascontiguousarray(r.normals, np.float32)
+            m = np.ascontiguousarray(r.mask, np.uint8)
+            self.keep += [d, n, m]
+            self.frames[k] = _Frame(_ptr(d, C.c_float), _ptr(n, C.c_float), _ptr(m, C.c_uint8),
+                                    cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height)
+        sets = []
+        for (i, j, pi, pj) in graph.matches:
+            if i in pos and j in pos and len(pi) > 0:
+                a = np.ascontiguousarray(pi, np.float32)
+                b = np.ascontiguousarray(pj, np.float32)
+                self.keep += [a, b]
+                sets.append(_MatchSet(pos[i], pos[j], len(a), _ptr(a, C.c_float), _ptr(b, C.c_float)))
+        self.n_sets = len(sets)
+        self.sets = (_MatchSet * max(1, len(sets)))(*sets)
+        self.n = len(nodes)
+        self.nodes = nodes
+        self.fixed = np.ascontiguousarray(np.asarray(graph.fixed)[nodes], np.int32)
+        self.pose_init = np.ascontiguousarray(np.asarray(graph.pose_init)[nodes], np.float64)
+
+
+def solve(graph, iters: int, params: Params | None = None, poses=None, n_threads: int | None = None,
+          nodes=None):
+    """Run the FP64 Gauss-Newton solve.  Returns dict(poses, cost_per_iter,
+    cost_final, status)."""
+    P = Problem(graph, nodes)
+    prm = (params or Params()).c()
+    X = np.ascontiguousarray(P.pose_init if poses is None else poses, np.float64).copy()
+    cpi = np.zeros(max(1, iters))
+    cf = np.zeros(1)
+    st = lib().orc_solve(P.frames, P.n, _ptr(X, C.c_double), _ptr(P.fixed, C.c_int32), P.sets, P.n_sets,
+                         C.byref(prm), iters, n_threads or default_threads(),
+                         _ptr(cpi, C.c_double), _ptr(cf, C.c_double))
+    return dict(poses=X, cost_per_iter=cpi[:iters], cost_final=float(cf[0]), status=int(st))
+
+
+def energy(graph, poses, params: Params | None = None, n_threads: int | None = None, nodes=None):
+    """Eq. 1 at `poses`: dict(total, dense, sparse, dense_count, sparse_count)."""
+    P = Problem(graph, nodes)
+    prm = (params or Params()).c()
+    X = np.ascontiguousarray(poses, np.float64)
+    out = np.zeros(5)
+    lib().orc_energy(P.frames, P.n, _ptr(X, C.c_double), P.sets, P.n_sets, C.byref(prm),
+                     n_threads or default_threads(), _ptr(out, C.c_double))
+    return dict(total=out[0], dense=out[1], sparse=out[2], dense_count=int(out[3]),
+                sparse_count=int(out[4]))
+
+
+def normal_equations(graph, poses, params: Params | None = None, n_threads: int | None = None,
+                     nodes=None):
+    """Full 6N x 6N H, 6N g and the energy at `poses` (no gauge applied)."""
+    P = Problem(graph, nodes)
+    prm = (params or Params()).c()
+    X = np.ascontiguousarray(poses, np.float64)
+    H = np.zeros((6 * P.n, 6 * P.n))
+    g = np.zeros(6 * P.n)
+    E = np.zeros(1)
+    cnt = lib().orc_normal_equations(P.frames, P.n, _ptr(X, C.c_double), P.sets, P.n_sets,
+                                     C.byref(prm), n_threads or default_threads(),
+                                     _ptr(H, C.c_double), _ptr(g, C.c_double), _ptr(E, C.c_double))
+    return H, g, float(E[0]), int(cnt)
+
+
+def associate(graph, i: int, j: int, poses, params: Params | None = None):
+    """Accepted (source pixel, target pixel) pairs of the ordered pair i -> j."""
+    P = Problem(graph)
+    prm = (params or Params()).c()
+    X = np.ascontiguousarray(poses, np.float64)
+    cap = graph.cams[i].width * graph.cams[i].height
+    sp = np.zeros(cap, np.int32)
+    tp = np.zeros(cap, np.int32)
+    n = lib().orc_associate(C.byref(P.frames[i]), C.byref(P.frames[j]), _ptr(X[i], C.c_double),
+                            _ptr(X[j], C.c_double), C.byref(prm), _ptr(sp, C.c_int32),
+                            _ptr(tp, C.c_int32), cap)
+    return sp[:n].copy(), tp[:n].copy()
+
+
+def dense_terms(graph, i: int, j: int, poses, src, tgt):
+    """Residuals (n,) and 12-column Jacobians (n,12) for a frozen association."""
+    P = Problem(graph)
+    X = np.ascontiguousarray(poses, np.float64)
+    src = np.ascontiguousarray(src, np.int32)
+    tgt = np.ascontiguousarray(tgt, np.int32)
+    n = len(src)
+    r = np.zeros(max(1, n))
+    J = np.zeros((max(1, n), 12))
+    lib().orc_dense_terms(C.byref(P.frames[i]), C.byref(P.frames[j]), _ptr(X[i], C.c_double),
+                          _ptr(X[j], C.c_double), _ptr(src, C.c_int32), _ptr(tgt, C.c_int32), n,
+                          _ptr(r, C.c_double), _ptr(J, C.c_double))
+    return r[:n].copy(), J[:n].copy()
+
+
+def sparse_terms(pts_i, pts_j, Ti, Tj):
+    """Residuals e (n,3) and Jacobians (n,3,12) of one correspondence set."""
+    a = np.ascontiguousarray(pts_i, np.float32)
+    b = np.ascontiguousarray(pts_j, np.float32)
+    n = len(a)
+    ms = _MatchSet(0, 1, n, _ptr(a, C.c_float), _ptr(b, C.c_float))
+    e = np.zeros((max(1, n), 3))
+    J = np.zeros((max(1, n), 3, 12))
+    Ti = np.ascontiguousarray(Ti, np.float64)
+    Tj = np.ascontiguousarray(Tj, np.float64)
+    lib().orc_sparse_terms(C.byref(ms), _ptr(Ti, C.c_double), _ptr(Tj, C.c_double),
+                           _ptr(e, C.c_double), _ptr(J, C.c_double))
+    return e[:n].copy(), J[:n].copy()
+
+
+def se3_exp(xi) -> np.ndarray:
+    xi = np.ascontiguousarray(xi, np.float64)
+    T = np.zeros(16)
+    lib().orc_se3_exp(_ptr(xi, C.c_double), _ptr(T, C.c_double))
+    return T.reshape(4, 4)
+
+
+def se3_log(T) -> np.ndarray:
+    T = np.ascontiguousarray(T, np.float64).reshape(16)
+    xi = np.zeros(6)
+    lib().orc_se3_log(_ptr(T, C.c_double), _ptr(xi, C.c_double))
+    return xi
+
+
+def cholesky_solve(A, b):
+    A = np.ascontiguousarray(A, np.float64).copy()
+    b = np.ascontiguousarray(b, np.float64).copy()
+    st = lib().orc_cholesky_solve(len(b), _ptr(A, C.c_double), _ptr(b, C.c_double))
+    return b, st
+
+
+def huber_rho(r, delta):
+    return lib().orc_huber_rho(float(r), float(delta))
+
+
+def huber_weight(r, delta):
+    return lib().orc_huber_weight(float(r), float(delta))
