@@ -244,6 +244,9 @@ int orc_associate(const orc_frame* fi, const orc_frame* fj, const double Ti[16],
     const float dmax2 = (float)(prm->dense_max_dist * prm->dense_max_dist);
     const float cmin = (float)cos(prm->dense_max_normal_deg * ORC_PI / 180.0);
     const float Wf = (float)fj->width, Hf = (float)fj->height;
+    /* reciprocal focal lengths, one IEEE single division each */
+    const float ifx_i = 1.0f / fi->fx, ify_i = 1.0f / fi->fy;
+    const float ifx_j = 1.0f / fj->fx, ify_j = 1.0f / fj->fy;
     int n = 0;
     for (int v = 0; v < fi->height; ++v) {
         for (int u = 0; u < fi->width; ++u) {
@@ -251,17 +254,18 @@ int orc_associate(const orc_frame* fi, const orc_frame* fj, const double Ti[16],
             if (!pixel_valid(fi, pix)) continue;
             /* source point p = pi_D^-1(x) in camera i (single precision) */
             float z = fi->depth[pix];
-            float px = (((float)u - fi->cx) * z) / fi->fx;
-            float py = (((float)v - fi->cy) * z) / fi->fy;
+            float px = (((float)u - fi->cx) * z) * ifx_i;
+            float py = (((float)v - fi->cy) * z) * ify_i;
             float pz = z;
             /* T_j T_i^-1 p */
             float qjx = ((m[0] * px + m[1] * py) + m[2] * pz) + m[3];
             float qjy = ((m[4] * px + m[5] * py) + m[6] * pz) + m[7];
             float qjz = ((m[8] * px + m[9] * py) + m[10] * pz) + m[11];
             if (!(qjz > 0.0f)) continue;
-            /* pi(.) and the nearest pixel */
-            float uf = (fj->fx * qjx) / qjz + fj->cx;
-            float vf = (fj->fy * qjy) / qjz + fj->cy;
+            /* pi(.) with one correctly rounded reciprocal, then the nearest pixel */
+            float rz = 1.0f / qjz;
+            float uf = ((fj->fx * qjx) * rz) + fj->cx;
+            float vf = ((fj->fy * qjy) * rz) + fj->cy;
             float uh = uf + 0.5f, vh = vf + 0.5f;
             if (!(uh >= 0.0f && uh < Wf && vh >= 0.0f && vh < Hf)) continue;
             int iu = (int)floorf(uh), iv = (int)floorf(vh);
@@ -269,8 +273,8 @@ int orc_associate(const orc_frame* fi, const orc_frame* fj, const double Ti[16],
             if (!pixel_valid(fj, tp)) continue;
             /* pi_D^-1 at the looked-up pixel, camera j */
             float zt = fj->depth[tp];
-            float tx = (((float)iu - fj->cx) * zt) / fj->fx;
-            float ty = (((float)iv - fj->cy) * zt) / fj->fy;
+            float tx = (((float)iu - fj->cx) * zt) * ifx_j;
+            float ty = (((float)iv - fj->cy) * zt) * ify_j;
             float tz = zt;
             /* gate 1: point-pair distance */
             float dx = tx - qjx, dy = ty - qjy, dz = tz - qjz;
