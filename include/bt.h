@@ -1,0 +1,205 @@
+/*
+ * bt.h -- C interface of the GB300 pose-graph library (libbt.so).
+ *
+ * The library implements the online pose-graph optimisation of BundleTrack
+ * (Wen & Bekris, IROS 2021, Sec. IV-D): for the current frame and the
+ * keyframes retrieved from the memory pool it minimises Eq. 1,
+ *
+ *     E = sum_{i != j} ( lambda_1 E_f(i,j) + lambda_2 E_g(i,j) ),
+ *
+ * where E_f (Eq. 2) is a Huber-robust point-to-point cost over sparse feature
+ * correspondences and E_g (Eq. 3) a Huber-robust point-to-plane cost over the
+ * dense projective association of every masked pixel, by iteratively
+ * re-weighted Gauss-Newton on se(3) with the first frame held fixed.
+ *
+ * Conventions used by every call:
+ *   - pose: 4x4 row-major double, maps OBJECT coordinates to CAMERA
+ *     coordinates of that frame (Sec. III, "the object pose in the camera's
+ *     frame"); the last row must be 0 0 0 1;
+ *   - pixel (u, v): u = column, v = row, pixel centres at integer coordinates;
+ *     pinhole model u = fx X/Z + cx, v = fy Y/Z + cy;
+ *   - depth: metres along the optical axis, row-major H x W float; values
+ *     <= 0 or non-finite mean "no measurement";
+ *   - normals: camera frame, row-major H x W x 3 float, non-finite = none;
+ *   - mask: row-major H x W uint8, nonzero = object (Sec. IV-A).
+ * A pixel takes part in the dense term (as source or as target) when it is
+ * masked, has a positive finite depth and a finite normal.
+ *
+ * Memory and threading:
+ *   - every call enqueues its GPU work on the stream given at creation
+ *     (a cudaStream_t passed as void*, NULL = the legacy default stream);
+ *   - input buffers stay owned by the caller and are copied (host) or read
+ *     (device) before the call returns, so they may be freed afterwards;
+ *   - output buffers are caller-allocated host memory;
+ *   - calls that return data to the host synchronise that stream;
+ *   - one graph may be used by one host thread at a time;
+ *   - no call aborts or throws: every failure is a negative status
+ *     (BT_ERR_*) and bt_last_error() gives a message for the calling thread.
+ */
+#ifndef BT_H
+#define BT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define BT_OK 0
+#define BT_ERR_INVALID (-1)   /* bad argument, size or state of an argument */
+#define BT_ERR_CUDA (-2)      /* a CUDA call failed (message has the detail) */
+#define BT_ERR_OOM (-3)       /* device or host allocation failed */
+#define BT_ERR_SINGULAR (-4)  /* normal equations not positive definite */
+#define BT_ERR_TIMEOUT (-5)   /* a bounded device-side wait ran out */
+#define BT_ERR_STATE (-6)     /* call not valid in the graph's current state */
+
+/* memory kinds of input pointers */
+#define BT_HOST 0
+#define BT_DEVICE 1
+
+/* storage precision of the per-pixel point/normal maps */
+#define BT_FP32 0
+#define BT_BF16 1
+#define BT_FP16 2
+
+#define BT_MAX_NODES 24          /* nodes in one solve (6*(N-1) <= 138 unknowns) */
+#define BT_MAX_REPORT_ITERS 64
+
+typedef struct bt_graph bt_graph;   /* opaque; created and freed by the library */
+
+typedef struct {
+    float fx, fy, cx, cy;   /* pinhole intrinsics, pixels */
+    int32_t width, height;  /* image size, pixels (>= 1) */
+} bt_intrinsics;
+
+/* Method constants.  bt_config_default() fills the values this library uses
+ * when the paper leaves a constant unstated:
+ *   huber_sparse = huber_dense = 0.005 m   (Huber thresholds of Eq. 2 / Eq. 3)
+ *   dense_max_dist = 0.02 m                (association gate on point-pair distance)
+ *   dense_max_normal_deg = 45              (association gate on normal angle)
+ *   lambda_sparse = lambda_dense = 1       (lambda_1, lambda_2 of Eq. 1)
+ *   precision = BT_FP32, max_frames = 0 (no limit on stored frames). */
+typedef struct {
+    double huber_sparse;
+    double huber_dense;
+    double dense_max_dist;
+    double dense_max_normal_deg;
+    double lambda_sparse;
+    double lambda_dense;
+    int32_t precision;
+    int32_t max_frames;
+} bt_config;
+
+/* Correspondences between a frame being added and an already stored frame
+ * (the set C_ij of Eq. 2; the paper caches it per pair, Sec. IV-D). */
+typedef struct {
+    int32_t other_frame;     /* id returned by an earlier bt_add_frame */
+    int32_t count;           /* number of pairs, >= 0 */
+    const float* pts_self;   /* count x 3, camera frame of the new frame */
+    const float* pts_other;  /* count x 3, camera frame of other_frame */
+} bt_matches;
+
+typedef struct {
+    int32_t iters_run;        /* Gauss-Newton iterations executed */
+    int32_t status;           /* BT_OK or the error the solve ended with */
+    int32_t used_warmstart;   /* reserved, 0 */
+    int32_t fell_back;        /* reserved, 0 */
+    double cost_init;         /* E (Eq. 1) at the starting poses */
+    double cost_final;        /* E at the returned poses (association recomputed) */
+    double dense_cost_final;  /* lambda_2 part of cost_final */
+    double sparse_cost_final; /* lambda_1 part of cost_final */
+    double cost_per_iter[BT_MAX_REPORT_ITERS]; /* E before iteration k */
+    int64_t dense_inliers;    /* accepted dense associations at the final poses */
+    int64_t dense_pixel_pairs;/* sum over ordered pairs of source pixels, x iters */
+} bt_solve_report;
+
+/* Fills *cfg with the defaults above.  Never fails. */
+void bt_config_default(bt_config* cfg);
+
+/* Creates an empty graph (Sec. IV-D, G = {V, E}).  cfg may be NULL (defaults).
+ * cuda_stream: cudaStream_t as void* (NULL = legacy default stream); the
+ * caller keeps ownership and must keep it alive until bt_graph_destroy.
+ * Returns BT_OK and *out, or BT_ERR_INVALID (bad cfg / out NULL),
+ * BT_ERR_CUDA, BT_ERR_OOM. */
+int bt_graph_create(const bt_config* cfg, void* cuda_stream, bt_graph** out);
+
+/* Frees the graph and all device memory it owns (synchronises its stream).
+ * NULL is ignored. */
+void bt_graph_destroy(bt_graph* g);
+
+/* Adds one RGB-D observation I_tau (Sec. III) with its mask M_tau and normal
+ * map, builds its device point/normal maps and its list of dense source
+ * pixels, and stores its initial pose.  The new frame joins the active node
+ * set at the end.  fixed != 0 holds the pose constant (the gauge: frame I_0,
+ * Sec. IV-D).  matches (n_matches entries, may be NULL when 0) add the
+ * correspondence sets between this frame and earlier frames.
+ *   depth:   H x W float;  normals: H x W x 3 float;  mask: H x W uint8;
+ *   mem_kind: BT_HOST (pageable or pinned host memory) or BT_DEVICE (device
+ *   pointers on this GPU) -- it applies to depth, normals, mask and the
+ *   match point arrays; intrinsics and pose_init are always host memory.
+ * On success *frame_id_out (may be NULL) receives the new frame's id.
+ * Errors: BT_ERR_INVALID (NULL required pointer, size <= 0, unknown
+ * other_frame, negative count, more than max_frames frames),
+ * BT_ERR_CUDA, BT_ERR_OOM.  On error the graph is unchanged. */
+int bt_add_frame(bt_graph* g, const float* depth, const float* normals, const uint8_t* mask,
+                 const bt_intrinsics* intrinsics, const double pose_init[16], int32_t fixed,
+                 const bt_matches* matches, int32_t n_matches, int32_t mem_kind,
+                 int32_t* frame_id_out);
+
+/* Sets (replaces) the correspondence set between two stored frames:
+ * pts_a[k] (camera frame of frame_a) matches pts_b[k] (camera frame of
+ * frame_b); count x 3 floats each, in memory of kind mem_kind.  count == 0
+ * removes the set.  Errors: BT_ERR_INVALID, BT_ERR_CUDA, BT_ERR_OOM. */
+int bt_set_matches(bt_graph* g, int32_t frame_a, int32_t frame_b, int32_t count,
+                   const float* pts_a, const float* pts_b, int32_t mem_kind);
+
+/* Removes a stored frame (and every correspondence set that involves it)
+ * and frees its device memory; it also leaves the active set.
+ * Errors: BT_ERR_INVALID (unknown id). */
+int bt_remove_frame(bt_graph* g, int32_t frame_id);
+
+/* Chooses which stored frames form the pose graph of the next solve, in node
+ * order (the keyframes selected for the current frame, Sec. IV-C), n >= 1,
+ * no repeats, n <= BT_MAX_NODES.  Until called, the active set is every frame
+ * in the order added.  Errors: BT_ERR_INVALID. */
+int bt_set_active(bt_graph* g, const int32_t* frame_ids, int32_t n);
+
+/* Number of active nodes, or a negative status. */
+int bt_num_active(const bt_graph* g);
+
+/* Replaces / reads the poses of the active nodes (n_active x 16 doubles,
+ * host, node order).  Errors: BT_ERR_INVALID. */
+int bt_set_poses(bt_graph* g, const double* poses);
+int bt_get_poses(const bt_graph* g, double* poses);
+
+/* Runs `iters` (0..BT_MAX_REPORT_ITERS) Gauss-Newton iterations of Sec.
+ * IV-D over the active nodes -- per iteration: dense association and
+ * point-to-plane residuals for every ordered pair, Huber point-to-point
+ * residuals for every correspondence set, reduction into 6x6 blocks,
+ * assembly of the normal equations over the non-fixed nodes, FP64 Cholesky
+ * solve, FP64 se(3) update -- then evaluates E at the final poses.  The new
+ * poses are stored in the graph (the memory write-back of Sec. IV-D) and, if
+ * poses_out != NULL, copied to it (n_active x 16 doubles, host).  rep may be
+ * NULL.  Synchronises the stream.
+ * Errors: BT_ERR_INVALID (iters out of range, no active nodes, more than
+ * BT_MAX_NODES), BT_ERR_SINGULAR (a system was not positive definite: poses
+ * are left as they were before the call), BT_ERR_CUDA, BT_ERR_OOM. */
+int bt_solve(bt_graph* g, int32_t iters, double* poses_out, bt_solve_report* rep);
+
+/* Evaluates Eq. 1 at the stored poses of the active nodes (association
+ * recomputed), without changing them.  cost_out[0] = E, [1] = dense part,
+ * [2] = sparse part (host, 3 doubles); dense_inliers may be NULL.
+ * Synchronises the stream.  Errors: BT_ERR_INVALID, BT_ERR_CUDA. */
+int bt_eval_cost(bt_graph* g, double* cost_out, int64_t* dense_inliers);
+
+/* Text for a status code (static storage). */
+const char* bt_status_str(int status);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* bt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,279 @@
+"""Python binding of libbt (include/bt.h): argument marshalling only.
+
+Every step of the pose-graph solve runs in the library's CUDA kernels; this
+module converts numpy arrays (host memory) or CUDA tensors (device memory) to
+pointers, calls the C functions of the same name, and turns status codes into
+exceptions.  Importing it loads the compiled library and fails loudly if it
+has not been built or cannot be loaded; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+
+BT_OK = 0
+BT_ERR_INVALID = -1
+BT_ERR_CUDA = -2
+BT_ERR_OOM = -3
+BT_ERR_SINGULAR = -4
+BT_ERR_TIMEOUT = -5
+BT_ERR_STATE = -6
+BT_HOST = 0
+BT_DEVICE = 1
+BT_FP32 = 0
+BT_BF16 = 1
+BT_FP16 = 2
+BT_MAX_NODES = 24
+BT_MAX_REPORT_ITERS = 64
+
+LIB_PATH = Path(__file__).resolve().parent / "_build" / "libbt.so"
+
+
+class bt_intrinsics(C.Structure):
+    _fields_ = [("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float),
+                ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class bt_config(C.Structure):
+    _fields_ = [("huber_sparse", C.c_double), ("huber_dense", C.c_double),
+                ("dense_max_dist", C.c_double), ("dense_max_normal_deg", C.c_double),
+                ("lambda_sparse", C.c_double), ("lambda_dense", C.c_double),
+                ("precision", C.c_int32), ("max_frames", C.c_int32)]
+
+
+class bt_matches(C.Structure):
+    _fields_ = [("other_frame", C.c_int32), ("count", C.c_int32),
+                ("pts_self", C.c_void_p), ("pts_other", C.c_void_p)]
+
+
+class bt_solve_report(C.Structure):
+    _fields_ = [("iters_run", C.c_int32), ("status", C.c_int32), ("used_warmstart", C.c_int32),
+                ("fell_back", C.c_int32), ("cost_init", C.c_double), ("cost_final", C.c_double),
+                ("dense_cost_final", C.c_double), ("sparse_cost_final", C.c_double),
+                ("cost_per_iter", C.c_double * BT_MAX_REPORT_ITERS), ("dense_inliers", C.c_int64),
+                ("dense_pixel_pairs", C.c_int64)]
+
+
+# name -> (restype, argtypes); every symbol include/bt.h declares
+SIGNATURES = {
+    "bt_config_default": (None, [C.POINTER(bt_config)]),
+    "bt_graph_create": (C.c_int, [C.POINTER(bt_config), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "bt_graph_destroy": (None, [C.c_void_p]),
+    "bt_add_frame": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(bt_intrinsics),
+                               C.POINTER(C.c_double), C.c_int32, C.POINTER(bt_matches), C.c_int32, C.c_int32,
+                               C.POINTER(C.c_int32)]),
+    "bt_set_matches": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                 C.c_int32]),
+    "bt_remove_frame": (C.c_int, [C.c_void_p, C.c_int32]),
+    "bt_set_active": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32]),
+    "bt_num_active": (C.c_int, [C.c_void_p]),
+    "bt_set_poses": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "bt_get_poses": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "bt_solve": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(bt_solve_report)]),
+    "bt_eval_cost": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "bt_status_str": (C.c_char_p, [C.c_int]),
+    "bt_last_error": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path: Path | str | None = None):
+    """Load libbt.so (once).  Raises RuntimeError if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = Path(path) if path else LIB_PATH
+    if not p.exists():
+        raise RuntimeError(f"libbt.so not found at {p}: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = C.CDLL(str(p))
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+class BTError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        L = load()
+        msg = L.bt_last_error().decode() or L.bt_status_str(status).decode()
+        super().__init__(f"{where}: {L.bt_status_str(status).decode()} ({status}): {msg}")
+        self.status = status
+
+
+def _check(st: int, where: str):
+    if st != BT_OK:
+        raise BTError(st, where)
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype, shape_check=None):
+    """(pointer, keepalive, mem_kind) for a numpy array or a CUDA tensor."""
+    if _is_torch(x):
+        if not x.is_cuda:
+            x = x.contiguous().numpy()
+        else:
+            x = x.contiguous()
+            return C.c_void_p(x.data_ptr()), x, BT_DEVICE
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return C.c_void_p(a.ctypes.data), a, BT_HOST
+
+
+def config_default() -> bt_config:
+    c = bt_config()
+    load().bt_config_default(C.byref(c))
+    return c
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)      # torch.cuda.Stream
+
+
+class PoseGraph:
+    """Owns one bt_graph.  Frames are numpy arrays (copied from host) or CUDA
+    tensors (read on the device); poses are 4x4 float64 object->camera."""
+
+    def __init__(self, config: bt_config | dict | None = None, stream=None):
+        L = load()
+        cfg = config_default()
+        if isinstance(config, dict):
+            for k, v in config.items():
+                setattr(cfg, k, v)
+        elif config is not None:
+            cfg = config
+        self._h = C.c_void_p()
+        self._stream = stream
+        _check(L.bt_graph_create(C.byref(cfg), _stream_handle(stream), C.byref(self._h)), "bt_graph_create")
+        self.config = cfg
+
+    def close(self):
+        if self._h:
+            load().bt_graph_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def add_frame(self, depth, normals, mask, intrinsics, pose, fixed=False, matches=()):
+        """matches: iterable of (other_frame_id, pts_self (n,3), pts_other (n,3))."""
+        L = load()
+        d, kd, mk = _ptr(depth, np.float32)
+        n, kn, mk2 = _ptr(normals, np.float32)
+        m, km, mk3 = _ptr(mask, np.uint8)
+        if not (mk == mk2 == mk3):
+            raise ValueError("depth, normals and mask must all be host arrays or all CUDA tensors")
+        fx, fy, cx, cy, w, h = intrinsics
+        K = bt_intrinsics(fx, fy, cx, cy, w, h)
+        P = np.ascontiguousarray(pose, np.float64).reshape(16)
+        keep = [kd, kn, km]
+        ms = (bt_matches * max(1, len(matches)))()
+        for k, (other, ps, po) in enumerate(matches):
+            a, ka, mka = _ptr(ps, np.float32)
+            b, kb, mkb = _ptr(po, np.float32)
+            if not (mka == mkb == mk):
+                raise ValueError("matches must use the same memory kind as the frame")
+            keep += [ka, kb]
+            ms[k] = bt_matches(int(other), int(len(ps)), a, b)
+        fid = C.c_int32(-1)
+        _check(L.bt_add_frame(self._h, d, n, m, C.byref(K), P.ctypes.data_as(C.POINTER(C.c_double)),
+                              int(bool(fixed)), ms, len(matches), mk, C.byref(fid)), "bt_add_frame")
+        return fid.value
+
+    def set_matches(self, frame_a, frame_b, pts_a, pts_b):
+        a, ka, mka = _ptr(pts_a, np.float32)
+        b, kb, mkb = _ptr(pts_b, np.float32)
+        if mka != mkb:
+            raise ValueError("pts_a and pts_b must share a memory kind")
+        _check(load().bt_set_matches(self._h, int(frame_a), int(frame_b), int(len(pts_a)), a, b, mka),
+               "bt_set_matches")
+
+    def remove_frame(self, frame_id):
+        _check(load().bt_remove_frame(self._h, int(frame_id)), "bt_remove_frame")
+
+    def set_active(self, ids):
+        arr = np.ascontiguousarray(ids, np.int32)
+        _check(load().bt_set_active(self._h, arr.ctypes.data_as(C.POINTER(C.c_int32)), len(arr)),
+               "bt_set_active")
+
+    @property
+    def num_active(self) -> int:
+        n = load().bt_num_active(self._h)
+        _check(min(n, 0), "bt_num_active")
+        return n
+
+    def set_poses(self, poses):
+        P = np.ascontiguousarray(poses, np.float64).reshape(-1)
+        if P.size != 16 * self.num_active:
+            raise ValueError("poses must be (n_active, 4, 4)")
+        _check(load().bt_set_poses(self._h, P.ctypes.data_as(C.POINTER(C.c_double))), "bt_set_poses")
+
+    def get_poses(self) -> np.ndarray:
+        out = np.zeros((self.num_active, 4, 4))
+        _check(load().bt_get_poses(self._h, out.ctypes.data_as(C.POINTER(C.c_double))), "bt_get_poses")
+        return out
+
+    def solve(self, iters: int, raise_on_error: bool = True):
+        """Returns (poses (N,4,4), report dict)."""
+        out = np.zeros((self.num_active, 4, 4))
+        rep = bt_solve_report()
+        st = load().bt_solve(self._h, int(iters), out.ctypes.data_as(C.POINTER(C.c_double)), C.byref(rep))
+        if raise_on_error:
+            _check(st, "bt_solve")
+        r = dict(status=st, iters_run=rep.iters_run, cost_init=rep.cost_init, cost_final=rep.cost_final,
+                 dense_cost_final=rep.dense_cost_final, sparse_cost_final=rep.sparse_cost_final,
+                 cost_per_iter=np.array(rep.cost_per_iter[:rep.iters_run]),
+                 dense_inliers=rep.dense_inliers, dense_pixel_pairs=rep.dense_pixel_pairs)
+        return out, r
+
+    def eval_cost(self):
+        c = (C.c_double * 3)()
+        n = C.c_int64()
+        _check(load().bt_eval_cost(self._h, c, C.byref(n)), "bt_eval_cost")
+        return dict(total=c[0], dense=c[1], sparse=c[2], dense_inliers=n.value)
+
+
+def graph_from_synth(sg, config=None, stream=None, device=None) -> PoseGraph:
+    """Loads a synthetic graph (attributes renders, cams, matches, pose_init,
+    fixed) into a PoseGraph; device = 'cuda' passes CUDA tensors instead of
+    host arrays."""
+    pg = PoseGraph(config, stream)
+    ids = []
+    if device is not None:
+        import torch
+
+        def conv(x):
+            return torch.as_tensor(np.ascontiguousarray(x), device=device)
+    else:
+        def conv(x):
+            return x
+    by_new = {}
+    for (i, j, pi, pj) in sg.matches:
+        by_new.setdefault(j, []).append((i, pj, pi))
+    for k in range(len(sg.renders)):
+        r, cam = sg.renders[k], sg.cams[k]
+        ms = [(ids[i], conv(ps), conv(po)) for (i, ps, po) in by_new.get(k, [])]
+        ids.append(pg.add_frame(conv(r.depth), conv(r.normals), conv(r.mask), cam.as_tuple(),
+                                sg.pose_init[k], bool(sg.fixed[k]), ms))
+    pg.frame_ids = ids
+    return pg

@@ -1,0 +1,619 @@
+// bt_api.cu -- host runtime behind the C interface in include/bt.h.
+//
+// A bt_graph owns the device copies of its frames (target map + compacted
+// source pixels, built on the GPU by the prep kernels), the correspondence
+// sets, and the per-solve work buffers (grow-only, so repeated solves do not
+// allocate).  bt_solve enqueues, on the graph's stream:
+//   xform  ->  iters x [residual(full) -> reduce(full)]  ->  residual(cost) -> reduce(cost)
+// and then one device-to-host copy of poses, costs and status.
+#include "bt.h"
+#include "bt_internal.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg)
+{
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? BT_ERR_OOM : BT_ERR_CUDA;
+}
+
+#define BT_CUDA(call, what)                         \
+    do {                                            \
+        cudaError_t e_ = (call);                    \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t bytes)
+    {
+        if (bytes <= cap) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        size_t want = std::max<size_t>(bytes, 256);
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e == cudaSuccess) cap = want;
+        return e;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+struct Frame {
+    int id = -1;
+    bt_intrinsics K{};
+    int fixed = 0;
+    double pose[16];
+    float4* tgt = nullptr;
+    float4* src_p = nullptr;
+    float4* src_n = nullptr;
+    int M = 0;
+};
+
+struct MatchSet {
+    int fa = -1, fb = -1;   // fa < fb; pa in camera fa, pb in camera fb
+    int count = 0;
+    float* pa = nullptr;
+    float* pb = nullptr;
+};
+
+bool finite_pose(const double* T)
+{
+    for (int k = 0; k < 16; ++k)
+        if (!std::isfinite(T[k])) return false;
+    return T[12] == 0.0 && T[13] == 0.0 && T[14] == 0.0 && T[15] == 1.0;
+}
+
+}  // namespace
+
+struct bt_graph {
+    bt_config cfg{};
+    cudaStream_t stream = nullptr;
+    int next_id = 0;
+    std::map<int, Frame> frames;
+    std::map<std::pair<int, int>, MatchSet> matches;
+    std::vector<int> active;
+    bool topo_dirty = true;
+
+    // scratch for uploads and frame preparation
+    DevBuf up_depth, up_normals, up_mask, prep_blk, prep_src_p, prep_src_n, prep_M;
+
+    // per-solve state
+    DevBuf d_nodes, d_edges, d_tile_node, d_pose, d_xf, d_xinv, d_dpart, d_spart, d_pairblk,
+        d_edgeblk, d_ctrl, d_costs;
+    bt::SolveArgs args{};
+    int64_t pixels_per_pass = 0;
+
+    ~bt_graph()
+    {
+        if (stream) cudaStreamSynchronize(stream);
+        else cudaDeviceSynchronize();
+        for (auto& kv : frames) {
+            cudaFree(kv.second.tgt);
+            cudaFree(kv.second.src_p);
+            cudaFree(kv.second.src_n);
+        }
+        for (auto& kv : matches) {
+            cudaFree(kv.second.pa);
+            cudaFree(kv.second.pb);
+        }
+        for (DevBuf* b : {&up_depth, &up_normals, &up_mask, &prep_blk, &prep_src_p, &prep_src_n,
+                          &prep_M, &d_nodes, &d_edges, &d_tile_node, &d_pose, &d_xf, &d_xinv,
+                          &d_dpart, &d_spart, &d_pairblk, &d_edgeblk, &d_ctrl, &d_costs})
+            b->release();
+    }
+};
+
+namespace {
+
+int validate_config(const bt_config& c)
+{
+    auto pos = [](double x) { return std::isfinite(x) && x > 0.0; };
+    if (!pos(c.huber_sparse) || !pos(c.huber_dense) || !pos(c.dense_max_dist))
+        return fail(BT_ERR_INVALID, "config: Huber thresholds and dense_max_dist must be finite and > 0");
+    if (!std::isfinite(c.dense_max_normal_deg) || c.dense_max_normal_deg < 0.0 || c.dense_max_normal_deg > 180.0)
+        return fail(BT_ERR_INVALID, "config: dense_max_normal_deg must be in [0, 180]");
+    if (!std::isfinite(c.lambda_sparse) || !std::isfinite(c.lambda_dense) || c.lambda_sparse < 0.0 ||
+        c.lambda_dense < 0.0)
+        return fail(BT_ERR_INVALID, "config: lambdas must be finite and >= 0");
+    if (c.precision != BT_FP32)
+        return fail(BT_ERR_INVALID, "config: only BT_FP32 storage is available in this build");
+    if (c.max_frames < 0) return fail(BT_ERR_INVALID, "config: max_frames must be >= 0");
+    return BT_OK;
+}
+
+// Copies a count x 3 point list (host or device) into a new device array.
+int upload_points(const float* src, int count, int mem_kind, cudaStream_t s, float** out)
+{
+    *out = nullptr;
+    if (count == 0) return BT_OK;
+    const size_t bytes = sizeof(float) * 3 * (size_t)count;
+    BT_CUDA(cudaMalloc(out, bytes), "cudaMalloc(matches)");
+    cudaError_t e = cudaMemcpyAsync(*out, src, bytes,
+                                    mem_kind == BT_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) {
+        cudaFree(*out);
+        *out = nullptr;
+        return cuda_fail(e, "cudaMemcpyAsync(matches)");
+    }
+    return BT_OK;
+}
+
+int put_matches(bt_graph* g, int fa, int fb, int count, const float* pa, const float* pb, int mem_kind)
+{
+    if (fa == fb) return fail(BT_ERR_INVALID, "matches: a frame cannot match itself");
+    if (!g->frames.count(fa) || !g->frames.count(fb)) return fail(BT_ERR_INVALID, "matches: unknown frame id");
+    if (count < 0) return fail(BT_ERR_INVALID, "matches: negative count");
+    if (count > 0 && (!pa || !pb)) return fail(BT_ERR_INVALID, "matches: NULL point array");
+    if (fa > fb) {
+        std::swap(fa, fb);
+        std::swap(pa, pb);
+    }
+    MatchSet ms;
+    ms.fa = fa;
+    ms.fb = fb;
+    ms.count = count;
+    int st = upload_points(pa, count, mem_kind, g->stream, &ms.pa);
+    if (st != BT_OK) return st;
+    st = upload_points(pb, count, mem_kind, g->stream, &ms.pb);
+    if (st != BT_OK) {
+        cudaFree(ms.pa);
+        return st;
+    }
+    auto key = std::make_pair(fa, fb);
+    auto it = g->matches.find(key);
+    if (it != g->matches.end()) {
+        cudaStreamSynchronize(g->stream);
+        cudaFree(it->second.pa);
+        cudaFree(it->second.pb);
+        g->matches.erase(it);
+    }
+    if (count > 0) g->matches[key] = ms;
+    g->topo_dirty = true;
+    return BT_OK;
+}
+
+// Rebuilds the node / tile / edge tables of the active set and sizes the
+// per-solve buffers.
+int build_topology(bt_graph* g)
+{
+    const int N = (int)g->active.size();
+    if (N < 1) return fail(BT_ERR_INVALID, "solve: no active nodes");
+    if (N > BT_MAX_NODES) return fail(BT_ERR_INVALID, "solve: more than BT_MAX_NODES active nodes");
+    std::vector<bt::NodeDev> nodes(N);
+    std::vector<int> tile_node;
+    int nfree = 0;
+    int64_t px = 0;
+    for (int k = 0; k < N; ++k) {
+        const Frame& f = g->frames.at(g->active[k]);
+        bt::NodeDev& d = nodes[k];
+        d.src_p = f.src_p;
+        d.src_n = f.src_n;
+        d.tgt = f.tgt;
+        d.M = f.M;
+        d.W = f.K.width;
+        d.H = f.K.height;
+        d.fx = f.K.fx;
+        d.fy = f.K.fy;
+        d.cx = f.K.cx;
+        d.cy = f.K.cy;
+        d.ifx = 1.0f / f.K.fx;
+        d.ify = 1.0f / f.K.fy;
+        d.tile0 = (int)tile_node.size();
+        d.ntiles = (f.M + bt::kTile - 1) / bt::kTile;
+        for (int t = 0; t < d.ntiles; ++t) tile_node.push_back(k);
+        d.free_idx = f.fixed ? -1 : nfree++;
+        px += (int64_t)f.M * (N - 1);
+    }
+    std::map<int, int> node_of;
+    for (int k = 0; k < N; ++k) node_of[g->active[k]] = k;
+    std::vector<bt::EdgeDev> edges;
+    for (auto& kv : g->matches) {
+        const MatchSet& m = kv.second;
+        auto ia = node_of.find(m.fa), ib = node_of.find(m.fb);
+        if (ia == node_of.end() || ib == node_of.end() || m.count <= 0) continue;
+        bt::EdgeDev e;
+        e.i = ia->second;
+        e.j = ib->second;
+        e.count = m.count;
+        e.pa = m.pa;
+        e.pb = m.pb;
+        edges.push_back(e);
+    }
+    const int T = (int)tile_node.size(), P = N * (N - 1), E = (int)edges.size();
+    cudaStream_t s = g->stream;
+    BT_CUDA(g->d_nodes.ensure(sizeof(bt::NodeDev) * N), "alloc nodes");
+    BT_CUDA(g->d_edges.ensure(sizeof(bt::EdgeDev) * std::max(E, 1)), "alloc edges");
+    BT_CUDA(g->d_tile_node.ensure(sizeof(int) * std::max(T, 1)), "alloc tiles");
+    BT_CUDA(g->d_pose.ensure(sizeof(double) * 12 * N), "alloc poses");
+    BT_CUDA(g->d_xf.ensure(sizeof(float) * 12 * N * N), "alloc xf");
+    BT_CUDA(g->d_xinv.ensure(sizeof(float) * 12 * N), "alloc xinv");
+    BT_CUDA(g->d_dpart.ensure(sizeof(float) * bt::kDenseVals * (size_t)std::max(T, 1) * std::max(N - 1, 1)),
+            "alloc dpart");
+    BT_CUDA(g->d_spart.ensure(sizeof(float) * bt::kSparseVals * std::max(E, 1)), "alloc spart");
+    BT_CUDA(g->d_pairblk.ensure(sizeof(double) * bt::kPairBlk * std::max(P, 1)), "alloc pairblk");
+    BT_CUDA(g->d_edgeblk.ensure(sizeof(double) * bt::kEdgeBlk * std::max(E, 1)), "alloc edgeblk");
+    BT_CUDA(g->d_ctrl.ensure(sizeof(bt::Control)), "alloc ctrl");
+    BT_CUDA(g->d_costs.ensure(sizeof(double) * 4 * (BT_MAX_REPORT_ITERS + 1)), "alloc costs");
+    BT_CUDA(cudaMemcpyAsync(g->d_nodes.p, nodes.data(), sizeof(bt::NodeDev) * N, cudaMemcpyHostToDevice, s),
+            "upload nodes");
+    if (E > 0)
+        BT_CUDA(cudaMemcpyAsync(g->d_edges.p, edges.data(), sizeof(bt::EdgeDev) * E, cudaMemcpyHostToDevice, s),
+                "upload edges");
+    if (T > 0)
+        BT_CUDA(cudaMemcpyAsync(g->d_tile_node.p, tile_node.data(), sizeof(int) * T, cudaMemcpyHostToDevice, s),
+                "upload tiles");
+    bt::SolveArgs& a = g->args;
+    a.N = N;
+    a.n_tiles = T;
+    a.n_pairs = P;
+    a.n_edges = E;
+    a.n_free = nfree;
+    const bt_config& c = g->cfg;
+    a.dmax2 = (float)(c.dense_max_dist * c.dense_max_dist);
+    a.cmin = (float)std::cos(c.dense_max_normal_deg * 3.14159265358979323846 / 180.0);
+    a.huber_dense = (float)c.huber_dense;
+    a.huber_sparse = (float)c.huber_sparse;
+    a.lambda_dense = c.lambda_dense;
+    a.lambda_sparse = c.lambda_sparse;
+    a.nodes = g->d_nodes.as<bt::NodeDev>();
+    a.edges = g->d_edges.as<bt::EdgeDev>();
+    a.tile_node = g->d_tile_node.as<int>();
+    a.pose = g->d_pose.as<double>();
+    a.xf = g->d_xf.as<float>();
+    a.xinv = g->d_xinv.as<float>();
+    a.dpart = g->d_dpart.as<float>();
+    a.spart = g->d_spart.as<float>();
+    a.pairblk = g->d_pairblk.as<double>();
+    a.edgeblk = g->d_edgeblk.as<double>();
+    a.ctrl = g->d_ctrl.as<bt::Control>();
+    a.costs = g->d_costs.as<double>();
+    g->pixels_per_pass = px;
+    // the tables above were copied from host vectors that go out of scope
+    BT_CUDA(cudaStreamSynchronize(s), "sync after table upload");
+    g->topo_dirty = false;
+    return BT_OK;
+}
+
+int upload_poses(bt_graph* g, std::vector<double>& staging)
+{
+    const int N = (int)g->active.size();
+    staging.resize(12 * (size_t)N);
+    for (int k = 0; k < N; ++k) {
+        const Frame& f = g->frames.at(g->active[k]);
+        std::memcpy(&staging[12 * (size_t)k], f.pose, sizeof(double) * 12);
+    }
+    BT_CUDA(cudaMemcpyAsync(g->d_pose.p, staging.data(), sizeof(double) * 12 * N, cudaMemcpyHostToDevice,
+                            g->stream),
+            "upload poses");
+    BT_CUDA(cudaMemsetAsync(g->d_ctrl.p, 0, sizeof(bt::Control), g->stream), "reset control");
+    BT_CUDA(bt::launch_xforms(g->args, g->stream), "launch xform");
+    return BT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void bt_config_default(bt_config* cfg)
+{
+    if (!cfg) return;
+    cfg->huber_sparse = 0.005;
+    cfg->huber_dense = 0.005;
+    cfg->dense_max_dist = 0.02;
+    cfg->dense_max_normal_deg = 45.0;
+    cfg->lambda_sparse = 1.0;
+    cfg->lambda_dense = 1.0;
+    cfg->precision = BT_FP32;
+    cfg->max_frames = 0;
+}
+
+int bt_graph_create(const bt_config* cfg, void* cuda_stream, bt_graph** out)
+{
+    g_err.clear();
+    if (!out) return fail(BT_ERR_INVALID, "bt_graph_create: out is NULL");
+    *out = nullptr;
+    bt_config c;
+    bt_config_default(&c);
+    if (cfg) c = *cfg;
+    int st = validate_config(c);
+    if (st != BT_OK) return st;
+    int dev = 0;
+    BT_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    bt_graph* g = new (std::nothrow) bt_graph();
+    if (!g) return fail(BT_ERR_OOM, "bt_graph_create: host allocation failed");
+    g->cfg = c;
+    g->stream = static_cast<cudaStream_t>(cuda_stream);
+    *out = g;
+    return BT_OK;
+}
+
+void bt_graph_destroy(bt_graph* g) { delete g; }
+
+int bt_add_frame(bt_graph* g, const float* depth, const float* normals, const uint8_t* mask,
+                 const bt_intrinsics* K, const double pose_init[16], int32_t fixed,
+                 const bt_matches* matches, int32_t n_matches, int32_t mem_kind, int32_t* frame_id_out)
+{
+    g_err.clear();
+    if (!g || !depth || !normals || !mask || !K || !pose_init)
+        return fail(BT_ERR_INVALID, "bt_add_frame: NULL argument");
+    if (mem_kind != BT_HOST && mem_kind != BT_DEVICE) return fail(BT_ERR_INVALID, "bt_add_frame: bad mem_kind");
+    if (K->width < 1 || K->height < 1 || (int64_t)K->width * K->height > (1 << 28))
+        return fail(BT_ERR_INVALID, "bt_add_frame: image size out of range");
+    if (!std::isfinite(K->fx) || !std::isfinite(K->fy) || K->fx == 0.f || K->fy == 0.f || !std::isfinite(K->cx) ||
+        !std::isfinite(K->cy))
+        return fail(BT_ERR_INVALID, "bt_add_frame: bad intrinsics");
+    if (!finite_pose(pose_init)) return fail(BT_ERR_INVALID, "bt_add_frame: pose must be finite with last row 0 0 0 1");
+    if (n_matches < 0 || (n_matches > 0 && !matches)) return fail(BT_ERR_INVALID, "bt_add_frame: bad matches");
+    if (g->cfg.max_frames > 0 && (int)g->frames.size() >= g->cfg.max_frames)
+        return fail(BT_ERR_INVALID, "bt_add_frame: max_frames reached");
+    for (int k = 0; k < n_matches; ++k) {
+        if (!g->frames.count(matches[k].other_frame)) return fail(BT_ERR_INVALID, "bt_add_frame: unknown other_frame");
+        if (matches[k].count < 0 || (matches[k].count > 0 && (!matches[k].pts_self || !matches[k].pts_other)))
+            return fail(BT_ERR_INVALID, "bt_add_frame: bad match set");
+    }
+    cudaStream_t s = g->stream;
+    const int W = K->width, H = K->height, HW = W * H;
+    const float *d_depth = depth, *d_normals = normals;
+    const uint8_t* d_mask = mask;
+    if (mem_kind == BT_HOST) {
+        BT_CUDA(g->up_depth.ensure(sizeof(float) * HW), "alloc upload");
+        BT_CUDA(g->up_normals.ensure(sizeof(float) * 3 * (size_t)HW), "alloc upload");
+        BT_CUDA(g->up_mask.ensure((size_t)HW), "alloc upload");
+        BT_CUDA(cudaMemcpyAsync(g->up_depth.p, depth, sizeof(float) * HW, cudaMemcpyHostToDevice, s), "upload depth");
+        BT_CUDA(cudaMemcpyAsync(g->up_normals.p, normals, sizeof(float) * 3 * (size_t)HW, cudaMemcpyHostToDevice, s),
+                "upload normals");
+        BT_CUDA(cudaMemcpyAsync(g->up_mask.p, mask, (size_t)HW, cudaMemcpyHostToDevice, s), "upload mask");
+        d_depth = g->up_depth.as<float>();
+        d_normals = g->up_normals.as<float>();
+        d_mask = g->up_mask.as<uint8_t>();
+    }
+    const int nblk = (HW + bt::kPrepPix - 1) / bt::kPrepPix;
+    BT_CUDA(g->prep_blk.ensure(sizeof(int) * (nblk + 1)), "alloc prep");
+    BT_CUDA(g->prep_src_p.ensure(sizeof(float4) * HW), "alloc prep");
+    BT_CUDA(g->prep_src_n.ensure(sizeof(float4) * HW), "alloc prep");
+    BT_CUDA(g->prep_M.ensure(sizeof(int)), "alloc prep");
+    Frame f;
+    BT_CUDA(cudaMalloc(&f.tgt, sizeof(float4) * HW), "cudaMalloc(target map)");
+    const float ifx = 1.0f / K->fx, ify = 1.0f / K->fy;
+    cudaError_t e = bt::launch_prep(d_depth, d_normals, d_mask, W, H, K->cx, K->cy, ifx, ify, f.tgt,
+                                    g->prep_src_p.as<float4>(), g->prep_src_n.as<float4>(), g->prep_blk.as<int>(),
+                                    g->prep_M.as<int>(), s);
+    int M = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&M, g->prep_M.p, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && M > 0) {
+        e = cudaMalloc(&f.src_p, sizeof(float4) * M);
+        if (e == cudaSuccess) e = cudaMalloc(&f.src_n, sizeof(float4) * M);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(f.src_p, g->prep_src_p.p, sizeof(float4) * M, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(f.src_n, g->prep_src_n.p, sizeof(float4) * M, cudaMemcpyDeviceToDevice, s);
+    }
+    if (e != cudaSuccess) {
+        cudaFree(f.tgt);
+        cudaFree(f.src_p);
+        cudaFree(f.src_n);
+        return cuda_fail(e, "bt_add_frame: preparation");
+    }
+    f.id = g->next_id;
+    f.K = *K;
+    f.fixed = fixed ? 1 : 0;
+    f.M = M;
+    std::memcpy(f.pose, pose_init, sizeof(double) * 16);
+    g->frames[f.id] = f;
+    g->next_id++;
+    for (int k = 0; k < n_matches; ++k) {
+        int st = put_matches(g, f.id, matches[k].other_frame, matches[k].count, matches[k].pts_self,
+                             matches[k].pts_other, mem_kind);
+        if (st != BT_OK) {
+            std::string msg = g_err;
+            bt_remove_frame(g, f.id);
+            g->next_id--;
+            g_err = msg;
+            return st;
+        }
+    }
+    g->active.push_back(f.id);
+    g->topo_dirty = true;
+    if (frame_id_out) *frame_id_out = f.id;
+    return BT_OK;
+}
+
+int bt_set_matches(bt_graph* g, int32_t frame_a, int32_t frame_b, int32_t count, const float* pts_a,
+                   const float* pts_b, int32_t mem_kind)
+{
+    g_err.clear();
+    if (!g) return fail(BT_ERR_INVALID, "bt_set_matches: NULL graph");
+    if (mem_kind != BT_HOST && mem_kind != BT_DEVICE) return fail(BT_ERR_INVALID, "bt_set_matches: bad mem_kind");
+    return put_matches(g, frame_a, frame_b, count, pts_a, pts_b, mem_kind);
+}
+
+int bt_remove_frame(bt_graph* g, int32_t frame_id)
+{
+    if (!g) return fail(BT_ERR_INVALID, "bt_remove_frame: NULL graph");
+    auto it = g->frames.find(frame_id);
+    if (it == g->frames.end()) return fail(BT_ERR_INVALID, "bt_remove_frame: unknown frame id");
+    cudaStreamSynchronize(g->stream);
+    cudaFree(it->second.tgt);
+    cudaFree(it->second.src_p);
+    cudaFree(it->second.src_n);
+    g->frames.erase(it);
+    for (auto m = g->matches.begin(); m != g->matches.end();) {
+        if (m->second.fa == frame_id || m->second.fb == frame_id) {
+            cudaFree(m->second.pa);
+            cudaFree(m->second.pb);
+            m = g->matches.erase(m);
+        } else {
+            ++m;
+        }
+    }
+    g->active.erase(std::remove(g->active.begin(), g->active.end(), frame_id), g->active.end());
+    g->topo_dirty = true;
+    return BT_OK;
+}
+
+int bt_set_active(bt_graph* g, const int32_t* ids, int32_t n)
+{
+    g_err.clear();
+    if (!g || !ids) return fail(BT_ERR_INVALID, "bt_set_active: NULL argument");
+    if (n < 1 || n > BT_MAX_NODES) return fail(BT_ERR_INVALID, "bt_set_active: n out of range");
+    std::vector<int> v(ids, ids + n);
+    for (int k = 0; k < n; ++k) {
+        if (!g->frames.count(v[k])) return fail(BT_ERR_INVALID, "bt_set_active: unknown frame id");
+        for (int q = 0; q < k; ++q)
+            if (v[q] == v[k]) return fail(BT_ERR_INVALID, "bt_set_active: repeated frame id");
+    }
+    if (v != g->active) {
+        g->active = v;
+        g->topo_dirty = true;
+    }
+    return BT_OK;
+}
+
+int bt_num_active(const bt_graph* g)
+{
+    if (!g) return fail(BT_ERR_INVALID, "bt_num_active: NULL graph");
+    return (int)g->active.size();
+}
+
+int bt_set_poses(bt_graph* g, const double* poses)
+{
+    g_err.clear();
+    if (!g || !poses) return fail(BT_ERR_INVALID, "bt_set_poses: NULL argument");
+    for (size_t k = 0; k < g->active.size(); ++k)
+        if (!finite_pose(poses + 16 * k)) return fail(BT_ERR_INVALID, "bt_set_poses: bad pose");
+    for (size_t k = 0; k < g->active.size(); ++k)
+        std::memcpy(g->frames.at(g->active[k]).pose, poses + 16 * k, sizeof(double) * 16);
+    return BT_OK;
+}
+
+int bt_get_poses(const bt_graph* g, double* poses)
+{
+    if (!g || !poses) return fail(BT_ERR_INVALID, "bt_get_poses: NULL argument");
+    for (size_t k = 0; k < g->active.size(); ++k)
+        std::memcpy(poses + 16 * k, g->frames.at(g->active[k]).pose, sizeof(double) * 16);
+    return BT_OK;
+}
+
+int bt_solve(bt_graph* g, int32_t iters, double* poses_out, bt_solve_report* rep)
+{
+    g_err.clear();
+    if (!g) return fail(BT_ERR_INVALID, "bt_solve: NULL graph");
+    if (iters < 0 || iters > BT_MAX_REPORT_ITERS) return fail(BT_ERR_INVALID, "bt_solve: iters out of range");
+    if (g->active.empty()) return fail(BT_ERR_INVALID, "bt_solve: no active nodes");
+    if (g->topo_dirty) {
+        int st = build_topology(g);
+        if (st != BT_OK) return st;
+    }
+    std::vector<double> staging;
+    int st = upload_poses(g, staging);
+    if (st != BT_OK) return st;
+    cudaStream_t s = g->stream;
+    const bt::SolveArgs& a = g->args;
+    for (int it = 0; it < iters; ++it) {
+        BT_CUDA(bt::launch_residual(a, true, s), "launch residual");
+        BT_CUDA(bt::launch_reduce(a, true, it, s), "launch reduce");
+    }
+    BT_CUDA(bt::launch_residual(a, false, s), "launch residual (cost)");
+    BT_CUDA(bt::launch_reduce(a, false, iters, s), "launch reduce (cost)");
+    const int N = a.N;
+    std::vector<double> pose(12 * (size_t)N), costs(4 * (size_t)(iters + 1));
+    bt::Control ctrl{};
+    BT_CUDA(cudaMemcpyAsync(pose.data(), a.pose, sizeof(double) * 12 * N, cudaMemcpyDeviceToHost, s), "read poses");
+    BT_CUDA(cudaMemcpyAsync(costs.data(), a.costs, sizeof(double) * 4 * (iters + 1), cudaMemcpyDeviceToHost, s),
+            "read costs");
+    BT_CUDA(cudaMemcpyAsync(&ctrl, a.ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost, s), "read status");
+    BT_CUDA(cudaStreamSynchronize(s), "bt_solve: synchronize");
+    const int status = ctrl.status == -4 ? BT_ERR_SINGULAR : BT_OK;
+    if (rep) {
+        std::memset(rep, 0, sizeof(*rep));
+        rep->iters_run = iters;
+        rep->status = status;
+        rep->cost_init = iters > 0 ? costs[0] : costs[4 * iters];
+        rep->cost_final = costs[4 * iters + 0];
+        rep->dense_cost_final = costs[4 * iters + 1];
+        rep->sparse_cost_final = costs[4 * iters + 2];
+        rep->dense_inliers = (int64_t)std::llround(costs[4 * iters + 3]);
+        for (int k = 0; k < iters; ++k) rep->cost_per_iter[k] = costs[4 * k];
+        rep->dense_pixel_pairs = g->pixels_per_pass * iters;
+    }
+    if (status != BT_OK) return fail(status, "bt_solve: normal equations not positive definite; poses unchanged");
+    for (int k = 0; k < N; ++k) {
+        Frame& f = g->frames.at(g->active[k]);
+        std::memcpy(f.pose, &pose[12 * (size_t)k], sizeof(double) * 12);
+        if (poses_out) std::memcpy(poses_out + 16 * (size_t)k, f.pose, sizeof(double) * 16);
+    }
+    return BT_OK;
+}
+
+int bt_eval_cost(bt_graph* g, double* cost_out, int64_t* dense_inliers)
+{
+    g_err.clear();
+    if (!g || !cost_out) return fail(BT_ERR_INVALID, "bt_eval_cost: NULL argument");
+    if (g->active.empty()) return fail(BT_ERR_INVALID, "bt_eval_cost: no active nodes");
+    if (g->topo_dirty) {
+        int st = build_topology(g);
+        if (st != BT_OK) return st;
+    }
+    std::vector<double> staging;
+    int st = upload_poses(g, staging);
+    if (st != BT_OK) return st;
+    cudaStream_t s = g->stream;
+    BT_CUDA(bt::launch_residual(g->args, false, s), "launch residual (cost)");
+    BT_CUDA(bt::launch_reduce(g->args, false, 0, s), "launch reduce (cost)");
+    double c[4];
+    BT_CUDA(cudaMemcpyAsync(c, g->args.costs, sizeof(c), cudaMemcpyDeviceToHost, s), "read costs");
+    BT_CUDA(cudaStreamSynchronize(s), "bt_eval_cost: synchronize");
+    cost_out[0] = c[0];
+    cost_out[1] = c[1];
+    cost_out[2] = c[2];
+    if (dense_inliers) *dense_inliers = (int64_t)std::llround(c[3]);
+    return BT_OK;
+}
+
+const char* bt_status_str(int status)
+{
+    switch (status) {
+    case BT_OK: return "ok";
+    case BT_ERR_INVALID: return "invalid argument";
+    case BT_ERR_CUDA: return "CUDA error";
+    case BT_ERR_OOM: return "out of memory";
+    case BT_ERR_SINGULAR: return "normal equations not positive definite";
+    case BT_ERR_TIMEOUT: return "device wait timed out";
+    case BT_ERR_STATE: return "invalid state";
+    default: return "unknown status";
+    }
+}
+
+const char* bt_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

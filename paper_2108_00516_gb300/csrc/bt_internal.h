@@ -1,0 +1,96 @@
+// bt_internal.h -- device data layout and kernel entry points of libbt.
+//
+// Layout in HBM (all device buffers are owned by a bt_graph):
+//   per stored frame
+//     tgt   float4[H*W]  (z, nx, ny, nz) per pixel, z = 0 where the pixel cannot
+//                        be a dense target (not masked / no depth / no normal);
+//                        16 B per pixel, read by the projective gather (Eq. 3)
+//     src_p float4[M]    (px, py, pz, 0) back-projected source points of the
+//                        M valid masked pixels, increasing pixel order
+//     src_n float4[M]    (nx, ny, nz, 0) their normals
+//   per correspondence set (unordered frame pair)
+//     pa, pb float[3*count]  the two camera-frame point lists of Eq. 2
+//   per solve (active node set of N nodes)
+//     NodeDev[N], EdgeDev[E], tile_node[T], pose double[N][12] (3x4),
+//     xf PairXf[N*N] (float camera i -> camera j), xinv float[N][12] (T^-1),
+//     dpart float[T][N-1][32] (per source tile and target: the 21 + 6 unique
+//     J^T W J / J^T W r terms, cost, count), spart float[E][40] (sparse
+//     moments), pairblk double[P][32], edgeblk double[E][96], control words.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bt {
+
+constexpr int kThreads = 256;                 // residual and reduce CTAs
+constexpr int kPixPerThread = 4;
+constexpr int kTile = kThreads * kPixPerThread;   // source pixels per dense tile
+constexpr int kDenseVals = 32;                // 21 H + 6 g + cost + count + 3 pad
+constexpr int kSparseVals = 40;               // 39 moments + pad
+constexpr int kPairBlk = 32;                  // 21 K' + 6 g' + cost + count + pad
+constexpr int kEdgeBlk = 96;                  // 21 Hii + 21 Hjj + 36 Hij + 6 gi + 6 gj + cost + count
+constexpr int kMaxNodes = 24;
+constexpr int kPrepPix = 1024;                // pixels per prep CTA (256 threads x 4)
+
+struct NodeDev {
+    const float4* src_p;
+    const float4* src_n;
+    const float4* tgt;
+    int M;          // valid source pixels
+    int W, H;
+    float fx, fy, cx, cy, ifx, ify;
+    int tile0, ntiles;
+    int free_idx;   // index among non-fixed nodes, -1 if fixed
+};
+
+struct EdgeDev {
+    int i, j;       // node indices, i != j; pa lives in camera i, pb in camera j
+    int count;
+    const float* pa;
+    const float* pb;
+};
+
+struct Control {
+    unsigned int counter;   // last-block detection of the reduce kernel
+    int status;             // 0 ok, -4 singular (sticky for the solve)
+    int pad[2];
+};
+
+struct SolveArgs {
+    int N, n_tiles, n_pairs, n_edges, n_free;
+    float dmax2, cmin, huber_dense, huber_sparse;
+    double lambda_dense, lambda_sparse;
+    const NodeDev* nodes;
+    const EdgeDev* edges;
+    const int* tile_node;
+    double* pose;       // [N][12]
+    float* xf;          // [N*N][12] camera i -> camera j
+    float* xinv;        // [N][12] object <- camera
+    float* dpart;       // [T][N-1][32]
+    float* spart;       // [E][40]
+    double* pairblk;    // [P][32]
+    double* edgeblk;    // [E][96]
+    Control* ctrl;
+    double* costs;      // [iter][4]: total, dense, sparse, dense count
+};
+
+// K0 (frame preparation).  All launches on `s`.  block_scratch must hold
+// ceil(H*W / kPrepPix) + 1 ints; *M_dev receives the valid source count.
+cudaError_t launch_prep(const float* depth, const float* normals, const uint8_t* mask,
+                        int W, int H, float cx, float cy, float ifx, float ify,
+                        float4* tgt, float4* src_p, float4* src_n, int* block_scratch,
+                        int* M_dev, cudaStream_t s);
+
+// Float transforms for the current FP64 poses (start of a solve).
+cudaError_t launch_xforms(const SolveArgs& a, cudaStream_t s);
+
+// One residual pass (dense tiles + sparse edges) and one reduce/solve pass.
+// full = true: Gauss-Newton iteration `iter` (records E before the update);
+// full = false: cost only, recorded at slot `iter`.
+cudaError_t launch_residual(const SolveArgs& a, bool full, cudaStream_t s);
+cudaError_t launch_reduce(const SolveArgs& a, bool full, int iter, cudaStream_t s);
+
+size_t reduce_smem_bytes(int n_free, int N);
+
+}  // namespace bt

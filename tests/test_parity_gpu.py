@@ -1,0 +1,203 @@
+"""GPU (through the C interface) against the FP64 CPU oracle.
+
+Tolerances.  The GPU computes residuals, Jacobians and their block sums in
+FP32 and everything from the 6x6 blocks on in FP64; the oracle is FP64
+throughout.  The association decision (integers) is specified in single
+precision on both sides, so from identical poses the accepted dense
+associations are identical and their count is compared exactly.  Per-pixel
+FP32 residuals carry ~1e-7 relative rounding on coordinates of ~0.5 m, i.e.
+~3e-8 m on residuals of ~1e-3 m; summed over thousands of pixels with random
+signs this is <= 1e-6 of the energy.  The solve tolerances are the ones the
+method's specification states for the FP32 path: relative final cost 1e-5,
+poses 1e-5 rad and 1e-6 m.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synthgen as S
+
+pytestmark = pytest.mark.gpu
+
+COST_RTOL_EVAL = 1e-6
+COST_RTOL = 1e-5
+ROT_TOL = 1e-5
+TRANS_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def bt():
+    import torch
+    from paper_2108_00516_gb300 import build as lbuild
+    lbuild.build()
+    from paper_2108_00516_gb300 import bt as _bt
+    _bt.load()
+    torch.cuda.init()
+    return _bt
+
+
+def pose_err(A, B):
+    rot = max(S.rotation_angle(a[:3, :3] @ b[:3, :3].T) for a, b in zip(A, B))
+    tr = max(np.abs(a[:3, 3] - b[:3, 3]).max() for a, b in zip(A, B))
+    return rot, tr
+
+
+@pytest.mark.parametrize("gid", [0, 1, 2])
+def test_eval_cost_matches_oracle(bt, gid):
+    """Eq. 1 at the same poses: identical association (exact count), energy
+    within FP32 rounding."""
+    g = S.tiny_graph(gid)
+    pg = bt.graph_from_synth(g)
+    c = pg.eval_cost()
+    o = O.energy(g, g.pose_init)
+    assert c["dense_inliers"] == o["dense_count"]
+    assert abs(c["total"] - o["total"]) <= COST_RTOL_EVAL * o["total"]
+    assert abs(c["dense"] - o["dense"]) <= COST_RTOL_EVAL * o["dense"]
+    assert abs(c["sparse"] - o["sparse"]) <= COST_RTOL_EVAL * o["sparse"]
+
+
+@pytest.mark.parametrize("gid", [0, 3, 7])
+def test_stepwise_iterations_match_oracle(bt, gid):
+    """Every Gauss-Newton iteration, started on both sides from the same poses
+    (the GPU's), gives the same energy, the same association count and the same
+    updated poses."""
+    g = S.tiny_graph(gid)
+    pg = bt.graph_from_synth(g)
+    P = g.pose_init.copy()
+    for it in range(7):
+        pg.set_poses(P)
+        Pg, rg = pg.solve(1)
+        ro = O.solve(g, 1, poses=P)
+        assert rg["status"] == 0 and ro["status"] == 0
+        assert abs(rg["cost_init"] - ro["cost_per_iter"][0]) <= COST_RTOL_EVAL * ro["cost_per_iter"][0]
+        rot, tr = pose_err(Pg, ro["poses"])
+        assert rot <= 1e-6 and tr <= 1e-7, (it, rot, tr)
+        e_o = O.energy(g, Pg)
+        assert rg["dense_inliers"] == e_o["dense_count"]
+        assert abs(rg["cost_final"] - e_o["total"]) <= COST_RTOL_EVAL * e_o["total"]
+        P = Pg
+
+
+@pytest.mark.parametrize("gid", [0, 1, 2, 3])
+def test_solve_matches_oracle_tiny(bt, gid):
+    """Free-running 7-iteration solve on the tiny workload (N=4, 160x120)."""
+    g = S.tiny_graph(gid)
+    pg = bt.graph_from_synth(g)
+    Pg, rg = pg.solve(7)
+    ro = O.solve(g, 7)
+    rot, tr = pose_err(Pg, ro["poses"])
+    e_at_gpu = O.energy(g, Pg)["total"]
+    # the GPU's own energy of its poses is the oracle's energy of them
+    assert abs(rg["cost_final"] - e_at_gpu) <= COST_RTOL_EVAL * e_at_gpu
+    assert abs(rg["cost_final"] - ro["cost_final"]) <= COST_RTOL * ro["cost_final"], (rot, tr)
+    assert rot <= ROT_TOL and tr <= TRANS_TOL
+
+
+def test_solve_matches_oracle_paper_shaped(bt):
+    """N=10 views at 640x480 (45 edges, 90 ordered pairs), 10 iterations."""
+    g = S.paper_graph(0)
+    pg = bt.graph_from_synth(g)
+    Pg, rg = pg.solve(10)
+    ro = O.solve(g, 10)
+    rot, tr = pose_err(Pg, ro["poses"])
+    assert abs(rg["cost_final"] - ro["cost_final"]) <= COST_RTOL * ro["cost_final"]
+    assert rot <= ROT_TOL and tr <= TRANS_TOL
+    assert rg["dense_pixel_pairs"] == 10 * 9 * sum(
+        int(((g.mask(k) > 0) & (g.depth(k) > 0) & np.isfinite(g.normals(k)).all(-1)).sum()) for k in range(10))
+
+
+def test_device_inputs_bitwise_equal_host_inputs(bt):
+    g = S.tiny_graph(4)
+    a = bt.graph_from_synth(g)
+    b = bt.graph_from_synth(g, device="cuda")
+    Pa, ra = a.solve(3)
+    Pb, rb = b.solve(3)
+    assert np.array_equal(Pa, Pb) and ra["cost_final"] == rb["cost_final"]
+
+
+def test_rerun_is_deterministic(bt):
+    g = S.tiny_graph(5)
+    a = bt.graph_from_synth(g)
+    P1, r1 = a.solve(4)
+    a.set_poses(g.pose_init)
+    P2, r2 = a.solve(4)
+    assert np.array_equal(P1, P2) and r1["cost_final"] == r2["cost_final"]
+
+
+def test_two_nodes_and_active_subset(bt):
+    g = S.tiny_graph(6)
+    pg = bt.graph_from_synth(g)
+    pg.set_active([pg.frame_ids[0], pg.frame_ids[2]])
+    Pg, rg = pg.solve(5)
+    ro = O.solve(g, 5, nodes=[0, 2])
+    rot, tr = pose_err(Pg, ro["poses"])
+    assert rot <= ROT_TOL and tr <= TRANS_TOL
+    assert abs(rg["cost_final"] - ro["cost_final"]) <= COST_RTOL * ro["cost_final"]
+
+
+def test_empty_mask_frame_and_missing_matches(bt):
+    """A frame with no valid pixel contributes no dense term; a pair without
+    correspondences contributes no sparse term."""
+    g = S.tiny_graph(8)
+    r3 = g.renders[3]
+    empty = S.Render(np.zeros_like(r3.depth), r3.normals, np.zeros_like(r3.mask), r3.depth_clean, r3.normals_true)
+    renders = list(g.renders[:3]) + [empty]
+    matches = [m for m in g.matches if (m[0], m[1]) != (0, 1)]
+    g2 = S.SynthGraph(g.cams, renders, g.pose_true, g.pose_init, g.fixed, matches, g.shape)
+    pg = bt.graph_from_synth(g2)
+    Pg, rg = pg.solve(4)
+    ro = O.solve(g2, 4)
+    rot, tr = pose_err(Pg, ro["poses"])
+    assert rot <= ROT_TOL and tr <= TRANS_TOL
+    assert abs(rg["cost_final"] - ro["cost_final"]) <= COST_RTOL * ro["cost_final"]
+
+
+def test_singular_system_leaves_poses(bt):
+    """A free node with no constraint at all: BT_ERR_SINGULAR, poses kept."""
+    g = S.tiny_graph(0)
+    cfg = bt.config_default()
+    cfg.lambda_dense = 0.0
+    g2 = S.SynthGraph(g.cams, g.renders, g.pose_true, g.pose_init, g.fixed, [], g.shape)
+    pg = bt.graph_from_synth(g2, config=cfg)
+    P0 = pg.get_poses()
+    _, rep = pg.solve(3, raise_on_error=False)
+    assert rep["status"] == bt.BT_ERR_SINGULAR
+    assert np.array_equal(pg.get_poses(), P0)
+
+
+def test_zero_iterations_and_fixed_only(bt):
+    g = S.tiny_graph(1)
+    pg = bt.graph_from_synth(g)
+    P, rep = pg.solve(0)
+    assert np.array_equal(P, g.pose_init)
+    o = O.energy(g, g.pose_init)
+    assert abs(rep["cost_final"] - o["total"]) <= COST_RTOL_EVAL * o["total"]
+    pg.set_active([pg.frame_ids[0]])
+    P1, rep1 = pg.solve(2)
+    assert np.array_equal(P1[0], g.pose_init[0]) and rep1["cost_final"] == 0.0
+
+
+def test_remove_frame(bt):
+    g = S.tiny_graph(2)
+    pg = bt.graph_from_synth(g)
+    pg.remove_frame(pg.frame_ids[3])
+    Pg, rg = pg.solve(4)
+    ro = O.solve(g, 4, nodes=[0, 1, 2])
+    rot, tr = pose_err(Pg, ro["poses"])
+    assert rot <= ROT_TOL and tr <= TRANS_TOL
+
+
+def test_invalid_arguments(bt):
+    pg = bt.PoseGraph()
+    with pytest.raises(bt.BTError):
+        pg.solve(1)            # no frames
+    g = S.tiny_graph(0)
+    r = g.renders[0]
+    with pytest.raises(bt.BTError):
+        pg.add_frame(r.depth, r.normals, r.mask, (140.0, 140.0, 80.0, 60.0, 0, 120), g.pose_init[0])
+    bad = g.pose_init[0].copy()
+    bad[3, 3] = 2.0
+    with pytest.raises(bt.BTError):
+        pg.add_frame(r.depth, r.normals, r.mask, g.cams[0].as_tuple(), bad)
+    with pytest.raises(bt.BTError):
+        pg.set_active([7])
