@@ -1,0 +1,457 @@
+#!/usr/bin/env python3
+"""Throughput of the pose-graph hot path on the paper-shaped workload.
+
+Workload: a seeded 300-frame synthetic RGB-D sequence (640x480, fx = fy = 600,
+mask coverage 15-30 % at the first view, depth noise 1 mm, 500 correspondences
+per frame pair with 20 % outliers).  For every frame t >= 1 the keyframes are
+selected greedily from the memory pool (at most 9, I_0 first, Sec. IV-C) and
+the pool grows by the 10-degree novelty rule (Sec. IV-E); the resulting graph
+(<= 10 nodes, fully connected) is solved with 10 Gauss-Newton iterations from
+poses perturbed by 5 deg / 1 cm (frame 0 fixed).  One step = the 299 solves of
+the sequence.
+
+  value : solves/s with every frame and correspondence set resident in HBM;
+  e2e   : the same through the C interface from host buffers -- each step
+          creates a graph, adds every frame from host memory when it arrives,
+          uploads the correspondence sets it needs, solves, reads the poses
+          back, and drops frames that do not join the pool.
+
+Multi-GPU (torchrun): each rank solves its own sequence (seed 2000 + rank);
+the units are independent, so there is no data-path collective (weak
+scaling).  --impl reference times the FP64 CPU oracle on a bounded sample of
+the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+if str(ROOT) not in sys.path:
+    sys.path.insert(0, str(ROOT))
+
+METRIC = "pose-graph solves/s & dense pixel-pairs/s; learned+batched vs plain at equal cost"
+WORKLOAD = ("paper-shaped sequence: 300 frames 640x480 fx=fy=600, coverage 15-30%, depth noise 1 mm, "
+            "500 matches/pair (20% outliers), greedy keyframes <= 9 + current, 10-deg pool rule, "
+            "10 GN iterations per solve from 5 deg / 1 cm")
+BYTES_PER_PIXEL_PAIR = 32      # source depth+normal 16 B + target depth+normal 16 B (FP32)
+BYTES_PER_SPARSE_PAIR = 24     # two FP32 3-vectors
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--frames", type=int, default=300)
+    ap.add_argument("--iters", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0, help="bounded oracle sample (CPU baseline)")
+    ap.add_argument("--workers", type=int, default=0, help="generator processes (0 = all cores)")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# --------------------------------------------------------------------------- workload
+
+def build_workload(seed: int, n_frames: int, workers: int):
+    import synthgen as S
+    from paper_2108_00516_gb300 import keyframes as KF
+    seq = S.paper_sequence(seed=seed, n_frames=n_frames)
+    graphs, history = KF.plan_sequence(seq.poses_true[:, :3, :3], max_nodes=10)
+    pairs = sorted({(min(a, b), max(a, b)) for g in graphs for a in g for b in g if a != b})
+    seq.prefetch(frames=range(n_frames), pairs=pairs, workers=workers or None)
+    inits = [[seq.init_pose(f, t + 1) for f in g] for t, g in enumerate(graphs)]
+    pools = [[0]] + history          # pool before solving frame t (t = 0..)
+    return seq, graphs, pools, pairs, inits
+
+
+def graph_view(seq, nodes, inits_t):
+    """A graph object the oracle understands, for the frames `nodes`."""
+    import numpy as np
+    import synthgen as S
+    pos = {f: k for k, f in enumerate(nodes)}
+    matches = []
+    for a in nodes:
+        for b in nodes:
+            if a < b:
+                pa, pb = seq.matches(a, b)
+                i, j = pos[a], pos[b]
+                matches.append((i, j, pa, pb) if i < j else (j, i, pb, pa))
+    fixed = np.array([1 if f == 0 else 0 for f in nodes], np.int32)
+    return S.SynthGraph([seq.cam] * len(nodes), [seq.frame(f) for f in nodes], seq.poses_true[nodes],
+                        np.stack(inits_t), fixed, matches, seq.shape)
+
+
+# --------------------------------------------------------------------------- measurements
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.proc = None
+        self.path = Path(os.environ.get("TMPDIR", "/tmp")) / f"bt_clocks_{os.getpid()}.csv"
+        cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if gpu_id:
+            cmd += ["-i", gpu_id]
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in self.path.read_text().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                try:
+                    rows.append((float(f[1]), float(f[2]), float(f[3]) if f[3] not in ("[N/A]", "") else 0.0, f[5:9]))
+                except ValueError:
+                    pass
+        try:
+            self.path.unlink()
+        except OSError:
+            pass
+        if not rows:
+            return None
+        pmax = max(r[2] for r in rows)
+        loaded = [r for r in rows if r[2] >= 0.5 * pmax] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[3][k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "power_w_max": pmax, "reasons": reasons}
+
+
+def hbm_peak():
+    p = ROOT / "MEASURED_PEAKS.json"
+    try:
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic_per_pixel_pair():
+    """DRAM bytes per dense pixel-pair of the residual kernel from the committed
+    ncu summary, if it was taken from the current kernel source."""
+    summ = ROOT / "profiles" / "residual_kernel_paper_sequence.md"
+    src = ROOT / "paper_2108_00516_gb300" / "csrc" / "bt_kernels.cu"
+    try:
+        text = summ.read_text()
+        sha = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+        m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+        m_b = re.search(r"dram_bytes_per_pixel_pair:\s*([0-9.eE+-]+)", text)
+        if m_sha and m_b and m_sha.group(1) == sha:
+            return float(m_b.group(1))
+    except Exception:
+        pass
+    return None
+
+
+def sample_order(n: int):
+    """Graph indices spread over the whole sequence (stride through it)."""
+    stride = 37 if n % 37 else 41
+    return [(k * stride) % n for k in range(n)]
+
+
+def cpu_baseline(seq, graphs, inits, seconds: float, iters: int):
+    """The FP64 oracle, as it stands, on a bounded sample of the same graphs."""
+    import oracle as O
+    n_threads = os.cpu_count() or 1
+    order = sample_order(len(graphs))
+    done, t0 = 0, time.perf_counter()
+    k = 0
+    while True:
+        t = order[k % len(graphs)]
+        g = graph_view(seq, graphs[t], inits[t])
+        r = O.solve(g, iters, n_threads=n_threads)
+        if r["status"] != 0:
+            raise RuntimeError("oracle solve failed")
+        done += 1
+        k += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": done / el, "unit": "solves/s", "cores": n_threads, "kind": "oracle",
+            "sample": f"{done} graphs spread over the sequence ({iters} GN iterations each, "
+                      f"{n_threads} threads over ordered pairs), {el:.1f} s", "seconds": el}
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def run_ours(args):
+    rank, world, local = dist_env()
+    # all synthetic data is made before CUDA is touched (the generator forks)
+    seq, graphs, pools, pairs, inits = build_workload(2000 + rank, args.frames, args.workers)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2108_00516_gb300 import build as lbuild
+    lbuild.build()
+    from paper_2108_00516_gb300 import bt
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+    flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    it = args.iters
+
+    # ---- device-resident workload
+    pg = bt.PoseGraph(stream=stream)
+    ids = []
+    for t in range(seq.n):
+        r = seq.frame(t)
+        ids.append(pg.add_frame(r.depth, r.normals, r.mask, seq.cam.as_tuple(), seq.poses_true[t], fixed=(t == 0)))
+    for (a, b) in pairs:
+        pa, pb = seq.matches(a, b)
+        pg.set_matches(ids[a], ids[b], pa, pb)
+    act = [np.array([ids[f] for f in g], np.int32) for g in graphs]
+    init_arr = [np.ascontiguousarray(np.stack(x)) for x in inits]
+
+    def step():
+        px = 0
+        for k in range(len(graphs)):
+            pg.set_active(act[k])
+            pg.set_poses(init_arr[k])
+            _, rep = pg.solve(it)
+            px += rep["dense_pixel_pairs"]
+        return px
+
+    for _ in range(args.warmup):
+        step()
+    gpu_id = None
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(local).uuid)
+        if not gpu_id.startswith("GPU-"):
+            gpu_id = "GPU-" + gpu_id
+    except Exception:
+        gpu_id = None
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(gpu_id)
+    pg.profile_enable(True)
+    px_total = 0
+    wall0 = time.perf_counter()
+    for s in range(args.steps):
+        flush_buf.fill_(float(s))               # L2 flush between timed steps (outside the events)
+        ev[s][0].record(stream)
+        px_total += step()
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    prof = pg.profile_read()
+    pg.profile_enable(False)
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_ms = sum(step_ms)
+    if world > 1:
+        x = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t_ms = float(x.item())
+    solves = len(graphs) * args.steps * world
+    value = solves / (t_ms / 1e3)
+    pps = px_total * world / (t_ms / 1e3)
+
+    # roofline of the dominant kernel (the residual pass), from events around
+    # each of its launches on the graph's stream inside the timed region
+    n_l = max(1, prof["timed_residual_launches"])
+    avg_s = prof["residual_ms"] / n_l / 1e3
+    bytes_per_launch = (BYTES_PER_PIXEL_PAIR * prof["dense_pixel_pairs"] +
+                        BYTES_PER_SPARSE_PAIR * prof["sparse_pairs"]) / n_l
+    achieved = bytes_per_launch / avg_s / 1e9
+    peak, peak_kind = hbm_peak()
+    tpp = ncu_traffic_per_pixel_pair()
+    traffic = tpp * prof["dense_pixel_pairs"] / n_l if tpp is not None else None
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
+                "kernel": "residual_kernel<full> (dense tiles + sparse sets)",
+                "avg_launch_us": round(avg_s * 1e6, 2), "algorithmic_bytes_per_launch": round(bytes_per_launch),
+                "share_of_step_time": round(prof["residual_ms"] / t_ms, 3) if world == 1 else None,
+                "reduce_ms_share": round(prof["reduce_ms"] / t_ms, 3) if world == 1 else None}
+    launches = prof["xform_launches"] + prof["residual_launches"] + prof["reduce_launches"]
+
+    # ---- end to end through the C interface from host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        e2e = run_e2e(bt, seq, graphs, pools, inits, stream, args, world)
+
+    base = None
+    if rank == 0 and world == 1 and args.cpu_seconds > 0:
+        base = cpu_baseline(seq, graphs, inits, args.cpu_seconds, it)
+        base["value_pixel_pairs_per_s"] = None
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 3),
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic (seeded ray-cast box+ellipsoid sequence; no dataset)",
+               "config": {"workload": WORKLOAD, "graphs_per_step": len(graphs), "iters": it,
+                          "max_nodes": 10, "solve_precision": "FP32 residual pass, FP64 assembly/Cholesky/exp",
+                          "l2": f"flushed ({L2_FLUSH_BYTES >> 20} MiB write) before every timed step; "
+                                f"sequence inputs {sum(seq.frame(t).depth.nbytes * 5 for t in range(seq.n)) / 1e9:.1f} GB "
+                                f"on device > L2",
+                          "parallelism": f"replicas x{world} (independent sequences)"},
+               "pixel_pairs_per_s": round(pps, 1),
+               "roofline": roofline, "gpu_launches": launches,
+               "e2e": e2e, "cpu_baseline": base, "clocks": clk,
+               "wall_s_timed": round(wall, 3)}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(bt, seq, graphs, pools, inits, stream, args, world):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    it = args.iters
+
+    def e2e_step():
+        h2d = d2h = 0
+        pg = bt.PoseGraph(stream=stream)
+        ids = {}
+        have = set()
+
+        def add(t):
+            nonlocal h2d
+            r = seq.frame(t)
+            ids[t] = pg.add_frame(r.depth, r.normals, r.mask, seq.cam.as_tuple(), seq.poses_true[t], fixed=(t == 0))
+            h2d += r.depth.nbytes + r.normals.nbytes + r.mask.nbytes
+
+        add(0)
+        for k, nodes in enumerate(graphs):
+            t = nodes[-1]
+            add(t)
+            for a in nodes:
+                for b in nodes:
+                    if a < b and (a, b) not in have:
+                        pa, pb = seq.matches(a, b)
+                        pg.set_matches(ids[a], ids[b], pa, pb)
+                        have.add((a, b))
+                        h2d += pa.nbytes + pb.nbytes
+            pg.set_active([ids[f] for f in nodes])
+            P0 = np.stack(inits[k])
+            pg.set_poses(P0)
+            h2d += 96 * len(nodes)
+            P, rep = pg.solve(it)
+            d2h += 96 * len(nodes) + 32 * (it + 1) + 16
+            # memory pool (Sec. IV-E): pools[t] is the pool after frame t;
+            # a frame that did not join it is dropped
+            if t not in pools[t]:
+                pg.remove_frame(ids[t])
+                have = {p for p in have if t not in p}
+        pg.close()
+        return h2d, d2h
+
+    e2e_step()                      # warm-up
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    h2d = d2h = 0
+    for _ in range(args.e2e_steps):
+        a, b = e2e_step()
+        h2d += a
+        d2h += b
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    if world > 1:
+        x = torch.tensor([el], dtype=torch.float64, device="cuda")
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        el = float(x.item())
+    return {"value": round(len(graphs) * args.e2e_steps * world / el, 3), "unit": "solves/s",
+            "h2d_bytes_per_step": h2d // args.e2e_steps, "d2h_bytes_per_step": d2h // args.e2e_steps,
+            "steps": args.e2e_steps,
+            "note": "host numpy buffers (pageable) through bt_add_frame / bt_set_matches / bt_solve; "
+                    "frames arrive one per solve; non-keyframes are removed after their solve"}
+
+
+# --------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import synthgen as S
+    from paper_2108_00516_gb300 import keyframes as KF
+    import oracle as O
+    seq = S.paper_sequence(seed=2000, n_frames=args.frames)
+    graphs, _ = KF.plan_sequence(seq.poses_true[:, :3, :3], max_nodes=10)
+    inits = [[seq.init_pose(f, t + 1) for f in g] for t, g in enumerate(graphs)]
+    n_threads = os.cpu_count() or 1
+    # each step: the oracle solves a bounded sample of the sequence's graphs
+    per_step = max(1, int(os.environ.get("BT_REF_GRAPHS_PER_STEP", "1")))
+    order = sample_order(len(graphs))
+    used = [order[k % len(graphs)] for k in range((args.warmup + args.steps) * per_step)]
+    need = sorted({f for t in used for f in graphs[t]})
+    pairs = sorted({(a, b) for t in used for a in graphs[t] for b in graphs[t] if a < b})
+    seq.prefetch(frames=need, pairs=pairs, workers=args.workers or None)   # outside the timed region
+
+    def step(s):
+        done = 0
+        for k in range(per_step):
+            t = order[(s * per_step + k) % len(graphs)]
+            g = graph_view(seq, graphs[t], inits[t])
+            r = O.solve(g, args.iters, n_threads=n_threads)
+            done += r["status"] == 0
+        return done
+
+    for s in range(args.warmup):
+        step(s)
+    t0 = time.perf_counter()
+    done = 0
+    for s in range(args.steps):
+        done += step(args.warmup + s)
+    el = time.perf_counter() - t0
+    value = done / el
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el * 1e3 / args.steps, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded ray-cast box+ellipsoid sequence; no dataset)",
+           "config": {"workload": WORKLOAD, "graphs_per_step": per_step, "iters": args.iters},
+           "cpu_baseline": {"value": round(value, 4), "unit": "solves/s", "cores": n_threads, "kind": "oracle",
+                            "sample": f"{per_step} graph(s) of the sequence per step, {args.iters} GN iterations"},
+           "e2e": {"value": round(value, 4), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -193,6 +193,30 @@ int bt_solve(bt_graph* g, int32_t iters, double* poses_out, bt_solve_report* rep
  * Synchronises the stream.  Errors: BT_ERR_INVALID, BT_ERR_CUDA. */
 int bt_eval_cost(bt_graph* g, double* cost_out, int64_t* dense_inliers);
 
+/* Profiling counters of one graph (the tracing facility; no paper
+ * counterpart).  Launch counts are always kept; kernel durations are summed
+ * from CUDA events recorded on the graph's stream around each launch of the
+ * residual and reduce kernels while profiling is enabled. */
+typedef struct {
+    int64_t prep_launches;      /* frame-preparation kernels (3 per frame) */
+    int64_t xform_launches;
+    int64_t residual_launches;  /* residual pass launches (dense + sparse) */
+    int64_t reduce_launches;    /* reduce / assemble / solve launches */
+    double residual_ms;         /* summed event time of timed residual launches */
+    double reduce_ms;           /* summed event time of timed reduce launches */
+    int64_t timed_residual_launches;
+    int64_t timed_reduce_launches;
+    int64_t dense_pixel_pairs;  /* source-pixel x target pairs of timed residual launches */
+    int64_t sparse_pairs;       /* correspondences of timed residual launches */
+} bt_profile;
+
+/* Enables (on != 0) or disables event timing and resets every counter.
+ * Errors: BT_ERR_INVALID, BT_ERR_CUDA. */
+int bt_profile_enable(bt_graph* g, int32_t on);
+
+/* Copies the counters to *out (host).  Errors: BT_ERR_INVALID. */
+int bt_profile_read(const bt_graph* g, bt_profile* out);
+
 /* Text for a status code (static storage). */
 const char* bt_status_str(int status);
 

@@ -56,6 +56,14 @@ class bt_solve_report(C.Structure):
                 ("dense_pixel_pairs", C.c_int64)]
 
 
+class bt_profile(C.Structure):
+    _fields_ = [("prep_launches", C.c_int64), ("xform_launches", C.c_int64),
+                ("residual_launches", C.c_int64), ("reduce_launches", C.c_int64),
+                ("residual_ms", C.c_double), ("reduce_ms", C.c_double),
+                ("timed_residual_launches", C.c_int64), ("timed_reduce_launches", C.c_int64),
+                ("dense_pixel_pairs", C.c_int64), ("sparse_pairs", C.c_int64)]
+
+
 # name -> (restype, argtypes); every symbol include/bt.h declares
 SIGNATURES = {
     "bt_config_default": (None, [C.POINTER(bt_config)]),
@@ -73,6 +81,8 @@ SIGNATURES = {
     "bt_get_poses": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "bt_solve": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(bt_solve_report)]),
     "bt_eval_cost": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "bt_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
+    "bt_profile_read": (C.c_int, [C.c_void_p, C.POINTER(bt_profile)]),
     "bt_status_str": (C.c_char_p, [C.c_int]),
     "bt_last_error": (C.c_char_p, []),
 }
@@ -245,6 +255,14 @@ class PoseGraph:
                  cost_per_iter=np.array(rep.cost_per_iter[:rep.iters_run]),
                  dense_inliers=rep.dense_inliers, dense_pixel_pairs=rep.dense_pixel_pairs)
         return out, r
+
+    def profile_enable(self, on: bool = True):
+        _check(load().bt_profile_enable(self._h, int(bool(on))), "bt_profile_enable")
+
+    def profile_read(self) -> dict:
+        p = bt_profile()
+        _check(load().bt_profile_read(self._h, C.byref(p)), "bt_profile_read")
+        return {k: getattr(p, k) for k, _ in bt_profile._fields_}
 
     def eval_cost(self):
         c = (C.c_double * 3)()

@@ -111,6 +111,12 @@ struct bt_graph {
         d_edgeblk, d_ctrl, d_costs;
     bt::SolveArgs args{};
     int64_t pixels_per_pass = 0;
+    int64_t sparse_per_pass = 0;
+
+    // profiling
+    bt_profile prof{};
+    bool prof_on = false;
+    std::vector<cudaEvent_t> events;
 
     ~bt_graph()
     {
@@ -125,6 +131,7 @@ struct bt_graph {
             cudaFree(kv.second.pa);
             cudaFree(kv.second.pb);
         }
+        for (cudaEvent_t e : events) cudaEventDestroy(e);
         for (DevBuf* b : {&up_depth, &up_normals, &up_mask, &prep_blk, &prep_src_p, &prep_src_n,
                           &prep_M, &d_nodes, &d_edges, &d_tile_node, &d_pose, &d_xf, &d_xinv,
                           &d_dpart, &d_spart, &d_pairblk, &d_edgeblk, &d_ctrl, &d_costs})
@@ -297,6 +304,9 @@ int build_topology(bt_graph* g)
     a.ctrl = g->d_ctrl.as<bt::Control>();
     a.costs = g->d_costs.as<double>();
     g->pixels_per_pass = px;
+    int64_t sp = 0;
+    for (const bt::EdgeDev& e : edges) sp += e.count;
+    g->sparse_per_pass = sp;
     // the tables above were copied from host vectors that go out of scope
     BT_CUDA(cudaStreamSynchronize(s), "sync after table upload");
     g->topo_dirty = false;
@@ -316,7 +326,64 @@ int upload_poses(bt_graph* g, std::vector<double>& staging)
             "upload poses");
     BT_CUDA(cudaMemsetAsync(g->d_ctrl.p, 0, sizeof(bt::Control), g->stream), "reset control");
     BT_CUDA(bt::launch_xforms(g->args, g->stream), "launch xform");
+    g->prof.xform_launches++;
     return BT_OK;
+}
+
+// Makes sure 4 * passes events exist (two per residual and reduce launch).
+int ensure_events(bt_graph* g, int passes)
+{
+    while ((int)g->events.size() < 4 * passes) {
+        cudaEvent_t e;
+        BT_CUDA(cudaEventCreate(&e), "cudaEventCreate");
+        g->events.push_back(e);
+    }
+    return BT_OK;
+}
+
+// Enqueues `iters` full passes and one cost pass; with profiling on, events
+// bracket every launch on the graph's stream.
+int enqueue_passes(bt_graph* g, int iters, bool cost_pass, int cost_slot)
+{
+    cudaStream_t s = g->stream;
+    const bt::SolveArgs& a = g->args;
+    const int passes = iters + (cost_pass ? 1 : 0);
+    if (g->prof_on) {
+        int st = ensure_events(g, passes);
+        if (st != BT_OK) return st;
+    }
+    for (int p = 0; p < passes; ++p) {
+        const bool full = p < iters;
+        const int slot = full ? p : cost_slot;
+        if (g->prof_on) BT_CUDA(cudaEventRecord(g->events[4 * p + 0], s), "event");
+        BT_CUDA(bt::launch_residual(a, full, s), "launch residual");
+        if (g->prof_on) BT_CUDA(cudaEventRecord(g->events[4 * p + 1], s), "event");
+        BT_CUDA(bt::launch_reduce(a, full, slot, s), "launch reduce");
+        if (g->prof_on) BT_CUDA(cudaEventRecord(g->events[4 * p + 2], s), "event");
+        if (a.n_edges + a.n_tiles > 0) g->prof.residual_launches++;
+        g->prof.reduce_launches++;
+    }
+    return BT_OK;
+}
+
+// After the stream has been synchronised: fold the event times in.
+void collect_events(bt_graph* g, int passes)
+{
+    if (!g->prof_on) return;
+    for (int p = 0; p < passes; ++p) {
+        float t1 = 0.f, t2 = 0.f;
+        if (cudaEventElapsedTime(&t1, g->events[4 * p + 0], g->events[4 * p + 1]) == cudaSuccess &&
+            g->args.n_edges + g->args.n_tiles > 0) {
+            g->prof.residual_ms += t1;
+            g->prof.timed_residual_launches++;
+            g->prof.dense_pixel_pairs += g->pixels_per_pass;
+            g->prof.sparse_pairs += g->sparse_per_pass;
+        }
+        if (cudaEventElapsedTime(&t2, g->events[4 * p + 1], g->events[4 * p + 2]) == cudaSuccess) {
+            g->prof.reduce_ms += t2;
+            g->prof.timed_reduce_launches++;
+        }
+    }
 }
 
 }  // namespace
@@ -407,6 +474,7 @@ int bt_add_frame(bt_graph* g, const float* depth, const float* normals, const ui
     cudaError_t e = bt::launch_prep(d_depth, d_normals, d_mask, W, H, K->cx, K->cy, ifx, ify, f.tgt,
                                     g->prep_src_p.as<float4>(), g->prep_src_n.as<float4>(), g->prep_blk.as<int>(),
                                     g->prep_M.as<int>(), s);
+    g->prof.prep_launches += 3;
     int M = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&M, g->prep_M.p, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -539,12 +607,8 @@ int bt_solve(bt_graph* g, int32_t iters, double* poses_out, bt_solve_report* rep
     if (st != BT_OK) return st;
     cudaStream_t s = g->stream;
     const bt::SolveArgs& a = g->args;
-    for (int it = 0; it < iters; ++it) {
-        BT_CUDA(bt::launch_residual(a, true, s), "launch residual");
-        BT_CUDA(bt::launch_reduce(a, true, it, s), "launch reduce");
-    }
-    BT_CUDA(bt::launch_residual(a, false, s), "launch residual (cost)");
-    BT_CUDA(bt::launch_reduce(a, false, iters, s), "launch reduce (cost)");
+    st = enqueue_passes(g, iters, true, iters);
+    if (st != BT_OK) return st;
     const int N = a.N;
     std::vector<double> pose(12 * (size_t)N), costs(4 * (size_t)(iters + 1));
     bt::Control ctrl{};
@@ -553,6 +617,7 @@ int bt_solve(bt_graph* g, int32_t iters, double* poses_out, bt_solve_report* rep
             "read costs");
     BT_CUDA(cudaMemcpyAsync(&ctrl, a.ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost, s), "read status");
     BT_CUDA(cudaStreamSynchronize(s), "bt_solve: synchronize");
+    collect_events(g, iters + 1);
     const int status = ctrl.status == -4 ? BT_ERR_SINGULAR : BT_OK;
     if (rep) {
         std::memset(rep, 0, sizeof(*rep));
@@ -588,15 +653,32 @@ int bt_eval_cost(bt_graph* g, double* cost_out, int64_t* dense_inliers)
     int st = upload_poses(g, staging);
     if (st != BT_OK) return st;
     cudaStream_t s = g->stream;
-    BT_CUDA(bt::launch_residual(g->args, false, s), "launch residual (cost)");
-    BT_CUDA(bt::launch_reduce(g->args, false, 0, s), "launch reduce (cost)");
+    st = enqueue_passes(g, 0, true, 0);
+    if (st != BT_OK) return st;
     double c[4];
     BT_CUDA(cudaMemcpyAsync(c, g->args.costs, sizeof(c), cudaMemcpyDeviceToHost, s), "read costs");
     BT_CUDA(cudaStreamSynchronize(s), "bt_eval_cost: synchronize");
+    collect_events(g, 1);
     cost_out[0] = c[0];
     cost_out[1] = c[1];
     cost_out[2] = c[2];
     if (dense_inliers) *dense_inliers = (int64_t)std::llround(c[3]);
+    return BT_OK;
+}
+
+int bt_profile_enable(bt_graph* g, int32_t on)
+{
+    if (!g) return fail(BT_ERR_INVALID, "bt_profile_enable: NULL graph");
+    BT_CUDA(g->stream ? cudaStreamSynchronize(g->stream) : cudaDeviceSynchronize(), "bt_profile_enable: sync");
+    std::memset(&g->prof, 0, sizeof(g->prof));
+    g->prof_on = on != 0;
+    return BT_OK;
+}
+
+int bt_profile_read(const bt_graph* g, bt_profile* out)
+{
+    if (!g || !out) return fail(BT_ERR_INVALID, "bt_profile_read: NULL argument");
+    *out = g->prof;
     return BT_OK;
 }
 

