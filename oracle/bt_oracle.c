@@ -29,8 +29,9 @@
  *   - The accept/reject decision of the association produces integers (pixel
  *     indices, keep/drop).  It is evaluated in IEEE single precision, the
  *     precision of the GPU's residual pass, with the operation order spelled
- *     out below and no fused multiply-add, so that both implementations take
- *     the same decisions from the same single-precision inputs.  Residuals,
+ *     out below (fused multiply-adds exactly where written, fmaf, and nowhere
+ *     else), so that both implementations take the same decisions from the
+ *     same single-precision inputs.  Residuals,
  *     Jacobians, weights and everything after are FP64.
  *   - Gauss-Newton step: solve H dxi = -g exactly (Cholesky, no damping) over
  *     the nodes not flagged fixed (the gauge: frame I_0 is held constant),
@@ -257,16 +258,15 @@ int orc_associate(const orc_frame* fi, const orc_frame* fj, const double Ti[16],
             float px = (((float)u - fi->cx) * z) * ifx_i;
             float py = (((float)v - fi->cy) * z) * ify_i;
             float pz = z;
-            /* T_j T_i^-1 p */
-            float qjx = ((m[0] * px + m[1] * py) + m[2] * pz) + m[3];
-            float qjy = ((m[4] * px + m[5] * py) + m[6] * pz) + m[7];
-            float qjz = ((m[8] * px + m[9] * py) + m[10] * pz) + m[11];
+            /* T_j T_i^-1 p: one fused multiply-add chain per row */
+            float qjx = fmaf(m[2], pz, fmaf(m[1], py, fmaf(m[0], px, m[3])));
+            float qjy = fmaf(m[6], pz, fmaf(m[5], py, fmaf(m[4], px, m[7])));
+            float qjz = fmaf(m[10], pz, fmaf(m[9], py, fmaf(m[8], px, m[11])));
             if (!(qjz > 0.0f)) continue;
             /* pi(.) with one correctly rounded reciprocal, then the nearest pixel */
             float rz = 1.0f / qjz;
-            float uf = ((fj->fx * qjx) * rz) + fj->cx;
-            float vf = ((fj->fy * qjy) * rz) + fj->cy;
-            float uh = uf + 0.5f, vh = vf + 0.5f;
+            float uh = fmaf(fj->fx * qjx, rz, fj->cx) + 0.5f;
+            float vh = fmaf(fj->fy * qjy, rz, fj->cy) + 0.5f;
             if (!(uh >= 0.0f && uh < Wf && vh >= 0.0f && vh < Hf)) continue;
             int iu = (int)floorf(uh), iv = (int)floorf(vh);
             long tp = (long)iv * fj->width + iu;
@@ -278,15 +278,15 @@ int orc_associate(const orc_frame* fi, const orc_frame* fj, const double Ti[16],
             float tz = zt;
             /* gate 1: point-pair distance */
             float dx = tx - qjx, dy = ty - qjy, dz = tz - qjz;
-            float d2 = (dx * dx + dy * dy) + dz * dz;
+            float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
             if (!(d2 <= dmax2)) continue;
             /* gate 2: angle between the rotated source normal and the target normal */
             const float* ns = fi->normals + 3 * pix;
             const float* nt = fj->normals + 3 * tp;
-            float nx = (m[0] * ns[0] + m[1] * ns[1]) + m[2] * ns[2];
-            float ny = (m[4] * ns[0] + m[5] * ns[1]) + m[6] * ns[2];
-            float nz = (m[8] * ns[0] + m[9] * ns[1]) + m[10] * ns[2];
-            float c = (nx * nt[0] + ny * nt[1]) + nz * nt[2];
+            float nx = fmaf(m[2], ns[2], fmaf(m[1], ns[1], m[0] * ns[0]));
+            float ny = fmaf(m[6], ns[2], fmaf(m[5], ns[1], m[4] * ns[0]));
+            float nz = fmaf(m[10], ns[2], fmaf(m[9], ns[1], m[8] * ns[0]));
+            float c = fmaf(nz, nt[2], fmaf(ny, nt[1], nx * nt[0]));
             if (!(c >= cmin)) continue;
             if (n < cap) {
                 src_pix[n] = (int32_t)pix;

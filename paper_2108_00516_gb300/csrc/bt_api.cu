@@ -107,8 +107,8 @@ struct bt_graph {
     DevBuf up_depth, up_normals, up_mask, prep_blk, prep_src_p, prep_src_n, prep_M;
 
     // per-solve state
-    DevBuf d_nodes, d_edges, d_tile_node, d_pose, d_xf, d_xinv, d_dpart, d_spart, d_pairblk,
-        d_edgeblk, d_ctrl, d_costs;
+    DevBuf d_nodes, d_edges, d_tile_node, d_upairs, d_upair_edge, d_pose, d_xf, d_xinv, d_dpart,
+        d_spart, d_upairblk, d_ctrl, d_costs;
     bt::SolveArgs args{};
     int64_t pixels_per_pass = 0;
     int64_t sparse_per_pass = 0;
@@ -133,8 +133,8 @@ struct bt_graph {
         }
         for (cudaEvent_t e : events) cudaEventDestroy(e);
         for (DevBuf* b : {&up_depth, &up_normals, &up_mask, &prep_blk, &prep_src_p, &prep_src_n,
-                          &prep_M, &d_nodes, &d_edges, &d_tile_node, &d_pose, &d_xf, &d_xinv,
-                          &d_dpart, &d_spart, &d_pairblk, &d_edgeblk, &d_ctrl, &d_costs})
+                          &prep_M, &d_nodes, &d_edges, &d_tile_node, &d_upairs, &d_upair_edge,
+                          &d_pose, &d_xf, &d_xinv, &d_dpart, &d_spart, &d_upairblk, &d_ctrl, &d_costs})
             b->release();
     }
 };
@@ -255,7 +255,15 @@ int build_topology(bt_graph* g)
         e.pb = m.pb;
         edges.push_back(e);
     }
-    const int T = (int)tile_node.size(), P = N * (N - 1), E = (int)edges.size();
+    const int T = (int)tile_node.size(), P = N * (N - 1), E = (int)edges.size(), U = N * (N - 1) / 2;
+    std::vector<int2> upairs;
+    std::vector<int> upair_edge(std::max(U, 1), -1);
+    for (int a = 0; a < N; ++a)
+        for (int b = a + 1; b < N; ++b) upairs.push_back(make_int2(a, b));
+    for (int e = 0; e < E; ++e) {
+        const int a = std::min(edges[e].i, edges[e].j), b = std::max(edges[e].i, edges[e].j);
+        upair_edge[a * N - a * (a + 1) / 2 + (b - a - 1)] = e;
+    }
     cudaStream_t s = g->stream;
     BT_CUDA(g->d_nodes.ensure(sizeof(bt::NodeDev) * N), "alloc nodes");
     BT_CUDA(g->d_edges.ensure(sizeof(bt::EdgeDev) * std::max(E, 1)), "alloc edges");
@@ -266,8 +274,9 @@ int build_topology(bt_graph* g)
     BT_CUDA(g->d_dpart.ensure(sizeof(float) * bt::kDenseVals * (size_t)std::max(T, 1) * std::max(N - 1, 1)),
             "alloc dpart");
     BT_CUDA(g->d_spart.ensure(sizeof(float) * bt::kSparseVals * std::max(E, 1)), "alloc spart");
-    BT_CUDA(g->d_pairblk.ensure(sizeof(double) * bt::kPairBlk * std::max(P, 1)), "alloc pairblk");
-    BT_CUDA(g->d_edgeblk.ensure(sizeof(double) * bt::kEdgeBlk * std::max(E, 1)), "alloc edgeblk");
+    BT_CUDA(g->d_upairs.ensure(sizeof(int2) * std::max(U, 1)), "alloc upairs");
+    BT_CUDA(g->d_upair_edge.ensure(sizeof(int) * std::max(U, 1)), "alloc upair edges");
+    BT_CUDA(g->d_upairblk.ensure(sizeof(double) * bt::kUPairBlk * std::max(U, 1)), "alloc upairblk");
     BT_CUDA(g->d_ctrl.ensure(sizeof(bt::Control)), "alloc ctrl");
     BT_CUDA(g->d_costs.ensure(sizeof(double) * 4 * (BT_MAX_REPORT_ITERS + 1)), "alloc costs");
     BT_CUDA(cudaMemcpyAsync(g->d_nodes.p, nodes.data(), sizeof(bt::NodeDev) * N, cudaMemcpyHostToDevice, s),
@@ -278,12 +287,19 @@ int build_topology(bt_graph* g)
     if (T > 0)
         BT_CUDA(cudaMemcpyAsync(g->d_tile_node.p, tile_node.data(), sizeof(int) * T, cudaMemcpyHostToDevice, s),
                 "upload tiles");
+    if (U > 0) {
+        BT_CUDA(cudaMemcpyAsync(g->d_upairs.p, upairs.data(), sizeof(int2) * U, cudaMemcpyHostToDevice, s),
+                "upload pairs");
+        BT_CUDA(cudaMemcpyAsync(g->d_upair_edge.p, upair_edge.data(), sizeof(int) * U, cudaMemcpyHostToDevice, s),
+                "upload pair edges");
+    }
     bt::SolveArgs& a = g->args;
     a.N = N;
     a.n_tiles = T;
     a.n_pairs = P;
     a.n_edges = E;
     a.n_free = nfree;
+    a.n_upairs = U;
     const bt_config& c = g->cfg;
     a.dmax2 = (float)(c.dense_max_dist * c.dense_max_dist);
     a.cmin = (float)std::cos(c.dense_max_normal_deg * 3.14159265358979323846 / 180.0);
@@ -294,13 +310,14 @@ int build_topology(bt_graph* g)
     a.nodes = g->d_nodes.as<bt::NodeDev>();
     a.edges = g->d_edges.as<bt::EdgeDev>();
     a.tile_node = g->d_tile_node.as<int>();
+    a.upairs = g->d_upairs.as<int2>();
+    a.upair_edge = g->d_upair_edge.as<int>();
     a.pose = g->d_pose.as<double>();
     a.xf = g->d_xf.as<float>();
     a.xinv = g->d_xinv.as<float>();
     a.dpart = g->d_dpart.as<float>();
     a.spart = g->d_spart.as<float>();
-    a.pairblk = g->d_pairblk.as<double>();
-    a.edgeblk = g->d_edgeblk.as<double>();
+    a.upairblk = g->d_upairblk.as<double>();
     a.ctrl = g->d_ctrl.as<bt::Control>();
     a.costs = g->d_costs.as<double>();
     g->pixels_per_pass = px;
@@ -433,7 +450,8 @@ int bt_add_frame(bt_graph* g, const float* depth, const float* normals, const ui
     if (!g || !depth || !normals || !mask || !K || !pose_init)
         return fail(BT_ERR_INVALID, "bt_add_frame: NULL argument");
     if (mem_kind != BT_HOST && mem_kind != BT_DEVICE) return fail(BT_ERR_INVALID, "bt_add_frame: bad mem_kind");
-    if (K->width < 1 || K->height < 1 || (int64_t)K->width * K->height > (1 << 28))
+    if (K->width < 1 || K->height < 1 || K->width > 32767 || K->height > 32767 ||
+        (int64_t)K->width * K->height > (1 << 28))
         return fail(BT_ERR_INVALID, "bt_add_frame: image size out of range");
     if (!std::isfinite(K->fx) || !std::isfinite(K->fy) || K->fx == 0.f || K->fy == 0.f || !std::isfinite(K->cx) ||
         !std::isfinite(K->cy))

@@ -15,7 +15,8 @@
 //     xf PairXf[N*N] (float camera i -> camera j), xinv float[N][12] (T^-1),
 //     dpart float[T][N-1][32] (per source tile and target: the 21 + 6 unique
 //     J^T W J / J^T W r terms, cost, count), spart float[E][40] (sparse
-//     moments), pairblk double[P][32], edgeblk double[E][96], control words.
+//     moments), upairblk double[U][96] (per unordered node pair: its combined
+//     FP64 contributions to H and g), control words.
 #pragma once
 
 #include <cstdint>
@@ -28,8 +29,10 @@ constexpr int kPixPerThread = 4;
 constexpr int kTile = kThreads * kPixPerThread;   // source pixels per dense tile
 constexpr int kDenseVals = 32;                // 21 H + 6 g + cost + count + 3 pad
 constexpr int kSparseVals = 40;               // 39 moments + pad
-constexpr int kPairBlk = 32;                  // 21 K' + 6 g' + cost + count + pad
-constexpr int kEdgeBlk = 96;                  // 21 Hii + 21 Hjj + 36 Hij + 6 gi + 6 gj + cost + count
+// per unordered pair {a < b}: [0..20] D_a (upper 6x6), [21..41] D_b, [42..77]
+// O_ab (rows of a, columns of b), [78..83] g_a, [84..89] g_b, [90] dense
+// cost, [91] sparse cost, [92] dense count
+constexpr int kUPairBlk = 96;
 constexpr int kMaxNodes = 24;
 constexpr int kPrepPix = 1024;                // pixels per prep CTA (256 threads x 4)
 
@@ -58,19 +61,20 @@ struct Control {
 };
 
 struct SolveArgs {
-    int N, n_tiles, n_pairs, n_edges, n_free;
+    int N, n_tiles, n_pairs, n_edges, n_free, n_upairs;
     float dmax2, cmin, huber_dense, huber_sparse;
     double lambda_dense, lambda_sparse;
     const NodeDev* nodes;
     const EdgeDev* edges;
     const int* tile_node;
+    const int2* upairs;     // [U] (a, b), a < b, lexicographic
+    const int* upair_edge;  // [U] correspondence set of the pair or -1
     double* pose;       // [N][12]
     float* xf;          // [N*N][12] camera i -> camera j
     float* xinv;        // [N][12] object <- camera
     float* dpart;       // [T][N-1][32]
     float* spart;       // [E][40]
-    double* pairblk;    // [P][32]
-    double* edgeblk;    // [E][96]
+    double* upairblk;   // [U][96]
     Control* ctrl;
     double* costs;      // [iter][4]: total, dense, sparse, dense count
 };
@@ -92,5 +96,6 @@ cudaError_t launch_residual(const SolveArgs& a, bool full, cudaStream_t s);
 cudaError_t launch_reduce(const SolveArgs& a, bool full, int iter, cudaStream_t s);
 
 size_t reduce_smem_bytes(int n_free, int N);
+size_t residual_smem_bytes(int N);
 
 }  // namespace bt

@@ -4,15 +4,17 @@
 //   prep_*          frame preparation: per-pixel target map (z, n) and the
 //                   compacted list of valid masked source pixels (pi_D^-1).
 //   residual_kernel one launch per Gauss-Newton iteration: CTAs [0, E) take
-//                   one correspondence set each (Eq. 2), CTAs [E, E+T) one
-//                   tile of 1024 source pixels each and loop over every target
-//                   node (Eq. 3): association, gates, point-to-plane residual,
-//                   Jacobian, Huber weight, and a deterministic block
-//                   reduction of the 21 + 6 unique J^T W J / J^T W r terms.
-//   reduce_kernel   one CTA per ordered pair / correspondence set turns the
-//                   FP32 partials into FP64 6x6 blocks; the last CTA to finish
-//                   assembles the normal equations over the free nodes, runs
-//                   the FP64 Cholesky solve and the FP64 se(3) update.
+//                   one correspondence set each (Eq. 2), CTAs [E, E+T) stage
+//                   one tile of 1024 source pixels in shared memory and loop
+//                   over every target node (Eq. 3): association, gates,
+//                   point-to-plane residual, Jacobian, Huber weight, and a
+//                   deterministic reduction of the 21 + 6 unique J^T W J /
+//                   J^T W r terms per (tile, target).
+//   reduce_kernel   one CTA per unordered node pair turns the FP32 partials of
+//                   both directions and the pair's correspondence set into
+//                   FP64 6x6 blocks; the last CTA to finish assembles the
+//                   normal equations over the free nodes, runs the FP64
+//                   Cholesky solve and the FP64 se(3) update.
 //
 // Perturbations.  The library solves for right perturbations,
 // T_i <- T_i exp(d_i) with d = (v, w).  This is a linear change of tangent
@@ -22,10 +24,11 @@
 // -K' to (i,j), (j,i).
 //
 // Association decision.  Keep / drop and the looked-up pixel are integers
-// decided in IEEE single precision with the operation order below and no
-// contraction into FMA (__fmul_rn / __fadd_rn / __frcp_rn), so that the same
-// single-precision inputs always give the same decisions as any other
-// implementation that follows the same specification.  Residual values,
+// decided in IEEE single precision with the operation order below: fused
+// multiply-adds exactly where written (__fmaf_rn), every other operation
+// rounded on its own (__fmul_rn / __fadd_rn / __fsub_rn / __frcp_rn), so that
+// the same single-precision inputs always give the same decisions as any
+// other implementation of the same specification.  Residual values,
 // Jacobians and weights use ordinary FP32 arithmetic.
 #include "bt_internal.h"
 
@@ -250,75 +253,39 @@ __device__ __forceinline__ float warp_transpose_reduce(float (&v)[kDenseVals], i
     return v[0];
 }
 
-// One dense pixel-pair: association (Eq. 3), gates, residual, Jacobian and the
-// Huber-weighted accumulation into acc (full) or cost/count only.
-template <bool kFull>
-__device__ __forceinline__ void pixel_pair(const float4 p, const float4 n, const PairConst& c,
-                                           float dmax2, float cmin, float hub, float (&acc)[kDenseVals])
+size_t residual_smem_bytes(int N)
 {
-    // T_j T_i^-1 p
-    const float qx = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c.m[0], p.x), __fmul_rn(c.m[1], p.y)), __fmul_rn(c.m[2], p.z)), c.m[3]);
-    const float qy = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c.m[4], p.x), __fmul_rn(c.m[5], p.y)), __fmul_rn(c.m[6], p.z)), c.m[7]);
-    const float qz = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c.m[8], p.x), __fmul_rn(c.m[9], p.y)), __fmul_rn(c.m[10], p.z)), c.m[11]);
-    if (!(qz > 0.f)) return;
-    // pi(.) and the nearest pixel
-    const float rz = __frcp_rn(qz);
-    const float uh = __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(c.fx, qx), rz), c.cx), 0.5f);
-    const float vh = __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(c.fy, qy), rz), c.cy), 0.5f);
-    if (!(uh >= 0.f && uh < c.Wf && vh >= 0.f && vh < c.Hf)) return;
-    const int iu = (int)floorf(uh), iv = (int)floorf(vh);
-    const float4 t = __ldg(c.tgt + (size_t)iv * c.W + iu);
-    if (!(t.x > 0.f)) return;
-    // pi_D^-1 at the looked-up pixel (camera j)
-    const float tx = __fmul_rn(__fmul_rn(__fsub_rn((float)iu, c.cx), t.x), c.ifx);
-    const float ty = __fmul_rn(__fmul_rn(__fsub_rn((float)iv, c.cy), t.x), c.ify);
-    const float tz = t.x;
-    const float dx = __fsub_rn(tx, qx), dy = __fsub_rn(ty, qy), dz = __fsub_rn(tz, qz);
-    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-    if (!(d2 <= dmax2)) return;
-    // source normal in camera j, angle gate against the target normal
-    const float nx = __fadd_rn(__fadd_rn(__fmul_rn(c.m[0], n.x), __fmul_rn(c.m[1], n.y)), __fmul_rn(c.m[2], n.z));
-    const float ny = __fadd_rn(__fadd_rn(__fmul_rn(c.m[4], n.x), __fmul_rn(c.m[5], n.y)), __fmul_rn(c.m[6], n.z));
-    const float nz = __fadd_rn(__fadd_rn(__fmul_rn(c.m[8], n.x), __fmul_rn(c.m[9], n.y)), __fmul_rn(c.m[10], n.z));
-    const float cs = __fadd_rn(__fadd_rn(__fmul_rn(nx, t.y), __fmul_rn(ny, t.z)), __fmul_rn(nz, t.w));
-    if (!(cs >= cmin)) return;
-    // accepted: r = n_j . (q - T_j T_i^-1 p), the point-to-plane distance of Eq. 3
-    // expressed in camera j; J~ = (n_j, q x n_j)
-    const float r = fmaf(nx, dx, fmaf(ny, dy, nz * dz));
-    const float ar = fabsf(r);
-    const bool inl = ar <= hub;
-    const float rho = inl ? 0.5f * r * r : hub * (ar - 0.5f * hub);
-    if constexpr (kFull) {
-        const float w = inl ? 1.f : hub / ar;
-        const float J[6] = {nx, ny, nz, fmaf(ty, nz, -tz * ny), fmaf(tz, nx, -tx * nz), fmaf(tx, ny, -ty * nx)};
-        float wJ[6];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) wJ[k] = w * J[k];
-        int idx = 0;
-#pragma unroll
-        for (int a = 0; a < 6; ++a)
-#pragma unroll
-            for (int b = a; b < 6; ++b) {
-                acc[idx] = fmaf(wJ[a], J[b], acc[idx]);
-                ++idx;
-            }
-#pragma unroll
-        for (int k = 0; k < 6; ++k) acc[21 + k] = fmaf(wJ[k], r, acc[21 + k]);
-    }
-    acc[27] += rho;
-    acc[28] += 1.f;
+    const int nt = N > 1 ? N - 1 : 1;
+    return 2 * sizeof(float4) * kTile + sizeof(PairConst) * kMaxNodes +
+           sizeof(float) * (size_t)nt * (kThreads / 32) * kDenseVals;
 }
 
+// One tile of source pixels of node i against every other node j.  Per target
+// the four pixels of a thread go through three phases -- projection and
+// bounds, the four target gathers (all in flight together), then gates,
+// residual, Jacobian and accumulation -- and the warp's 32 sums are parked in
+// shared memory; one barrier at the end, then the (N-1) x 32 block sums are
+// written to dpart[tile][j'].
 template <bool kFull>
-__device__ void dense_tile(const SolveArgs& a, int tile)
+__device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
 {
-    __shared__ PairConst pc[kMaxNodes];
-    __shared__ float red[kThreads / 32][kDenseVals];
     const int N = a.N;
     const int i = a.tile_node[tile];
     const NodeDev Ni = a.nodes[i];
     const int base = (tile - Ni.tile0) * kTile;
+    const int nvalid = min(kTile, Ni.M - base);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4* sp = reinterpret_cast<float4*>(dsm);
+    float4* sn = sp + kTile;
+    PairConst* pc = reinterpret_cast<PairConst*>(sn + kTile);
+    float* red = reinterpret_cast<float*>(pc + kMaxNodes);   // [N-1][8][32]
+#pragma unroll
+    for (int k = 0; k < kPixPerThread; ++k) {
+        const int s = k * kThreads + threadIdx.x;
+        const bool ok = s < nvalid;
+        sp[s] = ok ? __ldg(Ni.src_p + base + s) : make_float4(0.f, 0.f, 0.f, 0.f);
+        sn[s] = ok ? __ldg(Ni.src_n + base + s) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     if (threadIdx.x < N && threadIdx.x != i) {
         const int j = threadIdx.x;
         const NodeDev Nj = a.nodes[j];
@@ -328,37 +295,87 @@ __device__ void dense_tile(const SolveArgs& a, int tile)
         c.fx = Nj.fx; c.fy = Nj.fy; c.cx = Nj.cx; c.cy = Nj.cy; c.ifx = Nj.ifx; c.ify = Nj.ify;
         c.Wf = (float)Nj.W; c.Hf = (float)Nj.H; c.W = Nj.W; c.tgt = Nj.tgt;
     }
-    float4 P[kPixPerThread], Nn[kPixPerThread];
-    bool ok[kPixPerThread];
-#pragma unroll
-    for (int k = 0; k < kPixPerThread; ++k) {
-        const int idx = base + k * kThreads + threadIdx.x;
-        ok[k] = idx < Ni.M;
-        P[k] = ok[k] ? __ldg(Ni.src_p + idx) : make_float4(0.f, 0.f, 0.f, 0.f);
-        Nn[k] = ok[k] ? __ldg(Ni.src_n + idx) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
     __syncthreads();
     const float dmax2 = a.dmax2, cmin = a.cmin, hub = a.huber_dense;
     for (int jj = 0; jj < N - 1; ++jj) {
         const int j = jj < i ? jj : jj + 1;
+        const PairConst& c = pc[j];
+        const float m0 = c.m[0], m1 = c.m[1], m2 = c.m[2], m3 = c.m[3];
+        const float m4 = c.m[4], m5 = c.m[5], m6 = c.m[6], m7 = c.m[7];
+        const float m8 = c.m[8], m9 = c.m[9], m10 = c.m[10], m11 = c.m[11];
         float acc[kDenseVals];
 #pragma unroll
         for (int k = 0; k < kDenseVals; ++k) acc[k] = 0.f;
+        // phase 1: T_j T_i^-1 p, pi(.), nearest pixel, bounds
+        float qx[kPixPerThread], qy[kPixPerThread], qz[kPixPerThread];
+        int pix[kPixPerThread];
 #pragma unroll
-        for (int k = 0; k < kPixPerThread; ++k)
-            if (ok[k]) pixel_pair<kFull>(P[k], Nn[k], pc[j], dmax2, cmin, hub, acc);
-        float* out = a.dpart + ((size_t)tile * (N - 1) + jj) * kDenseVals;
-        if constexpr (kFull) {
-            const float v = warp_transpose_reduce(acc, lane);
-            red[warp][lane] = v;
-            __syncthreads();
-            if (threadIdx.x < kDenseVals) {
-                float s = 0.f;
+        for (int k = 0; k < kPixPerThread; ++k) {
+            const int s = k * kThreads + threadIdx.x;
+            const float4 p = sp[s];
+            qx[k] = __fmaf_rn(m2, p.z, __fmaf_rn(m1, p.y, __fmaf_rn(m0, p.x, m3)));
+            qy[k] = __fmaf_rn(m6, p.z, __fmaf_rn(m5, p.y, __fmaf_rn(m4, p.x, m7)));
+            qz[k] = __fmaf_rn(m10, p.z, __fmaf_rn(m9, p.y, __fmaf_rn(m8, p.x, m11)));
+            bool ok = s < nvalid && qz[k] > 0.f;
+            const float rz = __frcp_rn(qz[k]);
+            const float uh = __fadd_rn(__fmaf_rn(__fmul_rn(c.fx, qx[k]), rz, c.cx), 0.5f);
+            const float vh = __fadd_rn(__fmaf_rn(__fmul_rn(c.fy, qy[k]), rz, c.cy), 0.5f);
+            ok = ok && uh >= 0.f && uh < c.Wf && vh >= 0.f && vh < c.Hf;
+            pix[k] = ok ? (((int)floorf(vh)) << 16) | (int)floorf(uh) : -1;
+        }
+        // phase 2: the gathers of all four pixels in flight together
+        float4 t[kPixPerThread];
 #pragma unroll
-                for (int w = 0; w < kThreads / 32; ++w) s += red[w][threadIdx.x];
-                out[threadIdx.x] = s;
+        for (int k = 0; k < kPixPerThread; ++k) {
+            const int iu = pix[k] & 0xffff, iv = pix[k] >> 16;
+            t[k] = pix[k] >= 0 ? __ldg(c.tgt + (size_t)iv * c.W + iu) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        // phase 3: gates, residual, Jacobian, Huber, accumulation
+#pragma unroll
+        for (int k = 0; k < kPixPerThread; ++k) {
+            if (!(pix[k] >= 0 && t[k].x > 0.f)) continue;
+            const int iu = pix[k] & 0xffff, iv = pix[k] >> 16;
+            const float tz = t[k].x;
+            const float tx = __fmul_rn(__fmul_rn(__fsub_rn((float)iu, c.cx), tz), c.ifx);
+            const float ty = __fmul_rn(__fmul_rn(__fsub_rn((float)iv, c.cy), tz), c.ify);
+            const float dx = __fsub_rn(tx, qx[k]), dy = __fsub_rn(ty, qy[k]), dz = __fsub_rn(tz, qz[k]);
+            const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+            if (!(d2 <= dmax2)) continue;
+            const float4 n = sn[k * kThreads + threadIdx.x];
+            const float nx = __fmaf_rn(m2, n.z, __fmaf_rn(m1, n.y, __fmul_rn(m0, n.x)));
+            const float ny = __fmaf_rn(m6, n.z, __fmaf_rn(m5, n.y, __fmul_rn(m4, n.x)));
+            const float nz = __fmaf_rn(m10, n.z, __fmaf_rn(m9, n.y, __fmul_rn(m8, n.x)));
+            const float cs = __fmaf_rn(nz, t[k].w, __fmaf_rn(ny, t[k].z, __fmul_rn(nx, t[k].y)));
+            if (!(cs >= cmin)) continue;
+            // accepted: r = n_j . (q - T_j T_i^-1 p), the point-to-plane distance
+            // of Eq. 3 expressed in camera j; J~ = (n_j, q x n_j)
+            const float r = fmaf(nx, dx, fmaf(ny, dy, nz * dz));
+            const float ar = fabsf(r);
+            const bool inl = ar <= hub;
+            acc[27] += inl ? 0.5f * r * r : hub * (ar - 0.5f * hub);
+            acc[28] += 1.f;
+            if constexpr (kFull) {
+                const float w = inl ? 1.f : hub / ar;
+                const float J[6] = {nx, ny, nz, fmaf(ty, nz, -tz * ny), fmaf(tz, nx, -tx * nz),
+                                    fmaf(tx, ny, -ty * nx)};
+                float wJ[6];
+#pragma unroll
+                for (int q = 0; q < 6; ++q) wJ[q] = w * J[q];
+                int idx = 0;
+#pragma unroll
+                for (int u = 0; u < 6; ++u)
+#pragma unroll
+                    for (int v = u; v < 6; ++v) {
+                        acc[idx] = fmaf(wJ[u], J[v], acc[idx]);
+                        ++idx;
+                    }
+#pragma unroll
+                for (int q = 0; q < 6; ++q) acc[21 + q] = fmaf(wJ[q], r, acc[21 + q]);
             }
-            __syncthreads();
+        }
+        float* slot = red + ((size_t)jj * (kThreads / 32) + warp) * kDenseVals;
+        if constexpr (kFull) {
+            slot[lane] = warp_transpose_reduce(acc, lane);
         } else {
             float c0 = acc[27], c1 = acc[28];
 #pragma unroll
@@ -367,18 +384,20 @@ __device__ void dense_tile(const SolveArgs& a, int tile)
                 c1 += __shfl_xor_sync(0xffffffffu, c1, o);
             }
             if (lane == 0) {
-                red[warp][0] = c0;
-                red[warp][1] = c1;
+                slot[27] = c0;
+                slot[28] = c1;
             }
-            __syncthreads();
-            if (threadIdx.x < 2) {
-                float s = 0.f;
-#pragma unroll
-                for (int w = 0; w < kThreads / 32; ++w) s += red[w][threadIdx.x];
-                out[27 + threadIdx.x] = s;
-            }
-            __syncthreads();
         }
+    }
+    __syncthreads();
+    const int nout = (N - 1) * kDenseVals;
+    for (int o = threadIdx.x; o < nout; o += kThreads) {
+        const int jj = o / kDenseVals, v = o % kDenseVals;
+        if (!kFull && v != 27 && v != 28) continue;
+        float s = 0.f;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) s += red[((size_t)jj * (kThreads / 32) + w) * kDenseVals + v];
+        a.dpart[((size_t)tile * (N - 1) + jj) * kDenseVals + v] = s;
     }
 }
 
@@ -462,20 +481,29 @@ __device__ void sparse_edge(const SolveArgs& a, int e)
 template <bool kFull>
 __global__ void __launch_bounds__(kThreads, 2) residual_kernel(SolveArgs a)
 {
+    extern __shared__ __align__(16) unsigned char dsm[];
     if ((int)blockIdx.x < a.n_edges)
         sparse_edge<kFull>(a, blockIdx.x);
     else
-        dense_tile<kFull>(a, blockIdx.x - a.n_edges);
+        dense_tile<kFull>(a, blockIdx.x - a.n_edges, dsm);
 }
 
 cudaError_t launch_residual(const SolveArgs& a, bool full, cudaStream_t s)
 {
+    static bool attr_set = false;
+    if (!attr_set) {
+        const int mx = (int)residual_smem_bytes(kMaxNodes);
+        cudaFuncSetAttribute(residual_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(residual_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        attr_set = true;
+    }
     const int grid = a.n_edges + a.n_tiles;
     if (grid == 0) return cudaSuccess;
+    const size_t smem = residual_smem_bytes(a.N);
     if (full)
-        residual_kernel<true><<<grid, kThreads, 0, s>>>(a);
+        residual_kernel<true><<<grid, kThreads, smem, s>>>(a);
     else
-        residual_kernel<false><<<grid, kThreads, 0, s>>>(a);
+        residual_kernel<false><<<grid, kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -490,158 +518,185 @@ __device__ __forceinline__ int sym_idx(int r, int c)
     return a * 6 - (a * (a - 1)) / 2 + (b - a);
 }
 
-// Second stage of a dense ordered pair p = (i -> j): FP64 sum of the tile
-// partials, then K' = Ad_{T_j}^T K Ad_{T_j}, g' = Ad_{T_j}^T g~ (camera-j
-// left-perturbation block -> right perturbations), times lambda_2.
-template <bool kFull>
-__device__ void reduce_pair(const SolveArgs& a, int p, double* sm)
+__device__ __forceinline__ int upair_index(int a, int b, int N)
 {
-    const int N = a.N;
-    const int i = p / (N - 1), jj = p % (N - 1);
-    const int j = jj < i ? jj : jj + 1;
-    const NodeDev Ni = a.nodes[i];
-    const int v = threadIdx.x & 31, grp = threadIdx.x >> 5;
-    double s = 0.0;
-    if (kFull || v == 27 || v == 28)
-        for (int t = Ni.tile0 + grp; t < Ni.tile0 + Ni.ntiles; t += kThreads / 32)
-            s += (double)a.dpart[((size_t)t * (N - 1) + jj) * kDenseVals + v];
-    sm[grp * 32 + v] = s;
-    __syncthreads();
-    double* tot = sm + 256;     // 32
-    double* K = sm + 288;       // 36
-    double* Ad = sm + 324;      // 36
-    double* KA = sm + 360;      // 36
-    if (threadIdx.x < 32) {
-        double t = 0.0;
-#pragma unroll
-        for (int g = 0; g < kThreads / 32; ++g) t += sm[g * 32 + threadIdx.x];
-        tot[threadIdx.x] = t;
-    }
-    __syncthreads();
-    double* out = a.pairblk + (size_t)p * kPairBlk;
-    const double lam = a.lambda_dense;
-    if (!kFull) {
-        if (threadIdx.x == 0) {
-            out[27] = lam * tot[27];
-            out[28] = tot[28];
-        }
-        return;
-    }
-    if (threadIdx.x < 36) {
-        const int r = threadIdx.x / 6, c = threadIdx.x % 6;
-        K[threadIdx.x] = tot[sym_idx(r, c)];
-        // Ad_T = [[R, [t]x R], [0, R]] for T = T_j
-        const double* T = a.pose + j * 12;
-        double val;
-        if (r >= 3 && c < 3) {
-            val = 0.0;
-        } else if (r < 3 && c < 3) {
-            val = T[r * 4 + c];
-        } else if (r >= 3 && c >= 3) {
-            val = T[(r - 3) * 4 + (c - 3)];
-        } else {
-            // ([t]x R)[r][c-3]
-            const double tx = T[3], ty = T[7], tz = T[11];
-            const double sk[9] = {0.0, -tz, ty, tz, 0.0, -tx, -ty, tx, 0.0};
-            const int cc = c - 3;
-            val = sk[r * 3 + 0] * T[0 * 4 + cc] + sk[r * 3 + 1] * T[1 * 4 + cc] + sk[r * 3 + 2] * T[2 * 4 + cc];
-        }
-        Ad[threadIdx.x] = val;
-    }
-    __syncthreads();
-    if (threadIdx.x < 36) {
-        const int r = threadIdx.x / 6, c = threadIdx.x % 6;
-        double x = 0.0;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) x += K[r * 6 + k] * Ad[k * 6 + c];
-        KA[threadIdx.x] = x;
-    }
-    __syncthreads();
-    if (threadIdx.x < 36) {
-        const int r = threadIdx.x / 6, c = threadIdx.x % 6;
-        if (c >= r) {
-            double x = 0.0;
-#pragma unroll
-            for (int k = 0; k < 6; ++k) x += Ad[k * 6 + r] * KA[k * 6 + c];
-            out[sym_idx(r, c)] = lam * x;
-        }
-    } else if (threadIdx.x < 42) {
-        const int r = threadIdx.x - 36;
-        double x = 0.0;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) x += Ad[k * 6 + r] * tot[21 + k];
-        out[21 + r] = lam * x;
-    } else if (threadIdx.x == 42) {
-        out[27] = lam * tot[27];
-        out[28] = tot[28];
-    }
+    // a < b, lexicographic order of the unordered pairs
+    return a * N - (a * (a + 1)) / 2 + (b - a - 1);
 }
 
-// Second stage of a correspondence set: right-perturbation blocks from the
-// moments (J_i = -S(a), J_j = S(b), S(x) = [I | -[x]x]), times 2 lambda_1:
+// Entry (r, c) of Ad_T = [[R, [t]x R], [0, R]] for a 3x4 pose T.
+__device__ __forceinline__ double ad_entry(const double* T, int r, int c)
+{
+    if (r >= 3 && c < 3) return 0.0;
+    if (r < 3 && c < 3) return T[r * 4 + c];
+    if (r >= 3 && c >= 3) return T[(r - 3) * 4 + (c - 3)];
+    const double tx = T[3], ty = T[7], tz = T[11];
+    const int cc = c - 3;
+    const double R0 = T[0 * 4 + cc], R1 = T[1 * 4 + cc], R2 = T[2 * 4 + cc];
+    if (r == 0) return -tz * R1 + ty * R2;
+    if (r == 1) return tz * R0 - tx * R2;
+    return -ty * R0 + tx * R1;
+}
+
+// Right-perturbation blocks of a correspondence set from its moments m (see
+// sparse_edge), J_i = -S(a), J_j = S(b), S(x) = [I | -[x]x]:
 //   H_ii = [[W I, -[sa]x], [[sa]x, tr(Saa) I - Saa]]
 //   H_jj = [[W I, -[sb]x], [[sb]x, tr(Sbb) I - Sbb]]
 //   H_ij = -[[W I, -[sb]x], [[sa]x, tr(Sba) I - Sba]]
-//   g_i = -[sum w e; sum w a x e],  g_j = [sum w e; sum w b x e]
-template <bool kFull>
-__device__ void reduce_edge(const SolveArgs& a, int e, double* sm)
+// which: 0 = ii, 1 = jj, 2 = ij.
+__device__ __forceinline__ double skew_entry(const double* x, int r, int c)
 {
-    double* m = sm;   // 40
-    if (threadIdx.x < kSparseVals) m[threadIdx.x] = (double)a.spart[(size_t)e * kSparseVals + threadIdx.x];
-    __syncthreads();
-    double* out = a.edgeblk + (size_t)e * kEdgeBlk;
-    const double lam = 2.0 * a.lambda_sparse;
-    if (threadIdx.x == 0) {
-        out[90] = lam * m[37];
-        out[91] = m[38];
-    }
-    if (!kFull) return;
-    if (threadIdx.x < 36) {
-        const int r = threadIdx.x / 6, c = threadIdx.x % 6;
-        const double W = m[0];
-        const double sa[3] = {m[1], m[2], m[3]}, sb[3] = {m[4], m[5], m[6]};
-        // symmetric 3x3 from (xx xy xz yy yz zz)
-        auto S3 = [&](int base, int rr, int cc) {
-            const int lo = rr < cc ? rr : cc, hi = rr < cc ? cc : rr;
-            const int id = lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);
-            return m[base + id];
-        };
-        auto skew = [&](const double* x, int rr, int cc) {
-            // [x]x[rr][cc]
-            if (rr == cc) return 0.0;
-            if (rr == 0) return cc == 1 ? -x[2] : x[1];
-            if (rr == 1) return cc == 0 ? x[2] : -x[0];
-            return cc == 0 ? -x[1] : x[0];
-        };
-        auto block = [&](const double* s_row, const double* s_col, int mbase, bool mat_sym, int rr, int cc) {
-            // [[W I, -[s_col]x], [[s_row]x, tr(S) I - S]] entry (rr, cc)
-            if (rr < 3 && cc < 3) return rr == cc ? W : 0.0;
-            if (rr < 3) return -skew(s_col, rr, cc - 3);
-            if (cc < 3) return skew(s_row, rr - 3, cc);
-            const int a3 = rr - 3, b3 = cc - 3;
-            double tr, sv;
-            if (mat_sym) {
-                tr = S3(mbase, 0, 0) + S3(mbase, 1, 1) + S3(mbase, 2, 2);
-                sv = S3(mbase, a3, b3);
-            } else {
-                tr = m[mbase + 0] + m[mbase + 4] + m[mbase + 8];
-                sv = m[mbase + a3 * 3 + b3];
-            }
-            return (a3 == b3 ? tr : 0.0) - sv;
-        };
-        if (c >= r) {
-            out[sym_idx(r, c)] = lam * block(sa, sa, 7, true, r, c);
-            out[21 + sym_idx(r, c)] = lam * block(sb, sb, 13, true, r, c);
-        }
-        out[42 + threadIdx.x] = -lam * block(sa, sb, 19, false, r, c);
-    } else if (threadIdx.x < 42) {
-        const int r = threadIdx.x - 36;   // g_i = -[sum w e; sum w a x e], g_j = [sum w e; sum w b x e]
-        out[78 + r] = -lam * (r < 3 ? m[28 + r] : m[31 + r - 3]);
-        out[84 + r] = lam * (r < 3 ? m[28 + r] : m[34 + r - 3]);
-    }
+    if (r == c) return 0.0;
+    if (r == 0) return c == 1 ? -x[2] : x[1];
+    if (r == 1) return c == 0 ? x[2] : -x[0];
+    return c == 0 ? -x[1] : x[0];
 }
 
-__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+__device__ double sparse_block(const double* m, int which, int r, int c)
+{
+    const double W = m[0];
+    const double* sa = m + 1;
+    const double* sb = m + 4;
+    const double* s_row = which == 1 ? sb : sa;
+    const double* s_col = which == 0 ? sa : sb;
+    double v;
+    if (r < 3 && c < 3) {
+        v = r == c ? W : 0.0;
+    } else if (r < 3) {
+        v = -skew_entry(s_col, r, c - 3);
+    } else if (c < 3) {
+        v = skew_entry(s_row, r - 3, c);
+    } else {
+        const int a3 = r - 3, b3 = c - 3;
+        double tr, sv;
+        if (which == 2) {
+            tr = m[19] + m[23] + m[27];
+            sv = m[19 + a3 * 3 + b3];
+        } else {
+            const int base = which == 0 ? 7 : 13;   // (xx xy xz yy yz zz)
+            tr = m[base + 0] + m[base + 3] + m[base + 5];
+            const int lo = a3 < b3 ? a3 : b3, hi = a3 < b3 ? b3 : a3;
+            const int id = lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);
+            sv = m[base + id];
+        }
+        v = (a3 == b3 ? tr : 0.0) - sv;
+    }
+    return which == 2 ? -v : v;
+}
+
+// Second stage of an unordered pair {A < B}: FP64 sums of the tile partials of
+// both directions, K' = Ad_{T_dst}^T K Ad_{T_dst} and g' = Ad_{T_dst}^T g~ for
+// each (camera-j left blocks -> right perturbations), plus the pair's
+// correspondence set; written pre-combined:
+//   D_A = S + H_AA, D_B = S + H_BB, O_AB = -S + H_AB, g_A = gd + g_A^s,
+//   g_B = -gd + g_B^s with S = lambda_2 (K'_{A->B} + K'_{B->A}) and
+//   gd = lambda_2 (g'_{A->B} - g'_{B->A}).
+template <bool kFull>
+__device__ void reduce_upair(const SolveArgs& a, int u, double* sm)
+{
+    const int N = a.N;
+    const int2 ab = a.upairs[u];
+    const int A = ab.x, B = ab.y;
+    const int e = a.upair_edge[u];
+    const int tid = threadIdx.x;
+    const int dir = tid >> 7, v = tid & 31, grp = (tid >> 5) & 3;
+    const int src = dir ? B : A, dst = dir ? A : B;
+    const int jj = dst < src ? dst : dst - 1;
+    const NodeDev Ns = a.nodes[src];
+    double s = 0.0;
+    if (kFull || v == 27 || v == 28)
+        for (int t = Ns.tile0 + grp; t < Ns.tile0 + Ns.ntiles; t += 4)
+            s += (double)a.dpart[((size_t)t * (N - 1) + jj) * kDenseVals + v];
+    sm[tid] = s;
+    __syncthreads();
+    double* tot = sm + 256;   // [2][32]
+    if (tid < 64) {
+        const int d = tid >> 5, w = tid & 31;
+        tot[tid] = ((sm[d * 128 + w] + sm[d * 128 + 32 + w]) + sm[d * 128 + 64 + w]) + sm[d * 128 + 96 + w];
+    }
+    __syncthreads();
+    double* out = a.upairblk + (size_t)u * kUPairBlk;
+    const double lg = a.lambda_dense, ls = 2.0 * a.lambda_sparse;
+    if (!kFull) {
+        if (tid == 0) {
+            out[90] = lg * (tot[27] + tot[32 + 27]);
+            out[91] = e >= 0 ? ls * (double)a.spart[(size_t)e * kSparseVals + 37] : 0.0;
+            out[92] = tot[28] + tot[32 + 28];
+        }
+        return;
+    }
+    double* Ad = sm + 320;   // [2][36]: Ad_{T_B} for A->B, Ad_{T_A} for B->A
+    double* K = sm + 392;    // [2][36]
+    double* KA = sm + 464;   // [2][36]
+    double* mo = sm + 536;   // 40 sparse moments
+    double* S = sm + 576;    // [36]
+    double* gd = sm + 612;   // [6]
+    if (tid < 72) {
+        const int d = tid / 36, q = tid % 36, r = q / 6, c = q % 6;
+        Ad[tid] = ad_entry(a.pose + (d ? A : B) * 12, r, c);
+        K[tid] = tot[d * 32 + sym_idx(r, c)];
+    } else if (tid >= 128 && tid < 128 + kSparseVals) {
+        mo[tid - 128] = e >= 0 ? (double)a.spart[(size_t)e * kSparseVals + tid - 128] : 0.0;
+    }
+    __syncthreads();
+    if (tid < 72) {
+        const int d = tid / 36, q = tid % 36, r = q / 6, c = q % 6;
+        double x = 0.0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) x += K[d * 36 + r * 6 + k] * Ad[d * 36 + k * 6 + c];
+        KA[tid] = x;
+    }
+    __syncthreads();
+    if (tid < 36) {
+        const int r = tid / 6, c = tid % 6;
+        if (c >= r) {
+            double x0 = 0.0, x1 = 0.0;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                x0 += Ad[k * 6 + r] * KA[k * 6 + c];
+                x1 += Ad[36 + k * 6 + r] * KA[36 + k * 6 + c];
+            }
+            S[r * 6 + c] = S[c * 6 + r] = lg * (x0 + x1);
+        }
+    } else if (tid < 42) {
+        const int r = tid - 36;
+        double g0 = 0.0, g1 = 0.0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            g0 += Ad[k * 6 + r] * tot[21 + k];
+            g1 += Ad[36 + k * 6 + r] * tot[32 + 21 + k];
+        }
+        gd[r] = lg * (g0 - g1);
+    }
+    __syncthreads();
+    const bool has = e >= 0;
+    const bool fwd = has && a.edges[e].i == A;   // correspondence set stored as (A, B)
+    if (tid < 36) {
+        const int r = tid / 6, c = tid % 6;
+        double hAA = 0.0, hBB = 0.0, hAB = 0.0;
+        if (has) {
+            hAA = ls * sparse_block(mo, fwd ? 0 : 1, r, c);
+            hBB = ls * sparse_block(mo, fwd ? 1 : 0, r, c);
+            hAB = ls * (fwd ? sparse_block(mo, 2, r, c) : sparse_block(mo, 2, c, r));
+        }
+        if (c >= r) {
+            out[sym_idx(r, c)] = S[tid] + hAA;
+            out[21 + sym_idx(r, c)] = S[tid] + hBB;
+        }
+        out[42 + tid] = -S[tid] + hAB;
+    } else if (tid < 42) {
+        const int r = tid - 36;
+        // g_i = -[sum w e; sum w a x e], g_j = [sum w e; sum w b x e]
+        const double gi = has ? -ls * (r < 3 ? mo[28 + r] : mo[31 + r - 3]) : 0.0;
+        const double gj = has ? ls * (r < 3 ? mo[28 + r] : mo[34 + r - 3]) : 0.0;
+        out[78 + r] = gd[r] + (fwd ? gi : gj);
+        out[84 + r] = -gd[r] + (fwd ? gj : gi);
+    } else if (tid == 42) {
+        out[90] = lg * (tot[27] + tot[32 + 27]);
+        out[91] = has ? ls * mo[37] : 0.0;
+        out[92] = tot[28] + tot[32 + 28];
+    }
+}
 
 // SE(3) exponential of xi = (v, w) as a 3x4 matrix (Rodrigues form with the
 // V matrix; series for small angles).
@@ -682,145 +737,153 @@ __device__ void se3_exp_d(const double* xi, double* E)
     }
 }
 
-// Last CTA: assemble H, g over the free nodes, Cholesky, solve, update.
+// Last CTA: energies, then (full) assembly of H and g over the free nodes,
+// Cholesky H = L L^T, forward / backward substitution, T <- T exp(dx).
 template <bool kFull>
 __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
 {
-    const int N = a.N, P = a.n_pairs, NE = a.n_edges;
-    if (threadIdx.x == 0) {
+    const int N = a.N, U = a.n_upairs;
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid < 32) {
         double ed = 0.0, es = 0.0, cnt = 0.0;
-        for (int p = 0; p < P; ++p) {
-            ed += ldcg(a.pairblk + (size_t)p * kPairBlk + 27);
-            cnt += ldcg(a.pairblk + (size_t)p * kPairBlk + 28);
+        for (int u = lane; u < U; u += 32) {
+            const double* o = a.upairblk + (size_t)u * kUPairBlk;
+            ed += __ldcg(o + 90);
+            es += __ldcg(o + 91);
+            cnt += __ldcg(o + 92);
         }
-        for (int e = 0; e < NE; ++e) es += ldcg(a.edgeblk + (size_t)e * kEdgeBlk + 90);
-        a.costs[iter * 4 + 0] = ed + es;
-        a.costs[iter * 4 + 1] = ed;
-        a.costs[iter * 4 + 2] = es;
-        a.costs[iter * 4 + 3] = cnt;
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            ed += __shfl_xor_sync(0xffffffffu, ed, off);
+            es += __shfl_xor_sync(0xffffffffu, es, off);
+            cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+        }
+        if (lane == 0) {
+            a.costs[iter * 4 + 0] = ed + es;
+            a.costs[iter * 4 + 1] = ed;
+            a.costs[iter * 4 + 2] = es;
+            a.costs[iter * 4 + 3] = cnt;
+        }
     }
     if (!kFull) return;
     const int nf = a.n_free, n = 6 * nf;
     if (n == 0) return;
     const int status0 = *(volatile int*)&a.ctrl->status;
     if (status0 != 0) return;
-    double* H = sm;                 // n*n
-    double* g = H + n * n;          // n
-    int* node_of = (int*)(g + n);   // nf
-    int* edge_of = node_of + kMaxNodes;   // N*N
+    double* H = sm;              // n*n (lower triangle used)
+    double* y = H + n * n;       // n
+    double* invd = y + n;        // n
+    double* col = invd + n;      // n
+    int* node_of = reinterpret_cast<int*>(col + n);
     __shared__ int s_fail;
-    __shared__ double s_inv;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    for (int k = tid; k < N; k += blockDim.x) {
         const int f = a.nodes[k].free_idx;
         if (f >= 0) node_of[f] = k;
     }
-    for (int k = threadIdx.x; k < N * N; k += blockDim.x) edge_of[k] = -1;
-    if (threadIdx.x == 0) s_fail = 0;
+    if (tid == 0) s_fail = 0;
     __syncthreads();
-    for (int e = threadIdx.x; e < NE; e += blockDim.x) {
-        const EdgeDev E = a.edges[e];
-        edge_of[E.i * N + E.j] = e;
-        edge_of[E.j * N + E.i] = e;
-    }
-    __syncthreads();
-    auto pidx = [&](int from, int to) { return from * (N - 1) + (to < from ? to : to - 1); };
-    // lower triangle of H
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-        const int r = idx / n, c = idx % n;
+    const double* P = a.upairblk;
+    for (int idx = tid; idx < n * n; idx += blockDim.x) {
+        const int r = idx / n, c = idx - (idx / n) * n;
         if (c > r) continue;
         const int A = node_of[r / 6], B = node_of[c / 6], rr = r % 6, cc = c % 6;
-        const int s6 = sym_idx(rr, cc);
         double s = 0.0;
         if (A == B) {
+            const int s6 = sym_idx(rr, cc);
+#pragma unroll 4
             for (int k = 0; k < N; ++k) {
                 if (k == A) continue;
-                s += ldcg(a.pairblk + (size_t)pidx(A, k) * kPairBlk + s6);
-                s += ldcg(a.pairblk + (size_t)pidx(k, A) * kPairBlk + s6);
-                const int e = edge_of[A * N + k];
-                if (e >= 0) {
-                    const bool is_i = a.edges[e].i == A;
-                    s += ldcg(a.edgeblk + (size_t)e * kEdgeBlk + (is_i ? 0 : 21) + s6);
-                }
+                const int u = A < k ? upair_index(A, k, N) : upair_index(k, A, N);
+                s += __ldcg(P + (size_t)u * kUPairBlk + (A < k ? 0 : 21) + s6);
             }
         } else {
-            s = -ldcg(a.pairblk + (size_t)pidx(A, B) * kPairBlk + s6) -
-                ldcg(a.pairblk + (size_t)pidx(B, A) * kPairBlk + s6);
-            const int e = edge_of[A * N + B];
-            if (e >= 0) {
-                const bool is_i = a.edges[e].i == A;
-                s += ldcg(a.edgeblk + (size_t)e * kEdgeBlk + 42 + (is_i ? rr * 6 + cc : cc * 6 + rr));
-            }
+            const int u = A < B ? upair_index(A, B, N) : upair_index(B, A, N);
+            s = __ldcg(P + (size_t)u * kUPairBlk + 42 + (A < B ? rr * 6 + cc : cc * 6 + rr));
         }
         H[r * n + c] = s;
     }
-    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    for (int r = tid; r < n; r += blockDim.x) {
         const int A = node_of[r / 6], rr = r % 6;
         double s = 0.0;
+#pragma unroll 4
         for (int k = 0; k < N; ++k) {
             if (k == A) continue;
-            s += ldcg(a.pairblk + (size_t)pidx(A, k) * kPairBlk + 21 + rr);
-            s -= ldcg(a.pairblk + (size_t)pidx(k, A) * kPairBlk + 21 + rr);
-            const int e = edge_of[A * N + k];
-            if (e >= 0) {
-                const bool is_i = a.edges[e].i == A;
-                s += ldcg(a.edgeblk + (size_t)e * kEdgeBlk + (is_i ? 78 : 84) + rr);
-            }
+            const int u = A < k ? upair_index(A, k, N) : upair_index(k, A, N);
+            s += __ldcg(P + (size_t)u * kUPairBlk + (A < k ? 78 : 84) + rr);
         }
-        g[r] = -s;   // right-hand side of H dx = -g
+        y[r] = -s;   // right-hand side of H dx = -g
     }
     __syncthreads();
-    // Cholesky H = L L^T (lower triangle, in place)
-    for (int k = 0; k < n; ++k) {
-        if (threadIdx.x == 0) {
-            const double d = H[k * n + k];
-            if (!(d > 0.0)) {
-                s_fail = 1;
-            } else {
-                const double l = sqrt(d);
-                H[k * n + k] = l;
-                s_inv = 1.0 / l;
-            }
+    // Cholesky, right-looking, two barriers per column; the thread that
+    // updates the next diagonal entry also takes its square root.
+    if (tid == 0) {
+        const double d = H[0];
+        if (!(d > 0.0)) {
+            s_fail = 1;
+        } else {
+            const double l = sqrt(d);
+            H[0] = l;
+            invd[0] = 1.0 / l;
         }
-        __syncthreads();
+    }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
         if (s_fail) break;
-        const double inv = s_inv;
-        for (int r = k + 1 + threadIdx.x; r < n; r += blockDim.x) H[r * n + k] *= inv;
+        const double inv = invd[k];
+        for (int r = k + 1 + tid; r < n; r += blockDim.x) col[r] = H[r * n + k] * inv;
         __syncthreads();
         const int m = n - k - 1;
-        for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-            const int r = k + 1 + t / m, c = k + 1 + t % m;
-            if (c <= r) H[r * n + c] -= H[r * n + k] * H[c * n + k];
+        const int tri = m * (m + 1) / 2;
+        for (int t = tid; t < tri; t += blockDim.x) {
+            int ip = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+            while (ip * (ip + 1) / 2 > t) --ip;
+            while ((ip + 1) * (ip + 2) / 2 <= t) ++ip;
+            const int jp = t - ip * (ip + 1) / 2;
+            const int r = k + 1 + ip, c = k + 1 + jp;
+            const double h = H[r * n + c] - col[r] * col[c];
+            if (t == 0) {
+                // diagonal entry (k+1, k+1): next pivot
+                if (!(h > 0.0)) {
+                    s_fail = 1;
+                } else {
+                    const double l = sqrt(h);
+                    H[r * n + c] = l;
+                    invd[k + 1] = 1.0 / l;
+                }
+            } else {
+                H[r * n + c] = h;
+            }
         }
+        for (int r = k + 1 + tid; r < n; r += blockDim.x) H[r * n + k] = col[r];
         __syncthreads();
     }
     if (s_fail) {
-        if (threadIdx.x == 0) a.ctrl->status = -4;
+        if (tid == 0) a.ctrl->status = -4;
         return;
     }
-    // forward / backward substitution (one warp)
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
+    // L z = y, L^T x = z (one warp)
+    if (tid < 32) {
         for (int k = 0; k < n; ++k) {
-            const double yk = g[k] / H[k * n + k];
+            const double zk = y[k] * invd[k];
             __syncwarp();
-            if (lane == 0) g[k] = yk;
-            for (int r = k + 1 + lane; r < n; r += 32) g[r] -= H[r * n + k] * yk;
+            if (lane == 0) y[k] = zk;
+            for (int r = k + 1 + lane; r < n; r += 32) y[r] -= H[r * n + k] * zk;
             __syncwarp();
         }
         for (int k = n - 1; k >= 0; --k) {
-            const double xk = g[k] / H[k * n + k];
+            const double xk = y[k] * invd[k];
             __syncwarp();
-            if (lane == 0) g[k] = xk;
-            for (int r = lane; r < k; r += 32) g[r] -= H[k * n + r] * xk;
+            if (lane == 0) y[k] = xk;
+            for (int r = lane; r < k; r += 32) y[r] -= H[k * n + r] * xk;
             __syncwarp();
         }
     }
     __syncthreads();
     // T_A <- T_A exp(dx_A)
-    if (threadIdx.x < nf) {
-        const int A = node_of[threadIdx.x];
-        double E[12], T[12], Tn[12];
-        se3_exp_d(g + 6 * threadIdx.x, E);
+    if (tid < nf) {
+        const int A = node_of[tid];
+        double E[12], T[12];
+        se3_exp_d(y + 6 * tid, E);
 #pragma unroll
         for (int k = 0; k < 12; ++k) T[k] = a.pose[A * 12 + k];
 #pragma unroll
@@ -829,14 +892,12 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
             for (int c = 0; c < 4; ++c) {
                 double s = T[r * 4 + 0] * E[0 * 4 + c] + T[r * 4 + 1] * E[1 * 4 + c] + T[r * 4 + 2] * E[2 * 4 + c];
                 if (c == 3) s += T[r * 4 + 3];
-                Tn[r * 4 + c] = s;
+                a.pose[A * 12 + r * 4 + c] = s;
             }
         }
-#pragma unroll
-        for (int k = 0; k < 12; ++k) a.pose[A * 12 + k] = Tn[k];
     }
     __syncthreads();
-    write_xforms(a, threadIdx.x, blockDim.x);
+    write_xforms(a, tid, blockDim.x);
 }
 
 template <bool kFull>
@@ -845,10 +906,7 @@ __global__ void __launch_bounds__(kThreads) reduce_kernel(SolveArgs a, int iter)
     extern __shared__ double sm[];
     __shared__ int s_last;
     const int b = blockIdx.x;
-    if (b < a.n_pairs)
-        reduce_pair<kFull>(a, b, sm);
-    else if (b < a.n_pairs + a.n_edges)
-        reduce_edge<kFull>(a, b - a.n_pairs, sm);
+    if (b < a.n_upairs) reduce_upair<kFull>(a, b, sm);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -865,8 +923,8 @@ __global__ void __launch_bounds__(kThreads) reduce_kernel(SolveArgs a, int iter)
 size_t reduce_smem_bytes(int n_free, int N)
 {
     const size_t n = 6 * (size_t)n_free;
-    size_t fin = (n * n + n) * sizeof(double) + (kMaxNodes + (size_t)N * N) * sizeof(int);
-    size_t ph1 = 400 * sizeof(double);
+    size_t fin = (n * n + 3 * n) * sizeof(double) + kMaxNodes * sizeof(int);
+    size_t ph1 = 640 * sizeof(double);
     return fin > ph1 ? fin : ph1;
 }
 
@@ -878,7 +936,7 @@ cudaError_t launch_reduce(const SolveArgs& a, bool full, int iter, cudaStream_t 
         cudaFuncSetAttribute(reduce_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
     }
-    const int grid = a.n_pairs + a.n_edges > 0 ? a.n_pairs + a.n_edges : 1;
+    const int grid = a.n_upairs > 0 ? a.n_upairs : 1;
     const size_t smem = reduce_smem_bytes(a.n_free, a.N);
     if (full)
         reduce_kernel<true><<<grid, kThreads, smem, s>>>(a, iter);
