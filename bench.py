@@ -297,7 +297,9 @@ def run_ours(args):
                 "kernel": "residual_kernel<full> (dense tiles + sparse sets)",
                 "avg_launch_us": round(avg_s * 1e6, 2), "algorithmic_bytes_per_launch": round(bytes_per_launch),
                 "share_of_step_time": round(prof["residual_ms"] / t_ms, 3) if world == 1 else None,
-                "reduce_ms_share": round(prof["reduce_ms"] / t_ms, 3) if world == 1 else None}
+                "reduce_ms_share": round(prof["reduce_ms"] / t_ms, 3) if world == 1 else None,
+                "solve_stage_cycles_per_iter": [round(c / max(1, prof["timed_reduce_launches"] - len(graphs) * args.steps))
+                                                for c in prof["solve_phase_cycles"]]}
     launches = prof["xform_launches"] + prof["residual_launches"] + prof["reduce_launches"]
 
     # ---- end to end through the C interface from host buffers

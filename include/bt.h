@@ -208,6 +208,11 @@ typedef struct {
     int64_t timed_reduce_launches;
     int64_t dense_pixel_pairs;  /* source-pixel x target pairs of timed residual launches */
     int64_t sparse_pairs;       /* correspondences of timed residual launches */
+    /* SM clock cycles of the solve stage (the last CTA of each Gauss-Newton
+     * iteration): [0] gathering the pair blocks and assembling H, g;
+     * [1] Cholesky factorisation with the forward substitution; [2] back
+     * substitution; [3] pose update and single-precision transforms */
+    int64_t solve_phase_cycles[4];
 } bt_profile;
 
 /* Enables (on != 0) or disables event timing and resets every counter.

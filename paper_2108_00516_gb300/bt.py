@@ -61,7 +61,8 @@ class bt_profile(C.Structure):
                 ("residual_launches", C.c_int64), ("reduce_launches", C.c_int64),
                 ("residual_ms", C.c_double), ("reduce_ms", C.c_double),
                 ("timed_residual_launches", C.c_int64), ("timed_reduce_launches", C.c_int64),
-                ("dense_pixel_pairs", C.c_int64), ("sparse_pairs", C.c_int64)]
+                ("dense_pixel_pairs", C.c_int64), ("sparse_pairs", C.c_int64),
+                ("solve_phase_cycles", C.c_int64 * 4)]
 
 
 # name -> (restype, argtypes); every symbol include/bt.h declares
@@ -262,7 +263,9 @@ class PoseGraph:
     def profile_read(self) -> dict:
         p = bt_profile()
         _check(load().bt_profile_read(self._h, C.byref(p)), "bt_profile_read")
-        return {k: getattr(p, k) for k, _ in bt_profile._fields_}
+        out = {k: getattr(p, k) for k, _ in bt_profile._fields_}
+        out["solve_phase_cycles"] = list(p.solve_phase_cycles)
+        return out
 
     def eval_cost(self):
         c = (C.c_double * 3)()

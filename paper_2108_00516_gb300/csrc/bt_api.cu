@@ -300,6 +300,7 @@ int build_topology(bt_graph* g)
     a.n_edges = E;
     a.n_free = nfree;
     a.n_upairs = U;
+    a.stage_blocks = bt::reduce_stage_fits(nfree, N) ? 1 : 0;
     const bt_config& c = g->cfg;
     a.dmax2 = (float)(c.dense_max_dist * c.dense_max_dist);
     a.cmin = (float)std::cos(c.dense_max_normal_deg * 3.14159265358979323846 / 180.0);
@@ -636,6 +637,8 @@ int bt_solve(bt_graph* g, int32_t iters, double* poses_out, bt_solve_report* rep
     BT_CUDA(cudaMemcpyAsync(&ctrl, a.ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost, s), "read status");
     BT_CUDA(cudaStreamSynchronize(s), "bt_solve: synchronize");
     collect_events(g, iters + 1);
+    if (g->prof_on)
+        for (int k = 0; k < 4; ++k) g->prof.solve_phase_cycles[k] += (int64_t)ctrl.clk[k];
     const int status = ctrl.status == -4 ? BT_ERR_SINGULAR : BT_OK;
     if (rep) {
         std::memset(rep, 0, sizeof(*rep));

@@ -58,10 +58,17 @@ struct Control {
     unsigned int counter;   // last-block detection of the reduce kernel
     int status;             // 0 ok, -4 singular (sticky for the solve)
     int pad[2];
+    // SM clock cycles spent by the last CTA, summed over the solve's
+    // iterations: [0] gather + assembly, [1] factorisation (with forward
+    // substitution), [2] back substitution, [3] pose update + transforms
+    unsigned long long clk[4];
 };
+
+constexpr size_t kReduceSmemMax = 200 * 1024;
 
 struct SolveArgs {
     int N, n_tiles, n_pairs, n_edges, n_free, n_upairs;
+    int stage_blocks;       // 1: the last CTA copies the pair blocks to shared memory
     float dmax2, cmin, huber_dense, huber_sparse;
     double lambda_dense, lambda_sparse;
     const NodeDev* nodes;
@@ -96,6 +103,7 @@ cudaError_t launch_residual(const SolveArgs& a, bool full, cudaStream_t s);
 cudaError_t launch_reduce(const SolveArgs& a, bool full, int iter, cudaStream_t s);
 
 size_t reduce_smem_bytes(int n_free, int N);
+bool reduce_stage_fits(int n_free, int N);
 size_t residual_smem_bytes(int N);
 
 }  // namespace bt

@@ -163,61 +163,48 @@ cudaError_t launch_prep(const float* depth, const float* normals, const uint8_t*
 }
 
 // ---------------------------------------------------------------------------
-// FP64 rigid-transform helpers (3x4 row-major), no FMA contraction so that the
-// single-precision copies of M = T_j T_i^-1 are reproducible bit for bit.
+// Single-precision transforms of the FP64 poses.  M = T_j T_i^-1 is formed in
+// FP64 without FMA contraction, products and sums in a fixed order, so that
+// its rounding to single precision is reproducible bit for bit.
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ void pose_inv_d(const double* T, double* out)
+// Writes xf[i*N+j] = float(T_j T_i^-1) and xinv[i] = float(T_i^-1) with the
+// threads of one CTA, one matrix entry per thread (the FP64 inverse first, then
+// the products).  `tinv` is shared scratch of 12 * N doubles.
+__device__ void write_xforms(const SolveArgs& a, double* tinv)
 {
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) out[r * 4 + c] = T[c * 4 + r];
-        out[r * 4 + 3] = -__dadd_rn(__dadd_rn(__dmul_rn(T[0 * 4 + r], T[3]), __dmul_rn(T[1 * 4 + r], T[7])),
-                                    __dmul_rn(T[2 * 4 + r], T[11]));
+    const int N = a.N, tid = threadIdx.x, nt = blockDim.x;
+    for (int id = tid; id < N * 12; id += nt) {
+        const int i = id / 12, e = id % 12, r = e / 4, c = e % 4;
+        const double* T = a.pose + i * 12;
+        double v;
+        if (c < 3) {
+            v = T[c * 4 + r];
+        } else {
+            v = -__dadd_rn(__dadd_rn(__dmul_rn(T[0 * 4 + r], T[3]), __dmul_rn(T[1 * 4 + r], T[7])),
+                           __dmul_rn(T[2 * 4 + r], T[11]));
+        }
+        tinv[id] = v;
+        a.xinv[id] = __double2float_rn(v);
+    }
+    __syncthreads();
+    for (int id = tid; id < N * N * 12; id += nt) {
+        const int pr = id / 12, e = id % 12, r = e / 4, c = e % 4;
+        const int i = pr / N, j = pr % N;
+        const double* A = a.pose + j * 12;   // T_j
+        const double* B = tinv + i * 12;     // T_i^-1
+        double s = __dadd_rn(__dadd_rn(__dmul_rn(A[r * 4 + 0], B[0 * 4 + c]), __dmul_rn(A[r * 4 + 1], B[1 * 4 + c])),
+                             __dmul_rn(A[r * 4 + 2], B[2 * 4 + c]));
+        if (c == 3) s = __dadd_rn(s, A[r * 4 + 3]);
+        a.xf[id] = __double2float_rn(s);
     }
 }
 
-__device__ __forceinline__ void pose_mul_d(const double* A, const double* B, double* C)
+__global__ void xform_kernel(SolveArgs a)
 {
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            double s = __dadd_rn(__dadd_rn(__dmul_rn(A[r * 4 + 0], B[0 * 4 + c]), __dmul_rn(A[r * 4 + 1], B[1 * 4 + c])),
-                                 __dmul_rn(A[r * 4 + 2], B[2 * 4 + c]));
-            if (c == 3) s = __dadd_rn(s, A[r * 4 + 3]);
-            C[r * 4 + c] = s;
-        }
-    }
+    __shared__ double tinv[12 * kMaxNodes];
+    write_xforms(a, tinv);
 }
-
-// Writes xf[i*N+j] = float(T_j T_i^-1) and xinv[i] = float(T_i^-1) for the
-// threads' share of pairs; `pose` may be read through L1 (written by this CTA
-// or by an earlier kernel).
-__device__ void write_xforms(const SolveArgs& a, int tid, int nthreads)
-{
-    const int N = a.N;
-    for (int id = tid; id < N * N; id += nthreads) {
-        const int i = id / N, j = id % N;
-        double Ti[12], Tj[12], Tinv[12], M[12];
-#pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            Ti[k] = a.pose[i * 12 + k];
-            Tj[k] = a.pose[j * 12 + k];
-        }
-        pose_inv_d(Ti, Tinv);
-        pose_mul_d(Tj, Tinv, M);
-#pragma unroll
-        for (int k = 0; k < 12; ++k) a.xf[id * 12 + k] = __double2float_rn(M[k]);
-        if (j == 0) {
-#pragma unroll
-            for (int k = 0; k < 12; ++k) a.xinv[i * 12 + k] = __double2float_rn(Tinv[k]);
-        }
-    }
-}
-
-__global__ void xform_kernel(SolveArgs a) { write_xforms(a, threadIdx.x, blockDim.x); }
 
 cudaError_t launch_xforms(const SolveArgs& a, cudaStream_t s)
 {
@@ -737,13 +724,24 @@ __device__ void se3_exp_d(const double* xi, double* E)
     }
 }
 
+// 1/sqrt(d) for d > 0: single-precision seed refined by two FP64 Newton steps
+// (each doubles the correct bits: ~23 -> 46 -> full double precision).
+__device__ __forceinline__ double rsqrt_fp64(double d)
+{
+    double r = (d > 1e-30 && d < 1e30) ? (double)rsqrtf((float)d) : 1.0 / sqrt(d);
+    r = r * (1.5 - 0.5 * d * r * r);
+    r = r * (1.5 - 0.5 * d * r * r);
+    return r;
+}
+
 // Last CTA: energies, then (full) assembly of H and g over the free nodes,
-// Cholesky H = L L^T, forward / backward substitution, T <- T exp(dx).
+// Cholesky H = L L^T with the forward substitution L z = -g carried along,
+// back substitution L^T dx = z, and T <- T exp(dx).
 template <bool kFull>
 __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
 {
     const int N = a.N, U = a.n_upairs;
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, nt = blockDim.x;
     if (tid < 32) {
         double ed = 0.0, es = 0.0, cnt = 0.0;
         for (int u = lane; u < U; u += 32) {
@@ -770,71 +768,78 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
     if (n == 0) return;
     const int status0 = *(volatile int*)&a.ctrl->status;
     if (status0 != 0) return;
+    unsigned long long t0 = clock64();
     double* H = sm;              // n*n (lower triangle used)
     double* y = H + n * n;       // n
     double* invd = y + n;        // n
     double* col = invd + n;      // n
-    int* node_of = reinterpret_cast<int*>(col + n);
+    double* stage = col + n;     // staged pair blocks, later 12 * N transform scratch
+    const size_t stage_len = a.stage_blocks ? (size_t)U * kUPairBlk : 0;
+    int* node_of = reinterpret_cast<int*>(stage + (stage_len > 12 * kMaxNodes ? stage_len : 12 * kMaxNodes));
     __shared__ int s_fail;
-    for (int k = tid; k < N; k += blockDim.x) {
+    for (int k = tid; k < N; k += nt) {
         const int f = a.nodes[k].free_idx;
         if (f >= 0) node_of[f] = k;
     }
     if (tid == 0) s_fail = 0;
+    // stage every pair block with one coalesced sweep when they fit
+    for (size_t q = tid; q < stage_len; q += nt) stage[q] = __ldcg(a.upairblk + q);
     __syncthreads();
-    const double* P = a.upairblk;
-    for (int idx = tid; idx < n * n; idx += blockDim.x) {
+    const bool staged = a.stage_blocks != 0;
+    auto blk = [&](size_t q) { return staged ? stage[q] : __ldcg(a.upairblk + q); };
+    for (int idx = tid; idx < n * n; idx += nt) {
         const int r = idx / n, c = idx - (idx / n) * n;
         if (c > r) continue;
         const int A = node_of[r / 6], B = node_of[c / 6], rr = r % 6, cc = c % 6;
         double s = 0.0;
         if (A == B) {
             const int s6 = sym_idx(rr, cc);
-#pragma unroll 4
             for (int k = 0; k < N; ++k) {
                 if (k == A) continue;
                 const int u = A < k ? upair_index(A, k, N) : upair_index(k, A, N);
-                s += __ldcg(P + (size_t)u * kUPairBlk + (A < k ? 0 : 21) + s6);
+                s += blk((size_t)u * kUPairBlk + (A < k ? 0 : 21) + s6);
             }
         } else {
             const int u = A < B ? upair_index(A, B, N) : upair_index(B, A, N);
-            s = __ldcg(P + (size_t)u * kUPairBlk + 42 + (A < B ? rr * 6 + cc : cc * 6 + rr));
+            s = blk((size_t)u * kUPairBlk + 42 + (A < B ? rr * 6 + cc : cc * 6 + rr));
         }
         H[r * n + c] = s;
     }
-    for (int r = tid; r < n; r += blockDim.x) {
+    for (int r = tid; r < n; r += nt) {
         const int A = node_of[r / 6], rr = r % 6;
         double s = 0.0;
-#pragma unroll 4
         for (int k = 0; k < N; ++k) {
             if (k == A) continue;
             const int u = A < k ? upair_index(A, k, N) : upair_index(k, A, N);
-            s += __ldcg(P + (size_t)u * kUPairBlk + (A < k ? 78 : 84) + rr);
+            s += blk((size_t)u * kUPairBlk + (A < k ? 78 : 84) + rr);
         }
         y[r] = -s;   // right-hand side of H dx = -g
     }
     __syncthreads();
-    // Cholesky, right-looking, two barriers per column; the thread that
-    // updates the next diagonal entry also takes its square root.
+    unsigned long long t1 = clock64();
+    // right-looking Cholesky, two barriers per column; the thread that
+    // updates the next diagonal entry also forms its reciprocal square root
     if (tid == 0) {
         const double d = H[0];
         if (!(d > 0.0)) {
             s_fail = 1;
         } else {
-            const double l = sqrt(d);
-            H[0] = l;
-            invd[0] = 1.0 / l;
+            const double r = rsqrt_fp64(d);
+            H[0] = d * r;
+            invd[0] = r;
         }
     }
     __syncthreads();
     for (int k = 0; k < n; ++k) {
         if (s_fail) break;
         const double inv = invd[k];
-        for (int r = k + 1 + tid; r < n; r += blockDim.x) col[r] = H[r * n + k] * inv;
+        for (int r = k + 1 + tid; r < n; r += nt) col[r] = H[r * n + k] * inv;
+        if (tid == 0) y[k] *= inv;                       // z_k
         __syncthreads();
         const int m = n - k - 1;
         const int tri = m * (m + 1) / 2;
-        for (int t = tid; t < tri; t += blockDim.x) {
+        const double zk = y[k];
+        for (int t = tid; t < tri; t += nt) {
             int ip = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
             while (ip * (ip + 1) / 2 > t) --ip;
             while ((ip + 1) * (ip + 2) / 2 <= t) ++ip;
@@ -842,34 +847,30 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
             const int r = k + 1 + ip, c = k + 1 + jp;
             const double h = H[r * n + c] - col[r] * col[c];
             if (t == 0) {
-                // diagonal entry (k+1, k+1): next pivot
                 if (!(h > 0.0)) {
                     s_fail = 1;
                 } else {
-                    const double l = sqrt(h);
-                    H[r * n + c] = l;
-                    invd[k + 1] = 1.0 / l;
+                    const double rs = rsqrt_fp64(h);
+                    H[r * n + c] = h * rs;
+                    invd[k + 1] = rs;
                 }
             } else {
                 H[r * n + c] = h;
             }
         }
-        for (int r = k + 1 + tid; r < n; r += blockDim.x) H[r * n + k] = col[r];
+        for (int r = k + 1 + tid; r < n; r += nt) {
+            H[r * n + k] = col[r];
+            y[r] -= col[r] * zk;
+        }
         __syncthreads();
     }
     if (s_fail) {
         if (tid == 0) a.ctrl->status = -4;
         return;
     }
-    // L z = y, L^T x = z (one warp)
+    unsigned long long t2 = clock64();
+    // L^T dx = z (one warp)
     if (tid < 32) {
-        for (int k = 0; k < n; ++k) {
-            const double zk = y[k] * invd[k];
-            __syncwarp();
-            if (lane == 0) y[k] = zk;
-            for (int r = k + 1 + lane; r < n; r += 32) y[r] -= H[r * n + k] * zk;
-            __syncwarp();
-        }
         for (int k = n - 1; k >= 0; --k) {
             const double xk = y[k] * invd[k];
             __syncwarp();
@@ -879,6 +880,7 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
         }
     }
     __syncthreads();
+    unsigned long long t3 = clock64();
     // T_A <- T_A exp(dx_A)
     if (tid < nf) {
         const int A = node_of[tid];
@@ -897,7 +899,14 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
         }
     }
     __syncthreads();
-    write_xforms(a, tid, blockDim.x);
+    write_xforms(a, stage);
+    if (tid == 0) {
+        unsigned long long t4 = clock64();
+        a.ctrl->clk[0] += t1 - t0;
+        a.ctrl->clk[1] += t2 - t1;
+        a.ctrl->clk[2] += t3 - t2;
+        a.ctrl->clk[3] += t4 - t3;
+    }
 }
 
 template <bool kFull>
@@ -920,20 +929,30 @@ __global__ void __launch_bounds__(kThreads) reduce_kernel(SolveArgs a, int iter)
     final_phase<kFull>(a, iter, sm);
 }
 
-size_t reduce_smem_bytes(int n_free, int N)
+static size_t reduce_smem_bytes_for(int n_free, int N, bool stage)
 {
     const size_t n = 6 * (size_t)n_free;
-    size_t fin = (n * n + 3 * n) * sizeof(double) + kMaxNodes * sizeof(int);
+    const size_t U = (size_t)N * (N - 1) / 2;
+    const size_t sl = stage ? U * kUPairBlk : 0;
+    const size_t st = sl > 12 * (size_t)kMaxNodes ? sl : 12 * (size_t)kMaxNodes;
+    size_t fin = (n * n + 3 * n + st) * sizeof(double) + kMaxNodes * sizeof(int);
     size_t ph1 = 640 * sizeof(double);
     return fin > ph1 ? fin : ph1;
+}
+
+bool reduce_stage_fits(int n_free, int N) { return reduce_smem_bytes_for(n_free, N, true) <= kReduceSmemMax; }
+
+size_t reduce_smem_bytes(int n_free, int N)
+{
+    return reduce_smem_bytes_for(n_free, N, reduce_stage_fits(n_free, N));
 }
 
 cudaError_t launch_reduce(const SolveArgs& a, bool full, int iter, cudaStream_t s)
 {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(reduce_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(reduce_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(reduce_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReduceSmemMax);
+        cudaFuncSetAttribute(reduce_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReduceSmemMax);
         attr_set = true;
     }
     const int grid = a.n_upairs > 0 ? a.n_upairs : 1;
