@@ -685,24 +685,27 @@ __device__ void reduce_upair(const SolveArgs& a, int u, double* sm)
     }
 }
 
-// SE(3) exponential of xi = (v, w) as a 3x4 matrix (Rodrigues form with the
-// V matrix; series for small angles).
+// SE(3) exponential of xi = (v, w) as a 3x4 matrix: R = I + A W + B W^2,
+// t = (I + B W + C W^2) v with A = sin(th)/th, B = (1 - cos th)/th^2,
+// C = (th - sin th)/th^3.  Below th = 0.1 the coefficients come from their
+// Taylor series through th^8 (truncation < 3e-18), which keeps the FP64
+// dependency chain short; above it from sincos.
 __device__ void se3_exp_d(const double* xi, double* E)
 {
     const double wx = xi[3], wy = xi[4], wz = xi[5];
     const double th2 = wx * wx + wy * wy + wz * wz;
-    const double th = sqrt(th2);
     double A, B, C;
-    if (th < 1e-4) {
-        A = 1.0 - th2 / 6.0 + th2 * th2 / 120.0;
-        B = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
-        C = 1.0 / 6.0 - th2 / 120.0 + th2 * th2 / 5040.0;
+    if (th2 < 0.01) {
+        A = 1.0 + th2 * (-1.0 / 6.0 + th2 * (1.0 / 120.0 + th2 * (-1.0 / 5040.0 + th2 * (1.0 / 362880.0))));
+        B = 0.5 + th2 * (-1.0 / 24.0 + th2 * (1.0 / 720.0 + th2 * (-1.0 / 40320.0 + th2 * (1.0 / 3628800.0))));
+        C = 1.0 / 6.0 + th2 * (-1.0 / 120.0 + th2 * (1.0 / 5040.0 + th2 * (-1.0 / 362880.0 + th2 * (1.0 / 39916800.0))));
     } else {
-        double s, c;
-        sincos(th, &s, &c);
-        A = s / th;
-        B = (1.0 - c) / th2;
-        C = (th - s) / (th2 * th);
+        const double th = sqrt(th2);
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        A = sn / th;
+        B = (1.0 - cs) / th2;
+        C = (th - sn) / (th2 * th);
     }
     const double W[9] = {0.0, -wz, wy, wz, 0.0, -wx, -wy, wx, 0.0};
     double W2[9];
@@ -724,24 +727,19 @@ __device__ void se3_exp_d(const double* xi, double* E)
     }
 }
 
-// 1/sqrt(d) for d > 0: single-precision seed refined by two FP64 Newton steps
-// (each doubles the correct bits: ~23 -> 46 -> full double precision).
-__device__ __forceinline__ double rsqrt_fp64(double d)
-{
-    double r = (d > 1e-30 && d < 1e30) ? (double)rsqrtf((float)d) : 1.0 / sqrt(d);
-    r = r * (1.5 - 0.5 * d * r * r);
-    r = r * (1.5 - 0.5 * d * r * r);
-    return r;
-}
-
-// Last CTA: energies, then (full) assembly of H and g over the free nodes,
-// Cholesky H = L L^T with the forward substitution L z = -g carried along,
-// back substitution L^T dx = z, and T <- T exp(dx).
+// Last CTA: energies, then (full) assembly of H and g over the free nodes and
+// the FP64 solve of H dx = -g by the square-root-free Cholesky factorisation
+// H = L D L^T (right-looking, two barriers per column, the forward
+// substitution L z = -g carried along), D w = z, L^T dx = w, and finally
+// T <- T exp(dx).  On GB300 a dependent FP64 operation costs ~64 cycles, so
+// the loop is arranged for short dependency chains: each pivot reciprocal is
+// formed by the thread that finishes that diagonal entry, and the column is
+// scaled while a copy of its unscaled values feeds the trailing update.
 template <bool kFull>
 __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
 {
     const int N = a.N, U = a.n_upairs;
-    const int tid = threadIdx.x, lane = tid & 31, nt = blockDim.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
     if (tid < 32) {
         double ed = 0.0, es = 0.0, cnt = 0.0;
         for (int u = lane; u < U; u += 32) {
@@ -771,9 +769,10 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
     unsigned long long t0 = clock64();
     double* H = sm;              // n*n (lower triangle used)
     double* y = H + n * n;       // n
-    double* invd = y + n;        // n
-    double* col = invd + n;      // n
-    double* stage = col + n;     // staged pair blocks, later 12 * N transform scratch
+    double* rD = y + n;          // n: 1 / D_k
+    double* col = rD + n;        // n: L_ik of the current column
+    double* colu = col + n;      // n: its unscaled values
+    double* stage = colu + n;    // staged pair blocks, later 12 * N transform scratch
     const size_t stage_len = a.stage_blocks ? (size_t)U * kUPairBlk : 0;
     int* node_of = reinterpret_cast<int*>(stage + (stage_len > 12 * kMaxNodes ? stage_len : 12 * kMaxNodes));
     __shared__ int s_fail;
@@ -782,85 +781,79 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
         if (f >= 0) node_of[f] = k;
     }
     if (tid == 0) s_fail = 0;
-    // stage every pair block with one coalesced sweep when they fit
     for (size_t q = tid; q < stage_len; q += nt) stage[q] = __ldcg(a.upairblk + q);
     __syncthreads();
     const bool staged = a.stage_blocks != 0;
     auto blk = [&](size_t q) { return staged ? stage[q] : __ldcg(a.upairblk + q); };
-    for (int idx = tid; idx < n * n; idx += nt) {
-        const int r = idx / n, c = idx - (idx / n) * n;
-        if (c > r) continue;
-        const int A = node_of[r / 6], B = node_of[c / 6], rr = r % 6, cc = c % 6;
-        double s = 0.0;
-        if (A == B) {
-            const int s6 = sym_idx(rr, cc);
+    // diagonal blocks and gradient: one warp per free node, lanes 0-20 the
+    // unique block entries, lanes 21-26 the gradient entries
+    for (int f = warp; f < nf; f += nt / 32) {
+        const int A = node_of[f];
+        if (lane < 27) {
+            double s0 = 0.0, s1 = 0.0;
             for (int k = 0; k < N; ++k) {
                 if (k == A) continue;
                 const int u = A < k ? upair_index(A, k, N) : upair_index(k, A, N);
-                s += blk((size_t)u * kUPairBlk + (A < k ? 0 : 21) + s6);
+                const size_t off = (size_t)u * kUPairBlk +
+                                   (lane < 21 ? (A < k ? 0 : 21) + lane : (A < k ? 78 : 84) + lane - 21);
+                if (k & 1) s1 += blk(off); else s0 += blk(off);
             }
-        } else {
-            const int u = A < B ? upair_index(A, B, N) : upair_index(B, A, N);
-            s = blk((size_t)u * kUPairBlk + 42 + (A < B ? rr * 6 + cc : cc * 6 + rr));
+            const double s = s0 + s1;
+            if (lane < 21) {
+                int r = 0, q = lane;
+                while (q >= 6 - r) { q -= 6 - r; ++r; }
+                const int c = r + q;     // (r, c), c >= r, of the 6x6 block
+                H[(6 * f + c) * n + 6 * f + r] = s;
+            } else {
+                y[6 * f + lane - 21] = -s;   // right-hand side of H dx = -g
+            }
         }
-        H[r * n + c] = s;
     }
-    for (int r = tid; r < n; r += nt) {
-        const int A = node_of[r / 6], rr = r % 6;
-        double s = 0.0;
-        for (int k = 0; k < N; ++k) {
-            if (k == A) continue;
-            const int u = A < k ? upair_index(A, k, N) : upair_index(k, A, N);
-            s += blk((size_t)u * kUPairBlk + (A < k ? 78 : 84) + rr);
-        }
-        y[r] = -s;   // right-hand side of H dx = -g
+    // off-diagonal blocks (fa > fb)
+    const int nob = nf * (nf - 1) / 2;
+    for (int q = tid; q < nob * 36; q += nt) {
+        const int b = q / 36, e = q % 36, rr = e / 6, cc = e % 6;
+        int fa = 1, rem = b;
+        while (rem >= fa) { rem -= fa; ++fa; }
+        const int fb = rem;
+        const int A = node_of[fa], B = node_of[fb];
+        const int u = A < B ? upair_index(A, B, N) : upair_index(B, A, N);
+        H[(6 * fa + rr) * n + 6 * fb + cc] = blk((size_t)u * kUPairBlk + 42 + (A < B ? rr * 6 + cc : cc * 6 + rr));
     }
     __syncthreads();
     unsigned long long t1 = clock64();
-    // right-looking Cholesky, two barriers per column; the thread that
-    // updates the next diagonal entry also forms its reciprocal square root
     if (tid == 0) {
         const double d = H[0];
-        if (!(d > 0.0)) {
-            s_fail = 1;
-        } else {
-            const double r = rsqrt_fp64(d);
-            H[0] = d * r;
-            invd[0] = r;
-        }
+        if (!(d > 0.0)) s_fail = 1; else rD[0] = __drcp_rn(d);
     }
     __syncthreads();
     for (int k = 0; k < n; ++k) {
         if (s_fail) break;
-        const double inv = invd[k];
-        for (int r = k + 1 + tid; r < n; r += nt) col[r] = H[r * n + k] * inv;
-        if (tid == 0) y[k] *= inv;                       // z_k
+        const double r = rD[k];
+        for (int i = k + 1 + tid; i < n; i += nt) {
+            const double h = H[i * n + k];
+            colu[i] = h;
+            col[i] = h * r;
+        }
         __syncthreads();
         const int m = n - k - 1;
         const int tri = m * (m + 1) / 2;
-        const double zk = y[k];
         for (int t = tid; t < tri; t += nt) {
             int ip = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
             while (ip * (ip + 1) / 2 > t) --ip;
             while ((ip + 1) * (ip + 2) / 2 <= t) ++ip;
             const int jp = t - ip * (ip + 1) / 2;
-            const int r = k + 1 + ip, c = k + 1 + jp;
-            const double h = H[r * n + c] - col[r] * col[c];
+            const int i = k + 1 + ip, j = k + 1 + jp;
+            const double h = H[i * n + j] - col[i] * colu[j];
+            H[i * n + j] = h;
             if (t == 0) {
-                if (!(h > 0.0)) {
-                    s_fail = 1;
-                } else {
-                    const double rs = rsqrt_fp64(h);
-                    H[r * n + c] = h * rs;
-                    invd[k + 1] = rs;
-                }
-            } else {
-                H[r * n + c] = h;
+                if (!(h > 0.0)) s_fail = 1; else rD[k + 1] = __drcp_rn(h);
             }
         }
-        for (int r = k + 1 + tid; r < n; r += nt) {
-            H[r * n + k] = col[r];
-            y[r] -= col[r] * zk;
+        const double zk = y[k];
+        for (int i = k + 1 + tid; i < n; i += nt) {
+            H[i * n + k] = col[i];
+            y[i] -= col[i] * zk;
         }
         __syncthreads();
     }
@@ -868,14 +861,14 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
         if (tid == 0) a.ctrl->status = -4;
         return;
     }
+    for (int i = tid; i < n; i += nt) y[i] *= rD[i];   // D w = z
+    __syncthreads();
     unsigned long long t2 = clock64();
-    // L^T dx = z (one warp)
+    // L^T dx = w, unit diagonal (one warp)
     if (tid < 32) {
-        for (int k = n - 1; k >= 0; --k) {
-            const double xk = y[k] * invd[k];
-            __syncwarp();
-            if (lane == 0) y[k] = xk;
-            for (int r = lane; r < k; r += 32) y[r] -= H[k * n + r] * xk;
+        for (int k = n - 1; k > 0; --k) {
+            const double xk = y[k];
+            for (int i = lane; i < k; i += 32) y[i] -= H[k * n + i] * xk;
             __syncwarp();
         }
     }
@@ -935,7 +928,7 @@ static size_t reduce_smem_bytes_for(int n_free, int N, bool stage)
     const size_t U = (size_t)N * (N - 1) / 2;
     const size_t sl = stage ? U * kUPairBlk : 0;
     const size_t st = sl > 12 * (size_t)kMaxNodes ? sl : 12 * (size_t)kMaxNodes;
-    size_t fin = (n * n + 3 * n + st) * sizeof(double) + kMaxNodes * sizeof(int);
+    size_t fin = (n * n + 4 * n + st) * sizeof(double) + kMaxNodes * sizeof(int);
     size_t ph1 = 640 * sizeof(double);
     return fin > ph1 ? fin : ph1;
 }
