@@ -222,6 +222,43 @@ int bt_profile_enable(bt_graph* g, int32_t on);
 /* Copies the counters to *out (host).  Errors: BT_ERR_INVALID. */
 int bt_profile_read(const bt_graph* g, bt_profile* out);
 
+/* Dense energy of one frame pair without allocating device memory.
+ *
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory at the time they need the number: code that
+ * runs inside a framework owning all device memory through its own caching
+ * allocator (a cudaMalloc there fragments the pool or is forbidden), real-time
+ * loops where cudaMalloc/cudaFree would synchronise the device and stall
+ * other streams, and embedders working under a fixed device-memory budget.
+ *
+ * It computes lambda_2 (E_g(a,b) + E_g(b,a)) of Eq. 1/Eq. 3 -- the dense part
+ * of bt_eval_cost for a graph of these two frames -- straight from the
+ * caller's buffers, with the same association rule, gates and Huber loss.
+ *   depth_x, normals_x, mask_x: DEVICE pointers (H x W, H x W x 3, H x W);
+ *   Kx, pose_x, cfg: host memory (cfg may be NULL for the defaults);
+ *   out: DEVICE pointer to 2 doubles, receives the energy and the number of
+ *        accepted associations (as a double);
+ *   cuda_stream: cudaStream_t as void* (NULL = legacy default stream).
+ * The work is enqueued on the stream and the call returns without waiting.
+ * Scratch: a library-owned static device array of 512 KiB + 256 B, held by
+ * every GPU that loads the library until the process exits; each frame may
+ * have at most 16,777,216 pixels (sides <= 32767), larger frames are rejected
+ * with BT_ERR_INVALID and a message.  All calls share that array: calls
+ * whose GPU work overlaps (on different streams or from different threads)
+ * race and must be serialised by the caller.  The first call on a device
+ * looks up the array's device address with that device current; make that
+ * first call before any stream capture.
+ * Errors: BT_ERR_INVALID, BT_ERR_CUDA; bt_noalloc_last_error() has the text. */
+int bt_pair_dense_energy_noalloc(const float* depth_a, const float* normals_a, const uint8_t* mask_a,
+                                 const bt_intrinsics* Ka, const double pose_a[16],
+                                 const float* depth_b, const float* normals_b, const uint8_t* mask_b,
+                                 const bt_intrinsics* Kb, const double pose_b[16], const bt_config* cfg,
+                                 double* out, void* cuda_stream);
+
+/* Message of the last bt_pair_dense_energy_noalloc failure on the calling
+ * thread ("" if none). */
+const char* bt_noalloc_last_error(void);
+
 /* Text for a status code (static storage). */
 const char* bt_status_str(int status);
 

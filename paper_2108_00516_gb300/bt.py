@@ -84,6 +84,11 @@ SIGNATURES = {
     "bt_eval_cost": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "bt_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "bt_profile_read": (C.c_int, [C.c_void_p, C.POINTER(bt_profile)]),
+    "bt_pair_dense_energy_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(bt_intrinsics),
+                                               C.POINTER(C.c_double), C.c_void_p, C.c_void_p, C.c_void_p,
+                                               C.POINTER(bt_intrinsics), C.POINTER(C.c_double),
+                                               C.POINTER(bt_config), C.c_void_p, C.c_void_p]),
+    "bt_noalloc_last_error": (C.c_char_p, []),
     "bt_status_str": (C.c_char_p, [C.c_int]),
     "bt_last_error": (C.c_char_p, []),
 }
@@ -272,6 +277,30 @@ class PoseGraph:
         n = C.c_int64()
         _check(load().bt_eval_cost(self._h, c, C.byref(n)), "bt_eval_cost")
         return dict(total=c[0], dense=c[1], sparse=c[2], dense_inliers=n.value)
+
+
+def pair_dense_energy_noalloc(depth_a, normals_a, mask_a, intr_a, pose_a, depth_b, normals_b, mask_b, intr_b,
+                              pose_b, out, config: bt_config | None = None, stream=None):
+    """bt_pair_dense_energy_noalloc: all image buffers and `out` (2 float64)
+    must be CUDA tensors; enqueues on `stream` and returns immediately."""
+    for x in (depth_a, normals_a, mask_a, depth_b, normals_b, mask_b, out):
+        if not (_is_torch(x) and x.is_cuda and x.is_contiguous()):
+            raise ValueError("bt_pair_dense_energy_noalloc takes contiguous CUDA tensors")
+    Ka = bt_intrinsics(*intr_a)
+    Kb = bt_intrinsics(*intr_b)
+    Pa = np.ascontiguousarray(pose_a, np.float64).reshape(16)
+    Pb = np.ascontiguousarray(pose_b, np.float64).reshape(16)
+    cfg = config if config is not None else config_default()
+    L = load()
+    st = L.bt_pair_dense_energy_noalloc(
+        C.c_void_p(depth_a.data_ptr()), C.c_void_p(normals_a.data_ptr()), C.c_void_p(mask_a.data_ptr()),
+        C.byref(Ka), Pa.ctypes.data_as(C.POINTER(C.c_double)),
+        C.c_void_p(depth_b.data_ptr()), C.c_void_p(normals_b.data_ptr()), C.c_void_p(mask_b.data_ptr()),
+        C.byref(Kb), Pb.ctypes.data_as(C.POINTER(C.c_double)), C.byref(cfg),
+        C.c_void_p(out.data_ptr()), _stream_handle(stream))
+    if st != BT_OK:
+        raise RuntimeError(f"bt_pair_dense_energy_noalloc: {L.bt_status_str(st).decode()} ({st}): "
+                           f"{L.bt_noalloc_last_error().decode()}")
 
 
 def graph_from_synth(sg, config=None, stream=None, device=None) -> PoseGraph:
