@@ -171,12 +171,12 @@ cudaError_t launch_prep(const float* depth, const float* normals, const uint8_t*
 // Writes xf[i*N+j] = float(T_j T_i^-1) and xinv[i] = float(T_i^-1) with the
 // threads of one CTA, one matrix entry per thread (the FP64 inverse first, then
 // the products).  `tinv` is shared scratch of 12 * N doubles.
-__device__ void write_xforms(const SolveArgs& a, double* tinv)
+__device__ void write_xforms(const SolveArgs& a, double* tinv, const double* pose)
 {
     const int N = a.N, tid = threadIdx.x, nt = blockDim.x;
     for (int id = tid; id < N * 12; id += nt) {
         const int i = id / 12, e = id % 12, r = e / 4, c = e % 4;
-        const double* T = a.pose + i * 12;
+        const double* T = pose + i * 12;
         double v;
         if (c < 3) {
             v = T[c * 4 + r];
@@ -191,7 +191,7 @@ __device__ void write_xforms(const SolveArgs& a, double* tinv)
     for (int id = tid; id < N * N * 12; id += nt) {
         const int pr = id / 12, e = id % 12, r = e / 4, c = e % 4;
         const int i = pr / N, j = pr % N;
-        const double* A = a.pose + j * 12;   // T_j
+        const double* A = pose + j * 12;     // T_j
         const double* B = tinv + i * 12;     // T_i^-1
         double s = __dadd_rn(__dadd_rn(__dmul_rn(A[r * 4 + 0], B[0 * 4 + c]), __dmul_rn(A[r * 4 + 1], B[1 * 4 + c])),
                              __dmul_rn(A[r * 4 + 2], B[2 * 4 + c]));
@@ -203,7 +203,7 @@ __device__ void write_xforms(const SolveArgs& a, double* tinv)
 __global__ void xform_kernel(SolveArgs a)
 {
     __shared__ double tinv[12 * kMaxNodes];
-    write_xforms(a, tinv);
+    write_xforms(a, tinv, a.pose);
 }
 
 cudaError_t launch_xforms(const SolveArgs& a, cudaStream_t s)
@@ -767,21 +767,28 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
     const int status0 = *(volatile int*)&a.ctrl->status;
     if (status0 != 0) return;
     unsigned long long t0 = clock64();
-    double* H = sm;              // n*n (lower triangle used)
+    double* H = sm;              // n*n: lower triangle H, then L^T in the upper triangle
     double* y = H + n * n;       // n
     double* rD = y + n;          // n: 1 / D_k
-    double* col = rD + n;        // n: L_ik of the current column
-    double* colu = col + n;      // n: its unscaled values
-    double* stage = colu + n;    // staged pair blocks, later 12 * N transform scratch
+    double* ps = rD + n;         // 12 * N poses
+    double* tinv = ps + 12 * kMaxNodes;   // 12 * N
+    double* stage = tinv + 12 * kMaxNodes; // staged pair blocks
     const size_t stage_len = a.stage_blocks ? (size_t)U * kUPairBlk : 0;
-    int* node_of = reinterpret_cast<int*>(stage + (stage_len > 12 * kMaxNodes ? stage_len : 12 * kMaxNodes));
+    int* node_of = reinterpret_cast<int*>(stage + stage_len);
     __shared__ int s_fail;
     for (int k = tid; k < N; k += nt) {
         const int f = a.nodes[k].free_idx;
         if (f >= 0) node_of[f] = k;
     }
+    for (int q = tid; q < 12 * N; q += nt) ps[q] = a.pose[q];
     if (tid == 0) s_fail = 0;
-    for (size_t q = tid; q < stage_len; q += nt) stage[q] = __ldcg(a.upairblk + q);
+    {
+        const double2* src = reinterpret_cast<const double2*>(a.upairblk);
+        double2* dst = reinterpret_cast<double2*>(stage);
+        const int n2 = (int)(stage_len / 2);
+#pragma unroll 4
+        for (int q = tid; q < n2; q += nt) dst[q] = __ldcg(src + q);
+    }
     __syncthreads();
     const bool staged = a.stage_blocks != 0;
     auto blk = [&](size_t q) { return staged ? stage[q] : __ldcg(a.upairblk + q); };
@@ -822,38 +829,42 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
     }
     __syncthreads();
     unsigned long long t1 = clock64();
+    // LDL^T, right-looking, one barrier per column.  Column k: the owner of
+    // row i (chunk 0) forms l_ik = H_ik / D_k, stores it transposed at (k, i)
+    // and carries the forward substitution; every thread updates its share of
+    // row i, H_ij -= l_ik H_jk (H_jk still unscaled in the lower triangle);
+    // the thread that finishes (k+1, k+1) forms the next pivot reciprocal.
     if (tid == 0) {
         const double d = H[0];
         if (!(d > 0.0)) s_fail = 1; else rD[0] = __drcp_rn(d);
     }
     __syncthreads();
-    for (int k = 0; k < n; ++k) {
+    for (int k = 0; k < n - 1; ++k) {
         if (s_fail) break;
         const double r = rD[k];
-        for (int i = k + 1 + tid; i < n; i += nt) {
-            const double h = H[i * n + k];
-            colu[i] = h;
-            col[i] = h * r;
-        }
-        __syncthreads();
-        const int m = n - k - 1;
-        const int tri = m * (m + 1) / 2;
-        for (int t = tid; t < tri; t += nt) {
-            int ip = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
-            while (ip * (ip + 1) / 2 > t) --ip;
-            while ((ip + 1) * (ip + 2) / 2 <= t) ++ip;
-            const int jp = t - ip * (ip + 1) / 2;
-            const int i = k + 1 + ip, j = k + 1 + jp;
-            const double h = H[i * n + j] - col[i] * colu[j];
-            H[i * n + j] = h;
-            if (t == 0) {
-                if (!(h > 0.0)) s_fail = 1; else rD[k + 1] = __drcp_rn(h);
-            }
-        }
         const double zk = y[k];
-        for (int i = k + 1 + tid; i < n; i += nt) {
-            H[i * n + k] = col[i];
-            y[i] -= col[i] * zk;
+        const int m = n - k - 1;
+        const int S = m <= nt ? nt / m : 1;
+        const int rows_per_pass = m <= nt ? m : nt;
+        for (int base = 0; base < m; base += rows_per_pass) {
+            const int t = tid;
+            if (t >= rows_per_pass * S) continue;
+            const int i = k + 1 + base + t % rows_per_pass;
+            if (i >= n) continue;
+            const int c0 = t / rows_per_pass;
+            const double li = H[i * n + k] * r;
+            if (c0 == 0) {
+                H[k * n + i] = li;
+                y[i] -= li * zk;
+            }
+#pragma unroll 4
+            for (int j = k + 1 + c0; j <= i; j += S) {
+                const double h = H[i * n + j] - li * H[j * n + k];
+                H[i * n + j] = h;
+                if (j == k + 1 && i == k + 1) {
+                    if (!(h > 0.0)) s_fail = 1; else rD[k + 1] = __drcp_rn(h);
+                }
+            }
         }
         __syncthreads();
     }
@@ -864,11 +875,16 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
     for (int i = tid; i < n; i += nt) y[i] *= rD[i];   // D w = z
     __syncthreads();
     unsigned long long t2 = clock64();
-    // L^T dx = w, unit diagonal (one warp)
+    // L^T dx = w, unit diagonal, two columns per step (one warp); L_ki is
+    // stored at (i, k)
     if (tid < 32) {
-        for (int k = n - 1; k > 0; --k) {
+        int k = n - 1;
+        for (; k >= 1; k -= 2) {
             const double xk = y[k];
-            for (int i = lane; i < k; i += 32) y[i] -= H[k * n + i] * xk;
+            const double xk1 = y[k - 1] - H[(k - 1) * n + k] * xk;
+            __syncwarp();
+            if (lane == 0) y[k - 1] = xk1;
+            for (int i = lane; i < k - 1; i += 32) y[i] -= H[i * n + k] * xk + H[i * n + k - 1] * xk1;
             __syncwarp();
         }
     }
@@ -880,19 +896,20 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
         double E[12], T[12];
         se3_exp_d(y + 6 * tid, E);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) T[k] = a.pose[A * 12 + k];
+        for (int k = 0; k < 12; ++k) T[k] = ps[A * 12 + k];
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 double s = T[r * 4 + 0] * E[0 * 4 + c] + T[r * 4 + 1] * E[1 * 4 + c] + T[r * 4 + 2] * E[2 * 4 + c];
                 if (c == 3) s += T[r * 4 + 3];
-                a.pose[A * 12 + r * 4 + c] = s;
+                ps[A * 12 + r * 4 + c] = s;
             }
         }
     }
     __syncthreads();
-    write_xforms(a, stage);
+    for (int q = tid; q < 12 * N; q += nt) a.pose[q] = ps[q];
+    write_xforms(a, tinv, ps);
     if (tid == 0) {
         unsigned long long t4 = clock64();
         a.ctrl->clk[0] += t1 - t0;
@@ -927,8 +944,7 @@ static size_t reduce_smem_bytes_for(int n_free, int N, bool stage)
     const size_t n = 6 * (size_t)n_free;
     const size_t U = (size_t)N * (N - 1) / 2;
     const size_t sl = stage ? U * kUPairBlk : 0;
-    const size_t st = sl > 12 * (size_t)kMaxNodes ? sl : 12 * (size_t)kMaxNodes;
-    size_t fin = (n * n + 4 * n + st) * sizeof(double) + kMaxNodes * sizeof(int);
+    size_t fin = (n * n + 2 * n + 24 * (size_t)kMaxNodes + sl) * sizeof(double) + kMaxNodes * sizeof(int);
     size_t ph1 = 640 * sizeof(double);
     return fin > ph1 ? fin : ph1;
 }
