@@ -857,14 +857,30 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
                 H[k * n + i] = li;
                 y[i] -= li * zk;
             }
-#pragma unroll 4
-            for (int j = k + 1 + c0; j <= i; j += S) {
-                const double h = H[i * n + j] - li * H[j * n + k];
-                H[i * n + j] = h;
-                if (j == k + 1 && i == k + 1) {
+            if (i == k + 1) {
+                // the row of the next pivot has the single entry (k+1, k+1)
+                if (c0 == 0) {
+                    const double h = H[i * n + i] - li * H[i * n + k];
+                    H[i * n + i] = h;
                     if (!(h > 0.0)) s_fail = 1; else rD[k + 1] = __drcp_rn(h);
                 }
+                continue;
             }
+            double* Hi = H + i * n;
+            int j = k + 1 + c0;
+            // four entries per step: all loads first, then the FMAs, then the
+            // stores, so that the dependent-latency chains overlap
+            for (; j + 3 * S <= i; j += 4 * S) {
+                const double a0 = Hi[j], a1 = Hi[j + S], a2 = Hi[j + 2 * S], a3 = Hi[j + 3 * S];
+                const double b0 = H[j * n + k], b1 = H[(j + S) * n + k], b2 = H[(j + 2 * S) * n + k],
+                             b3 = H[(j + 3 * S) * n + k];
+                const double h0 = a0 - li * b0, h1 = a1 - li * b1, h2 = a2 - li * b2, h3 = a3 - li * b3;
+                Hi[j] = h0;
+                Hi[j + S] = h1;
+                Hi[j + 2 * S] = h2;
+                Hi[j + 3 * S] = h3;
+            }
+            for (; j <= i; j += S) Hi[j] -= li * H[j * n + k];
         }
         __syncthreads();
     }
@@ -875,17 +891,34 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
     for (int i = tid; i < n; i += nt) y[i] *= rD[i];   // D w = z
     __syncthreads();
     unsigned long long t2 = clock64();
-    // L^T dx = w, unit diagonal, two columns per step (one warp); L_ki is
-    // stored at (i, k)
+    // L^T dx = w, unit diagonal (one warp; L_ki is stored at (i, k)).  Lane l
+    // keeps w_i for i = l, l + 32, ... in registers; x_k is broadcast from its
+    // owner with a shuffle, so each step is one shuffle and one FMA deep.
     if (tid < 32) {
-        int k = n - 1;
-        for (; k >= 1; k -= 2) {
-            const double xk = y[k];
-            const double xk1 = y[k - 1] - H[(k - 1) * n + k] * xk;
-            __syncwarp();
-            if (lane == 0) y[k - 1] = xk1;
-            for (int i = lane; i < k - 1; i += 32) y[i] -= H[i * n + k] * xk + H[i * n + k - 1] * xk1;
-            __syncwarp();
+        constexpr int kSlots = (6 * (kMaxNodes - 1) + 31) / 32;
+        double w[kSlots];
+#pragma unroll
+        for (int q = 0; q < kSlots; ++q) {
+            const int i = lane + 32 * q;
+            w[q] = i < n ? y[i] : 0.0;
+        }
+        for (int k = n - 1; k >= 1; --k) {
+            const int slot = k >> 5, owner = k & 31;
+            double v = w[0];
+#pragma unroll
+            for (int q = 1; q < kSlots; ++q)
+                if (slot == q) v = w[q];
+            const double xk = __shfl_sync(0xffffffffu, v, owner);
+#pragma unroll
+            for (int q = 0; q < kSlots; ++q) {
+                const int i = lane + 32 * q;
+                if (i < k) w[q] -= H[i * n + k] * xk;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kSlots; ++q) {
+            const int i = lane + 32 * q;
+            if (i < n) y[i] = w[q];
         }
     }
     __syncthreads();
