@@ -171,7 +171,7 @@ cudaError_t launch_prep(const float* depth, const float* normals, const uint8_t*
 // Writes xf[i*N+j] = float(T_j T_i^-1) and xinv[i] = float(T_i^-1) with the
 // threads of one CTA, one matrix entry per thread (the FP64 inverse first, then
 // the products).  `tinv` is shared scratch of 12 * N doubles.
-__device__ void write_xforms(const SolveArgs& a, double* tinv, const double* pose)
+__device__ void write_xforms(const SolveArgs& a, double* __restrict__ tinv, const double* __restrict__ pose)
 {
     const int N = a.N, tid = threadIdx.x, nt = blockDim.x;
     for (int id = tid; id < N * 12; id += nt) {
@@ -727,6 +727,19 @@ __device__ void se3_exp_d(const double* xi, double* E)
     }
 }
 
+// 1/d for a positive FP64 pivot: the hardware approximation (rcp.approx.f64)
+// refined by two Newton steps r <- r + r (1 - d r), each exact to FMA
+// rounding; a shorter dependency chain than a correctly rounded division.
+__device__ __forceinline__ double rcp_fp64(double d)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+    double e = fma(-d, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-d, r, 1.0);
+    return fma(r, e, r);
+}
+
 // Last CTA: energies, then (full) assembly of H and g over the free nodes and
 // the FP64 solve of H dx = -g by the square-root-free Cholesky factorisation
 // H = L D L^T (right-looking, two barriers per column, the forward
@@ -767,8 +780,9 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
     const int status0 = *(volatile int*)&a.ctrl->status;
     if (status0 != 0) return;
     unsigned long long t0 = clock64();
-    double* H = sm;              // n*n: lower triangle H, then L^T in the upper triangle
-    double* y = H + n * n;       // n
+    const int ld = n + 1;        // odd leading dimension: conflict-free FP64 rows
+    double* H = sm;              // n*ld: lower triangle H, then L^T in the upper triangle
+    double* y = H + n * ld;      // n
     double* rD = y + n;          // n: 1 / D_k
     double* ps = rD + n;         // 12 * N poses
     double* tinv = ps + 12 * kMaxNodes;   // 12 * N
@@ -810,7 +824,7 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
                 int r = 0, q = lane;
                 while (q >= 6 - r) { q -= 6 - r; ++r; }
                 const int c = r + q;     // (r, c), c >= r, of the 6x6 block
-                H[(6 * f + c) * n + 6 * f + r] = s;
+                H[(6 * f + c) * ld + 6 * f + r] = s;
             } else {
                 y[6 * f + lane - 21] = -s;   // right-hand side of H dx = -g
             }
@@ -825,62 +839,58 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
         const int fb = rem;
         const int A = node_of[fa], B = node_of[fb];
         const int u = A < B ? upair_index(A, B, N) : upair_index(B, A, N);
-        H[(6 * fa + rr) * n + 6 * fb + cc] = blk((size_t)u * kUPairBlk + 42 + (A < B ? rr * 6 + cc : cc * 6 + rr));
+        H[(6 * fa + rr) * ld + 6 * fb + cc] = blk((size_t)u * kUPairBlk + 42 + (A < B ? rr * 6 + cc : cc * 6 + rr));
     }
     __syncthreads();
     unsigned long long t1 = clock64();
-    // LDL^T, right-looking, one barrier per column.  Column k: the owner of
-    // row i (chunk 0) forms l_ik = H_ik / D_k, stores it transposed at (k, i)
-    // and carries the forward substitution; every thread updates its share of
-    // row i, H_ij -= l_ik H_jk (H_jk still unscaled in the lower triangle);
-    // the thread that finishes (k+1, k+1) forms the next pivot reciprocal.
+    // LDL^T, right-looking, one barrier per column.  Thread t owns row
+    // i = t mod n and the column chunk c0 = t div n (stride C) for the whole
+    // factorisation.  Column k: the row owner forms l_ik = H_ik / D_k, stores
+    // it transposed at (k, i) and carries the forward substitution; the
+    // chunks update H_ij -= l_ik H_jk (H_jk still unscaled in the lower
+    // triangle); the owner of (k+1, k+1) forms the next pivot reciprocal.
     if (tid == 0) {
         const double d = H[0];
-        if (!(d > 0.0)) s_fail = 1; else rD[0] = __drcp_rn(d);
+        if (!(d > 0.0)) s_fail = 1; else rD[0] = rcp_fp64(d);
     }
+    const int C = nt >= n ? nt / n : 1;
+    const int i_own = tid % n, c0 = tid / n;
+    const bool active = tid < n * C;
     __syncthreads();
     for (int k = 0; k < n - 1; ++k) {
         if (s_fail) break;
-        const double r = rD[k];
-        const double zk = y[k];
-        const int m = n - k - 1;
-        const int S = m <= nt ? nt / m : 1;
-        const int rows_per_pass = m <= nt ? m : nt;
-        for (int base = 0; base < m; base += rows_per_pass) {
-            const int t = tid;
-            if (t >= rows_per_pass * S) continue;
-            const int i = k + 1 + base + t % rows_per_pass;
-            if (i >= n) continue;
-            const int c0 = t / rows_per_pass;
-            const double li = H[i * n + k] * r;
+        if (active && i_own > k) {
+            const int i = i_own;
+            const double r = rD[k];
+            const double hik = H[i * ld + k];
+            const double li = hik * r;
             if (c0 == 0) {
-                H[k * n + i] = li;
-                y[i] -= li * zk;
+                H[k * ld + i] = li;
+                y[i] -= li * y[k];
             }
+            double* Hi = H + i * ld;
             if (i == k + 1) {
-                // the row of the next pivot has the single entry (k+1, k+1)
                 if (c0 == 0) {
-                    const double h = H[i * n + i] - li * H[i * n + k];
-                    H[i * n + i] = h;
-                    if (!(h > 0.0)) s_fail = 1; else rD[k + 1] = __drcp_rn(h);
+                    const double h = Hi[i] - li * hik;
+                    Hi[i] = h;
+                    if (!(h > 0.0)) s_fail = 1; else rD[k + 1] = rcp_fp64(h);
                 }
-                continue;
+            } else {
+                int j = k + 1 + c0;
+                // four entries per step: all loads first, then the FMAs, then
+                // the stores, so that the dependent-latency chains overlap
+                for (; j + 3 * C <= i; j += 4 * C) {
+                    const double a0 = Hi[j], a1 = Hi[j + C], a2 = Hi[j + 2 * C], a3 = Hi[j + 3 * C];
+                    const double b0 = H[j * ld + k], b1 = H[(j + C) * ld + k], b2 = H[(j + 2 * C) * ld + k],
+                                 b3 = H[(j + 3 * C) * ld + k];
+                    const double h0 = a0 - li * b0, h1 = a1 - li * b1, h2 = a2 - li * b2, h3 = a3 - li * b3;
+                    Hi[j] = h0;
+                    Hi[j + C] = h1;
+                    Hi[j + 2 * C] = h2;
+                    Hi[j + 3 * C] = h3;
+                }
+                for (; j <= i; j += C) Hi[j] -= li * H[j * ld + k];
             }
-            double* Hi = H + i * n;
-            int j = k + 1 + c0;
-            // four entries per step: all loads first, then the FMAs, then the
-            // stores, so that the dependent-latency chains overlap
-            for (; j + 3 * S <= i; j += 4 * S) {
-                const double a0 = Hi[j], a1 = Hi[j + S], a2 = Hi[j + 2 * S], a3 = Hi[j + 3 * S];
-                const double b0 = H[j * n + k], b1 = H[(j + S) * n + k], b2 = H[(j + 2 * S) * n + k],
-                             b3 = H[(j + 3 * S) * n + k];
-                const double h0 = a0 - li * b0, h1 = a1 - li * b1, h2 = a2 - li * b2, h3 = a3 - li * b3;
-                Hi[j] = h0;
-                Hi[j + S] = h1;
-                Hi[j + 2 * S] = h2;
-                Hi[j + 3 * S] = h3;
-            }
-            for (; j <= i; j += S) Hi[j] -= li * H[j * n + k];
         }
         __syncthreads();
     }
@@ -904,15 +914,20 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
         }
         for (int k = n - 1; k >= 1; --k) {
             const int slot = k >> 5, owner = k & 31;
-            double v = w[0];
-#pragma unroll
-            for (int q = 1; q < kSlots; ++q)
-                if (slot == q) v = w[q];
+            double v;
+            switch (slot) {     // warp-uniform
+            case 0: v = w[0]; break;
+            case 1: v = w[1]; break;
+            case 2: v = w[2]; break;
+            case 3: v = w[3]; break;
+            default: v = w[kSlots - 1]; break;
+            }
             const double xk = __shfl_sync(0xffffffffu, v, owner);
 #pragma unroll
             for (int q = 0; q < kSlots; ++q) {
+                if (32 * q >= k) break;      // warp-uniform
                 const int i = lane + 32 * q;
-                if (i < k) w[q] -= H[i * n + k] * xk;
+                if (i < k) w[q] -= H[i * ld + k] * xk;
             }
         }
 #pragma unroll
@@ -977,7 +992,7 @@ static size_t reduce_smem_bytes_for(int n_free, int N, bool stage)
     const size_t n = 6 * (size_t)n_free;
     const size_t U = (size_t)N * (N - 1) / 2;
     const size_t sl = stage ? U * kUPairBlk : 0;
-    size_t fin = (n * n + 2 * n + 24 * (size_t)kMaxNodes + sl) * sizeof(double) + kMaxNodes * sizeof(int);
+    size_t fin = (n * (n + 1) + 2 * n + 24 * (size_t)kMaxNodes + sl) * sizeof(double) + kMaxNodes * sizeof(int);
     size_t ph1 = 640 * sizeof(double);
     return fin > ph1 ? fin : ph1;
 }
