@@ -786,7 +786,12 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
     double* rD = y + n;          // n: 1 / D_k
     double* ps = rD + n;         // 12 * N poses
     double* tinv = ps + 12 * kMaxNodes;   // 12 * N
-    double* stage = tinv + 12 * kMaxNodes; // staged pair blocks
+    // tinv + 12 * kMaxNodes: [2][n] scaled columns, then the triangle index
+    // table (n (n+1) / 2 ints, rounded up to whole doubles), then the staged
+    // pair blocks
+    const size_t tab_dbl = ((size_t)n * (n + 1) / 2 + 1) / 2;
+    double* stage = tinv + 12 * kMaxNodes + 2 * n + tab_dbl;
+    if (((size_t)(stage - sm)) & 1) ++stage;               // 16-byte alignment for double2
     const size_t stage_len = a.stage_blocks ? (size_t)U * kUPairBlk : 0;
     int* node_of = reinterpret_cast<int*>(stage + stage_len);
     __shared__ int s_fail;
@@ -843,53 +848,88 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
     }
     __syncthreads();
     unsigned long long t1 = clock64();
-    // LDL^T, right-looking, one barrier per column.  Thread t owns row
-    // i = t mod n and the column chunk c0 = t div n (stride C) for the whole
-    // factorisation.  Column k: the row owner forms l_ik = H_ik / D_k, stores
-    // it transposed at (k, i) and carries the forward substitution; the
-    // chunks update H_ij -= l_ik H_jk (H_jk still unscaled in the lower
-    // triangle); the owner of (k+1, k+1) forms the next pivot reciprocal.
-    if (tid == 0) {
-        const double d = H[0];
-        if (!(d > 0.0)) s_fail = 1; else rD[0] = rcp_fp64(d);
+    // LDL^T with a one-column look-ahead, one barrier per column.  At step k
+    // warp 0 prepares column k+1 -- its update by column k, the pivot
+    // D_{k+1} and reciprocal, and the scaled l_{i,k+1} -- while warps
+    // {1,2,3,5,6,7} (no FP64 pipe shared with warp 0) apply column k to the
+    // trailing triangle of rows and columns >= k+2 and carry the forward
+    // substitution.  The scaled column is double-buffered; L is stored
+    // transposed in the upper triangle, L_ik at (k, i).
+    double* colb = tinv + 12 * kMaxNodes;   // [2][n]
+    int* tab = reinterpret_cast<int*>(colb + 2 * n);
+    for (int ip = tid; ip < n; ip += nt)
+        for (int jp = 0; jp <= ip; ++jp) tab[ip * (ip + 1) / 2 + jp] = (ip << 16) | jp;
+    if (warp == 0) {
+        double r = 0.0;
+        if (lane == 0) {
+            const double d = H[0];
+            if (!(d > 0.0)) s_fail = 1; else r = rcp_fp64(d);
+            rD[0] = r;
+        }
+        r = __shfl_sync(0xffffffffu, r, 0);
+        for (int i = 1 + lane; i < n; i += 32) {
+            const double l = H[i * ld] * r;
+            colb[i] = l;
+            H[i] = l;
+        }
     }
-    const int C = nt >= n ? nt / n : 1;
-    const int i_own = tid % n, c0 = tid / n;
-    const bool active = tid < n * C;
     __syncthreads();
+    const bool bulk = warp != 0 && warp != 4 && warp < 8;
+    const int nbulk = (nt / 32 >= 8 ? 6 : 0) * 32;
+    const int bt = bulk ? (warp < 4 ? warp - 1 : warp - 2) * 32 + lane : -1;
     for (int k = 0; k < n - 1; ++k) {
         if (s_fail) break;
-        if (active && i_own > k) {
-            const int i = i_own;
-            const double r = rD[k];
-            const double hik = H[i * ld + k];
-            const double li = hik * r;
-            if (c0 == 0) {
-                H[k * ld + i] = li;
-                y[i] -= li * y[k];
+        const double* ck = colb + (k & 1) * n;        // l_{i,k}
+        double* cn = colb + ((k + 1) & 1) * n;        // l_{i,k+1}, written now
+        if (warp == 0) {
+            const int p = k + 1;
+            const double hpk = H[p * ld + k];         // unscaled H_{k+1,k}
+            double rp = 0.0;
+            if (lane == 0) {
+                const double h = H[p * ld + p] - ck[p] * hpk;
+                H[p * ld + p] = h;
+                if (!(h > 0.0)) s_fail = 1; else rp = rcp_fp64(h);
+                rD[p] = rp;
             }
-            double* Hi = H + i * ld;
-            if (i == k + 1) {
-                if (c0 == 0) {
-                    const double h = Hi[i] - li * hik;
-                    Hi[i] = h;
-                    if (!(h > 0.0)) s_fail = 1; else rD[k + 1] = rcp_fp64(h);
+            constexpr int kRows = (6 * (kMaxNodes - 1) + 31) / 32;
+            double u[kRows];
+#pragma unroll
+            for (int q = 0; q < kRows; ++q) {
+                const int i = p + 1 + lane + 32 * q;
+                if (i < n) {
+                    u[q] = H[i * ld + p] - ck[i] * hpk;
+                    H[i * ld + p] = u[q];
                 }
-            } else {
-                int j = k + 1 + c0;
-                // four entries per step: all loads first, then the FMAs, then
-                // the stores, so that the dependent-latency chains overlap
-                for (; j + 3 * C <= i; j += 4 * C) {
-                    const double a0 = Hi[j], a1 = Hi[j + C], a2 = Hi[j + 2 * C], a3 = Hi[j + 3 * C];
-                    const double b0 = H[j * ld + k], b1 = H[(j + C) * ld + k], b2 = H[(j + 2 * C) * ld + k],
-                                 b3 = H[(j + 3 * C) * ld + k];
-                    const double h0 = a0 - li * b0, h1 = a1 - li * b1, h2 = a2 - li * b2, h3 = a3 - li * b3;
-                    Hi[j] = h0;
-                    Hi[j + C] = h1;
-                    Hi[j + 2 * C] = h2;
-                    Hi[j + 3 * C] = h3;
+            }
+            rp = __shfl_sync(0xffffffffu, rp, 0);
+#pragma unroll
+            for (int q = 0; q < kRows; ++q) {
+                const int i = p + 1 + lane + 32 * q;
+                if (i < n) {
+                    const double l = u[q] * rp;
+                    cn[i] = l;
+                    H[p * ld + i] = l;
                 }
-                for (; j <= i; j += C) Hi[j] -= li * H[j * ld + k];
+            }
+        } else if (bulk) {
+            const int m1 = n - k - 2, tri = m1 * (m1 + 1) / 2;
+            const double zk = y[k];
+            for (int i = k + 1 + bt; i < n; i += nbulk) y[i] -= ck[i] * zk;
+            int t = bt;
+            for (; t + nbulk < tri; t += 2 * nbulk) {
+                const int e0 = tab[t], e1 = tab[t + nbulk];
+                const int i0 = k + 2 + (e0 >> 16), j0 = k + 2 + (e0 & 0xffff);
+                const int i1 = k + 2 + (e1 >> 16), j1 = k + 2 + (e1 & 0xffff);
+                const double a0 = H[i0 * ld + j0], a1 = H[i1 * ld + j1];
+                const double l0 = ck[i0], l1 = ck[i1];
+                const double b0 = H[j0 * ld + k], b1 = H[j1 * ld + k];
+                H[i0 * ld + j0] = a0 - l0 * b0;
+                H[i1 * ld + j1] = a1 - l1 * b1;
+            }
+            for (; t < tri; t += nbulk) {
+                const int e = tab[t];
+                const int i = k + 2 + (e >> 16), j = k + 2 + (e & 0xffff);
+                H[i * ld + j] -= ck[i] * H[j * ld + k];
             }
         }
         __syncthreads();
@@ -992,7 +1032,9 @@ static size_t reduce_smem_bytes_for(int n_free, int N, bool stage)
     const size_t n = 6 * (size_t)n_free;
     const size_t U = (size_t)N * (N - 1) / 2;
     const size_t sl = stage ? U * kUPairBlk : 0;
-    size_t fin = (n * (n + 1) + 2 * n + 24 * (size_t)kMaxNodes + sl) * sizeof(double) + kMaxNodes * sizeof(int);
+    const size_t tab_dbl = (n * (n + 1) / 2 + 1) / 2;
+    size_t fin = (n * (n + 1) + 4 * n + 24 * (size_t)kMaxNodes + tab_dbl + 1 + sl) * sizeof(double) +
+                 kMaxNodes * sizeof(int);
     size_t ph1 = 640 * sizeof(double);
     return fin > ph1 ? fin : ph1;
 }
