@@ -24,9 +24,12 @@
 
 namespace bt {
 
-constexpr int kThreads = 256;                 // residual and reduce CTAs
-constexpr int kPixPerThread = 4;
-constexpr int kTile = kThreads * kPixPerThread;   // source pixels per dense tile
+constexpr int kThreads = 256;                 // reduce CTAs, sparse CTAs, prep CTAs
+constexpr int kPixPerThread = 4;              // prep
+constexpr int kResThreads = 128;              // dense residual CTAs
+constexpr int kResBatch = 4;                  // pixels per phased batch
+constexpr int kResBatches = 2;                // batches per thread and target
+constexpr int kTile = kResThreads * kResBatch * kResBatches;   // source pixels per dense tile
 constexpr int kDenseVals = 32;                // 21 H + 6 g + cost + count + 3 pad
 constexpr int kSparseVals = 40;               // 39 moments + pad
 // per unordered pair {a < b}: [0..20] D_a (upper 6x6), [21..41] D_b, [42..77]

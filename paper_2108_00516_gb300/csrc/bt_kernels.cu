@@ -244,18 +244,59 @@ size_t residual_smem_bytes(int N)
 {
     const int nt = N > 1 ? N - 1 : 1;
     return 2 * sizeof(float4) * kTile + sizeof(PairConst) * kMaxNodes +
-           sizeof(float) * (size_t)nt * (kThreads / 32) * kDenseVals;
+           sizeof(float) * (size_t)nt * (kResThreads / 32) * kDenseVals;
+}
+
+// Packed single-precision FMA on two lanes of a 64-bit register pair:
+// (c0, c1) += (a0, a1) * (b0, b1).
+__device__ __forceinline__ void ffma2(float& c0, float& c1, float a0, float a1, float b0, float b1)
+{
+    asm("{\n\t.reg .b64 ra, rb, rc;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rc, {%0, %1};\n\t"
+        "fma.rn.f32x2 rc, ra, rb, rc;\n\t"
+        "mov.b64 {%0, %1}, rc;\n\t}"
+        : "+f"(c0), "+f"(c1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+
+// acc[0..20] += w J J^T (upper triangle, row-major), acc[21..26] += w J r,
+// acc[27] += rho, acc[28] += 1.  Two entries per packed FMA: rows (0,1),
+// (2,3), (4,5) of the same column share the broadcast J_b.
+__device__ __forceinline__ void accumulate_pair(float (&acc)[kDenseVals], const float (&J)[6], float w, float r,
+                                                float rho)
+{
+    float wJ[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) wJ[q] = w * J[q];
+    // upper-triangle indices: row a, column b >= a
+    // (0,b) = b, (1,b) = 5 + b, (2,b) = 9 + b, (3,b) = 12 + b, (4,b) = 14 + b, (5,5) = 20
+    acc[0] = fmaf(wJ[0], J[0], acc[0]);
+#pragma unroll
+    for (int b = 1; b < 6; ++b) ffma2(acc[b], acc[5 + b], wJ[0], wJ[1], J[b], J[b]);
+    acc[11] = fmaf(wJ[2], J[2], acc[11]);
+#pragma unroll
+    for (int b = 3; b < 6; ++b) ffma2(acc[9 + b], acc[12 + b], wJ[2], wJ[3], J[b], J[b]);
+    acc[18] = fmaf(wJ[4], J[4], acc[18]);
+    ffma2(acc[19], acc[20], wJ[4], wJ[5], J[5], J[5]);
+    ffma2(acc[21], acc[22], wJ[0], wJ[1], r, r);
+    ffma2(acc[23], acc[24], wJ[2], wJ[3], r, r);
+    ffma2(acc[25], acc[26], wJ[4], wJ[5], r, r);
+    acc[27] += rho;
+    acc[28] += 1.f;
 }
 
 // One tile of source pixels of node i against every other node j.  Per target
-// the four pixels of a thread go through three phases -- projection and
-// bounds, the four target gathers (all in flight together), then gates,
-// residual, Jacobian and accumulation -- and the warp's 32 sums are parked in
-// shared memory; one barrier at the end, then the (N-1) x 32 block sums are
-// written to dpart[tile][j'].
+// each thread takes its eight pixels in two batches of four; a batch goes
+// through three phases -- projection and bounds, the four target gathers (all
+// in flight together), then gates, residual, Jacobian and accumulation.  The
+// warp's 32 sums are parked in shared memory; one barrier at the end, then
+// the (N-1) x 32 block sums are written to dpart[tile][j'].
 template <bool kFull>
 __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
 {
+    constexpr int kW = kResThreads / 32;
     const int N = a.N;
     const int i = a.tile_node[tile];
     const NodeDev Ni = a.nodes[i];
@@ -265,10 +306,8 @@ __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
     float4* sp = reinterpret_cast<float4*>(dsm);
     float4* sn = sp + kTile;
     PairConst* pc = reinterpret_cast<PairConst*>(sn + kTile);
-    float* red = reinterpret_cast<float*>(pc + kMaxNodes);   // [N-1][8][32]
-#pragma unroll
-    for (int k = 0; k < kPixPerThread; ++k) {
-        const int s = k * kThreads + threadIdx.x;
+    float* red = reinterpret_cast<float*>(pc + kMaxNodes);   // [N-1][kW][32]
+    for (int s = threadIdx.x; s < kTile; s += kResThreads) {
         const bool ok = s < nvalid;
         sp[s] = ok ? __ldg(Ni.src_p + base + s) : make_float4(0.f, 0.f, 0.f, 0.f);
         sn[s] = ok ? __ldg(Ni.src_n + base + s) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -293,74 +332,67 @@ __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
         float acc[kDenseVals];
 #pragma unroll
         for (int k = 0; k < kDenseVals; ++k) acc[k] = 0.f;
-        // phase 1: T_j T_i^-1 p, pi(.), nearest pixel, bounds
-        float qx[kPixPerThread], qy[kPixPerThread], qz[kPixPerThread];
-        int pix[kPixPerThread];
+#pragma unroll 1
+        for (int bb = 0; bb < kResBatches; ++bb) {
+            // phase 1: T_j T_i^-1 p, pi(.), nearest pixel, bounds
+            float qx[kResBatch], qy[kResBatch], qz[kResBatch];
+            int pix[kResBatch];
 #pragma unroll
-        for (int k = 0; k < kPixPerThread; ++k) {
-            const int s = k * kThreads + threadIdx.x;
-            const float4 p = sp[s];
-            qx[k] = __fmaf_rn(m2, p.z, __fmaf_rn(m1, p.y, __fmaf_rn(m0, p.x, m3)));
-            qy[k] = __fmaf_rn(m6, p.z, __fmaf_rn(m5, p.y, __fmaf_rn(m4, p.x, m7)));
-            qz[k] = __fmaf_rn(m10, p.z, __fmaf_rn(m9, p.y, __fmaf_rn(m8, p.x, m11)));
-            bool ok = s < nvalid && qz[k] > 0.f;
-            const float rz = __frcp_rn(qz[k]);
-            const float uh = __fadd_rn(__fmaf_rn(__fmul_rn(c.fx, qx[k]), rz, c.cx), 0.5f);
-            const float vh = __fadd_rn(__fmaf_rn(__fmul_rn(c.fy, qy[k]), rz, c.cy), 0.5f);
-            ok = ok && uh >= 0.f && uh < c.Wf && vh >= 0.f && vh < c.Hf;
-            pix[k] = ok ? (((int)floorf(vh)) << 16) | (int)floorf(uh) : -1;
-        }
-        // phase 2: the gathers of all four pixels in flight together
-        float4 t[kPixPerThread];
+            for (int k = 0; k < kResBatch; ++k) {
+                const int s = (bb * kResBatch + k) * kResThreads + threadIdx.x;
+                const float4 p = sp[s];
+                qx[k] = __fmaf_rn(m2, p.z, __fmaf_rn(m1, p.y, __fmaf_rn(m0, p.x, m3)));
+                qy[k] = __fmaf_rn(m6, p.z, __fmaf_rn(m5, p.y, __fmaf_rn(m4, p.x, m7)));
+                qz[k] = __fmaf_rn(m10, p.z, __fmaf_rn(m9, p.y, __fmaf_rn(m8, p.x, m11)));
+                bool ok = s < nvalid && qz[k] > 0.f;
+                const float rz = __frcp_rn(qz[k]);
+                const float uh = __fadd_rn(__fmaf_rn(__fmul_rn(c.fx, qx[k]), rz, c.cx), 0.5f);
+                const float vh = __fadd_rn(__fmaf_rn(__fmul_rn(c.fy, qy[k]), rz, c.cy), 0.5f);
+                ok = ok && uh >= 0.f && uh < c.Wf && vh >= 0.f && vh < c.Hf;
+                pix[k] = ok ? (((int)floorf(vh)) << 16) | (int)floorf(uh) : -1;
+            }
+            // phase 2: the gathers of the batch in flight together
+            float4 t[kResBatch];
 #pragma unroll
-        for (int k = 0; k < kPixPerThread; ++k) {
-            const int iu = pix[k] & 0xffff, iv = pix[k] >> 16;
-            t[k] = pix[k] >= 0 ? __ldg(c.tgt + (size_t)iv * c.W + iu) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        // phase 3: gates, residual, Jacobian, Huber, accumulation
+            for (int k = 0; k < kResBatch; ++k) {
+                const int iu = pix[k] & 0xffff, iv = pix[k] >> 16;
+                t[k] = pix[k] >= 0 ? __ldg(c.tgt + (size_t)iv * c.W + iu) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            // phase 3: gates, residual, Jacobian, Huber, accumulation
 #pragma unroll
-        for (int k = 0; k < kPixPerThread; ++k) {
-            if (!(pix[k] >= 0 && t[k].x > 0.f)) continue;
-            const int iu = pix[k] & 0xffff, iv = pix[k] >> 16;
-            const float tz = t[k].x;
-            const float tx = __fmul_rn(__fmul_rn(__fsub_rn((float)iu, c.cx), tz), c.ifx);
-            const float ty = __fmul_rn(__fmul_rn(__fsub_rn((float)iv, c.cy), tz), c.ify);
-            const float dx = __fsub_rn(tx, qx[k]), dy = __fsub_rn(ty, qy[k]), dz = __fsub_rn(tz, qz[k]);
-            const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-            if (!(d2 <= dmax2)) continue;
-            const float4 n = sn[k * kThreads + threadIdx.x];
-            const float nx = __fmaf_rn(m2, n.z, __fmaf_rn(m1, n.y, __fmul_rn(m0, n.x)));
-            const float ny = __fmaf_rn(m6, n.z, __fmaf_rn(m5, n.y, __fmul_rn(m4, n.x)));
-            const float nz = __fmaf_rn(m10, n.z, __fmaf_rn(m9, n.y, __fmul_rn(m8, n.x)));
-            const float cs = __fmaf_rn(nz, t[k].w, __fmaf_rn(ny, t[k].z, __fmul_rn(nx, t[k].y)));
-            if (!(cs >= cmin)) continue;
-            // accepted: r = n_j . (q - T_j T_i^-1 p), the point-to-plane distance
-            // of Eq. 3 expressed in camera j; J~ = (n_j, q x n_j)
-            const float r = fmaf(nx, dx, fmaf(ny, dy, nz * dz));
-            const float ar = fabsf(r);
-            const bool inl = ar <= hub;
-            acc[27] += inl ? 0.5f * r * r : hub * (ar - 0.5f * hub);
-            acc[28] += 1.f;
-            if constexpr (kFull) {
-                const float w = inl ? 1.f : hub / ar;
-                const float J[6] = {nx, ny, nz, fmaf(ty, nz, -tz * ny), fmaf(tz, nx, -tx * nz),
-                                    fmaf(tx, ny, -ty * nx)};
-                float wJ[6];
-#pragma unroll
-                for (int q = 0; q < 6; ++q) wJ[q] = w * J[q];
-                int idx = 0;
-#pragma unroll
-                for (int u = 0; u < 6; ++u)
-#pragma unroll
-                    for (int v = u; v < 6; ++v) {
-                        acc[idx] = fmaf(wJ[u], J[v], acc[idx]);
-                        ++idx;
-                    }
-#pragma unroll
-                for (int q = 0; q < 6; ++q) acc[21 + q] = fmaf(wJ[q], r, acc[21 + q]);
+            for (int k = 0; k < kResBatch; ++k) {
+                if (!(pix[k] >= 0 && t[k].x > 0.f)) continue;
+                const int iu = pix[k] & 0xffff, iv = pix[k] >> 16;
+                const float tz = t[k].x;
+                const float tx = __fmul_rn(__fmul_rn(__fsub_rn((float)iu, c.cx), tz), c.ifx);
+                const float ty = __fmul_rn(__fmul_rn(__fsub_rn((float)iv, c.cy), tz), c.ify);
+                const float dx = __fsub_rn(tx, qx[k]), dy = __fsub_rn(ty, qy[k]), dz = __fsub_rn(tz, qz[k]);
+                const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+                if (!(d2 <= dmax2)) continue;
+                const float4 n = sn[(bb * kResBatch + k) * kResThreads + threadIdx.x];
+                const float nx = __fmaf_rn(m2, n.z, __fmaf_rn(m1, n.y, __fmul_rn(m0, n.x)));
+                const float ny = __fmaf_rn(m6, n.z, __fmaf_rn(m5, n.y, __fmul_rn(m4, n.x)));
+                const float nz = __fmaf_rn(m10, n.z, __fmaf_rn(m9, n.y, __fmul_rn(m8, n.x)));
+                const float cs = __fmaf_rn(nz, t[k].w, __fmaf_rn(ny, t[k].z, __fmul_rn(nx, t[k].y)));
+                if (!(cs >= cmin)) continue;
+                // accepted: r = n_j . (q - T_j T_i^-1 p), the point-to-plane
+                // distance of Eq. 3 expressed in camera j; J~ = (n_j, q x n_j)
+                const float r = fmaf(nx, dx, fmaf(ny, dy, nz * dz));
+                const float ar = fabsf(r);
+                const bool inl = ar <= hub;
+                const float rho = inl ? 0.5f * r * r : hub * (ar - 0.5f * hub);
+                if constexpr (kFull) {
+                    const float w = inl ? 1.f : __fdividef(hub, ar);
+                    const float J[6] = {nx, ny, nz, fmaf(ty, nz, -tz * ny), fmaf(tz, nx, -tx * nz),
+                                        fmaf(tx, ny, -ty * nx)};
+                    accumulate_pair(acc, J, w, r, rho);
+                } else {
+                    acc[27] += rho;
+                    acc[28] += 1.f;
+                }
             }
         }
-        float* slot = red + ((size_t)jj * (kThreads / 32) + warp) * kDenseVals;
+        float* slot = red + ((size_t)jj * kW + warp) * kDenseVals;
         if constexpr (kFull) {
             slot[lane] = warp_transpose_reduce(acc, lane);
         } else {
@@ -378,12 +410,12 @@ __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
     }
     __syncthreads();
     const int nout = (N - 1) * kDenseVals;
-    for (int o = threadIdx.x; o < nout; o += kThreads) {
+    for (int o = threadIdx.x; o < nout; o += kResThreads) {
         const int jj = o / kDenseVals, v = o % kDenseVals;
         if (!kFull && v != 27 && v != 28) continue;
         float s = 0.f;
 #pragma unroll
-        for (int w = 0; w < kThreads / 32; ++w) s += red[((size_t)jj * (kThreads / 32) + w) * kDenseVals + v];
+        for (int w = 0; w < kW; ++w) s += red[((size_t)jj * kW + w) * kDenseVals + v];
         a.dpart[((size_t)tile * (N - 1) + jj) * kDenseVals + v] = s;
     }
 }
@@ -397,7 +429,7 @@ __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
 template <bool kFull>
 __device__ void sparse_edge(const SolveArgs& a, int e)
 {
-    __shared__ float sred[kThreads / 32][kSparseVals];
+    __shared__ float sred[kResThreads / 32][kSparseVals];
     const EdgeDev E = a.edges[e];
     float Ti[12], Tj[12];
 #pragma unroll
@@ -409,7 +441,7 @@ __device__ void sparse_edge(const SolveArgs& a, int e)
     float acc[kSparseVals];
 #pragma unroll
     for (int k = 0; k < kSparseVals; ++k) acc[k] = 0.f;
-    for (int k = threadIdx.x; k < E.count; k += kThreads) {
+    for (int k = threadIdx.x; k < E.count; k += kResThreads) {
         const float pmx = __ldg(E.pa + 3 * k), pmy = __ldg(E.pa + 3 * k + 1), pmz = __ldg(E.pa + 3 * k + 2);
         const float pnx = __ldg(E.pb + 3 * k), pny = __ldg(E.pb + 3 * k + 1), pnz = __ldg(E.pb + 3 * k + 2);
         const float ax = fmaf(Ti[0], pmx, fmaf(Ti[1], pmy, fmaf(Ti[2], pmz, Ti[3])));
@@ -460,13 +492,13 @@ __device__ void sparse_edge(const SolveArgs& a, int e)
     if (threadIdx.x < kSparseVals && (kFull || threadIdx.x >= 37)) {
         float s = 0.f;
 #pragma unroll
-        for (int w = 0; w < kThreads / 32; ++w) s += sred[w][threadIdx.x];
+        for (int w = 0; w < kResThreads / 32; ++w) s += sred[w][threadIdx.x];
         a.spart[(size_t)e * kSparseVals + threadIdx.x] = s;
     }
 }
 
 template <bool kFull>
-__global__ void __launch_bounds__(kThreads, 2) residual_kernel(SolveArgs a)
+__global__ void __launch_bounds__(kResThreads, 5) residual_kernel(SolveArgs a)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     if ((int)blockIdx.x < a.n_edges)
@@ -488,9 +520,9 @@ cudaError_t launch_residual(const SolveArgs& a, bool full, cudaStream_t s)
     if (grid == 0) return cudaSuccess;
     const size_t smem = residual_smem_bytes(a.N);
     if (full)
-        residual_kernel<true><<<grid, kThreads, smem, s>>>(a);
+        residual_kernel<true><<<grid, kResThreads, smem, s>>>(a);
     else
-        residual_kernel<false><<<grid, kThreads, smem, s>>>(a);
+        residual_kernel<false><<<grid, kResThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
