@@ -97,11 +97,13 @@ _lib = None
 
 
 def load(path: Path | str | None = None):
-    """Load libbt.so (once).  Raises RuntimeError if it is missing."""
+    """Load libbt.so (once): `path`, else $BT_LIB, else the in-tree build.
+    Raises RuntimeError if it is missing."""
     global _lib
     if _lib is not None:
         return _lib
-    p = Path(path) if path else LIB_PATH
+    import os
+    p = Path(path) if path else Path(os.environ.get("BT_LIB") or LIB_PATH)
     if not p.exists():
         raise RuntimeError(f"libbt.so not found at {p}: build it with "
                            "`python -c 'import __graft_entry__ as g; g.build()'`")

@@ -28,7 +28,7 @@ constexpr int kThreads = 256;                 // reduce CTAs, sparse CTAs, prep 
 constexpr int kPixPerThread = 4;              // prep
 constexpr int kResThreads = 128;              // dense residual CTAs
 constexpr int kResBatch = 4;                  // pixels per phased batch
-constexpr int kResBatches = 2;                // batches per thread and target
+constexpr int kResBatches = 1;                // batches per thread and target (A/B: 1 x 4 beats 2 x 4)
 constexpr int kTile = kResThreads * kResBatch * kResBatches;   // source pixels per dense tile
 constexpr int kDenseVals = 32;                // 21 H + 6 g + cost + count + 3 pad
 constexpr int kSparseVals = 40;               // 39 moments + pad
