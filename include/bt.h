@@ -193,6 +193,50 @@ int bt_solve(bt_graph* g, int32_t iters, double* poses_out, bt_solve_report* rep
  * Synchronises the stream.  Errors: BT_ERR_INVALID, BT_ERR_CUDA. */
 int bt_eval_cost(bt_graph* g, double* cost_out, int64_t* dense_inliers);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent pose graphs solved together (not in the paper: the
+ * throughput form of the same optimisation).  Each Gauss-Newton iteration of
+ * the whole batch is three launches -- the residual pass over every graph's
+ * tiles and correspondence sets, the FP64 pair reduction over every graph's
+ * node pairs, and one solve CTA per graph -- and the iterations are captured
+ * once as a CUDA graph and replayed.  The residual pass's CTA shape (threads
+ * x source pixels per thread, i.e. the tile size of the first reduction
+ * stage) is chosen by timing each candidate on the batch itself
+ * (autotuning) unless fixed with bt_batch_set_shape. */
+typedef struct bt_batch bt_batch;
+
+/* Creates an empty batch working on cuda_stream (NULL: the batch creates and
+ * owns a non-blocking stream; the legacy default stream cannot be captured).
+ * Errors: BT_ERR_INVALID, BT_ERR_CUDA, BT_ERR_OOM. */
+int bt_batch_create(void* cuda_stream, bt_batch** out);
+void bt_batch_destroy(bt_batch* b);
+
+/* Adds a graph (not owned: it must outlive the batch and must not be solved
+ * through bt_solve while a batch solve is running).  Its active node set and
+ * stored poses at the time of each bt_batch_solve are what is solved.
+ * Errors: BT_ERR_INVALID (NULL, already added, no or too many active nodes). */
+int bt_batch_add(bt_batch* b, bt_graph* g);
+
+/* Number of graphs, or a negative status. */
+int bt_batch_size(const bt_batch* b);
+
+/* Fixes the residual CTA shape (0..3) or re-enables autotuning (-1, the
+ * default).  Errors: BT_ERR_INVALID. */
+int bt_batch_set_shape(bt_batch* b, int32_t shape);
+
+/* The shape in use and the autotuner's measured time per shape (4 doubles,
+ * microseconds of one full residual pass; 0 where not measured).  Either
+ * pointer may be NULL.  Errors: BT_ERR_INVALID. */
+int bt_batch_tuning(const bt_batch* b, int32_t* shape_out, double* us_per_shape);
+
+/* Solves every graph of the batch from its stored poses with `iters`
+ * Gauss-Newton iterations (the same algorithm as bt_solve) and writes the
+ * results back into the graphs.  reps: NULL or bt_batch_size() reports in the
+ * order graphs were added.  Synchronises the batch stream.
+ * Errors: BT_ERR_INVALID, BT_ERR_SINGULAR (the affected graphs keep their
+ * poses, the others are updated), BT_ERR_CUDA, BT_ERR_OOM. */
+int bt_batch_solve(bt_batch* b, int32_t iters, bt_solve_report* reps);
+
 /* Profiling counters of one graph (the tracing facility; no paper
  * counterpart).  Launch counts are always kept; kernel durations are summed
  * from CUDA events recorded on the graph's stream around each launch of the

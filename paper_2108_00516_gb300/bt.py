@@ -82,6 +82,13 @@ SIGNATURES = {
     "bt_get_poses": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "bt_solve": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(bt_solve_report)]),
     "bt_eval_cost": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "bt_batch_create": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
+    "bt_batch_destroy": (None, [C.c_void_p]),
+    "bt_batch_add": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "bt_batch_size": (C.c_int, [C.c_void_p]),
+    "bt_batch_set_shape": (C.c_int, [C.c_void_p, C.c_int32]),
+    "bt_batch_tuning": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
+    "bt_batch_solve": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(bt_solve_report)]),
     "bt_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "bt_profile_read": (C.c_int, [C.c_void_p, C.POINTER(bt_profile)]),
     "bt_pair_dense_energy_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(bt_intrinsics),
@@ -279,6 +286,56 @@ class PoseGraph:
         n = C.c_int64()
         _check(load().bt_eval_cost(self._h, c, C.byref(n)), "bt_eval_cost")
         return dict(total=c[0], dense=c[1], sparse=c[2], dense_inliers=n.value)
+
+
+def _report_dict(rep, st):
+    return dict(status=st, iters_run=rep.iters_run, cost_init=rep.cost_init, cost_final=rep.cost_final,
+                dense_cost_final=rep.dense_cost_final, sparse_cost_final=rep.sparse_cost_final,
+                cost_per_iter=np.array(rep.cost_per_iter[:rep.iters_run]),
+                dense_inliers=rep.dense_inliers, dense_pixel_pairs=rep.dense_pixel_pairs)
+
+
+class Batch:
+    """bt_batch: solves many PoseGraphs together (CUDA-graph replay of the
+    Gauss-Newton loop, autotuned residual CTA shape)."""
+
+    def __init__(self, stream=None):
+        self._h = C.c_void_p()
+        self.graphs = []
+        _check(load().bt_batch_create(_stream_handle(stream), C.byref(self._h)), "bt_batch_create")
+
+    def add(self, graph: "PoseGraph"):
+        _check(load().bt_batch_add(self._h, graph._h), "bt_batch_add")
+        self.graphs.append(graph)
+
+    def set_shape(self, shape: int):
+        _check(load().bt_batch_set_shape(self._h, int(shape)), "bt_batch_set_shape")
+
+    def tuning(self):
+        sh = C.c_int32()
+        us = (C.c_double * 4)()
+        _check(load().bt_batch_tuning(self._h, C.byref(sh), us), "bt_batch_tuning")
+        return sh.value, list(us)
+
+    def solve(self, iters: int, raise_on_error: bool = True):
+        """Returns a list of report dicts (poses are written into the graphs)."""
+        n = len(self.graphs)
+        reps = (bt_solve_report * max(1, n))()
+        st = load().bt_batch_solve(self._h, int(iters), reps)
+        if raise_on_error:
+            _check(st, "bt_batch_solve")
+        return [_report_dict(reps[k], reps[k].status) for k in range(n)]
+
+    def close(self):
+        if self._h:
+            load().bt_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def pair_dense_energy_noalloc(depth_a, normals_a, mask_a, intr_a, pose_a, depth_b, normals_b, mask_b, intr_b,

@@ -112,6 +112,8 @@ struct bt_graph {
     bt::SolveArgs args{};
     int64_t pixels_per_pass = 0;
     int64_t sparse_per_pass = 0;
+    int built_tile = 0;     // tile size the current tables were built for
+    std::vector<double> pose_stage;   // host staging of poses for batched uploads
 
     // profiling
     bt_profile prof{};
@@ -210,7 +212,7 @@ int put_matches(bt_graph* g, int fa, int fb, int count, const float* pa, const f
 
 // Rebuilds the node / tile / edge tables of the active set and sizes the
 // per-solve buffers.
-int build_topology(bt_graph* g)
+int build_topology(bt_graph* g, int tile)
 {
     const int N = (int)g->active.size();
     if (N < 1) return fail(BT_ERR_INVALID, "solve: no active nodes");
@@ -235,7 +237,7 @@ int build_topology(bt_graph* g)
         d.ifx = 1.0f / f.K.fx;
         d.ify = 1.0f / f.K.fy;
         d.tile0 = (int)tile_node.size();
-        d.ntiles = (f.M + bt::kTile - 1) / bt::kTile;
+        d.ntiles = (f.M + tile - 1) / tile;
         for (int t = 0; t < d.ntiles; ++t) tile_node.push_back(k);
         d.free_idx = f.fixed ? -1 : nfree++;
         px += (int64_t)f.M * (N - 1);
@@ -300,6 +302,7 @@ int build_topology(bt_graph* g)
     a.n_edges = E;
     a.n_free = nfree;
     a.n_upairs = U;
+    a.tile = tile;
     a.stage_blocks = bt::reduce_stage_fits(nfree, N) ? 1 : 0;
     const bt_config& c = g->cfg;
     a.dmax2 = (float)(c.dense_max_dist * c.dense_max_dist);
@@ -328,6 +331,7 @@ int build_topology(bt_graph* g)
     // the tables above were copied from host vectors that go out of scope
     BT_CUDA(cudaStreamSynchronize(s), "sync after table upload");
     g->topo_dirty = false;
+    g->built_tile = tile;
     return BT_OK;
 }
 
@@ -617,8 +621,8 @@ int bt_solve(bt_graph* g, int32_t iters, double* poses_out, bt_solve_report* rep
     if (!g) return fail(BT_ERR_INVALID, "bt_solve: NULL graph");
     if (iters < 0 || iters > BT_MAX_REPORT_ITERS) return fail(BT_ERR_INVALID, "bt_solve: iters out of range");
     if (g->active.empty()) return fail(BT_ERR_INVALID, "bt_solve: no active nodes");
-    if (g->topo_dirty) {
-        int st = build_topology(g);
+    if (g->topo_dirty || g->built_tile != bt::shape_tile(0)) {
+        int st = build_topology(g, bt::shape_tile(0));
         if (st != BT_OK) return st;
     }
     std::vector<double> staging;
@@ -666,8 +670,8 @@ int bt_eval_cost(bt_graph* g, double* cost_out, int64_t* dense_inliers)
     g_err.clear();
     if (!g || !cost_out) return fail(BT_ERR_INVALID, "bt_eval_cost: NULL argument");
     if (g->active.empty()) return fail(BT_ERR_INVALID, "bt_eval_cost: no active nodes");
-    if (g->topo_dirty) {
-        int st = build_topology(g);
+    if (g->topo_dirty || g->built_tile != bt::shape_tile(0)) {
+        int st = build_topology(g, bt::shape_tile(0));
         if (st != BT_OK) return st;
     }
     std::vector<double> staging;
@@ -718,5 +722,313 @@ const char* bt_status_str(int status)
 }
 
 const char* bt_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched solver
+// ---------------------------------------------------------------------------
+
+struct bt_batch {
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<bt_graph*> graphs;
+    int shape = -1;          // fixed CTA shape, or -1 = autotune
+    int tuned_shape = -1;    // autotuner's choice for the current graph set
+    bool dirty = true;       // graph set / topology changed since the last build
+    DevBuf d_args, d_work_res, d_work_pair;
+    int n_work_res = 0, n_work_pair = 0, max_N = 1;
+    size_t solve_smem = 0;
+    int64_t pixels_per_pass = 0;
+    cudaGraphExec_t exec = nullptr;
+    int exec_iters = -1, exec_shape = -1;
+    std::vector<double> tune_us;   // autotuner timings per shape (microseconds)
+
+    ~bt_batch()
+    {
+        if (stream) cudaStreamSynchronize(stream);
+        if (exec) cudaGraphExecDestroy(exec);
+        d_args.release();
+        d_work_res.release();
+        d_work_pair.release();
+        if (own_stream && stream) cudaStreamDestroy(stream);
+    }
+};
+
+namespace {
+
+// (Re)builds every graph's tables for `shape` and the batch's work lists.
+int batch_build(bt_batch* b, int shape)
+{
+    const int tile = bt::shape_tile(shape);
+    std::vector<bt::SolveArgs> args;
+    std::vector<int2> wres, wpair;
+    b->max_N = 1;
+    b->solve_smem = 0;
+    b->pixels_per_pass = 0;
+    for (size_t k = 0; k < b->graphs.size(); ++k) {
+        bt_graph* g = b->graphs[k];
+        if (g->topo_dirty || g->built_tile != tile) {
+            int st = build_topology(g, tile);
+            if (st != BT_OK) return st;
+        }
+        const bt::SolveArgs& a = g->args;
+        args.push_back(a);
+        for (int e = 0; e < a.n_edges; ++e) wres.push_back(make_int2((int)k, e));
+        for (int t = 0; t < a.n_tiles; ++t) wres.push_back(make_int2((int)k, a.n_edges + t));
+        for (int u = 0; u < a.n_upairs; ++u) wpair.push_back(make_int2((int)k, u));
+        b->max_N = std::max(b->max_N, a.N);
+        b->solve_smem = std::max(b->solve_smem, bt::reduce_smem_bytes(a.n_free, a.N));
+        b->pixels_per_pass += g->pixels_per_pass;
+    }
+    cudaStream_t s = b->stream;
+    BT_CUDA(b->d_args.ensure(sizeof(bt::SolveArgs) * std::max<size_t>(args.size(), 1)), "alloc batch args");
+    BT_CUDA(b->d_work_res.ensure(sizeof(int2) * std::max<size_t>(wres.size(), 1)), "alloc batch work");
+    BT_CUDA(b->d_work_pair.ensure(sizeof(int2) * std::max<size_t>(wpair.size(), 1)), "alloc batch work");
+    if (!args.empty())
+        BT_CUDA(cudaMemcpyAsync(b->d_args.p, args.data(), sizeof(bt::SolveArgs) * args.size(), cudaMemcpyHostToDevice, s),
+                "upload batch args");
+    if (!wres.empty())
+        BT_CUDA(cudaMemcpyAsync(b->d_work_res.p, wres.data(), sizeof(int2) * wres.size(), cudaMemcpyHostToDevice, s),
+                "upload batch work");
+    if (!wpair.empty())
+        BT_CUDA(cudaMemcpyAsync(b->d_work_pair.p, wpair.data(), sizeof(int2) * wpair.size(), cudaMemcpyHostToDevice, s),
+                "upload batch work");
+    BT_CUDA(cudaStreamSynchronize(s), "sync after batch upload");
+    b->n_work_res = (int)wres.size();
+    b->n_work_pair = (int)wpair.size();
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    b->exec_shape = shape;
+    return BT_OK;
+}
+
+// Uploads the stored poses of every graph and clears its control words.
+int batch_upload_state(bt_batch* b)
+{
+    for (bt_graph* g : b->graphs) {
+        const int N = (int)g->active.size();
+        std::vector<double>& st = g->pose_stage;
+        st.resize(12 * (size_t)N);
+        for (int k = 0; k < N; ++k) std::memcpy(&st[12 * (size_t)k], g->frames.at(g->active[k]).pose, sizeof(double) * 12);
+        BT_CUDA(cudaMemcpyAsync(g->d_pose.p, st.data(), sizeof(double) * 12 * N, cudaMemcpyHostToDevice, b->stream),
+                "upload batch poses");
+        BT_CUDA(cudaMemsetAsync(g->d_ctrl.p, 0, sizeof(bt::Control), b->stream), "reset control");
+    }
+    return BT_OK;
+}
+
+// Enqueues the whole solve (xforms, iters full passes, one cost pass).
+int batch_enqueue(bt_batch* b, int iters, int shape)
+{
+    const bt::SolveArgs* A = b->d_args.as<bt::SolveArgs>();
+    const int G = (int)b->graphs.size();
+    cudaStream_t s = b->stream;
+    BT_CUDA(bt::launch_batch_xforms(A, G, s), "batch xforms");
+    for (int p = 0; p <= iters; ++p) {
+        const bool full = p < iters;
+        BT_CUDA(bt::launch_batch_residual(A, b->d_work_res.as<int2>(), b->n_work_res, b->max_N, full, shape, s),
+                "batch residual");
+        BT_CUDA(bt::launch_batch_pairs(A, b->d_work_pair.as<int2>(), b->n_work_pair, full, s), "batch pairs");
+        BT_CUDA(bt::launch_batch_solve(A, G, b->solve_smem, full, p, s), "batch solve");
+    }
+    return BT_OK;
+}
+
+// Times one full residual pass per CTA shape and keeps the fastest.
+int batch_autotune(bt_batch* b)
+{
+    cudaEvent_t e0, e1;
+    BT_CUDA(cudaEventCreate(&e0), "event");
+    BT_CUDA(cudaEventCreate(&e1), "event");
+    b->tune_us.assign(bt::kNumShapes, 0.0);
+    int best = 0;
+    double best_us = 1e300;
+    for (int sh = 0; sh < bt::kNumShapes; ++sh) {
+        int st = batch_build(b, sh);
+        if (st == BT_OK) st = batch_upload_state(b);
+        if (st != BT_OK) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return st;
+        }
+        const bt::SolveArgs* A = b->d_args.as<bt::SolveArgs>();
+        BT_CUDA(bt::launch_batch_xforms(A, (int)b->graphs.size(), b->stream), "batch xforms");
+        float ms = 0.f, tot = 0.f;
+        for (int rep = 0; rep < 3; ++rep) {
+            BT_CUDA(cudaEventRecord(e0, b->stream), "event");
+            BT_CUDA(bt::launch_batch_residual(A, b->d_work_res.as<int2>(), b->n_work_res, b->max_N, true, sh, b->stream),
+                    "batch residual");
+            BT_CUDA(cudaEventRecord(e1, b->stream), "event");
+            BT_CUDA(cudaEventSynchronize(e1), "event sync");
+            BT_CUDA(cudaEventElapsedTime(&ms, e0, e1), "event time");
+            if (rep > 0) tot += ms;
+        }
+        const double us = 1e3 * tot / 2.0;
+        b->tune_us[sh] = us;
+        if (us < best_us) {
+            best_us = us;
+            best = sh;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->tuned_shape = best;
+    return BT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bt_batch_create(void* cuda_stream, bt_batch** out)
+{
+    g_err.clear();
+    if (!out) return fail(BT_ERR_INVALID, "bt_batch_create: out is NULL");
+    *out = nullptr;
+    bt_batch* b = new (std::nothrow) bt_batch();
+    if (!b) return fail(BT_ERR_OOM, "bt_batch_create: host allocation failed");
+    if (cuda_stream) {
+        b->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete b;
+            return cuda_fail(e, "bt_batch_create: stream");
+        }
+        b->own_stream = true;
+    }
+    *out = b;
+    return BT_OK;
+}
+
+void bt_batch_destroy(bt_batch* b) { delete b; }
+
+int bt_batch_add(bt_batch* b, bt_graph* g)
+{
+    g_err.clear();
+    if (!b || !g) return fail(BT_ERR_INVALID, "bt_batch_add: NULL argument");
+    if (g->active.empty() || (int)g->active.size() > BT_MAX_NODES)
+        return fail(BT_ERR_INVALID, "bt_batch_add: graph needs 1..BT_MAX_NODES active nodes");
+    for (bt_graph* h : b->graphs)
+        if (h == g) return fail(BT_ERR_INVALID, "bt_batch_add: graph already in the batch");
+    b->graphs.push_back(g);
+    b->dirty = true;
+    b->tuned_shape = -1;
+    return BT_OK;
+}
+
+int bt_batch_size(const bt_batch* b)
+{
+    if (!b) return fail(BT_ERR_INVALID, "bt_batch_size: NULL batch");
+    return (int)b->graphs.size();
+}
+
+int bt_batch_set_shape(bt_batch* b, int32_t shape)
+{
+    if (!b) return fail(BT_ERR_INVALID, "bt_batch_set_shape: NULL batch");
+    if (shape < -1 || shape >= bt::kNumShapes) return fail(BT_ERR_INVALID, "bt_batch_set_shape: unknown shape");
+    b->shape = shape;
+    b->dirty = true;
+    return BT_OK;
+}
+
+int bt_batch_tuning(const bt_batch* b, int32_t* shape_out, double* us_per_shape)
+{
+    if (!b) return fail(BT_ERR_INVALID, "bt_batch_tuning: NULL batch");
+    if (shape_out) *shape_out = b->shape >= 0 ? b->shape : b->tuned_shape;
+    if (us_per_shape)
+        for (int k = 0; k < bt::kNumShapes; ++k)
+            us_per_shape[k] = k < (int)b->tune_us.size() ? b->tune_us[k] : 0.0;
+    return BT_OK;
+}
+
+int bt_batch_solve(bt_batch* b, int32_t iters, bt_solve_report* reps)
+{
+    g_err.clear();
+    if (!b) return fail(BT_ERR_INVALID, "bt_batch_solve: NULL batch");
+    if (iters < 0 || iters > BT_MAX_REPORT_ITERS) return fail(BT_ERR_INVALID, "bt_batch_solve: iters out of range");
+    if (b->graphs.empty()) return fail(BT_ERR_INVALID, "bt_batch_solve: empty batch");
+    bt::prepare_launch_attributes();
+    bool topo_changed = b->dirty;
+    for (bt_graph* g : b->graphs) topo_changed |= g->topo_dirty;
+    if (topo_changed) {
+        b->dirty = false;
+        if (b->shape < 0) {
+            int st = batch_autotune(b);
+            if (st != BT_OK) return st;
+        }
+    }
+    const int shape = b->shape >= 0 ? b->shape : (b->tuned_shape >= 0 ? b->tuned_shape : 0);
+    if (topo_changed || b->exec_shape != shape) {
+        int st = batch_build(b, shape);
+        if (st != BT_OK) return st;
+    }
+    int st = batch_upload_state(b);
+    if (st != BT_OK) return st;
+    cudaStream_t s = b->stream;
+    if (!b->exec || b->exec_iters != iters) {
+        if (b->exec) {
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+        cudaGraph_t graph;
+        BT_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
+        st = batch_enqueue(b, iters, shape);
+        cudaError_t e = cudaStreamEndCapture(s, &graph);
+        if (st != BT_OK) return st;
+        if (e != cudaSuccess) return cuda_fail(e, "end capture");
+        e = cudaGraphInstantiate(&b->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+        b->exec_iters = iters;
+    }
+    BT_CUDA(cudaGraphLaunch(b->exec, s), "graph launch");
+    const size_t G = b->graphs.size();
+    std::vector<std::vector<double>> poses(G), costs(G);
+    std::vector<bt::Control> ctrl(G);
+    for (size_t k = 0; k < G; ++k) {
+        bt_graph* g = b->graphs[k];
+        const int N = g->args.N;
+        poses[k].resize(12 * (size_t)N);
+        costs[k].resize(4 * (size_t)(iters + 1));
+        BT_CUDA(cudaMemcpyAsync(poses[k].data(), g->args.pose, sizeof(double) * 12 * N, cudaMemcpyDeviceToHost, s),
+                "read poses");
+        BT_CUDA(cudaMemcpyAsync(costs[k].data(), g->args.costs, sizeof(double) * 4 * (iters + 1),
+                                cudaMemcpyDeviceToHost, s),
+                "read costs");
+        BT_CUDA(cudaMemcpyAsync(&ctrl[k], g->args.ctrl, sizeof(bt::Control), cudaMemcpyDeviceToHost, s), "read status");
+    }
+    BT_CUDA(cudaStreamSynchronize(s), "bt_batch_solve: synchronize");
+    int worst = BT_OK;
+    for (size_t k = 0; k < G; ++k) {
+        bt_graph* g = b->graphs[k];
+        const int status = ctrl[k].status == -4 ? BT_ERR_SINGULAR : BT_OK;
+        if (reps) {
+            bt_solve_report* rep = &reps[k];
+            std::memset(rep, 0, sizeof(*rep));
+            const std::vector<double>& c = costs[k];
+            rep->iters_run = iters;
+            rep->status = status;
+            rep->cost_init = iters > 0 ? c[0] : c[4 * iters];
+            rep->cost_final = c[4 * iters + 0];
+            rep->dense_cost_final = c[4 * iters + 1];
+            rep->sparse_cost_final = c[4 * iters + 2];
+            rep->dense_inliers = (int64_t)std::llround(c[4 * iters + 3]);
+            for (int q = 0; q < iters; ++q) rep->cost_per_iter[q] = c[4 * q];
+            rep->dense_pixel_pairs = g->pixels_per_pass * iters;
+        }
+        if (status != BT_OK) {
+            worst = status;
+            continue;
+        }
+        for (int q = 0; q < g->args.N; ++q)
+            std::memcpy(g->frames.at(g->active[q]).pose, &poses[k][12 * (size_t)q], sizeof(double) * 12);
+    }
+    if (worst != BT_OK) return fail(worst, "bt_batch_solve: some graphs were singular; their poses are unchanged");
+    return BT_OK;
+}
 
 }  // extern "C"

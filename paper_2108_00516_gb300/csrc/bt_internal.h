@@ -26,10 +26,14 @@ namespace bt {
 
 constexpr int kThreads = 256;                 // reduce CTAs, sparse CTAs, prep CTAs
 constexpr int kPixPerThread = 4;              // prep
-constexpr int kResThreads = 128;              // dense residual CTAs
-constexpr int kResBatch = 4;                  // pixels per phased batch
-constexpr int kResBatches = 1;                // batches per thread and target (A/B: 1 x 4 beats 2 x 4)
-constexpr int kTile = kResThreads * kResBatch * kResBatches;   // source pixels per dense tile
+// Dense residual CTA shapes (threads x source pixels per thread); the tile of
+// a CTA is their product.  Shape 0 is the default of the single-graph path;
+// the batched solver's autotuner picks among all of them.
+constexpr int kNumShapes = 4;
+constexpr int kShapeThreads[kNumShapes] = {128, 128, 256, 64};
+constexpr int kShapePix[kNumShapes] = {4, 2, 4, 4};
+constexpr int kResThreads = 128;              // sparse CTAs of the residual launch
+constexpr int kMaxTile = 1024;
 constexpr int kDenseVals = 32;                // 21 H + 6 g + cost + count + 3 pad
 constexpr int kSparseVals = 40;               // 39 moments + pad
 // per unordered pair {a < b}: [0..20] D_a (upper 6x6), [21..41] D_b, [42..77]
@@ -71,6 +75,7 @@ constexpr size_t kReduceSmemMax = 200 * 1024;
 
 struct SolveArgs {
     int N, n_tiles, n_pairs, n_edges, n_free, n_upairs;
+    int tile;               // source pixels per dense tile (CTA shape product)
     int stage_blocks;       // 1: the last CTA copies the pair blocks to shared memory
     float dmax2, cmin, huber_dense, huber_sparse;
     double lambda_dense, lambda_sparse;
@@ -102,11 +107,26 @@ cudaError_t launch_xforms(const SolveArgs& a, cudaStream_t s);
 // One residual pass (dense tiles + sparse edges) and one reduce/solve pass.
 // full = true: Gauss-Newton iteration `iter` (records E before the update);
 // full = false: cost only, recorded at slot `iter`.
-cudaError_t launch_residual(const SolveArgs& a, bool full, cudaStream_t s);
+cudaError_t launch_residual(const SolveArgs& a, bool full, cudaStream_t s, int shape = 0);
 cudaError_t launch_reduce(const SolveArgs& a, bool full, int iter, cudaStream_t s);
 
 size_t reduce_smem_bytes(int n_free, int N);
 bool reduce_stage_fits(int n_free, int N);
-size_t residual_smem_bytes(int N);
+size_t residual_smem_bytes(int N, int shape);
+inline int shape_tile(int shape) { return kShapeThreads[shape] * kShapePix[shape]; }
+
+// Batched solver: one launch each per Gauss-Newton iteration over every graph.
+//   work_res: (graph, item) per residual CTA, item < n_edges = correspondence
+//             set, else dense tile item - n_edges
+//   work_pair: (graph, unordered pair) per pair-reduction CTA
+cudaError_t launch_batch_xforms(const SolveArgs* args_dev, int n_graphs, cudaStream_t s);
+cudaError_t launch_batch_residual(const SolveArgs* args_dev, const int2* work_res, int n_work, int max_N,
+                                  bool full, int shape, cudaStream_t s);
+cudaError_t launch_batch_pairs(const SolveArgs* args_dev, const int2* work_pair, int n_work, bool full,
+                               cudaStream_t s);
+cudaError_t launch_batch_solve(const SolveArgs* args_dev, int n_graphs, size_t smem, bool full, int iter,
+                               cudaStream_t s);
+// Sets every kernel's shared-memory attribute (call before a stream capture).
+void prepare_launch_attributes();
 
 }  // namespace bt

@@ -240,11 +240,11 @@ __device__ __forceinline__ float warp_transpose_reduce(float (&v)[kDenseVals], i
     return v[0];
 }
 
-size_t residual_smem_bytes(int N)
+size_t residual_smem_bytes(int N, int shape)
 {
     const int nt = N > 1 ? N - 1 : 1;
-    return 2 * sizeof(float4) * kTile + sizeof(PairConst) * kMaxNodes +
-           sizeof(float) * (size_t)nt * (kResThreads / 32) * kDenseVals;
+    return 2 * sizeof(float4) * shape_tile(shape) + sizeof(PairConst) * kMaxNodes +
+           sizeof(float) * (size_t)nt * (kShapeThreads[shape] / 32) * kDenseVals;
 }
 
 // Packed single-precision FMA on two lanes of a 64-bit register pair:
@@ -288,15 +288,19 @@ __device__ __forceinline__ void accumulate_pair(float (&acc)[kDenseVals], const 
 }
 
 // One tile of source pixels of node i against every other node j.  Per target
-// each thread takes its eight pixels in two batches of four; a batch goes
-// through three phases -- projection and bounds, the four target gathers (all
+// each thread takes its kB pixels as one batch that goes through three
+// phases -- projection and bounds, the four target gathers (all
 // in flight together), then gates, residual, Jacobian and accumulation.  The
 // warp's 32 sums are parked in shared memory; one barrier at the end, then
 // the (N-1) x 32 block sums are written to dpart[tile][j'].
-template <bool kFull>
+template <bool kFull, int kT, int kB>
 __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
 {
-    constexpr int kW = kResThreads / 32;
+    constexpr int kW = kT / 32;
+    constexpr int kTile = kT * kB;
+    constexpr int kResThreads = kT;
+    constexpr int kResBatch = kB;
+    constexpr int kResBatches = 1;
     const int N = a.N;
     const int i = a.tile_node[tile];
     const NodeDev Ni = a.nodes[i];
@@ -429,7 +433,7 @@ __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
 template <bool kFull>
 __device__ void sparse_edge(const SolveArgs& a, int e)
 {
-    __shared__ float sred[kResThreads / 32][kSparseVals];
+    __shared__ float sred[kThreads / 32][kSparseVals];
     const EdgeDev E = a.edges[e];
     float Ti[12], Tj[12];
 #pragma unroll
@@ -441,7 +445,7 @@ __device__ void sparse_edge(const SolveArgs& a, int e)
     float acc[kSparseVals];
 #pragma unroll
     for (int k = 0; k < kSparseVals; ++k) acc[k] = 0.f;
-    for (int k = threadIdx.x; k < E.count; k += kResThreads) {
+    for (int k = threadIdx.x; k < E.count; k += blockDim.x) {
         const float pmx = __ldg(E.pa + 3 * k), pmy = __ldg(E.pa + 3 * k + 1), pmz = __ldg(E.pa + 3 * k + 2);
         const float pnx = __ldg(E.pb + 3 * k), pny = __ldg(E.pb + 3 * k + 1), pnz = __ldg(E.pb + 3 * k + 2);
         const float ax = fmaf(Ti[0], pmx, fmaf(Ti[1], pmy, fmaf(Ti[2], pmz, Ti[3])));
@@ -492,37 +496,107 @@ __device__ void sparse_edge(const SolveArgs& a, int e)
     if (threadIdx.x < kSparseVals && (kFull || threadIdx.x >= 37)) {
         float s = 0.f;
 #pragma unroll
-        for (int w = 0; w < kResThreads / 32; ++w) s += sred[w][threadIdx.x];
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sred[w][threadIdx.x];
         a.spart[(size_t)e * kSparseVals + threadIdx.x] = s;
     }
 }
 
-template <bool kFull>
-__global__ void __launch_bounds__(kResThreads, 5) residual_kernel(SolveArgs a)
+template <bool kFull, int kT, int kB>
+__global__ void __launch_bounds__(kT, 640 / kT) residual_kernel(SolveArgs a)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     if ((int)blockIdx.x < a.n_edges)
         sparse_edge<kFull>(a, blockIdx.x);
     else
-        dense_tile<kFull>(a, blockIdx.x - a.n_edges, dsm);
+        dense_tile<kFull, kT, kB>(a, blockIdx.x - a.n_edges, dsm);
 }
 
-cudaError_t launch_residual(const SolveArgs& a, bool full, cudaStream_t s)
+// Batched residual pass: CTA b takes work item work[b] = (graph, item).
+template <bool kFull, int kT, int kB>
+__global__ void __launch_bounds__(kT, 640 / kT) batch_residual_kernel(const SolveArgs* __restrict__ args,
+                                                                       const int2* __restrict__ work)
 {
-    static bool attr_set = false;
-    if (!attr_set) {
-        const int mx = (int)residual_smem_bytes(kMaxNodes);
-        cudaFuncSetAttribute(residual_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        cudaFuncSetAttribute(residual_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        attr_set = true;
-    }
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ SolveArgs sa;
+    const int2 w = work[blockIdx.x];
+    if (threadIdx.x == 0) sa = args[w.x];
+    __syncthreads();
+    if (w.y < sa.n_edges)
+        sparse_edge<kFull>(sa, w.y);
+    else
+        dense_tile<kFull, kT, kB>(sa, w.y - sa.n_edges, dsm);
+}
+
+template <int S>
+static void set_residual_attrs()
+{
+    constexpr int kT = kShapeThreads[S], kB = kShapePix[S];
+    const int mx = (int)residual_smem_bytes(kMaxNodes, S);
+    cudaFuncSetAttribute(residual_kernel<true, kT, kB>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(residual_kernel<false, kT, kB>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(batch_residual_kernel<true, kT, kB>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(batch_residual_kernel<false, kT, kB>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+}
+
+static void ensure_residual_attrs()
+{
+    static bool done = false;
+    if (done) return;
+    set_residual_attrs<0>();
+    set_residual_attrs<1>();
+    set_residual_attrs<2>();
+    set_residual_attrs<3>();
+    done = true;
+}
+
+template <int S>
+static void launch_residual_shape(const SolveArgs& a, bool full, int grid, size_t smem, cudaStream_t s)
+{
+    constexpr int kT = kShapeThreads[S], kB = kShapePix[S];
+    if (full)
+        residual_kernel<true, kT, kB><<<grid, kT, smem, s>>>(a);
+    else
+        residual_kernel<false, kT, kB><<<grid, kT, smem, s>>>(a);
+}
+
+cudaError_t launch_residual(const SolveArgs& a, bool full, cudaStream_t s, int shape)
+{
+    ensure_residual_attrs();
     const int grid = a.n_edges + a.n_tiles;
     if (grid == 0) return cudaSuccess;
-    const size_t smem = residual_smem_bytes(a.N);
+    const size_t smem = residual_smem_bytes(a.N, shape);
+    switch (shape) {
+    case 1: launch_residual_shape<1>(a, full, grid, smem, s); break;
+    case 2: launch_residual_shape<2>(a, full, grid, smem, s); break;
+    case 3: launch_residual_shape<3>(a, full, grid, smem, s); break;
+    default: launch_residual_shape<0>(a, full, grid, smem, s); break;
+    }
+    return cudaGetLastError();
+}
+
+template <int S>
+static void launch_batch_residual_shape(const SolveArgs* args, const int2* work, int n, size_t smem, bool full,
+                                        cudaStream_t s)
+{
+    constexpr int kT = kShapeThreads[S], kB = kShapePix[S];
     if (full)
-        residual_kernel<true><<<grid, kResThreads, smem, s>>>(a);
+        batch_residual_kernel<true, kT, kB><<<n, kT, smem, s>>>(args, work);
     else
-        residual_kernel<false><<<grid, kResThreads, smem, s>>>(a);
+        batch_residual_kernel<false, kT, kB><<<n, kT, smem, s>>>(args, work);
+}
+
+cudaError_t launch_batch_residual(const SolveArgs* args_dev, const int2* work_res, int n_work, int max_N, bool full,
+                                  int shape, cudaStream_t s)
+{
+    ensure_residual_attrs();
+    if (n_work == 0) return cudaSuccess;
+    const size_t smem = residual_smem_bytes(max_N, shape);
+    switch (shape) {
+    case 1: launch_batch_residual_shape<1>(args_dev, work_res, n_work, smem, full, s); break;
+    case 2: launch_batch_residual_shape<2>(args_dev, work_res, n_work, smem, full, s); break;
+    case 3: launch_batch_residual_shape<3>(args_dev, work_res, n_work, smem, full, s); break;
+    default: launch_batch_residual_shape<0>(args_dev, work_res, n_work, smem, full, s); break;
+    }
     return cudaGetLastError();
 }
 
@@ -1093,6 +1167,85 @@ cudaError_t launch_reduce(const SolveArgs& a, bool full, int iter, cudaStream_t 
     else
         reduce_kernel<false><<<grid, kThreads, smem, s>>>(a, iter);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Batched solver kernels (one CTA per graph or per (graph, pair))
+// ---------------------------------------------------------------------------
+
+__global__ void batch_xform_kernel(const SolveArgs* __restrict__ args)
+{
+    __shared__ double tinv[12 * kMaxNodes];
+    __shared__ SolveArgs sa;
+    if (threadIdx.x == 0) sa = args[blockIdx.x];
+    __syncthreads();
+    write_xforms(sa, tinv, sa.pose);
+}
+
+template <bool kFull>
+__global__ void __launch_bounds__(kThreads) batch_pair_kernel(const SolveArgs* __restrict__ args,
+                                                              const int2* __restrict__ work)
+{
+    __shared__ double sm[640];
+    __shared__ SolveArgs sa;
+    const int2 w = work[blockIdx.x];
+    if (threadIdx.x == 0) sa = args[w.x];
+    __syncthreads();
+    reduce_upair<kFull>(sa, w.y, sm);
+}
+
+template <bool kFull>
+__global__ void __launch_bounds__(kThreads) batch_solve_kernel(const SolveArgs* __restrict__ args, int iter)
+{
+    extern __shared__ double smd[];
+    __shared__ SolveArgs sa;
+    if (threadIdx.x == 0) sa = args[blockIdx.x];
+    __syncthreads();
+    final_phase<kFull>(sa, iter, smd);
+}
+
+cudaError_t launch_batch_xforms(const SolveArgs* args_dev, int n_graphs, cudaStream_t s)
+{
+    if (n_graphs == 0) return cudaSuccess;
+    batch_xform_kernel<<<n_graphs, kThreads, 0, s>>>(args_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_pairs(const SolveArgs* args_dev, const int2* work_pair, int n_work, bool full,
+                               cudaStream_t s)
+{
+    if (n_work == 0) return cudaSuccess;
+    if (full)
+        batch_pair_kernel<true><<<n_work, kThreads, 0, s>>>(args_dev, work_pair);
+    else
+        batch_pair_kernel<false><<<n_work, kThreads, 0, s>>>(args_dev, work_pair);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_solve(const SolveArgs* args_dev, int n_graphs, size_t smem, bool full, int iter,
+                               cudaStream_t s)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(batch_solve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReduceSmemMax);
+        cudaFuncSetAttribute(batch_solve_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReduceSmemMax);
+        attr_set = true;
+    }
+    if (n_graphs == 0) return cudaSuccess;
+    if (full)
+        batch_solve_kernel<true><<<n_graphs, kThreads, smem, s>>>(args_dev, iter);
+    else
+        batch_solve_kernel<false><<<n_graphs, kThreads, smem, s>>>(args_dev, iter);
+    return cudaGetLastError();
+}
+
+void prepare_launch_attributes()
+{
+    ensure_residual_attrs();
+    cudaFuncSetAttribute(batch_solve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReduceSmemMax);
+    cudaFuncSetAttribute(batch_solve_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReduceSmemMax);
+    cudaFuncSetAttribute(reduce_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReduceSmemMax);
+    cudaFuncSetAttribute(reduce_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReduceSmemMax);
 }
 
 }  // namespace bt

@@ -492,3 +492,46 @@ def paper_graph(graph_id: int = 0, n_frames: int = 10, **kw) -> SynthGraph:
                 coverage_target=float(rng.uniform(0.15, 0.30)))
     args.update(kw)
     return random_graph(2000 + graph_id, **args)
+
+
+def batched_graph(graph_id: int, strip: bool = True) -> SynthGraph:
+    """One graph of the batched workload (seed 4000 + graph_id): N uniform in
+    3..20 views, all 320x240 (fx=fy=300) or all 640x480 (fx=fy=600) with equal
+    probability, mask coverage U[5, 40] % at the first view, U{100..800}
+    correspondences per pair with U[10, 30] % outliers, init 5 deg / 1 cm.
+    strip drops the renderer-only arrays (clean depth, analytic normals)."""
+    rng = _rng(4000, 99, graph_id)
+    n = int(rng.integers(3, 21))
+    cam = VGA_CAMERA if rng.random() < 0.5 else QVGA_CAMERA
+    cov = float(rng.uniform(0.05, 0.40))
+    n_m = int(rng.integers(100, 801))
+    outl = float(rng.uniform(0.10, 0.30))
+    g = random_graph(4000 + graph_id, n, cam, n_m, outl, coverage_target=cov)
+    if strip:
+        for r in g.renders:
+            r.depth_clean = None
+            r.normals_true = None
+    g.meta.update(n_frames=n, width=cam.width, coverage=cov, matches=n_m, outliers=outl)
+    return g
+
+
+def _batched_job(k):
+    return batched_graph(k)
+
+
+def batched_graphs(ids, workers: int | None = None) -> list:
+    """Graphs of the batched workload, made in forked worker processes (call
+    before the calling process initialises CUDA)."""
+    import multiprocessing as mp
+    import os
+    import sys
+    from concurrent.futures import ProcessPoolExecutor
+    torch = sys.modules.get("torch")
+    if torch is not None and torch.cuda.is_initialized():
+        raise RuntimeError("batched_graphs forks worker processes; call it before CUDA is initialised")
+    ids = list(ids)
+    workers = workers or max(1, min(32, os.cpu_count() or 1))
+    if workers == 1 or len(ids) == 1:
+        return [batched_graph(k) for k in ids]
+    with ProcessPoolExecutor(workers, mp_context=mp.get_context("fork")) as ex:
+        return list(ex.map(_batched_job, ids))

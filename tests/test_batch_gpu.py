@@ -1,0 +1,130 @@
+"""Batched solver (bt_batch_*) against the single-graph path and the oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synthgen as S
+
+pytestmark = pytest.mark.gpu
+
+ROT_TOL = 1e-5
+TRANS_TOL = 1e-6
+COST_RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def bt():
+    from paper_2108_00516_gb300 import build as lbuild
+    lbuild.build()
+    from paper_2108_00516_gb300 import bt as _bt
+    _bt.load()
+    return _bt
+
+
+def pose_err(A, B):
+    rot = max(S.rotation_angle(a[:3, :3] @ b[:3, :3].T) for a, b in zip(A, B))
+    tr = max(np.abs(a[:3, 3] - b[:3, 3]).max() for a, b in zip(A, B))
+    return rot, tr
+
+
+def _graphs():
+    # uneven sizes: N = 2..5, two resolutions
+    out = [S.tiny_graph(k) for k in range(3)]
+    out.append(S.random_graph(4321, 5, S.QVGA_CAMERA, 300, 0.2, coverage_target=0.12))
+    out.append(S.random_graph(4322, 2, S.TINY_CAMERA, 150, 0.1))
+    return out
+
+
+def test_batch_matches_single_graph_bitwise(bt):
+    """With the single-graph path's CTA shape the batch runs the same
+    arithmetic in the same order: results are bit-identical."""
+    gs = _graphs()
+    singles = []
+    for g in gs:
+        pg = bt.graph_from_synth(g)
+        singles.append(pg.solve(6))
+    batch = bt.Batch()
+    pgs = [bt.graph_from_synth(g) for g in gs]
+    for pg in pgs:
+        batch.add(pg)
+    batch.set_shape(0)
+    reps = batch.solve(6)
+    for pg, (P, rep), r in zip(pgs, singles, reps):
+        assert np.array_equal(pg.get_poses(), P)
+        assert r["cost_final"] == rep["cost_final"]
+        assert r["dense_inliers"] == rep["dense_inliers"]
+
+
+def test_batch_autotuned_matches_oracle(bt):
+    gs = _graphs()
+    batch = bt.Batch()
+    pgs = [bt.graph_from_synth(g) for g in gs]
+    for pg in pgs:
+        batch.add(pg)
+    reps = batch.solve(7)
+    shape, us = batch.tuning()
+    assert 0 <= shape < 4 and all(u > 0 for u in us)
+    for g, pg, r in zip(gs, pgs, reps):
+        ro = O.solve(g, 7)
+        rot, tr = pose_err(pg.get_poses(), ro["poses"])
+        assert abs(r["cost_final"] - ro["cost_final"]) <= COST_RTOL * ro["cost_final"]
+        assert rot <= ROT_TOL and tr <= TRANS_TOL
+
+
+def test_batch_replay_and_every_shape(bt):
+    """The captured CUDA graph is replayed on the next solve; every CTA shape
+    gives the same energies to FP32 summation-order rounding."""
+    gs = _graphs()[:3]
+    pgs = [bt.graph_from_synth(g) for g in gs]
+    batch = bt.Batch()
+    for pg in pgs:
+        batch.add(pg)
+    results = []
+    for shape in range(4):
+        batch.set_shape(shape)
+        for g, pg in zip(gs, pgs):
+            pg.set_poses(g.pose_init)
+        reps = batch.solve(3)
+        for g, pg in zip(gs, pgs):      # replay from the same start
+            pg.set_poses(g.pose_init)
+        reps2 = batch.solve(3)
+        assert [r["cost_final"] for r in reps] == [r["cost_final"] for r in reps2]
+        results.append([r["cost_init"] for r in reps])
+    for res in results[1:]:
+        for a, b in zip(res, results[0]):
+            assert abs(a - b) <= 1e-6 * b
+
+
+def test_batch_singular_graph_is_reported(bt):
+    good = S.tiny_graph(1)
+    bad = S.tiny_graph(2)
+    cfg = bt.config_default()
+    pg_good = bt.graph_from_synth(good)
+    bad2 = S.SynthGraph(bad.cams, bad.renders, bad.pose_true, bad.pose_init, bad.fixed, [], bad.shape)
+    cfg.lambda_dense = 0.0
+    pg_bad = bt.graph_from_synth(bad2, config=cfg)
+    batch = bt.Batch()
+    batch.add(pg_good)
+    batch.add(pg_bad)
+    batch.set_shape(0)
+    reps = batch.solve(3, raise_on_error=False)
+    assert reps[0]["status"] == 0 and reps[1]["status"] == bt.BT_ERR_SINGULAR
+    assert np.array_equal(pg_bad.get_poses(), bad2.pose_init)
+    assert not np.array_equal(pg_good.get_poses(), good.pose_init)
+
+
+def test_batched_workload_sample(bt):
+    """Two graphs of the batched workload (mixed sizes/resolutions) through
+    the autotuned batch, checked stepwise against the oracle on one
+    iteration from identical poses."""
+    gs = [S.batched_graph(k) for k in (7, 9)]
+    pgs = [bt.graph_from_synth(g) for g in gs]
+    batch = bt.Batch()
+    for pg in pgs:
+        batch.add(pg)
+    reps = batch.solve(1)
+    for g, pg, r in zip(gs, pgs, reps):
+        ro = O.solve(g, 1)
+        assert abs(r["cost_init"] - ro["cost_per_iter"][0]) <= 1e-6 * ro["cost_per_iter"][0]
+        rot, tr = pose_err(pg.get_poses(), ro["poses"])
+        assert rot <= ROT_TOL and tr <= TRANS_TOL
