@@ -58,6 +58,8 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="bounded oracle sample (CPU baseline)")
     ap.add_argument("--workers", type=int, default=0, help="generator processes (0 = all cores)")
+    ap.add_argument("--batch-graphs", type=int, default=64, help="graphs of the batched workload (0 = skip)")
+    ap.add_argument("--batch-steps", type=int, default=3)
     return ap.parse_args()
 
 
@@ -204,10 +206,83 @@ def cpu_baseline(seq, graphs, inits, seconds: float, iters: int):
 
 # --------------------------------------------------------------------------- GPU arm
 
+BATCH_WORKLOAD = ("batched: graphs with N ~ U{3..20} views, all 320x240 or all 640x480, coverage U[5,40]%, "
+                  "U{100..800} matches/pair with U[10,30]% outliers, 10 GN iterations from 5 deg / 1 cm")
+
+
+def run_batched(bt, graphs_b, stream, args):
+    """Plain (one graph per bt_solve) vs batched (bt_batch_solve, CUDA graph,
+    autotuned CTA shape) on the batched workload, at equal final cost."""
+    import numpy as np
+    import torch
+    it = args.iters
+    pgs = [bt.graph_from_synth(g, stream=stream) for g in graphs_b]
+    inits = [np.ascontiguousarray(g.pose_init) for g in graphs_b]
+
+    def reset():
+        for pg, P in zip(pgs, inits):
+            pg.set_poses(P)
+
+    # plain: the same kernels, one graph per solve
+    plain_cost = []
+    for _ in range(2):                         # warm-up
+        reset()
+        for pg in pgs:
+            pg.solve(it)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(args.batch_steps):
+        reset()
+        plain_cost = [pg.solve(it)[1]["cost_final"] for pg in pgs]
+    torch.cuda.synchronize()
+    t_plain = (time.perf_counter() - t0) / args.batch_steps
+    batch = bt.Batch(stream=stream)
+    for pg in pgs:
+        batch.add(pg)
+    reset()
+    batch.solve(it)                            # autotune + capture
+    reset()
+    batch.solve(it)                            # warm-up replay
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(args.batch_steps):
+        reset()
+        reps = batch.solve(it)
+    torch.cuda.synchronize()
+    t_batch = (time.perf_counter() - t0) / args.batch_steps
+    shape, tune_us = batch.tuning()
+    px_pass = sum(r["dense_pixel_pairs"] for r in reps) / max(1, it)
+    rel = [(r["cost_final"] - c) / c for r, c in zip(reps, plain_cost)]
+    us = tune_us[shape]
+    peak, peak_kind = hbm_peak()
+    achieved = BYTES_PER_PIXEL_PAIR * px_pass / (us * 1e-6) / 1e9 if us > 0 else None
+    nbytes = sum(r.depth.nbytes * 5 for g in graphs_b for r in g.renders)
+    batch.close()
+    for pg in pgs:
+        pg.close()
+    return {"workload": BATCH_WORKLOAD, "graphs": len(graphs_b),
+            "frames": sum(g.n for g in graphs_b), "device_bytes_approx": nbytes,
+            "plain_solves_per_s": round(len(pgs) / t_plain, 2),
+            "batched_solves_per_s": round(len(pgs) / t_batch, 2),
+            "speedup": round(t_plain / t_batch, 3),
+            "equal_cost": {"max_rel_above_plain": max(rel), "bound": 0.01, "ok": max(rel) <= 0.01},
+            "cta_shape": shape, "autotune_us_per_shape": [round(u, 1) for u in tune_us],
+            "residual_roofline": {"bound": "hbm", "achieved": round(achieved, 1) if achieved else None,
+                                  "peak": peak, "unit": "GB/s",
+                                  "frac": round(achieved / peak, 4) if achieved else None,
+                                  "pixel_pairs_per_pass": int(px_pass),
+                                  "pass_us": round(us, 1), "peak_kind": peak_kind},
+            "pixel_pairs_per_s": round(px_pass * it / t_batch, 1)}
+
+
 def run_ours(args):
     rank, world, local = dist_env()
-    # all synthetic data is made before CUDA is touched (the generator forks)
+    # all synthetic data is made before CUDA is touched (the generators fork)
     seq, graphs, pools, pairs, inits = build_workload(2000 + rank, args.frames, args.workers)
+    graphs_b = []
+    if args.batch_graphs > 0:
+        import synthgen as S
+        graphs_b = S.batched_graphs(range(64 * rank, 64 * rank + args.batch_graphs), workers=args.workers or None)
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -307,6 +382,8 @@ def run_ours(args):
     if args.e2e_steps > 0:
         e2e = run_e2e(bt, seq, graphs, pools, inits, stream, args, world)
 
+    batched = run_batched(bt, graphs_b, stream, args) if graphs_b else None
+
     base = None
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
         base = cpu_baseline(seq, graphs, inits, args.cpu_seconds, it)
@@ -325,7 +402,7 @@ def run_ours(args):
                           "parallelism": f"replicas x{world} (independent sequences)"},
                "pixel_pairs_per_s": round(pps, 1),
                "roofline": roofline, "gpu_launches": launches,
-               "e2e": e2e, "cpu_baseline": base, "clocks": clk,
+               "e2e": e2e, "cpu_baseline": base, "clocks": clk, "batched": batched,
                "wall_s_timed": round(wall, 3)}
         print(json.dumps(out), flush=True)
     if world > 1:
