@@ -67,6 +67,24 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest value of x over all ranks (the job's time is its slowest
+    rank's); identity on one rank."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, world: int, slowest_seconds: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time (weak scaling: each rank has its own units)."""
+    return units_per_rank * world / slowest_seconds
+
+
 # --------------------------------------------------------------------------- workload
 
 def build_workload(seed: int, n_frames: int, workers: int):
@@ -348,14 +366,9 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_ms = sum(step_ms)
-    if world > 1:
-        x = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(x, op=dist.ReduceOp.MAX)
-        t_ms = float(x.item())
-    solves = len(graphs) * args.steps * world
-    value = solves / (t_ms / 1e3)
-    pps = px_total * world / (t_ms / 1e3)
+    t_ms = max_over_ranks(sum(step_ms), world, "cuda")
+    value = job_throughput(len(graphs) * args.steps, world, t_ms / 1e3)
+    pps = job_throughput(px_total, world, t_ms / 1e3)
 
     # roofline of the dominant kernel (the residual pass), from events around
     # each of its launches on the graph's stream inside the timed region
@@ -463,12 +476,8 @@ def run_e2e(bt, seq, graphs, pools, inits, stream, args, world):
         h2d += a
         d2h += b
     torch.cuda.synchronize()
-    el = time.perf_counter() - t0
-    if world > 1:
-        x = torch.tensor([el], dtype=torch.float64, device="cuda")
-        dist.all_reduce(x, op=dist.ReduceOp.MAX)
-        el = float(x.item())
-    return {"value": round(len(graphs) * args.e2e_steps * world / el, 3), "unit": "solves/s",
+    el = max_over_ranks(time.perf_counter() - t0, world, "cuda")
+    return {"value": round(job_throughput(len(graphs) * args.e2e_steps, world, el), 3), "unit": "solves/s",
             "h2d_bytes_per_step": h2d // args.e2e_steps, "d2h_bytes_per_step": d2h // args.e2e_steps,
             "steps": args.e2e_steps,
             "note": "host numpy buffers (pageable) through bt_add_frame / bt_set_matches / bt_solve; "
