@@ -58,7 +58,11 @@ extern "C" {
 #define BT_HOST 0
 #define BT_DEVICE 1
 
-/* storage precision of the per-pixel point/normal maps */
+/* storage precision of the per-pixel point/normal maps (arithmetic is FP32
+ * for the residual pass and FP64 for the solve in every case).  BT_BF16 and
+ * BT_FP16 store normals and the in-plane point coordinates directly and depth
+ * as an offset from the frame's mean valid depth, 8 bytes per target pixel
+ * and 16 per source pixel instead of 16 and 32 (not in the paper). */
 #define BT_FP32 0
 #define BT_BF16 1
 #define BT_FP16 2
@@ -79,7 +83,9 @@ typedef struct {
  *   dense_max_dist = 0.02 m                (association gate on point-pair distance)
  *   dense_max_normal_deg = 45              (association gate on normal angle)
  *   lambda_sparse = lambda_dense = 1       (lambda_1, lambda_2 of Eq. 1)
- *   precision = BT_FP32, max_frames = 0 (no limit on stored frames). */
+ *   precision = BT_FP32, max_frames = 0 (no limit on stored frames).
+ * precision selects the storage of the per-pixel maps (BT_FP32 / BT_BF16 /
+ * BT_FP16); it is fixed for the graph's lifetime. */
 typedef struct {
     double huber_sparse;
     double huber_dense;
@@ -214,7 +220,9 @@ void bt_batch_destroy(bt_batch* b);
 /* Adds a graph (not owned: it must outlive the batch and must not be solved
  * through bt_solve while a batch solve is running).  Its active node set and
  * stored poses at the time of each bt_batch_solve are what is solved.
- * Errors: BT_ERR_INVALID (NULL, already added, no or too many active nodes). */
+ * Every graph of a batch must use the same storage precision.
+ * Errors: BT_ERR_INVALID (NULL, already added, no or too many active nodes,
+ * different precision). */
 int bt_batch_add(bt_batch* b, bt_graph* g);
 
 /* Number of graphs, or a negative status. */

@@ -72,9 +72,10 @@ struct Frame {
     bt_intrinsics K{};
     int fixed = 0;
     double pose[16];
-    float4* tgt = nullptr;
-    float4* src_p = nullptr;
-    float4* src_n = nullptr;
+    void* tgt = nullptr;     // target map, element size bt::pixel_bytes(precision)
+    void* src_p = nullptr;   // source points
+    void* src_n = nullptr;   // source normals
+    float zref = 0.f;        // reference depth of the 16-bit encodings
     int M = 0;
 };
 
@@ -153,8 +154,8 @@ int validate_config(const bt_config& c)
     if (!std::isfinite(c.lambda_sparse) || !std::isfinite(c.lambda_dense) || c.lambda_sparse < 0.0 ||
         c.lambda_dense < 0.0)
         return fail(BT_ERR_INVALID, "config: lambdas must be finite and >= 0");
-    if (c.precision != BT_FP32)
-        return fail(BT_ERR_INVALID, "config: only BT_FP32 storage is available in this build");
+    if (c.precision != BT_FP32 && c.precision != BT_BF16 && c.precision != BT_FP16)
+        return fail(BT_ERR_INVALID, "config: precision must be BT_FP32, BT_BF16 or BT_FP16");
     if (c.max_frames < 0) return fail(BT_ERR_INVALID, "config: max_frames must be >= 0");
     return BT_OK;
 }
@@ -227,6 +228,7 @@ int build_topology(bt_graph* g, int tile)
         d.src_p = f.src_p;
         d.src_n = f.src_n;
         d.tgt = f.tgt;
+        d.zref = f.zref;
         d.M = f.M;
         d.W = f.K.width;
         d.H = f.K.height;
@@ -303,6 +305,7 @@ int build_topology(bt_graph* g, int tile)
     a.n_free = nfree;
     a.n_upairs = U;
     a.tile = tile;
+    a.precision = g->cfg.precision;
     a.stage_blocks = bt::reduce_stage_fits(nfree, N) ? 1 : 0;
     const bt_config& c = g->cfg;
     a.dmax2 = (float)(c.dense_max_dist * c.dense_max_dist);
@@ -486,28 +489,27 @@ int bt_add_frame(bt_graph* g, const float* depth, const float* normals, const ui
         d_normals = g->up_normals.as<float>();
         d_mask = g->up_mask.as<uint8_t>();
     }
-    const int nblk = (HW + bt::kPrepPix - 1) / bt::kPrepPix;
-    BT_CUDA(g->prep_blk.ensure(sizeof(int) * (nblk + 1)), "alloc prep");
-    BT_CUDA(g->prep_src_p.ensure(sizeof(float4) * HW), "alloc prep");
-    BT_CUDA(g->prep_src_n.ensure(sizeof(float4) * HW), "alloc prep");
-    BT_CUDA(g->prep_M.ensure(sizeof(int)), "alloc prep");
+    const int P = g->cfg.precision;
+    const size_t pb = bt::pixel_bytes(P);
+    BT_CUDA(g->prep_blk.ensure(bt::prep_scratch_bytes(HW)), "alloc prep");
+    BT_CUDA(g->prep_src_p.ensure(pb * HW), "alloc prep");
+    BT_CUDA(g->prep_src_n.ensure(pb * HW), "alloc prep");
+    BT_CUDA(g->prep_M.ensure(2 * sizeof(int)), "alloc prep");
     Frame f;
-    BT_CUDA(cudaMalloc(&f.tgt, sizeof(float4) * HW), "cudaMalloc(target map)");
+    BT_CUDA(cudaMalloc(&f.tgt, pb * HW), "cudaMalloc(target map)");
     const float ifx = 1.0f / K->fx, ify = 1.0f / K->fy;
-    cudaError_t e = bt::launch_prep(d_depth, d_normals, d_mask, W, H, K->cx, K->cy, ifx, ify, f.tgt,
-                                    g->prep_src_p.as<float4>(), g->prep_src_n.as<float4>(), g->prep_blk.as<int>(),
-                                    g->prep_M.as<int>(), s);
+    cudaError_t e = bt::launch_prep(d_depth, d_normals, d_mask, W, H, K->cx, K->cy, ifx, ify, P, f.tgt,
+                                    g->prep_src_p.p, g->prep_src_n.p, g->prep_blk.p, g->prep_M.as<int>(), s);
     g->prof.prep_launches += 3;
-    int M = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&M, g->prep_M.p, sizeof(int), cudaMemcpyDeviceToHost, s);
+    int out2[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out2, g->prep_M.p, sizeof(out2), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    const int M = out2[0];
     if (e == cudaSuccess && M > 0) {
-        e = cudaMalloc(&f.src_p, sizeof(float4) * M);
-        if (e == cudaSuccess) e = cudaMalloc(&f.src_n, sizeof(float4) * M);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(f.src_p, g->prep_src_p.p, sizeof(float4) * M, cudaMemcpyDeviceToDevice, s);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(f.src_n, g->prep_src_n.p, sizeof(float4) * M, cudaMemcpyDeviceToDevice, s);
+        e = cudaMalloc(&f.src_p, pb * M);
+        if (e == cudaSuccess) e = cudaMalloc(&f.src_n, pb * M);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(f.src_p, g->prep_src_p.p, pb * M, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(f.src_n, g->prep_src_n.p, pb * M, cudaMemcpyDeviceToDevice, s);
     }
     if (e != cudaSuccess) {
         cudaFree(f.tgt);
@@ -515,6 +517,7 @@ int bt_add_frame(bt_graph* g, const float* depth, const float* normals, const ui
         cudaFree(f.src_n);
         return cuda_fail(e, "bt_add_frame: preparation");
     }
+    std::memcpy(&f.zref, &out2[1], sizeof(float));
     f.id = g->next_id;
     f.K = *K;
     f.fixed = fixed ? 1 : 0;
@@ -734,6 +737,7 @@ struct bt_batch {
     bool own_stream = false;
     std::vector<bt_graph*> graphs;
     int shape = -1;          // fixed CTA shape, or -1 = autotune
+    int precision = -1;      // storage precision shared by every graph of the batch
     int tuned_shape = -1;    // autotuner's choice for the current graph set
     bool dirty = true;       // graph set / topology changed since the last build
     DevBuf d_args, d_work_res, d_work_pair;
@@ -829,7 +833,8 @@ int batch_enqueue(bt_batch* b, int iters, int shape)
     BT_CUDA(bt::launch_batch_xforms(A, G, s), "batch xforms");
     for (int p = 0; p <= iters; ++p) {
         const bool full = p < iters;
-        BT_CUDA(bt::launch_batch_residual(A, b->d_work_res.as<int2>(), b->n_work_res, b->max_N, full, shape, s),
+        BT_CUDA(bt::launch_batch_residual(A, b->d_work_res.as<int2>(), b->n_work_res, b->max_N, full, shape,
+                                          b->precision, s),
                 "batch residual");
         BT_CUDA(bt::launch_batch_pairs(A, b->d_work_pair.as<int2>(), b->n_work_pair, full, s), "batch pairs");
         BT_CUDA(bt::launch_batch_solve(A, G, b->solve_smem, full, p, s), "batch solve");
@@ -859,7 +864,8 @@ int batch_autotune(bt_batch* b)
         float ms = 0.f, tot = 0.f;
         for (int rep = 0; rep < 3; ++rep) {
             BT_CUDA(cudaEventRecord(e0, b->stream), "event");
-            BT_CUDA(bt::launch_batch_residual(A, b->d_work_res.as<int2>(), b->n_work_res, b->max_N, true, sh, b->stream),
+            BT_CUDA(bt::launch_batch_residual(A, b->d_work_res.as<int2>(), b->n_work_res, b->max_N, true, sh,
+                                              b->precision, b->stream),
                     "batch residual");
             BT_CUDA(cudaEventRecord(e1, b->stream), "event");
             BT_CUDA(cudaEventSynchronize(e1), "event sync");
@@ -914,6 +920,9 @@ int bt_batch_add(bt_batch* b, bt_graph* g)
         return fail(BT_ERR_INVALID, "bt_batch_add: graph needs 1..BT_MAX_NODES active nodes");
     for (bt_graph* h : b->graphs)
         if (h == g) return fail(BT_ERR_INVALID, "bt_batch_add: graph already in the batch");
+    if (b->precision >= 0 && g->cfg.precision != b->precision)
+        return fail(BT_ERR_INVALID, "bt_batch_add: every graph of a batch must use the same storage precision");
+    b->precision = g->cfg.precision;
     b->graphs.push_back(g);
     b->dirty = true;
     b->tuned_shape = -1;

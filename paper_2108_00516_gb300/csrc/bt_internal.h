@@ -1,13 +1,16 @@
 // bt_internal.h -- device data layout and kernel entry points of libbt.
 //
 // Layout in HBM (all device buffers are owned by a bt_graph):
-//   per stored frame
-//     tgt   float4[H*W]  (z, nx, ny, nz) per pixel, z = 0 where the pixel cannot
-//                        be a dense target (not masked / no depth / no normal);
-//                        16 B per pixel, read by the projective gather (Eq. 3)
-//     src_p float4[M]    (px, py, pz, 0) back-projected source points of the
-//                        M valid masked pixels, increasing pixel order
-//     src_n float4[M]    (nx, ny, nz, 0) their normals
+//   per stored frame (storage precision P of the graph: FP32, BF16 or FP16)
+//     tgt   [H*W]  (z, nx, ny, nz) per pixel, read by the projective gather
+//                  (Eq. 3).  FP32: float4, z = 0 where the pixel cannot be a
+//                  dense target (not masked / no depth / no normal), 16 B.
+//                  BF16/FP16: 4 x 16 bit (z - zref, nx, ny, nz), z - zref =
+//                  NaN where invalid, 8 B; zref = the frame's mean valid depth
+//     src_p [M]    back-projected source points of the M valid masked pixels,
+//                  increasing pixel order: float4 (px, py, pz, 0) or
+//                  4 x 16 bit (px, py, pz - zref, 0)
+//     src_n [M]    their normals: float4 (nx, ny, nz, 0) or 4 x 16 bit
 //   per correspondence set (unordered frame pair)
 //     pa, pb float[3*count]  the two camera-frame point lists of Eq. 2
 //   per solve (active node set of N nodes)
@@ -44,9 +47,10 @@ constexpr int kMaxNodes = 24;
 constexpr int kPrepPix = 1024;                // pixels per prep CTA (256 threads x 4)
 
 struct NodeDev {
-    const float4* src_p;
-    const float4* src_n;
-    const float4* tgt;
+    const void* src_p;
+    const void* src_n;
+    const void* tgt;
+    float zref;     // reference depth of the 16-bit encodings (0 for FP32)
     int M;          // valid source pixels
     int W, H;
     float fx, fy, cx, cy, ifx, ify;
@@ -75,6 +79,7 @@ constexpr size_t kReduceSmemMax = 200 * 1024;
 
 struct SolveArgs {
     int N, n_tiles, n_pairs, n_edges, n_free, n_upairs;
+    int precision;          // storage precision of the per-pixel maps (BT_FP32 / BT_BF16 / BT_FP16)
     int tile;               // source pixels per dense tile (CTA shape product)
     int stage_blocks;       // 1: the last CTA copies the pair blocks to shared memory
     float dmax2, cmin, huber_dense, huber_sparse;
@@ -94,12 +99,16 @@ struct SolveArgs {
     double* costs;      // [iter][4]: total, dense, sparse, dense count
 };
 
-// K0 (frame preparation).  All launches on `s`.  block_scratch must hold
-// ceil(H*W / kPrepPix) + 1 ints; *M_dev receives the valid source count.
+// K0 (frame preparation) for storage precision `precision`.  All launches
+// on `s`.  block_scratch must hold prep_scratch_bytes(W*H) bytes; out2[0]
+// receives the valid source count (int) and out2[1] the reference depth
+// (float bits).  tgt / src_p / src_n are sized for the precision.
+size_t prep_scratch_bytes(int HW);
+inline size_t pixel_bytes(int precision) { return precision == 0 ? 16 : 8; }
 cudaError_t launch_prep(const float* depth, const float* normals, const uint8_t* mask,
-                        int W, int H, float cx, float cy, float ifx, float ify,
-                        float4* tgt, float4* src_p, float4* src_n, int* block_scratch,
-                        int* M_dev, cudaStream_t s);
+                        int W, int H, float cx, float cy, float ifx, float ify, int precision,
+                        void* tgt, void* src_p, void* src_n, void* block_scratch,
+                        int* out2, cudaStream_t s);
 
 // Float transforms for the current FP64 poses (start of a solve).
 cudaError_t launch_xforms(const SolveArgs& a, cudaStream_t s);
@@ -121,7 +130,7 @@ inline int shape_tile(int shape) { return kShapeThreads[shape] * kShapePix[shape
 //   work_pair: (graph, unordered pair) per pair-reduction CTA
 cudaError_t launch_batch_xforms(const SolveArgs* args_dev, int n_graphs, cudaStream_t s);
 cudaError_t launch_batch_residual(const SolveArgs* args_dev, const int2* work_res, int n_work, int max_N,
-                                  bool full, int shape, cudaStream_t s);
+                                  bool full, int shape, int precision, cudaStream_t s);
 cudaError_t launch_batch_pairs(const SolveArgs* args_dev, const int2* work_pair, int n_work, bool full,
                                cudaStream_t s);
 cudaError_t launch_batch_solve(const SolveArgs* args_dev, int n_graphs, size_t smem, bool full, int iter,

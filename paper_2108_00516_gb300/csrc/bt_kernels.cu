@@ -32,8 +32,11 @@
 // Jacobians and weights use ordinary FP32 arithmetic.
 #include "bt_internal.h"
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
 
 namespace bt {
 
@@ -79,49 +82,98 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* total, int* sm /
     return before + x - v;
 }
 
+// 16-bit storage helpers (BF16 / FP16 as raw bits)
+template <int P>
+__device__ __forceinline__ unsigned short to16(float x)
+{
+    if constexpr (P == 1) return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+    else return __half_as_ushort(__float2half_rn(x));
+}
+template <int P>
+__device__ __forceinline__ float from16(unsigned short b)
+{
+    if constexpr (P == 1) return __bfloat162float(__ushort_as_bfloat16(b));
+    else return __half2float(__ushort_as_half(b));
+}
+template <int P>
+__device__ __forceinline__ unsigned short nan16()
+{
+    return P == 1 ? (unsigned short)0x7FC0 : (unsigned short)0x7E00;
+}
+
+size_t prep_scratch_bytes(int HW)
+{
+    const size_t nblk = (HW + kPrepPix - 1) / kPrepPix;
+    return (nblk + 1) * (sizeof(int) + sizeof(double)) + 16;
+}
+
+// Validity, count and depth sum of each block of kPrepPix pixels.
 __global__ void __launch_bounds__(kThreads) prep_count_kernel(
     const float* __restrict__ depth, const float* __restrict__ normals,
-    const uint8_t* __restrict__ mask, int HW, float4* __restrict__ tgt, int* __restrict__ blockcnt)
+    const uint8_t* __restrict__ mask, int HW, int* __restrict__ blockcnt, double* __restrict__ blocksum)
 {
     __shared__ int sm[33];
+    __shared__ double sz[kThreads / 32];
     const int base = blockIdx.x * kPrepPix + threadIdx.x * kPixPerThread;
     int c = 0;
+    float zs = 0.f;
 #pragma unroll
     for (int k = 0; k < kPixPerThread; ++k) {
         const int pix = base + k;
         if (pix < HW) {
             float z;
             float3 n;
-            const bool ok = pixel_valid(depth, normals, mask, pix, z, n);
-            tgt[pix] = ok ? make_float4(z, n.x, n.y, n.z) : make_float4(0.f, 0.f, 0.f, 0.f);
-            c += ok;
+            if (pixel_valid(depth, normals, mask, pix, z, n)) {
+                ++c;
+                zs += z;
+            }
         }
     }
     int total;
     block_exclusive_scan(c, &total, sm);
-    if (threadIdx.x == 0) blockcnt[blockIdx.x] = total;
+    double dz = zs;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) dz += __shfl_xor_sync(0xffffffffu, dz, o);
+    if ((threadIdx.x & 31) == 0) sz[threadIdx.x >> 5] = dz;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) t += sz[w];
+        blockcnt[blockIdx.x] = total;
+        blocksum[blockIdx.x] = t;
+    }
 }
 
-__global__ void prep_scan_kernel(int* __restrict__ blockcnt, int nblk, int* __restrict__ M_out)
+// Exclusive scan of the block counts; M and the reference depth (mean valid
+// depth, used by the 16-bit encodings).
+__global__ void prep_scan_kernel(int* __restrict__ blockcnt, const double* __restrict__ blocksum, int nblk,
+                                 int* __restrict__ out2)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         int s = 0;
+        double z = 0.0;
         for (int b = 0; b < nblk; ++b) {
             const int c = blockcnt[b];
             blockcnt[b] = s;
             s += c;
+            z += blocksum[b];
         }
-        *M_out = s;
+        out2[0] = s;
+        out2[1] = __float_as_int(s > 0 ? (float)(z / s) : 0.f);
     }
 }
 
+// Target map of every pixel and the compacted source list of the valid ones.
+template <int P>
 __global__ void __launch_bounds__(kThreads) prep_write_kernel(
     const float* __restrict__ depth, const float* __restrict__ normals,
     const uint8_t* __restrict__ mask, int W, int HW, float cx, float cy, float ifx, float ify,
-    const int* __restrict__ blockoff, float4* __restrict__ src_p, float4* __restrict__ src_n)
+    const int* __restrict__ blockoff, const int* __restrict__ out2, void* __restrict__ tgt_v,
+    void* __restrict__ src_p_v, void* __restrict__ src_n_v)
 {
     __shared__ int sm[33];
     const int base = blockIdx.x * kPrepPix + threadIdx.x * kPixPerThread;
+    const float zref = P == 0 ? 0.f : __int_as_float(out2[1]);
     bool ok[kPixPerThread];
     float zz[kPixPerThread];
     float3 nn[kPixPerThread];
@@ -131,6 +183,19 @@ __global__ void __launch_bounds__(kThreads) prep_write_kernel(
         const int pix = base + k;
         ok[k] = pix < HW && pixel_valid(depth, normals, mask, pix, zz[k], nn[k]);
         c += ok[k];
+        if (pix < HW) {
+            if constexpr (P == 0) {
+                reinterpret_cast<float4*>(tgt_v)[pix] =
+                    ok[k] ? make_float4(zz[k], nn[k].x, nn[k].y, nn[k].z) : make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                ushort4 t;
+                t.x = ok[k] ? to16<P>(zz[k] - zref) : nan16<P>();
+                t.y = ok[k] ? to16<P>(nn[k].x) : (unsigned short)0;
+                t.z = ok[k] ? to16<P>(nn[k].y) : (unsigned short)0;
+                t.w = ok[k] ? to16<P>(nn[k].z) : (unsigned short)0;
+                reinterpret_cast<ushort4*>(tgt_v)[pix] = t;
+            }
+        }
     }
     int total;
     int off = blockoff[blockIdx.x] + block_exclusive_scan(c, &total, sm);
@@ -143,22 +208,38 @@ __global__ void __launch_bounds__(kThreads) prep_write_kernel(
         // pi_D^-1(x): ((u - cx) z) * (1/fx), ((v - cy) z) * (1/fy), z
         const float px = __fmul_rn(__fmul_rn(__fsub_rn((float)u, cx), z), ifx);
         const float py = __fmul_rn(__fmul_rn(__fsub_rn((float)v, cy), z), ify);
-        src_p[off] = make_float4(px, py, z, 0.f);
-        src_n[off] = make_float4(nn[k].x, nn[k].y, nn[k].z, 0.f);
+        if constexpr (P == 0) {
+            reinterpret_cast<float4*>(src_p_v)[off] = make_float4(px, py, z, 0.f);
+            reinterpret_cast<float4*>(src_n_v)[off] = make_float4(nn[k].x, nn[k].y, nn[k].z, 0.f);
+        } else {
+            reinterpret_cast<ushort4*>(src_p_v)[off] = make_ushort4(to16<P>(px), to16<P>(py), to16<P>(z - zref), 0);
+            reinterpret_cast<ushort4*>(src_n_v)[off] =
+                make_ushort4(to16<P>(nn[k].x), to16<P>(nn[k].y), to16<P>(nn[k].z), 0);
+        }
         ++off;
     }
 }
 
-cudaError_t launch_prep(const float* depth, const float* normals, const uint8_t* mask, int W, int H,
-                        float cx, float cy, float ifx, float ify, float4* tgt, float4* src_p,
-                        float4* src_n, int* block_scratch, int* M_dev, cudaStream_t s)
+cudaError_t launch_prep(const float* depth, const float* normals, const uint8_t* mask, int W, int H, float cx,
+                        float cy, float ifx, float ify, int precision, void* tgt, void* src_p, void* src_n,
+                        void* block_scratch, int* out2, cudaStream_t s)
 {
     const int HW = W * H;
     const int nblk = (HW + kPrepPix - 1) / kPrepPix;
-    prep_count_kernel<<<nblk, kThreads, 0, s>>>(depth, normals, mask, HW, tgt, block_scratch);
-    prep_scan_kernel<<<1, 32, 0, s>>>(block_scratch, nblk, M_dev);
-    prep_write_kernel<<<nblk, kThreads, 0, s>>>(depth, normals, mask, W, HW, cx, cy, ifx, ify,
-                                                block_scratch, src_p, src_n);
+    int* blockcnt = static_cast<int*>(block_scratch);
+    double* blocksum = reinterpret_cast<double*>(
+        (reinterpret_cast<uintptr_t>(blockcnt + nblk + 1) + 15) & ~static_cast<uintptr_t>(15));
+    prep_count_kernel<<<nblk, kThreads, 0, s>>>(depth, normals, mask, HW, blockcnt, blocksum);
+    prep_scan_kernel<<<1, 32, 0, s>>>(blockcnt, blocksum, nblk, out2);
+    if (precision == 1)
+        prep_write_kernel<1><<<nblk, kThreads, 0, s>>>(depth, normals, mask, W, HW, cx, cy, ifx, ify, blockcnt, out2,
+                                                       tgt, src_p, src_n);
+    else if (precision == 2)
+        prep_write_kernel<2><<<nblk, kThreads, 0, s>>>(depth, normals, mask, W, HW, cx, cy, ifx, ify, blockcnt, out2,
+                                                       tgt, src_p, src_n);
+    else
+        prep_write_kernel<0><<<nblk, kThreads, 0, s>>>(depth, normals, mask, W, HW, cx, cy, ifx, ify, blockcnt, out2,
+                                                       tgt, src_p, src_n);
     return cudaGetLastError();
 }
 
@@ -219,9 +300,36 @@ cudaError_t launch_xforms(const SolveArgs& a, cudaStream_t s)
 struct PairConst {
     float m[12];                         // camera i -> camera j (single)
     float fx, fy, cx, cy, ifx, ify, Wf, Hf;
-    int W, pad;
-    const float4* tgt;
+    float zref;                          // target frame's reference depth (16-bit maps)
+    int W;
+    const void* tgt;
 };
+
+// Target-map gather: (z, nx, ny, nz) as FP32 whatever the storage.
+template <int P>
+__device__ __forceinline__ float4 load_target(const void* tgt, size_t idx, float zref)
+{
+    if constexpr (P == 0) {
+        return __ldg(reinterpret_cast<const float4*>(tgt) + idx);
+    } else {
+        const ushort4 v = __ldg(reinterpret_cast<const ushort4*>(tgt) + idx);
+        return make_float4(zref + from16<P>(v.x), from16<P>(v.y), from16<P>(v.z), from16<P>(v.w));
+    }
+}
+
+template <int P>
+__device__ __forceinline__ void load_source(const NodeDev& Ni, int idx, float4& p, float4& n)
+{
+    if constexpr (P == 0) {
+        p = __ldg(reinterpret_cast<const float4*>(Ni.src_p) + idx);
+        n = __ldg(reinterpret_cast<const float4*>(Ni.src_n) + idx);
+    } else {
+        const ushort4 a = __ldg(reinterpret_cast<const ushort4*>(Ni.src_p) + idx);
+        const ushort4 b = __ldg(reinterpret_cast<const ushort4*>(Ni.src_n) + idx);
+        p = make_float4(from16<P>(a.x), from16<P>(a.y), Ni.zref + from16<P>(a.z), 0.f);
+        n = make_float4(from16<P>(b.x), from16<P>(b.y), from16<P>(b.z), 0.f);
+    }
+}
 
 // Warp reduce-scatter of 32 values: afterwards lane l holds the warp total of
 // value l (recursive halving, 31 shuffles instead of 5 x 32).
@@ -293,7 +401,7 @@ __device__ __forceinline__ void accumulate_pair(float (&acc)[kDenseVals], const 
 // in flight together), then gates, residual, Jacobian and accumulation.  The
 // warp's 32 sums are parked in shared memory; one barrier at the end, then
 // the (N-1) x 32 block sums are written to dpart[tile][j'].
-template <bool kFull, int kT, int kB>
+template <bool kFull, int kT, int kB, int P>
 __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
 {
     constexpr int kW = kT / 32;
@@ -312,9 +420,10 @@ __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
     PairConst* pc = reinterpret_cast<PairConst*>(sn + kTile);
     float* red = reinterpret_cast<float*>(pc + kMaxNodes);   // [N-1][kW][32]
     for (int s = threadIdx.x; s < kTile; s += kResThreads) {
-        const bool ok = s < nvalid;
-        sp[s] = ok ? __ldg(Ni.src_p + base + s) : make_float4(0.f, 0.f, 0.f, 0.f);
-        sn[s] = ok ? __ldg(Ni.src_n + base + s) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 pp = make_float4(0.f, 0.f, 0.f, 0.f), nn = pp;
+        if (s < nvalid) load_source<P>(Ni, base + s, pp, nn);
+        sp[s] = pp;
+        sn[s] = nn;
     }
     if (threadIdx.x < N && threadIdx.x != i) {
         const int j = threadIdx.x;
@@ -323,7 +432,7 @@ __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
 #pragma unroll
         for (int k = 0; k < 12; ++k) c.m[k] = a.xf[(i * N + j) * 12 + k];
         c.fx = Nj.fx; c.fy = Nj.fy; c.cx = Nj.cx; c.cy = Nj.cy; c.ifx = Nj.ifx; c.ify = Nj.ify;
-        c.Wf = (float)Nj.W; c.Hf = (float)Nj.H; c.W = Nj.W; c.tgt = Nj.tgt;
+        c.Wf = (float)Nj.W; c.Hf = (float)Nj.H; c.W = Nj.W; c.tgt = Nj.tgt; c.zref = Nj.zref;
     }
     __syncthreads();
     const float dmax2 = a.dmax2, cmin = a.cmin, hub = a.huber_dense;
@@ -360,7 +469,8 @@ __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
 #pragma unroll
             for (int k = 0; k < kResBatch; ++k) {
                 const int iu = pix[k] & 0xffff, iv = pix[k] >> 16;
-                t[k] = pix[k] >= 0 ? __ldg(c.tgt + (size_t)iv * c.W + iu) : make_float4(0.f, 0.f, 0.f, 0.f);
+                t[k] = pix[k] >= 0 ? load_target<P>(c.tgt, (size_t)iv * c.W + iu, c.zref)
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
             }
             // phase 3: gates, residual, Jacobian, Huber, accumulation
 #pragma unroll
@@ -418,8 +528,20 @@ __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
         const int jj = o / kDenseVals, v = o % kDenseVals;
         if (!kFull && v != 27 && v != 28) continue;
         float s = 0.f;
+        if constexpr (P == 0) {
 #pragma unroll
-        for (int w = 0; w < kW; ++w) s += red[((size_t)jj * kW + w) * kDenseVals + v];
+            for (int w = 0; w < kW; ++w) s += red[((size_t)jj * kW + w) * kDenseVals + v];
+        } else {
+            // compensated (Kahan) sum of the warps' block sums
+            float cmp = 0.f;
+#pragma unroll
+            for (int w = 0; w < kW; ++w) {
+                const float y = red[((size_t)jj * kW + w) * kDenseVals + v] - cmp;
+                const float t2 = s + y;
+                cmp = (t2 - s) - y;
+                s = t2;
+            }
+        }
         a.dpart[((size_t)tile * (N - 1) + jj) * kDenseVals + v] = s;
     }
 }
@@ -501,18 +623,18 @@ __device__ void sparse_edge(const SolveArgs& a, int e)
     }
 }
 
-template <bool kFull, int kT, int kB>
+template <bool kFull, int kT, int kB, int P>
 __global__ void __launch_bounds__(kT, 640 / kT) residual_kernel(SolveArgs a)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     if ((int)blockIdx.x < a.n_edges)
         sparse_edge<kFull>(a, blockIdx.x);
     else
-        dense_tile<kFull, kT, kB>(a, blockIdx.x - a.n_edges, dsm);
+        dense_tile<kFull, kT, kB, P>(a, blockIdx.x - a.n_edges, dsm);
 }
 
 // Batched residual pass: CTA b takes work item work[b] = (graph, item).
-template <bool kFull, int kT, int kB>
+template <bool kFull, int kT, int kB, int P>
 __global__ void __launch_bounds__(kT, 640 / kT) batch_residual_kernel(const SolveArgs* __restrict__ args,
                                                                        const int2* __restrict__ work)
 {
@@ -524,18 +646,26 @@ __global__ void __launch_bounds__(kT, 640 / kT) batch_residual_kernel(const Solv
     if (w.y < sa.n_edges)
         sparse_edge<kFull>(sa, w.y);
     else
-        dense_tile<kFull, kT, kB>(sa, w.y - sa.n_edges, dsm);
+        dense_tile<kFull, kT, kB, P>(sa, w.y - sa.n_edges, dsm);
+}
+
+template <int S, int P>
+static void set_residual_attrs_p()
+{
+    constexpr int kT = kShapeThreads[S], kB = kShapePix[S];
+    const int mx = (int)residual_smem_bytes(kMaxNodes, S);
+    cudaFuncSetAttribute(residual_kernel<true, kT, kB, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(residual_kernel<false, kT, kB, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(batch_residual_kernel<true, kT, kB, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(batch_residual_kernel<false, kT, kB, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
 }
 
 template <int S>
 static void set_residual_attrs()
 {
-    constexpr int kT = kShapeThreads[S], kB = kShapePix[S];
-    const int mx = (int)residual_smem_bytes(kMaxNodes, S);
-    cudaFuncSetAttribute(residual_kernel<true, kT, kB>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(residual_kernel<false, kT, kB>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(batch_residual_kernel<true, kT, kB>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(batch_residual_kernel<false, kT, kB>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    set_residual_attrs_p<S, 0>();
+    set_residual_attrs_p<S, 1>();
+    set_residual_attrs_p<S, 2>();
 }
 
 static void ensure_residual_attrs()
@@ -549,14 +679,22 @@ static void ensure_residual_attrs()
     done = true;
 }
 
-template <int S>
+template <int S, int P>
 static void launch_residual_shape(const SolveArgs& a, bool full, int grid, size_t smem, cudaStream_t s)
 {
     constexpr int kT = kShapeThreads[S], kB = kShapePix[S];
     if (full)
-        residual_kernel<true, kT, kB><<<grid, kT, smem, s>>>(a);
+        residual_kernel<true, kT, kB, P><<<grid, kT, smem, s>>>(a);
     else
-        residual_kernel<false, kT, kB><<<grid, kT, smem, s>>>(a);
+        residual_kernel<false, kT, kB, P><<<grid, kT, smem, s>>>(a);
+}
+
+template <int S>
+static void launch_residual_s(const SolveArgs& a, bool full, int grid, size_t smem, cudaStream_t s)
+{
+    if (a.precision == 1) launch_residual_shape<S, 1>(a, full, grid, smem, s);
+    else if (a.precision == 2) launch_residual_shape<S, 2>(a, full, grid, smem, s);
+    else launch_residual_shape<S, 0>(a, full, grid, smem, s);
 }
 
 cudaError_t launch_residual(const SolveArgs& a, bool full, cudaStream_t s, int shape)
@@ -566,36 +704,45 @@ cudaError_t launch_residual(const SolveArgs& a, bool full, cudaStream_t s, int s
     if (grid == 0) return cudaSuccess;
     const size_t smem = residual_smem_bytes(a.N, shape);
     switch (shape) {
-    case 1: launch_residual_shape<1>(a, full, grid, smem, s); break;
-    case 2: launch_residual_shape<2>(a, full, grid, smem, s); break;
-    case 3: launch_residual_shape<3>(a, full, grid, smem, s); break;
-    default: launch_residual_shape<0>(a, full, grid, smem, s); break;
+    case 1: launch_residual_s<1>(a, full, grid, smem, s); break;
+    case 2: launch_residual_s<2>(a, full, grid, smem, s); break;
+    case 3: launch_residual_s<3>(a, full, grid, smem, s); break;
+    default: launch_residual_s<0>(a, full, grid, smem, s); break;
     }
     return cudaGetLastError();
 }
 
-template <int S>
+template <int S, int P>
 static void launch_batch_residual_shape(const SolveArgs* args, const int2* work, int n, size_t smem, bool full,
                                         cudaStream_t s)
 {
     constexpr int kT = kShapeThreads[S], kB = kShapePix[S];
     if (full)
-        batch_residual_kernel<true, kT, kB><<<n, kT, smem, s>>>(args, work);
+        batch_residual_kernel<true, kT, kB, P><<<n, kT, smem, s>>>(args, work);
     else
-        batch_residual_kernel<false, kT, kB><<<n, kT, smem, s>>>(args, work);
+        batch_residual_kernel<false, kT, kB, P><<<n, kT, smem, s>>>(args, work);
+}
+
+template <int S>
+static void launch_batch_residual_s(const SolveArgs* args, const int2* work, int n, size_t smem, bool full,
+                                    int precision, cudaStream_t s)
+{
+    if (precision == 1) launch_batch_residual_shape<S, 1>(args, work, n, smem, full, s);
+    else if (precision == 2) launch_batch_residual_shape<S, 2>(args, work, n, smem, full, s);
+    else launch_batch_residual_shape<S, 0>(args, work, n, smem, full, s);
 }
 
 cudaError_t launch_batch_residual(const SolveArgs* args_dev, const int2* work_res, int n_work, int max_N, bool full,
-                                  int shape, cudaStream_t s)
+                                  int shape, int precision, cudaStream_t s)
 {
     ensure_residual_attrs();
     if (n_work == 0) return cudaSuccess;
     const size_t smem = residual_smem_bytes(max_N, shape);
     switch (shape) {
-    case 1: launch_batch_residual_shape<1>(args_dev, work_res, n_work, smem, full, s); break;
-    case 2: launch_batch_residual_shape<2>(args_dev, work_res, n_work, smem, full, s); break;
-    case 3: launch_batch_residual_shape<3>(args_dev, work_res, n_work, smem, full, s); break;
-    default: launch_batch_residual_shape<0>(args_dev, work_res, n_work, smem, full, s); break;
+    case 1: launch_batch_residual_s<1>(args_dev, work_res, n_work, smem, full, precision, s); break;
+    case 2: launch_batch_residual_s<2>(args_dev, work_res, n_work, smem, full, precision, s); break;
+    case 3: launch_batch_residual_s<3>(args_dev, work_res, n_work, smem, full, precision, s); break;
+    default: launch_batch_residual_s<0>(args_dev, work_res, n_work, smem, full, precision, s); break;
     }
     return cudaGetLastError();
 }

@@ -1,0 +1,84 @@
+"""16-bit storage of the per-pixel maps (BT_BF16, BT_FP16) against the FP64
+oracle run on the original FP32 inputs.
+
+The arithmetic stays FP32 / FP64; only the stored points and normals are
+rounded (depth as an offset from the frame's mean valid depth).  FP16 keeps 11
+significand bits (~5e-4 relative: ~0.03-0.07 mm on the stored coordinates),
+BF16 8 bits (~4e-3: ~0.2-0.6 mm), against 1 mm depth noise, so the final
+energy moves by well under the noise floor for FP16 and by a visible fraction
+for BF16.  The bounds below are sanity bounds; the measured errors are printed
+as a table (run pytest with -s).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synthgen as S
+
+pytestmark = pytest.mark.gpu
+
+BOUNDS = {  # dtype: (rel cost, rad, m)
+    "fp16": (0.02, 2e-3, 2e-4),
+    "bf16": (0.5, 2e-2, 2e-3),
+}
+
+
+@pytest.fixture(scope="module")
+def bt():
+    from paper_2108_00516_gb300 import build as lbuild
+    lbuild.build()
+    from paper_2108_00516_gb300 import bt as _bt
+    _bt.load()
+    return _bt
+
+
+def pose_err(A, B):
+    rot = max(S.rotation_angle(a[:3, :3] @ b[:3, :3].T) for a, b in zip(A, B))
+    tr = max(np.abs(a[:3, 3] - b[:3, 3]).max() for a, b in zip(A, B))
+    return rot, tr
+
+
+@pytest.fixture(scope="module")
+def cases():
+    return [("tiny-%d" % k, S.tiny_graph(k), 7) for k in range(3)] + [("paper-0", S.paper_graph(0), 10)]
+
+
+def test_precision_error_table(bt, cases):
+    rows = []
+    for name, g, iters in cases:
+        ro = O.solve(g, iters)
+        for dtype, code in (("fp32", bt.BT_FP32), ("fp16", bt.BT_FP16), ("bf16", bt.BT_BF16)):
+            cfg = bt.config_default()
+            cfg.precision = code
+            pg = bt.graph_from_synth(g, config=cfg)
+            P, rep = pg.solve(iters)
+            pg.close()
+            rel = abs(rep["cost_final"] - ro["cost_final"]) / ro["cost_final"]
+            rot, tr = pose_err(P, ro["poses"])
+            rows.append((name, dtype, rel, rot, tr))
+            if dtype in BOUNDS:
+                b = BOUNDS[dtype]
+                assert rel <= b[0] and rot <= b[1] and tr <= b[2], (name, dtype, rel, rot, tr)
+    print("\n| graph | storage | rel. final cost vs FP64 oracle | pose rad | pose m |")
+    print("|---|---|---|---|---|")
+    for r in rows:
+        print("| %s | %s | %.2e | %.2e | %.2e |" % r)
+
+
+def test_half_storage_batches_and_rejects_mixing(bt):
+    g = S.tiny_graph(1)
+    cfg = bt.config_default()
+    cfg.precision = bt.BT_FP16
+    a = bt.graph_from_synth(g, config=cfg)
+    b = bt.graph_from_synth(S.tiny_graph(2), config=cfg)
+    batch = bt.Batch()
+    batch.add(a)
+    batch.add(b)
+    batch.set_shape(0)
+    reps = batch.solve(4)
+    single = bt.graph_from_synth(g, config=cfg)
+    P, rep = single.solve(4)
+    assert np.array_equal(a.get_poses(), P) and reps[0]["cost_final"] == rep["cost_final"]
+    c = bt.graph_from_synth(S.tiny_graph(3))      # FP32 storage
+    with pytest.raises(bt.BTError):
+        batch.add(c)
