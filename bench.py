@@ -43,6 +43,7 @@ WORKLOAD = ("paper-shaped sequence: 300 frames 640x480 fx=fy=600, coverage 15-30
             "500 matches/pair (20% outliers), greedy keyframes <= 9 + current, 10-deg pool rule, "
             "10 GN iterations per solve from 5 deg / 1 cm")
 BYTES_PER_PIXEL_PAIR = 32      # source depth+normal 16 B + target depth+normal 16 B (FP32)
+HALF_BYTES_PER_PIXEL_PAIR = 16  # the same four values per side in 16 bits (BT_FP16 / BT_BF16 storage)
 BYTES_PER_SPARSE_PAIR = 24     # two FP32 3-vectors
 L2_FLUSH_BYTES = 512 << 20
 
@@ -180,7 +181,7 @@ def ncu_traffic_per_pixel_pair():
     """DRAM bytes per dense pixel-pair of the residual kernel from the committed
     ncu summary, if it was taken from the current kernel source."""
     summ = ROOT / "profiles" / "residual_kernel_paper_sequence.md"
-    src = ROOT / "paper_2108_00516_gb300" / "csrc" / "bt_kernels.cu"
+    src = ROOT / "paper_2108_00516_gb300" / "csrc" / "bt_residual.cu"
     try:
         text = summ.read_text()
         sha = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
@@ -278,6 +279,11 @@ def run_batched(bt, graphs_b, stream, args):
     batch.close()
     for pg in pgs:
         pg.close()
+    storage = {"fp32": {"batched_solves_per_s": round(len(pgs) / t_batch, 2), "pass_us": round(us, 1),
+                        "bytes_per_pixel_pair": BYTES_PER_PIXEL_PAIR,
+                        "frac": round(achieved / peak, 4) if achieved else None}}
+    for name, code in (("fp16", bt.BT_FP16), ("bf16", bt.BT_BF16)):
+        storage[name] = run_storage(bt, graphs_b, inits, stream, args, code, reps, peak)
     return {"workload": BATCH_WORKLOAD, "graphs": len(graphs_b),
             "frames": sum(g.n for g in graphs_b), "device_bytes_approx": nbytes,
             "plain_solves_per_s": round(len(pgs) / t_plain, 2),
@@ -290,7 +296,51 @@ def run_batched(bt, graphs_b, stream, args):
                                   "frac": round(achieved / peak, 4) if achieved else None,
                                   "pixel_pairs_per_pass": int(px_pass),
                                   "pass_us": round(us, 1), "peak_kind": peak_kind},
-            "pixel_pairs_per_s": round(px_pass * it / t_batch, 1)}
+            "pixel_pairs_per_s": round(px_pass * it / t_batch, 1),
+            "storage": storage}
+
+
+def run_storage(bt, graphs_b, inits, stream, args, code, ref_reps, peak):
+    """The batched solve with the per-pixel maps stored in 16 bits (FP32
+    arithmetic): solves/s, residual-pass roofline at the half-storage
+    algorithmic bytes, and the final cost against the FP32-storage batch."""
+    import torch
+    it = args.iters
+    cfg = bt.config_default()
+    cfg.precision = code
+    pgs = [bt.graph_from_synth(g, config=cfg, stream=stream) for g in graphs_b]
+
+    def reset():
+        for pg, P in zip(pgs, inits):
+            pg.set_poses(P)
+
+    batch = bt.Batch(stream=stream)
+    for pg in pgs:
+        batch.add(pg)
+    reset()
+    batch.solve(it)                            # autotune + capture
+    reset()
+    batch.solve(it)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(args.batch_steps):
+        reset()
+        reps = batch.solve(it)
+    torch.cuda.synchronize()
+    t = (time.perf_counter() - t0) / args.batch_steps
+    shape, tune_us = batch.tuning()
+    us = tune_us[shape]
+    px_pass = sum(r["dense_pixel_pairs"] for r in reps) / max(1, it)
+    achieved = HALF_BYTES_PER_PIXEL_PAIR * px_pass / (us * 1e-6) / 1e9 if us > 0 else None
+    rel = [abs(r["cost_final"] - c["cost_final"]) / c["cost_final"] for r, c in zip(reps, ref_reps)]
+    batch.close()
+    for pg in pgs:
+        pg.close()
+    return {"batched_solves_per_s": round(len(graphs_b) / t, 2), "cta_shape": shape, "pass_us": round(us, 1),
+            "bytes_per_pixel_pair": HALF_BYTES_PER_PIXEL_PAIR,
+            "achieved_gbs": round(achieved, 1) if achieved else None,
+            "frac": round(achieved / peak, 4) if achieved else None,
+            "final_cost_rel_vs_fp32": {"max": float(max(rel)), "median": float(sorted(rel)[len(rel) // 2])}}
 
 
 def run_ours(args):

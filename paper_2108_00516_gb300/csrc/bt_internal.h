@@ -137,5 +137,6 @@ cudaError_t launch_batch_solve(const SolveArgs* args_dev, int n_graphs, size_t s
                                cudaStream_t s);
 // Sets every kernel's shared-memory attribute (call before a stream capture).
 void prepare_launch_attributes();
+void prepare_residual_attributes();
 
 }  // namespace bt

@@ -1,20 +1,17 @@
-// bt_kernels.cu -- sm_103a kernels of the pose-graph hot path (BundleTrack,
-// Sec. IV-D, Eq. 1-3).
+// bt_residual.cu -- sm_103a kernels of the pose-graph hot path (BundleTrack,
+// Sec. IV-D, Eq. 1-3): frame preparation and the residual pass.
 //
 //   prep_*          frame preparation: per-pixel target map (z, n) and the
 //                   compacted list of valid masked source pixels (pi_D^-1).
 //   residual_kernel one launch per Gauss-Newton iteration: CTAs [0, E) take
 //                   one correspondence set each (Eq. 2), CTAs [E, E+T) stage
-//                   one tile of 1024 source pixels in shared memory and loop
-//                   over every target node (Eq. 3): association, gates,
+//                   one tile of source pixels in shared memory and loop over
+//                   every target node (Eq. 3): association, gates,
 //                   point-to-plane residual, Jacobian, Huber weight, and a
 //                   deterministic reduction of the 21 + 6 unique J^T W J /
 //                   J^T W r terms per (tile, target).
-//   reduce_kernel   one CTA per unordered node pair turns the FP32 partials of
-//                   both directions and the pair's correspondence set into
-//                   FP64 6x6 blocks; the last CTA to finish assembles the
-//                   normal equations over the free nodes, runs the FP64
-//                   Cholesky solve and the FP64 se(3) update.
+//
+// The reduction into FP64 blocks, the solve and the update are in bt_solve.cu.
 //
 // Perturbations.  The library solves for right perturbations,
 // T_i <- T_i exp(d_i) with d = (v, w).  This is a linear change of tangent
@@ -240,56 +237,6 @@ cudaError_t launch_prep(const float* depth, const float* normals, const uint8_t*
     else
         prep_write_kernel<0><<<nblk, kThreads, 0, s>>>(depth, normals, mask, W, HW, cx, cy, ifx, ify, blockcnt, out2,
                                                        tgt, src_p, src_n);
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Single-precision transforms of the FP64 poses.  M = T_j T_i^-1 is formed in
-// FP64 without FMA contraction, products and sums in a fixed order, so that
-// its rounding to single precision is reproducible bit for bit.
-// ---------------------------------------------------------------------------
-
-// Writes xf[i*N+j] = float(T_j T_i^-1) and xinv[i] = float(T_i^-1) with the
-// threads of one CTA, one matrix entry per thread (the FP64 inverse first, then
-// the products).  `tinv` is shared scratch of 12 * N doubles.
-__device__ void write_xforms(const SolveArgs& a, double* __restrict__ tinv, const double* __restrict__ pose)
-{
-    const int N = a.N, tid = threadIdx.x, nt = blockDim.x;
-    for (int id = tid; id < N * 12; id += nt) {
-        const int i = id / 12, e = id % 12, r = e / 4, c = e % 4;
-        const double* T = pose + i * 12;
-        double v;
-        if (c < 3) {
-            v = T[c * 4 + r];
-        } else {
-            v = -__dadd_rn(__dadd_rn(__dmul_rn(T[0 * 4 + r], T[3]), __dmul_rn(T[1 * 4 + r], T[7])),
-                           __dmul_rn(T[2 * 4 + r], T[11]));
-        }
-        tinv[id] = v;
-        a.xinv[id] = __double2float_rn(v);
-    }
-    __syncthreads();
-    for (int id = tid; id < N * N * 12; id += nt) {
-        const int pr = id / 12, e = id % 12, r = e / 4, c = e % 4;
-        const int i = pr / N, j = pr % N;
-        const double* A = pose + j * 12;     // T_j
-        const double* B = tinv + i * 12;     // T_i^-1
-        double s = __dadd_rn(__dadd_rn(__dmul_rn(A[r * 4 + 0], B[0 * 4 + c]), __dmul_rn(A[r * 4 + 1], B[1 * 4 + c])),
-                             __dmul_rn(A[r * 4 + 2], B[2 * 4 + c]));
-        if (c == 3) s = __dadd_rn(s, A[r * 4 + 3]);
-        a.xf[id] = __double2float_rn(s);
-    }
-}
-
-__global__ void xform_kernel(SolveArgs a)
-{
-    __shared__ double tinv[12 * kMaxNodes];
-    write_xforms(a, tinv, a.pose);
-}
-
-cudaError_t launch_xforms(const SolveArgs& a, cudaStream_t s)
-{
-    xform_kernel<<<1, kThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -747,652 +694,6 @@ cudaError_t launch_batch_residual(const SolveArgs* args_dev, const int2* work_re
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// Reduce / assemble / solve / update
-// ---------------------------------------------------------------------------
-
-__device__ __forceinline__ int sym_idx(int r, int c)
-{
-    // index of (min, max) in the row-major upper triangle of a 6x6 matrix
-    const int a = r < c ? r : c, b = r < c ? c : r;
-    return a * 6 - (a * (a - 1)) / 2 + (b - a);
-}
-
-__device__ __forceinline__ int upair_index(int a, int b, int N)
-{
-    // a < b, lexicographic order of the unordered pairs
-    return a * N - (a * (a + 1)) / 2 + (b - a - 1);
-}
-
-// Entry (r, c) of Ad_T = [[R, [t]x R], [0, R]] for a 3x4 pose T.
-__device__ __forceinline__ double ad_entry(const double* T, int r, int c)
-{
-    if (r >= 3 && c < 3) return 0.0;
-    if (r < 3 && c < 3) return T[r * 4 + c];
-    if (r >= 3 && c >= 3) return T[(r - 3) * 4 + (c - 3)];
-    const double tx = T[3], ty = T[7], tz = T[11];
-    const int cc = c - 3;
-    const double R0 = T[0 * 4 + cc], R1 = T[1 * 4 + cc], R2 = T[2 * 4 + cc];
-    if (r == 0) return -tz * R1 + ty * R2;
-    if (r == 1) return tz * R0 - tx * R2;
-    return -ty * R0 + tx * R1;
-}
-
-// Right-perturbation blocks of a correspondence set from its moments m (see
-// sparse_edge), J_i = -S(a), J_j = S(b), S(x) = [I | -[x]x]:
-//   H_ii = [[W I, -[sa]x], [[sa]x, tr(Saa) I - Saa]]
-//   H_jj = [[W I, -[sb]x], [[sb]x, tr(Sbb) I - Sbb]]
-//   H_ij = -[[W I, -[sb]x], [[sa]x, tr(Sba) I - Sba]]
-// which: 0 = ii, 1 = jj, 2 = ij.
-__device__ __forceinline__ double skew_entry(const double* x, int r, int c)
-{
-    if (r == c) return 0.0;
-    if (r == 0) return c == 1 ? -x[2] : x[1];
-    if (r == 1) return c == 0 ? x[2] : -x[0];
-    return c == 0 ? -x[1] : x[0];
-}
-
-__device__ double sparse_block(const double* m, int which, int r, int c)
-{
-    const double W = m[0];
-    const double* sa = m + 1;
-    const double* sb = m + 4;
-    const double* s_row = which == 1 ? sb : sa;
-    const double* s_col = which == 0 ? sa : sb;
-    double v;
-    if (r < 3 && c < 3) {
-        v = r == c ? W : 0.0;
-    } else if (r < 3) {
-        v = -skew_entry(s_col, r, c - 3);
-    } else if (c < 3) {
-        v = skew_entry(s_row, r - 3, c);
-    } else {
-        const int a3 = r - 3, b3 = c - 3;
-        double tr, sv;
-        if (which == 2) {
-            tr = m[19] + m[23] + m[27];
-            sv = m[19 + a3 * 3 + b3];
-        } else {
-            const int base = which == 0 ? 7 : 13;   // (xx xy xz yy yz zz)
-            tr = m[base + 0] + m[base + 3] + m[base + 5];
-            const int lo = a3 < b3 ? a3 : b3, hi = a3 < b3 ? b3 : a3;
-            const int id = lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);
-            sv = m[base + id];
-        }
-        v = (a3 == b3 ? tr : 0.0) - sv;
-    }
-    return which == 2 ? -v : v;
-}
-
-// Second stage of an unordered pair {A < B}: FP64 sums of the tile partials of
-// both directions, K' = Ad_{T_dst}^T K Ad_{T_dst} and g' = Ad_{T_dst}^T g~ for
-// each (camera-j left blocks -> right perturbations), plus the pair's
-// correspondence set; written pre-combined:
-//   D_A = S + H_AA, D_B = S + H_BB, O_AB = -S + H_AB, g_A = gd + g_A^s,
-//   g_B = -gd + g_B^s with S = lambda_2 (K'_{A->B} + K'_{B->A}) and
-//   gd = lambda_2 (g'_{A->B} - g'_{B->A}).
-template <bool kFull>
-__device__ void reduce_upair(const SolveArgs& a, int u, double* sm)
-{
-    const int N = a.N;
-    const int2 ab = a.upairs[u];
-    const int A = ab.x, B = ab.y;
-    const int e = a.upair_edge[u];
-    const int tid = threadIdx.x;
-    const int dir = tid >> 7, v = tid & 31, grp = (tid >> 5) & 3;
-    const int src = dir ? B : A, dst = dir ? A : B;
-    const int jj = dst < src ? dst : dst - 1;
-    const NodeDev Ns = a.nodes[src];
-    double s = 0.0;
-    if (kFull || v == 27 || v == 28)
-        for (int t = Ns.tile0 + grp; t < Ns.tile0 + Ns.ntiles; t += 4)
-            s += (double)a.dpart[((size_t)t * (N - 1) + jj) * kDenseVals + v];
-    sm[tid] = s;
-    __syncthreads();
-    double* tot = sm + 256;   // [2][32]
-    if (tid < 64) {
-        const int d = tid >> 5, w = tid & 31;
-        tot[tid] = ((sm[d * 128 + w] + sm[d * 128 + 32 + w]) + sm[d * 128 + 64 + w]) + sm[d * 128 + 96 + w];
-    }
-    __syncthreads();
-    double* out = a.upairblk + (size_t)u * kUPairBlk;
-    const double lg = a.lambda_dense, ls = 2.0 * a.lambda_sparse;
-    if (!kFull) {
-        if (tid == 0) {
-            out[90] = lg * (tot[27] + tot[32 + 27]);
-            out[91] = e >= 0 ? ls * (double)a.spart[(size_t)e * kSparseVals + 37] : 0.0;
-            out[92] = tot[28] + tot[32 + 28];
-        }
-        return;
-    }
-    double* Ad = sm + 320;   // [2][36]: Ad_{T_B} for A->B, Ad_{T_A} for B->A
-    double* K = sm + 392;    // [2][36]
-    double* KA = sm + 464;   // [2][36]
-    double* mo = sm + 536;   // 40 sparse moments
-    double* S = sm + 576;    // [36]
-    double* gd = sm + 612;   // [6]
-    if (tid < 72) {
-        const int d = tid / 36, q = tid % 36, r = q / 6, c = q % 6;
-        Ad[tid] = ad_entry(a.pose + (d ? A : B) * 12, r, c);
-        K[tid] = tot[d * 32 + sym_idx(r, c)];
-    } else if (tid >= 128 && tid < 128 + kSparseVals) {
-        mo[tid - 128] = e >= 0 ? (double)a.spart[(size_t)e * kSparseVals + tid - 128] : 0.0;
-    }
-    __syncthreads();
-    if (tid < 72) {
-        const int d = tid / 36, q = tid % 36, r = q / 6, c = q % 6;
-        double x = 0.0;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) x += K[d * 36 + r * 6 + k] * Ad[d * 36 + k * 6 + c];
-        KA[tid] = x;
-    }
-    __syncthreads();
-    if (tid < 36) {
-        const int r = tid / 6, c = tid % 6;
-        if (c >= r) {
-            double x0 = 0.0, x1 = 0.0;
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                x0 += Ad[k * 6 + r] * KA[k * 6 + c];
-                x1 += Ad[36 + k * 6 + r] * KA[36 + k * 6 + c];
-            }
-            S[r * 6 + c] = S[c * 6 + r] = lg * (x0 + x1);
-        }
-    } else if (tid < 42) {
-        const int r = tid - 36;
-        double g0 = 0.0, g1 = 0.0;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            g0 += Ad[k * 6 + r] * tot[21 + k];
-            g1 += Ad[36 + k * 6 + r] * tot[32 + 21 + k];
-        }
-        gd[r] = lg * (g0 - g1);
-    }
-    __syncthreads();
-    const bool has = e >= 0;
-    const bool fwd = has && a.edges[e].i == A;   // correspondence set stored as (A, B)
-    if (tid < 36) {
-        const int r = tid / 6, c = tid % 6;
-        double hAA = 0.0, hBB = 0.0, hAB = 0.0;
-        if (has) {
-            hAA = ls * sparse_block(mo, fwd ? 0 : 1, r, c);
-            hBB = ls * sparse_block(mo, fwd ? 1 : 0, r, c);
-            hAB = ls * (fwd ? sparse_block(mo, 2, r, c) : sparse_block(mo, 2, c, r));
-        }
-        if (c >= r) {
-            out[sym_idx(r, c)] = S[tid] + hAA;
-            out[21 + sym_idx(r, c)] = S[tid] + hBB;
-        }
-        out[42 + tid] = -S[tid] + hAB;
-    } else if (tid < 42) {
-        const int r = tid - 36;
-        // g_i = -[sum w e; sum w a x e], g_j = [sum w e; sum w b x e]
-        const double gi = has ? -ls * (r < 3 ? mo[28 + r] : mo[31 + r - 3]) : 0.0;
-        const double gj = has ? ls * (r < 3 ? mo[28 + r] : mo[34 + r - 3]) : 0.0;
-        out[78 + r] = gd[r] + (fwd ? gi : gj);
-        out[84 + r] = -gd[r] + (fwd ? gj : gi);
-    } else if (tid == 42) {
-        out[90] = lg * (tot[27] + tot[32 + 27]);
-        out[91] = has ? ls * mo[37] : 0.0;
-        out[92] = tot[28] + tot[32 + 28];
-    }
-}
-
-// SE(3) exponential of xi = (v, w) as a 3x4 matrix: R = I + A W + B W^2,
-// t = (I + B W + C W^2) v with A = sin(th)/th, B = (1 - cos th)/th^2,
-// C = (th - sin th)/th^3.  Below th = 0.1 the coefficients come from their
-// Taylor series through th^8 (truncation < 3e-18), which keeps the FP64
-// dependency chain short; above it from sincos.
-__device__ void se3_exp_d(const double* xi, double* E)
-{
-    const double wx = xi[3], wy = xi[4], wz = xi[5];
-    const double th2 = wx * wx + wy * wy + wz * wz;
-    double A, B, C;
-    if (th2 < 0.01) {
-        A = 1.0 + th2 * (-1.0 / 6.0 + th2 * (1.0 / 120.0 + th2 * (-1.0 / 5040.0 + th2 * (1.0 / 362880.0))));
-        B = 0.5 + th2 * (-1.0 / 24.0 + th2 * (1.0 / 720.0 + th2 * (-1.0 / 40320.0 + th2 * (1.0 / 3628800.0))));
-        C = 1.0 / 6.0 + th2 * (-1.0 / 120.0 + th2 * (1.0 / 5040.0 + th2 * (-1.0 / 362880.0 + th2 * (1.0 / 39916800.0))));
-    } else {
-        const double th = sqrt(th2);
-        double sn, cs;
-        sincos(th, &sn, &cs);
-        A = sn / th;
-        B = (1.0 - cs) / th2;
-        C = (th - sn) / (th2 * th);
-    }
-    const double W[9] = {0.0, -wz, wy, wz, 0.0, -wx, -wy, wx, 0.0};
-    double W2[9];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-            W2[r * 3 + c] = W[r * 3 + 0] * W[0 * 3 + c] + W[r * 3 + 1] * W[1 * 3 + c] + W[r * 3 + 2] * W[2 * 3 + c];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        double t = 0.0;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const double id = r == c ? 1.0 : 0.0;
-            E[r * 4 + c] = id + A * W[r * 3 + c] + B * W2[r * 3 + c];
-            t += (id + B * W[r * 3 + c] + C * W2[r * 3 + c]) * xi[c];
-        }
-        E[r * 4 + 3] = t;
-    }
-}
-
-// 1/d for a positive FP64 pivot: the hardware approximation (rcp.approx.f64)
-// refined by two Newton steps r <- r + r (1 - d r), each exact to FMA
-// rounding; a shorter dependency chain than a correctly rounded division.
-__device__ __forceinline__ double rcp_fp64(double d)
-{
-    double r;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
-    double e = fma(-d, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-d, r, 1.0);
-    return fma(r, e, r);
-}
-
-// Last CTA: energies, then (full) assembly of H and g over the free nodes and
-// the FP64 solve of H dx = -g by the square-root-free Cholesky factorisation
-// H = L D L^T (right-looking, two barriers per column, the forward
-// substitution L z = -g carried along), D w = z, L^T dx = w, and finally
-// T <- T exp(dx).  On GB300 a dependent FP64 operation costs ~64 cycles, so
-// the loop is arranged for short dependency chains: each pivot reciprocal is
-// formed by the thread that finishes that diagonal entry, and the column is
-// scaled while a copy of its unscaled values feeds the trailing update.
-template <bool kFull>
-__device__ void final_phase(const SolveArgs& a, int iter, double* sm)
-{
-    const int N = a.N, U = a.n_upairs;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
-    if (tid < 32) {
-        double ed = 0.0, es = 0.0, cnt = 0.0;
-        for (int u = lane; u < U; u += 32) {
-            const double* o = a.upairblk + (size_t)u * kUPairBlk;
-            ed += __ldcg(o + 90);
-            es += __ldcg(o + 91);
-            cnt += __ldcg(o + 92);
-        }
-#pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) {
-            ed += __shfl_xor_sync(0xffffffffu, ed, off);
-            es += __shfl_xor_sync(0xffffffffu, es, off);
-            cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
-        }
-        if (lane == 0) {
-            a.costs[iter * 4 + 0] = ed + es;
-            a.costs[iter * 4 + 1] = ed;
-            a.costs[iter * 4 + 2] = es;
-            a.costs[iter * 4 + 3] = cnt;
-        }
-    }
-    if (!kFull) return;
-    const int nf = a.n_free, n = 6 * nf;
-    if (n == 0) return;
-    const int status0 = *(volatile int*)&a.ctrl->status;
-    if (status0 != 0) return;
-    unsigned long long t0 = clock64();
-    const int ld = n + 1;        // odd leading dimension: conflict-free FP64 rows
-    double* H = sm;              // n*ld: lower triangle H, then L^T in the upper triangle
-    double* y = H + n * ld;      // n
-    double* rD = y + n;          // n: 1 / D_k
-    double* ps = rD + n;         // 12 * N poses
-    double* tinv = ps + 12 * kMaxNodes;   // 12 * N
-    // tinv + 12 * kMaxNodes: [2][n] scaled columns, then the triangle index
-    // table (n (n+1) / 2 ints, rounded up to whole doubles), then the staged
-    // pair blocks
-    const size_t tab_dbl = ((size_t)n * (n + 1) / 2 + 1) / 2;
-    double* stage = tinv + 12 * kMaxNodes + 2 * n + tab_dbl;
-    if (((size_t)(stage - sm)) & 1) ++stage;               // 16-byte alignment for double2
-    const size_t stage_len = a.stage_blocks ? (size_t)U * kUPairBlk : 0;
-    int* node_of = reinterpret_cast<int*>(stage + stage_len);
-    __shared__ int s_fail;
-    for (int k = tid; k < N; k += nt) {
-        const int f = a.nodes[k].free_idx;
-        if (f >= 0) node_of[f] = k;
-    }
-    for (int q = tid; q < 12 * N; q += nt) ps[q] = a.pose[q];
-    if (tid == 0) s_fail = 0;
-    {
-        const double2* src = reinterpret_cast<const double2*>(a.upairblk);
-        double2* dst = reinterpret_cast<double2*>(stage);
-        const int n2 = (int)(stage_len / 2);
-#pragma unroll 4
-        for (int q = tid; q < n2; q += nt) dst[q] = __ldcg(src + q);
-    }
-    __syncthreads();
-    const bool staged = a.stage_blocks != 0;
-    auto blk = [&](size_t q) { return staged ? stage[q] : __ldcg(a.upairblk + q); };
-    // diagonal blocks and gradient: one warp per free node, lanes 0-20 the
-    // unique block entries, lanes 21-26 the gradient entries
-    for (int f = warp; f < nf; f += nt / 32) {
-        const int A = node_of[f];
-        if (lane < 27) {
-            double s0 = 0.0, s1 = 0.0;
-            for (int k = 0; k < N; ++k) {
-                if (k == A) continue;
-                const int u = A < k ? upair_index(A, k, N) : upair_index(k, A, N);
-                const size_t off = (size_t)u * kUPairBlk +
-                                   (lane < 21 ? (A < k ? 0 : 21) + lane : (A < k ? 78 : 84) + lane - 21);
-                if (k & 1) s1 += blk(off); else s0 += blk(off);
-            }
-            const double s = s0 + s1;
-            if (lane < 21) {
-                int r = 0, q = lane;
-                while (q >= 6 - r) { q -= 6 - r; ++r; }
-                const int c = r + q;     // (r, c), c >= r, of the 6x6 block
-                H[(6 * f + c) * ld + 6 * f + r] = s;
-            } else {
-                y[6 * f + lane - 21] = -s;   // right-hand side of H dx = -g
-            }
-        }
-    }
-    // off-diagonal blocks (fa > fb)
-    const int nob = nf * (nf - 1) / 2;
-    for (int q = tid; q < nob * 36; q += nt) {
-        const int b = q / 36, e = q % 36, rr = e / 6, cc = e % 6;
-        int fa = 1, rem = b;
-        while (rem >= fa) { rem -= fa; ++fa; }
-        const int fb = rem;
-        const int A = node_of[fa], B = node_of[fb];
-        const int u = A < B ? upair_index(A, B, N) : upair_index(B, A, N);
-        H[(6 * fa + rr) * ld + 6 * fb + cc] = blk((size_t)u * kUPairBlk + 42 + (A < B ? rr * 6 + cc : cc * 6 + rr));
-    }
-    __syncthreads();
-    unsigned long long t1 = clock64();
-    // LDL^T with a one-column look-ahead, one barrier per column.  At step k
-    // warp 0 prepares column k+1 -- its update by column k, the pivot
-    // D_{k+1} and reciprocal, and the scaled l_{i,k+1} -- while warps
-    // {1,2,3,5,6,7} (no FP64 pipe shared with warp 0) apply column k to the
-    // trailing triangle of rows and columns >= k+2 and carry the forward
-    // substitution.  The scaled column is double-buffered; L is stored
-    // transposed in the upper triangle, L_ik at (k, i).
-    double* colb = tinv + 12 * kMaxNodes;   // [2][n]
-    int* tab = reinterpret_cast<int*>(colb + 2 * n);
-    for (int ip = tid; ip < n; ip += nt)
-        for (int jp = 0; jp <= ip; ++jp) tab[ip * (ip + 1) / 2 + jp] = (ip << 16) | jp;
-    if (warp == 0) {
-        double r = 0.0;
-        if (lane == 0) {
-            const double d = H[0];
-            if (!(d > 0.0)) s_fail = 1; else r = rcp_fp64(d);
-            rD[0] = r;
-        }
-        r = __shfl_sync(0xffffffffu, r, 0);
-        for (int i = 1 + lane; i < n; i += 32) {
-            const double l = H[i * ld] * r;
-            colb[i] = l;
-            H[i] = l;
-        }
-    }
-    __syncthreads();
-    const bool bulk = warp != 0 && warp != 4 && warp < 8;
-    const int nbulk = (nt / 32 >= 8 ? 6 : 0) * 32;
-    const int bt = bulk ? (warp < 4 ? warp - 1 : warp - 2) * 32 + lane : -1;
-    for (int k = 0; k < n - 1; ++k) {
-        if (s_fail) break;
-        const double* ck = colb + (k & 1) * n;        // l_{i,k}
-        double* cn = colb + ((k + 1) & 1) * n;        // l_{i,k+1}, written now
-        if (warp == 0) {
-            const int p = k + 1;
-            const double hpk = H[p * ld + k];         // unscaled H_{k+1,k}
-            double rp = 0.0;
-            if (lane == 0) {
-                const double h = H[p * ld + p] - ck[p] * hpk;
-                H[p * ld + p] = h;
-                if (!(h > 0.0)) s_fail = 1; else rp = rcp_fp64(h);
-                rD[p] = rp;
-            }
-            constexpr int kRows = (6 * (kMaxNodes - 1) + 31) / 32;
-            double u[kRows];
-#pragma unroll
-            for (int q = 0; q < kRows; ++q) {
-                const int i = p + 1 + lane + 32 * q;
-                if (i < n) {
-                    u[q] = H[i * ld + p] - ck[i] * hpk;
-                    H[i * ld + p] = u[q];
-                }
-            }
-            rp = __shfl_sync(0xffffffffu, rp, 0);
-#pragma unroll
-            for (int q = 0; q < kRows; ++q) {
-                const int i = p + 1 + lane + 32 * q;
-                if (i < n) {
-                    const double l = u[q] * rp;
-                    cn[i] = l;
-                    H[p * ld + i] = l;
-                }
-            }
-        } else if (bulk) {
-            const int m1 = n - k - 2, tri = m1 * (m1 + 1) / 2;
-            const double zk = y[k];
-            for (int i = k + 1 + bt; i < n; i += nbulk) y[i] -= ck[i] * zk;
-            int t = bt;
-            for (; t + nbulk < tri; t += 2 * nbulk) {
-                const int e0 = tab[t], e1 = tab[t + nbulk];
-                const int i0 = k + 2 + (e0 >> 16), j0 = k + 2 + (e0 & 0xffff);
-                const int i1 = k + 2 + (e1 >> 16), j1 = k + 2 + (e1 & 0xffff);
-                const double a0 = H[i0 * ld + j0], a1 = H[i1 * ld + j1];
-                const double l0 = ck[i0], l1 = ck[i1];
-                const double b0 = H[j0 * ld + k], b1 = H[j1 * ld + k];
-                H[i0 * ld + j0] = a0 - l0 * b0;
-                H[i1 * ld + j1] = a1 - l1 * b1;
-            }
-            for (; t < tri; t += nbulk) {
-                const int e = tab[t];
-                const int i = k + 2 + (e >> 16), j = k + 2 + (e & 0xffff);
-                H[i * ld + j] -= ck[i] * H[j * ld + k];
-            }
-        }
-        __syncthreads();
-    }
-    if (s_fail) {
-        if (tid == 0) a.ctrl->status = -4;
-        return;
-    }
-    for (int i = tid; i < n; i += nt) y[i] *= rD[i];   // D w = z
-    __syncthreads();
-    unsigned long long t2 = clock64();
-    // L^T dx = w, unit diagonal (one warp; L_ki is stored at (i, k)).  Lane l
-    // keeps w_i for i = l, l + 32, ... in registers; x_k is broadcast from its
-    // owner with a shuffle, so each step is one shuffle and one FMA deep.
-    if (tid < 32) {
-        constexpr int kSlots = (6 * (kMaxNodes - 1) + 31) / 32;
-        double w[kSlots];
-#pragma unroll
-        for (int q = 0; q < kSlots; ++q) {
-            const int i = lane + 32 * q;
-            w[q] = i < n ? y[i] : 0.0;
-        }
-        for (int k = n - 1; k >= 1; --k) {
-            const int slot = k >> 5, owner = k & 31;
-            double v;
-            switch (slot) {     // warp-uniform
-            case 0: v = w[0]; break;
-            case 1: v = w[1]; break;
-            case 2: v = w[2]; break;
-            case 3: v = w[3]; break;
-            default: v = w[kSlots - 1]; break;
-            }
-            const double xk = __shfl_sync(0xffffffffu, v, owner);
-#pragma unroll
-            for (int q = 0; q < kSlots; ++q) {
-                if (32 * q >= k) break;      // warp-uniform
-                const int i = lane + 32 * q;
-                if (i < k) w[q] -= H[i * ld + k] * xk;
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < kSlots; ++q) {
-            const int i = lane + 32 * q;
-            if (i < n) y[i] = w[q];
-        }
-    }
-    __syncthreads();
-    unsigned long long t3 = clock64();
-    // T_A <- T_A exp(dx_A)
-    if (tid < nf) {
-        const int A = node_of[tid];
-        double E[12], T[12];
-        se3_exp_d(y + 6 * tid, E);
-#pragma unroll
-        for (int k = 0; k < 12; ++k) T[k] = ps[A * 12 + k];
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                double s = T[r * 4 + 0] * E[0 * 4 + c] + T[r * 4 + 1] * E[1 * 4 + c] + T[r * 4 + 2] * E[2 * 4 + c];
-                if (c == 3) s += T[r * 4 + 3];
-                ps[A * 12 + r * 4 + c] = s;
-            }
-        }
-    }
-    __syncthreads();
-    for (int q = tid; q < 12 * N; q += nt) a.pose[q] = ps[q];
-    write_xforms(a, tinv, ps);
-    if (tid == 0) {
-        unsigned long long t4 = clock64();
-        a.ctrl->clk[0] += t1 - t0;
-        a.ctrl->clk[1] += t2 - t1;
-        a.ctrl->clk[2] += t3 - t2;
-        a.ctrl->clk[3] += t4 - t3;
-    }
-}
-
-template <bool kFull>
-__global__ void __launch_bounds__(kThreads) reduce_kernel(SolveArgs a, int iter)
-{
-    extern __shared__ double sm[];
-    __shared__ int s_last;
-    const int b = blockIdx.x;
-    if (b < a.n_upairs) reduce_upair<kFull>(a, b, sm);
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned t = atomicAdd(&a.ctrl->counter, 1u);
-        s_last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    if (threadIdx.x == 0) a.ctrl->counter = 0u;
-    final_phase<kFull>(a, iter, sm);
-}
-
-static size_t reduce_smem_bytes_for(int n_free, int N, bool stage)
-{
-    const size_t n = 6 * (size_t)n_free;
-    const size_t U = (size_t)N * (N - 1) / 2;
-    const size_t sl = stage ? U * kUPairBlk : 0;
-    const size_t tab_dbl = (n * (n + 1) / 2 + 1) / 2;
-    size_t fin = (n * (n + 1) + 4 * n + 24 * (size_t)kMaxNodes + tab_dbl + 1 + sl) * sizeof(double) +
-                 kMaxNodes * sizeof(int);
-    size_t ph1 = 640 * sizeof(double);
-    return fin > ph1 ? fin : ph1;
-}
-
-bool reduce_stage_fits(int n_free, int N) { return reduce_smem_bytes_for(n_free, N, true) <= kReduceSmemMax; }
-
-size_t reduce_smem_bytes(int n_free, int N)
-{
-    return reduce_smem_bytes_for(n_free, N, reduce_stage_fits(n_free, N));
-}
-
-cudaError_t launch_reduce(const SolveArgs& a, bool full, int iter, cudaStream_t s)
-{
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(reduce_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReduceSmemMax);
-        cudaFuncSetAttribute(reduce_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReduceSmemMax);
-        attr_set = true;
-    }
-    const int grid = a.n_upairs > 0 ? a.n_upairs : 1;
-    const size_t smem = reduce_smem_bytes(a.n_free, a.N);
-    if (full)
-        reduce_kernel<true><<<grid, kThreads, smem, s>>>(a, iter);
-    else
-        reduce_kernel<false><<<grid, kThreads, smem, s>>>(a, iter);
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Batched solver kernels (one CTA per graph or per (graph, pair))
-// ---------------------------------------------------------------------------
-
-__global__ void batch_xform_kernel(const SolveArgs* __restrict__ args)
-{
-    __shared__ double tinv[12 * kMaxNodes];
-    __shared__ SolveArgs sa;
-    if (threadIdx.x == 0) sa = args[blockIdx.x];
-    __syncthreads();
-    write_xforms(sa, tinv, sa.pose);
-}
-
-template <bool kFull>
-__global__ void __launch_bounds__(kThreads) batch_pair_kernel(const SolveArgs* __restrict__ args,
-                                                              const int2* __restrict__ work)
-{
-    __shared__ double sm[640];
-    __shared__ SolveArgs sa;
-    const int2 w = work[blockIdx.x];
-    if (threadIdx.x == 0) sa = args[w.x];
-    __syncthreads();
-    reduce_upair<kFull>(sa, w.y, sm);
-}
-
-template <bool kFull>
-__global__ void __launch_bounds__(kThreads) batch_solve_kernel(const SolveArgs* __restrict__ args, int iter)
-{
-    extern __shared__ double smd[];
-    __shared__ SolveArgs sa;
-    if (threadIdx.x == 0) sa = args[blockIdx.x];
-    __syncthreads();
-    final_phase<kFull>(sa, iter, smd);
-}
-
-cudaError_t launch_batch_xforms(const SolveArgs* args_dev, int n_graphs, cudaStream_t s)
-{
-    if (n_graphs == 0) return cudaSuccess;
-    batch_xform_kernel<<<n_graphs, kThreads, 0, s>>>(args_dev);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_batch_pairs(const SolveArgs* args_dev, const int2* work_pair, int n_work, bool full,
-                               cudaStream_t s)
-{
-    if (n_work == 0) return cudaSuccess;
-    if (full)
-        batch_pair_kernel<true><<<n_work, kThreads, 0, s>>>(args_dev, work_pair);
-    else
-        batch_pair_kernel<false><<<n_work, kThreads, 0, s>>>(args_dev, work_pair);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_batch_solve(const SolveArgs* args_dev, int n_graphs, size_t smem, bool full, int iter,
-                               cudaStream_t s)
-{
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(batch_solve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReduceSmemMax);
-        cudaFuncSetAttribute(batch_solve_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReduceSmemMax);
-        attr_set = true;
-    }
-    if (n_graphs == 0) return cudaSuccess;
-    if (full)
-        batch_solve_kernel<true><<<n_graphs, kThreads, smem, s>>>(args_dev, iter);
-    else
-        batch_solve_kernel<false><<<n_graphs, kThreads, smem, s>>>(args_dev, iter);
-    return cudaGetLastError();
-}
-
-void prepare_launch_attributes()
-{
-    ensure_residual_attrs();
-    cudaFuncSetAttribute(batch_solve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReduceSmemMax);
-    cudaFuncSetAttribute(batch_solve_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReduceSmemMax);
-    cudaFuncSetAttribute(reduce_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReduceSmemMax);
-    cudaFuncSetAttribute(reduce_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReduceSmemMax);
-}
+void prepare_residual_attributes() { ensure_residual_attrs(); }
 
 }  // namespace bt
