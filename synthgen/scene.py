@@ -300,15 +300,17 @@ def coverage(shape: Shape, cam: Camera, T: np.ndarray) -> float:
 
 
 def distance_for_coverage(shape: Shape, cam: Camera, R: np.ndarray, target: float,
-                          lateral: np.ndarray | None = None) -> float:
+                          lateral: np.ndarray | None = None, probe_width: int = 160,
+                          steps: int = 22) -> float:
     """Bisect the object distance so that the mask covers `target` of the image."""
     lo, hi = 0.08, 3.0
     lat = np.zeros(2) if lateral is None else lateral
-    # coverage is (nearly) resolution independent: bisect on a 1/4-scale camera
-    f = max(1, cam.width // 160)
+    # coverage is (nearly) resolution independent: bisect on a camera of at
+    # most probe_width pixels across
+    f = max(1, cam.width // probe_width)
     small = Camera(cam.fx / f, cam.fy / f, (cam.cx + 0.5) / f - 0.5, (cam.cy + 0.5) / f - 0.5,
                    cam.width // f, cam.height // f)
-    for _ in range(22):
+    for _ in range(steps):
         mid = 0.5 * (lo + hi)
         c = coverage(shape, small, make_pose(R, np.array([lat[0], lat[1], mid])))
         if c > target:
