@@ -245,6 +245,87 @@ int bt_batch_tuning(const bt_batch* b, int32_t* shape_out, double* us_per_shape)
  * poses, the others are updated), BT_ERR_CUDA, BT_ERR_OOM. */
 int bt_batch_solve(bt_batch* b, int32_t iters, bt_solve_report* reps);
 
+/* ---------------------------------------------------------- warm start
+ * Learned initialisation of all nodes of a pose graph (not in the paper: it
+ * takes the place of the coarse pose from sparse matches, RANSAC and a
+ * closed-form fit, of Sec. IV-B).  For every correspondence set (edge i -> j,
+ * points p in camera i, q in camera j, initial relative pose
+ * M0 = T_j T_i^-1) a set network predicts an increment D of the edge's
+ * relative pose, M = D M0:
+ *   features  x = ((M0 p - c) / 0.1 m, (q - M0 p) / 0.01 m), c = mean of q
+ *   network   x -> 128 -> 256 (ReLU, shared over the set) -> max over the
+ *             set -> 128 (ReLU) -> 6 = (omega / 0.1 rad, u / 0.01 m)
+ *   increment D(x) = exp(omega) (x - c) + c + u
+ * with BF16 weight copies of an FP32 master vector and FP32 sums.  The node
+ * poses then follow from one FP64 linear least-squares relative-pose
+ * averaging solve: each free node is first anchored on its edge to the
+ * lowest-indexed fixed node, then left increments d_i minimise
+ *   sum over edges |d_j - Ad(M_ij) d_i - log(D_ij M0_ij M_ij^-1)|^2_W,
+ *   W = diag(1/0.01^2 x3, 1/0.1^2 x3) on (v, omega),
+ * by Cholesky, and T_i <- exp(d_i) T_i.  Training (mean of 1/2 |y - y*|^2
+ * over a minibatch, Adam with beta = (0.9, 0.999), eps = 1e-8) runs on a
+ * device-resident set of samples whose labels y* come from the poses a solve
+ * converged to.  Parameters: BT_WS_NUM_PARAMS floats in the order
+ * W1[128][6], b1[128], W2[256][128], b2[256], W3[128][256], b3[128],
+ * W4[6][128], b4[6] (row = output unit). */
+#define BT_WS_NUM_PARAMS 67590
+typedef struct bt_warmstart bt_warmstart;
+
+/* Creates a warm start working on cuda_stream (NULL: it creates and owns a
+ * non-blocking stream).  Parameters must be set before use.
+ * Errors: BT_ERR_INVALID, BT_ERR_CUDA, BT_ERR_OOM. */
+int bt_warmstart_create(void* cuda_stream, bt_warmstart** out);
+void bt_warmstart_destroy(bt_warmstart* ws);
+/* BT_WS_NUM_PARAMS (for bindings that check their layout). */
+int32_t bt_warmstart_num_params(void);
+
+/* Sets the FP32 master parameters (host or device array of
+ * BT_WS_NUM_PARAMS) and refreshes the BF16 copies; clears the Adam moments
+ * and step count.  Errors: BT_ERR_INVALID (NULL, non-finite), BT_ERR_CUDA. */
+int bt_warmstart_set_params(bt_warmstart* ws, const float* params, int32_t mem_kind);
+/* Copies the FP32 master parameters out.  Errors: BT_ERR_INVALID, BT_ERR_STATE
+ * (no parameters set), BT_ERR_CUDA. */
+int bt_warmstart_get_params(const bt_warmstart* ws, float* params, int32_t mem_kind);
+
+/* Appends one training sample: count > 0 point pairs (pts_i, pts_j: count x 3
+ * float, host or device), the initial relative pose rel_init = T_j T_i^-1
+ * (4x4 row-major) and, optionally, the converged one rel_label (NULL: label
+ * 0).  The data is copied.  Errors: BT_ERR_INVALID, BT_ERR_CUDA, BT_ERR_OOM. */
+int bt_warmstart_add_set(bt_warmstart* ws, const float* pts_i, const float* pts_j, int32_t count,
+                         const double* rel_init, const double* rel_label, int32_t mem_kind);
+/* Appends one sample per non-empty correspondence set between active nodes
+ * of g (in the order of its edges: pairs of frame ids in increasing order),
+ * with initial and label poses given per active node (N x 4x4 host arrays,
+ * active order; poses_label may be NULL).  Point data is copied on the
+ * device.  Errors: BT_ERR_INVALID, BT_ERR_CUDA, BT_ERR_OOM. */
+int bt_warmstart_add_graph(bt_warmstart* ws, bt_graph* g, const double* poses_init, const double* poses_label);
+/* Number of stored samples, or a negative status. */
+int32_t bt_warmstart_num_samples(const bt_warmstart* ws);
+/* Drops every stored sample (device memory is kept for reuse). */
+int bt_warmstart_clear_samples(bt_warmstart* ws);
+/* The centre c (3 floats) and label y* (6 floats) of sample id; either
+ * pointer may be NULL.  Errors: BT_ERR_INVALID, BT_ERR_CUDA. */
+int bt_warmstart_get_sample(const bt_warmstart* ws, int32_t id, float* centre, float* label);
+
+/* Network outputs (n x 6 floats, host) for samples ids[0..n) (host array).
+ * Errors: BT_ERR_INVALID (id out of range), BT_ERR_STATE, BT_ERR_CUDA. */
+int bt_warmstart_predict(bt_warmstart* ws, const int32_t* ids, int32_t n, float* y_out);
+/* Gradient (BT_WS_NUM_PARAMS floats, host; may be NULL) and value (may be
+ * NULL) of the mean loss over samples ids[0..n), without an update. */
+int bt_warmstart_gradient(bt_warmstart* ws, const int32_t* ids, int32_t n, float* grad_out, double* loss_out);
+/* One Adam step with learning rate lr on the mean loss over samples
+ * ids[0..n).  loss_out: NULL (no synchronisation) or the loss before the step. */
+int bt_warmstart_train_step(bt_warmstart* ws, const int32_t* ids, int32_t n, float lr, double* loss_out);
+
+/* Replaces the stored poses of g's free active nodes by the warm start
+ * computed from its correspondence sets at its stored poses (fixed nodes are
+ * kept).  Errors: BT_ERR_INVALID, BT_ERR_STATE, BT_ERR_SINGULAR (a free node
+ * without correspondences; poses unchanged), BT_ERR_CUDA, BT_ERR_OOM. */
+int bt_warmstart_apply(bt_warmstart* ws, bt_graph* g);
+/* The same for every graph of a batch, in one launch per kernel; status_out:
+ * NULL or bt_batch_size() statuses.  Graphs that fail keep their poses. */
+int bt_warmstart_apply_batch(bt_warmstart* ws, bt_batch* b, int32_t* status_out);
+
 /* Profiling counters of one graph (the tracing facility; no paper
  * counterpart).  Launch counts are always kept; kernel durations are summed
  * from CUDA events recorded on the graph's stream around each launch of the

@@ -89,6 +89,24 @@ SIGNATURES = {
     "bt_batch_set_shape": (C.c_int, [C.c_void_p, C.c_int32]),
     "bt_batch_tuning": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
     "bt_batch_solve": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(bt_solve_report)]),
+    "bt_warmstart_create": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
+    "bt_warmstart_destroy": (None, [C.c_void_p]),
+    "bt_warmstart_num_params": (C.c_int32, []),
+    "bt_warmstart_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "bt_warmstart_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "bt_warmstart_add_set": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double), C.c_int32]),
+    "bt_warmstart_add_graph": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "bt_warmstart_num_samples": (C.c_int32, [C.c_void_p]),
+    "bt_warmstart_clear_samples": (C.c_int, [C.c_void_p]),
+    "bt_warmstart_get_sample": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+    "bt_warmstart_predict": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_float)]),
+    "bt_warmstart_gradient": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_float),
+                                        C.POINTER(C.c_double)]),
+    "bt_warmstart_train_step": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32, C.c_float,
+                                          C.POINTER(C.c_double)]),
+    "bt_warmstart_apply": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "bt_warmstart_apply_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
     "bt_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "bt_profile_read": (C.c_int, [C.c_void_p, C.POINTER(bt_profile)]),
     "bt_pair_dense_energy_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(bt_intrinsics),
@@ -329,6 +347,121 @@ class Batch:
     def close(self):
         if self._h:
             load().bt_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+WS_NUM_PARAMS = 67590
+
+
+def _ids(ids) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(ids, dtype=np.int32).ravel())
+
+
+class WarmStart:
+    """bt_warmstart: the learned warm start (set network + FP64 relative-pose
+    averaging), its device-resident training set and its training step."""
+
+    def __init__(self, params=None, stream=None):
+        self._h = C.c_void_p()
+        _check(load().bt_warmstart_create(_stream_handle(stream), C.byref(self._h)), "bt_warmstart_create")
+        if params is not None:
+            self.set_params(params)
+
+    def set_params(self, params):
+        if _is_torch(params) and params.is_cuda:
+            if params.dtype.itemsize != 4 or params.numel() != WS_NUM_PARAMS or not params.is_contiguous():
+                raise ValueError("parameters: contiguous float32 tensor of %d" % WS_NUM_PARAMS)
+            _check(load().bt_warmstart_set_params(self._h, C.c_void_p(params.data_ptr()), BT_DEVICE),
+                   "bt_warmstart_set_params")
+            return
+        a = np.ascontiguousarray(np.asarray(params, dtype=np.float32).ravel())
+        if a.size != WS_NUM_PARAMS:
+            raise ValueError("parameters: %d floats expected, got %d" % (WS_NUM_PARAMS, a.size))
+        _check(load().bt_warmstart_set_params(self._h, C.c_void_p(a.ctypes.data), BT_HOST),
+               "bt_warmstart_set_params")
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(WS_NUM_PARAMS, np.float32)
+        _check(load().bt_warmstart_get_params(self._h, C.c_void_p(out.ctypes.data), BT_HOST),
+               "bt_warmstart_get_params")
+        return out
+
+    def add_set(self, pts_i, pts_j, rel_init, rel_label=None):
+        pi, ki, kind = _ptr(pts_i, np.float32)
+        pj, kj, kind2 = _ptr(pts_j, np.float32)
+        if kind != kind2:
+            raise ValueError("both point arrays must live in the same memory")
+        n = int(ki.shape[0])
+        M0 = np.ascontiguousarray(rel_init, np.float64).reshape(16)
+        ML = None if rel_label is None else np.ascontiguousarray(rel_label, np.float64).reshape(16)
+        _check(load().bt_warmstart_add_set(self._h, pi, pj, n, M0.ctypes.data_as(C.POINTER(C.c_double)),
+                                           None if ML is None else ML.ctypes.data_as(C.POINTER(C.c_double)), kind),
+               "bt_warmstart_add_set")
+
+    def add_graph(self, graph: "PoseGraph", poses_init, poses_label=None):
+        P0 = np.ascontiguousarray(poses_init, np.float64)
+        PL = None if poses_label is None else np.ascontiguousarray(poses_label, np.float64)
+        _check(load().bt_warmstart_add_graph(self._h, graph._h, P0.ctypes.data_as(C.POINTER(C.c_double)),
+                                             None if PL is None else PL.ctypes.data_as(C.POINTER(C.c_double))),
+               "bt_warmstart_add_graph")
+
+    def num_samples(self) -> int:
+        n = load().bt_warmstart_num_samples(self._h)
+        _check(min(n, 0), "bt_warmstart_num_samples")
+        return n
+
+    def clear_samples(self):
+        _check(load().bt_warmstart_clear_samples(self._h), "bt_warmstart_clear_samples")
+
+    def sample(self, k: int):
+        c = (C.c_float * 3)()
+        y = (C.c_float * 6)()
+        _check(load().bt_warmstart_get_sample(self._h, int(k), c, y), "bt_warmstart_get_sample")
+        return np.array(c[:], np.float32), np.array(y[:], np.float32)
+
+    def predict(self, ids) -> np.ndarray:
+        a = _ids(ids)
+        out = np.empty((a.size, 6), np.float32)
+        _check(load().bt_warmstart_predict(self._h, a.ctypes.data_as(C.POINTER(C.c_int32)), a.size,
+                                           out.ctypes.data_as(C.POINTER(C.c_float))), "bt_warmstart_predict")
+        return out
+
+    def gradient(self, ids):
+        a = _ids(ids)
+        g = np.empty(WS_NUM_PARAMS, np.float32)
+        loss = C.c_double()
+        _check(load().bt_warmstart_gradient(self._h, a.ctypes.data_as(C.POINTER(C.c_int32)), a.size,
+                                            g.ctypes.data_as(C.POINTER(C.c_float)), C.byref(loss)),
+               "bt_warmstart_gradient")
+        return loss.value, g
+
+    def train_step(self, ids, lr: float, want_loss: bool = False):
+        a = _ids(ids)
+        loss = C.c_double()
+        _check(load().bt_warmstart_train_step(self._h, a.ctypes.data_as(C.POINTER(C.c_int32)), a.size, float(lr),
+                                              C.byref(loss) if want_loss else None), "bt_warmstart_train_step")
+        return loss.value if want_loss else None
+
+    def apply(self, graph: "PoseGraph"):
+        _check(load().bt_warmstart_apply(self._h, graph._h), "bt_warmstart_apply")
+
+    def apply_batch(self, batch: "Batch", raise_on_error: bool = True):
+        n = len(batch.graphs)
+        st_arr = (C.c_int32 * max(1, n))()
+        st = load().bt_warmstart_apply_batch(self._h, batch._h, st_arr)
+        if raise_on_error:
+            _check(st, "bt_warmstart_apply_batch")
+        return list(st_arr[:n])
+
+    def close(self):
+        if self._h:
+            load().bt_warmstart_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

@@ -6,8 +6,7 @@
 // allocate).  bt_solve enqueues, on the graph's stream:
 //   xform  ->  iters x [residual(full) -> reduce(full)]  ->  residual(cost) -> reduce(cost)
 // and then one device-to-host copy of poses, costs and status.
-#include "bt.h"
-#include "bt_internal.h"
+#include "bt_host.h"
 
 #include <cuda_runtime.h>
 
@@ -21,126 +20,15 @@
 #include <utility>
 #include <vector>
 
-namespace {
+using namespace bthost;
 
-thread_local std::string g_err;
-
-int fail(int code, const std::string& msg)
+std::string& bthost::last_error()
 {
-    g_err = msg;
-    return code;
+    thread_local std::string s;
+    return s;
 }
 
-int cuda_fail(cudaError_t e, const char* what)
-{
-    g_err = std::string(what) + ": " + cudaGetErrorString(e);
-    return e == cudaErrorMemoryAllocation ? BT_ERR_OOM : BT_ERR_CUDA;
-}
 
-#define BT_CUDA(call, what)                         \
-    do {                                            \
-        cudaError_t e_ = (call);                    \
-        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
-    } while (0)
-
-struct DevBuf {
-    void* p = nullptr;
-    size_t cap = 0;
-    cudaError_t ensure(size_t bytes)
-    {
-        if (bytes <= cap) return cudaSuccess;
-        if (p) cudaFree(p);
-        p = nullptr;
-        cap = 0;
-        size_t want = std::max<size_t>(bytes, 256);
-        cudaError_t e = cudaMalloc(&p, want);
-        if (e == cudaSuccess) cap = want;
-        return e;
-    }
-    void release()
-    {
-        if (p) cudaFree(p);
-        p = nullptr;
-        cap = 0;
-    }
-    template <class T>
-    T* as() const { return static_cast<T*>(p); }
-};
-
-struct Frame {
-    int id = -1;
-    bt_intrinsics K{};
-    int fixed = 0;
-    double pose[16];
-    void* tgt = nullptr;     // target map, element size bt::pixel_bytes(precision)
-    void* src_p = nullptr;   // source points
-    void* src_n = nullptr;   // source normals
-    float zref = 0.f;        // reference depth of the 16-bit encodings
-    int M = 0;
-};
-
-struct MatchSet {
-    int fa = -1, fb = -1;   // fa < fb; pa in camera fa, pb in camera fb
-    int count = 0;
-    float* pa = nullptr;
-    float* pb = nullptr;
-};
-
-bool finite_pose(const double* T)
-{
-    for (int k = 0; k < 16; ++k)
-        if (!std::isfinite(T[k])) return false;
-    return T[12] == 0.0 && T[13] == 0.0 && T[14] == 0.0 && T[15] == 1.0;
-}
-
-}  // namespace
-
-struct bt_graph {
-    bt_config cfg{};
-    cudaStream_t stream = nullptr;
-    int next_id = 0;
-    std::map<int, Frame> frames;
-    std::map<std::pair<int, int>, MatchSet> matches;
-    std::vector<int> active;
-    bool topo_dirty = true;
-
-    // scratch for uploads and frame preparation
-    DevBuf up_depth, up_normals, up_mask, prep_blk, prep_src_p, prep_src_n, prep_M;
-
-    // per-solve state
-    DevBuf d_nodes, d_edges, d_tile_node, d_upairs, d_upair_edge, d_pose, d_xf, d_xinv, d_dpart,
-        d_spart, d_upairblk, d_ctrl, d_costs;
-    bt::SolveArgs args{};
-    int64_t pixels_per_pass = 0;
-    int64_t sparse_per_pass = 0;
-    int built_tile = 0;     // tile size the current tables were built for
-    std::vector<double> pose_stage;   // host staging of poses for batched uploads
-
-    // profiling
-    bt_profile prof{};
-    bool prof_on = false;
-    std::vector<cudaEvent_t> events;
-
-    ~bt_graph()
-    {
-        if (stream) cudaStreamSynchronize(stream);
-        else cudaDeviceSynchronize();
-        for (auto& kv : frames) {
-            cudaFree(kv.second.tgt);
-            cudaFree(kv.second.src_p);
-            cudaFree(kv.second.src_n);
-        }
-        for (auto& kv : matches) {
-            cudaFree(kv.second.pa);
-            cudaFree(kv.second.pb);
-        }
-        for (cudaEvent_t e : events) cudaEventDestroy(e);
-        for (DevBuf* b : {&up_depth, &up_normals, &up_mask, &prep_blk, &prep_src_p, &prep_src_n,
-                          &prep_M, &d_nodes, &d_edges, &d_tile_node, &d_upairs, &d_upair_edge,
-                          &d_pose, &d_xf, &d_xinv, &d_dpart, &d_spart, &d_upairblk, &d_ctrl, &d_costs})
-            b->release();
-    }
-};
 
 namespace {
 
@@ -213,7 +101,9 @@ int put_matches(bt_graph* g, int fa, int fb, int count, const float* pa, const f
 
 // Rebuilds the node / tile / edge tables of the active set and sizes the
 // per-solve buffers.
-int build_topology(bt_graph* g, int tile)
+}  // namespace
+
+int bthost::build_topology(bt_graph* g, int tile)
 {
     const int N = (int)g->active.size();
     if (N < 1) return fail(BT_ERR_INVALID, "solve: no active nodes");
@@ -338,7 +228,7 @@ int build_topology(bt_graph* g, int tile)
     return BT_OK;
 }
 
-int upload_poses(bt_graph* g, std::vector<double>& staging)
+int bthost::upload_poses(bt_graph* g, std::vector<double>& staging)
 {
     const int N = (int)g->active.size();
     staging.resize(12 * (size_t)N);
@@ -354,6 +244,8 @@ int upload_poses(bt_graph* g, std::vector<double>& staging)
     g->prof.xform_launches++;
     return BT_OK;
 }
+
+namespace {
 
 // Makes sure 4 * passes events exist (two per residual and reduce launch).
 int ensure_events(bt_graph* g, int passes)
@@ -430,7 +322,7 @@ void bt_config_default(bt_config* cfg)
 
 int bt_graph_create(const bt_config* cfg, void* cuda_stream, bt_graph** out)
 {
-    g_err.clear();
+    last_error().clear();
     if (!out) return fail(BT_ERR_INVALID, "bt_graph_create: out is NULL");
     *out = nullptr;
     bt_config c;
@@ -454,7 +346,7 @@ int bt_add_frame(bt_graph* g, const float* depth, const float* normals, const ui
                  const bt_intrinsics* K, const double pose_init[16], int32_t fixed,
                  const bt_matches* matches, int32_t n_matches, int32_t mem_kind, int32_t* frame_id_out)
 {
-    g_err.clear();
+    last_error().clear();
     if (!g || !depth || !normals || !mask || !K || !pose_init)
         return fail(BT_ERR_INVALID, "bt_add_frame: NULL argument");
     if (mem_kind != BT_HOST && mem_kind != BT_DEVICE) return fail(BT_ERR_INVALID, "bt_add_frame: bad mem_kind");
@@ -529,10 +421,10 @@ int bt_add_frame(bt_graph* g, const float* depth, const float* normals, const ui
         int st = put_matches(g, f.id, matches[k].other_frame, matches[k].count, matches[k].pts_self,
                              matches[k].pts_other, mem_kind);
         if (st != BT_OK) {
-            std::string msg = g_err;
+            std::string msg = last_error();
             bt_remove_frame(g, f.id);
             g->next_id--;
-            g_err = msg;
+            last_error() = msg;
             return st;
         }
     }
@@ -545,7 +437,7 @@ int bt_add_frame(bt_graph* g, const float* depth, const float* normals, const ui
 int bt_set_matches(bt_graph* g, int32_t frame_a, int32_t frame_b, int32_t count, const float* pts_a,
                    const float* pts_b, int32_t mem_kind)
 {
-    g_err.clear();
+    last_error().clear();
     if (!g) return fail(BT_ERR_INVALID, "bt_set_matches: NULL graph");
     if (mem_kind != BT_HOST && mem_kind != BT_DEVICE) return fail(BT_ERR_INVALID, "bt_set_matches: bad mem_kind");
     return put_matches(g, frame_a, frame_b, count, pts_a, pts_b, mem_kind);
@@ -577,7 +469,7 @@ int bt_remove_frame(bt_graph* g, int32_t frame_id)
 
 int bt_set_active(bt_graph* g, const int32_t* ids, int32_t n)
 {
-    g_err.clear();
+    last_error().clear();
     if (!g || !ids) return fail(BT_ERR_INVALID, "bt_set_active: NULL argument");
     if (n < 1 || n > BT_MAX_NODES) return fail(BT_ERR_INVALID, "bt_set_active: n out of range");
     std::vector<int> v(ids, ids + n);
@@ -601,7 +493,7 @@ int bt_num_active(const bt_graph* g)
 
 int bt_set_poses(bt_graph* g, const double* poses)
 {
-    g_err.clear();
+    last_error().clear();
     if (!g || !poses) return fail(BT_ERR_INVALID, "bt_set_poses: NULL argument");
     for (size_t k = 0; k < g->active.size(); ++k)
         if (!finite_pose(poses + 16 * k)) return fail(BT_ERR_INVALID, "bt_set_poses: bad pose");
@@ -620,7 +512,7 @@ int bt_get_poses(const bt_graph* g, double* poses)
 
 int bt_solve(bt_graph* g, int32_t iters, double* poses_out, bt_solve_report* rep)
 {
-    g_err.clear();
+    last_error().clear();
     if (!g) return fail(BT_ERR_INVALID, "bt_solve: NULL graph");
     if (iters < 0 || iters > BT_MAX_REPORT_ITERS) return fail(BT_ERR_INVALID, "bt_solve: iters out of range");
     if (g->active.empty()) return fail(BT_ERR_INVALID, "bt_solve: no active nodes");
@@ -670,7 +562,7 @@ int bt_solve(bt_graph* g, int32_t iters, double* poses_out, bt_solve_report* rep
 
 int bt_eval_cost(bt_graph* g, double* cost_out, int64_t* dense_inliers)
 {
-    g_err.clear();
+    last_error().clear();
     if (!g || !cost_out) return fail(BT_ERR_INVALID, "bt_eval_cost: NULL argument");
     if (g->active.empty()) return fail(BT_ERR_INVALID, "bt_eval_cost: no active nodes");
     if (g->topo_dirty || g->built_tile != bt::shape_tile(0)) {
@@ -724,7 +616,7 @@ const char* bt_status_str(int status)
     }
 }
 
-const char* bt_last_error(void) { return g_err.c_str(); }
+const char* bt_last_error(void) { return last_error().c_str(); }
 
 }  // extern "C"
 
@@ -732,32 +624,6 @@ const char* bt_last_error(void) { return g_err.c_str(); }
 // Batched solver
 // ---------------------------------------------------------------------------
 
-struct bt_batch {
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    std::vector<bt_graph*> graphs;
-    int shape = -1;          // fixed CTA shape, or -1 = autotune
-    int precision = -1;      // storage precision shared by every graph of the batch
-    int tuned_shape = -1;    // autotuner's choice for the current graph set
-    bool dirty = true;       // graph set / topology changed since the last build
-    DevBuf d_args, d_work_res, d_work_pair;
-    int n_work_res = 0, n_work_pair = 0, max_N = 1;
-    size_t solve_smem = 0;
-    int64_t pixels_per_pass = 0;
-    cudaGraphExec_t exec = nullptr;
-    int exec_iters = -1, exec_shape = -1;
-    std::vector<double> tune_us;   // autotuner timings per shape (microseconds)
-
-    ~bt_batch()
-    {
-        if (stream) cudaStreamSynchronize(stream);
-        if (exec) cudaGraphExecDestroy(exec);
-        d_args.release();
-        d_work_res.release();
-        d_work_pair.release();
-        if (own_stream && stream) cudaStreamDestroy(stream);
-    }
-};
 
 namespace {
 
@@ -891,7 +757,7 @@ extern "C" {
 
 int bt_batch_create(void* cuda_stream, bt_batch** out)
 {
-    g_err.clear();
+    last_error().clear();
     if (!out) return fail(BT_ERR_INVALID, "bt_batch_create: out is NULL");
     *out = nullptr;
     bt_batch* b = new (std::nothrow) bt_batch();
@@ -914,7 +780,7 @@ void bt_batch_destroy(bt_batch* b) { delete b; }
 
 int bt_batch_add(bt_batch* b, bt_graph* g)
 {
-    g_err.clear();
+    last_error().clear();
     if (!b || !g) return fail(BT_ERR_INVALID, "bt_batch_add: NULL argument");
     if (g->active.empty() || (int)g->active.size() > BT_MAX_NODES)
         return fail(BT_ERR_INVALID, "bt_batch_add: graph needs 1..BT_MAX_NODES active nodes");
@@ -956,7 +822,7 @@ int bt_batch_tuning(const bt_batch* b, int32_t* shape_out, double* us_per_shape)
 
 int bt_batch_solve(bt_batch* b, int32_t iters, bt_solve_report* reps)
 {
-    g_err.clear();
+    last_error().clear();
     if (!b) return fail(BT_ERR_INVALID, "bt_batch_solve: NULL batch");
     if (iters < 0 || iters > BT_MAX_REPORT_ITERS) return fail(BT_ERR_INVALID, "bt_batch_solve: iters out of range");
     if (b->graphs.empty()) return fail(BT_ERR_INVALID, "bt_batch_solve: empty batch");
