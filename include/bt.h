@@ -287,12 +287,14 @@ int bt_warmstart_set_params(bt_warmstart* ws, const float* params, int32_t mem_k
  * (no parameters set), BT_ERR_CUDA. */
 int bt_warmstart_get_params(const bt_warmstart* ws, float* params, int32_t mem_kind);
 
-/* Appends one training sample: count > 0 point pairs (pts_i, pts_j: count x 3
- * float, host or device), the initial relative pose rel_init = T_j T_i^-1
- * (4x4 row-major) and, optionally, the converged one rel_label (NULL: label
- * 0).  The data is copied.  Errors: BT_ERR_INVALID, BT_ERR_CUDA, BT_ERR_OOM. */
+/* Appends one training sample: count > 0 point pairs (pts_i in camera i,
+ * pts_j in camera j: count x 3 float, host or device), the initial poses of
+ * the two frames (4x4 row-major; M0 = T_j T_i^-1) and, optionally, the poses
+ * a solve converged to (both NULL: label 0).  The data is copied.
+ * Errors: BT_ERR_INVALID, BT_ERR_CUDA, BT_ERR_OOM. */
 int bt_warmstart_add_set(bt_warmstart* ws, const float* pts_i, const float* pts_j, int32_t count,
-                         const double* rel_init, const double* rel_label, int32_t mem_kind);
+                         const double* pose_i, const double* pose_j, const double* label_i, const double* label_j,
+                         int32_t mem_kind);
 /* Appends one sample per non-empty correspondence set between active nodes
  * of g (in the order of its edges: pairs of frame ids in increasing order),
  * with initial and label poses given per active node (N x 4x4 host arrays,

@@ -95,7 +95,8 @@ SIGNATURES = {
     "bt_warmstart_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "bt_warmstart_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "bt_warmstart_add_set": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_double),
-                                       C.POINTER(C.c_double), C.c_int32]),
+                                       C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                       C.c_int32]),
     "bt_warmstart_add_graph": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "bt_warmstart_num_samples": (C.c_int32, [C.c_void_p]),
     "bt_warmstart_clear_samples": (C.c_int, [C.c_void_p]),
@@ -392,17 +393,18 @@ class WarmStart:
                "bt_warmstart_get_params")
         return out
 
-    def add_set(self, pts_i, pts_j, rel_init, rel_label=None):
+    def add_set(self, pts_i, pts_j, pose_i, pose_j, label_i=None, label_j=None):
+        """One training sample: point pairs and the two frames' initial poses
+        (and, optionally, the poses a solve converged to)."""
         pi, ki, kind = _ptr(pts_i, np.float32)
         pj, kj, kind2 = _ptr(pts_j, np.float32)
         if kind != kind2:
             raise ValueError("both point arrays must live in the same memory")
         n = int(ki.shape[0])
-        M0 = np.ascontiguousarray(rel_init, np.float64).reshape(16)
-        ML = None if rel_label is None else np.ascontiguousarray(rel_label, np.float64).reshape(16)
-        _check(load().bt_warmstart_add_set(self._h, pi, pj, n, M0.ctypes.data_as(C.POINTER(C.c_double)),
-                                           None if ML is None else ML.ctypes.data_as(C.POINTER(C.c_double)), kind),
-               "bt_warmstart_add_set")
+        poses = [None if T is None else np.ascontiguousarray(T, np.float64).reshape(16)
+                 for T in (pose_i, pose_j, label_i, label_j)]
+        ptrs = [None if T is None else T.ctypes.data_as(C.POINTER(C.c_double)) for T in poses]
+        _check(load().bt_warmstart_add_set(self._h, pi, pj, n, *ptrs, kind), "bt_warmstart_add_set")
 
     def add_graph(self, graph: "PoseGraph", poses_init, poses_label=None):
         P0 = np.ascontiguousarray(poses_init, np.float64)

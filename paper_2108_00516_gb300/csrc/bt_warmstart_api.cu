@@ -46,8 +46,6 @@ struct bt_warmstart {
 
 namespace {
 
-const double kIdentity34[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};
-
 // Grows a device buffer to `bytes`, keeping its first `keep` bytes.
 int grow(DevBuf& b, size_t bytes, size_t keep, cudaStream_t s, void** old_out = nullptr)
 {
@@ -337,14 +335,17 @@ int bt_warmstart_get_params(const bt_warmstart* ws, float* params, int32_t mem_k
 }
 
 int bt_warmstart_add_set(bt_warmstart* ws, const float* pts_i, const float* pts_j, int32_t count,
-                         const double* rel_init, const double* rel_label, int32_t mem_kind)
+                         const double* pose_i, const double* pose_j, const double* label_i, const double* label_j,
+                         int32_t mem_kind)
 {
     last_error().clear();
-    if (!ws || !pts_i || !pts_j || !rel_init) return fail(BT_ERR_INVALID, "bt_warmstart_add_set: NULL argument");
+    if (!ws || !pts_i || !pts_j || !pose_i || !pose_j) return fail(BT_ERR_INVALID, "bt_warmstart_add_set: NULL argument");
     if (count <= 0) return fail(BT_ERR_INVALID, "bt_warmstart_add_set: count must be > 0");
     if (mem_kind != BT_HOST && mem_kind != BT_DEVICE) return fail(BT_ERR_INVALID, "bt_warmstart_add_set: mem_kind");
-    if (!finite_pose(rel_init) || (rel_label && !finite_pose(rel_label)))
-        return fail(BT_ERR_INVALID, "bt_warmstart_add_set: bad transform");
+    if ((label_i == nullptr) != (label_j == nullptr))
+        return fail(BT_ERR_INVALID, "bt_warmstart_add_set: give both label poses or neither");
+    if (!finite_pose(pose_i) || !finite_pose(pose_j) || (label_i && (!finite_pose(label_i) || !finite_pose(label_j))))
+        return fail(BT_ERR_INVALID, "bt_warmstart_add_set: bad pose");
     int st = reserve(ws, count, 1);
     if (st != BT_OK) return st;
     cudaStream_t s = ws->stream;
@@ -359,16 +360,17 @@ int bt_warmstart_add_set(bt_warmstart* ws, const float* pts_i, const float* pts_
     x.n = count;
     BT_CUDA(cudaMemcpyAsync(ws->samples.as<W::Sample>() + ws->n_samples, &x, sizeof(x), cudaMemcpyHostToDevice, s),
             "upload sample");
-    // poses: identity, M0, identity, M (the prep kernel forms Tj Ti^-1)
     double stage[48];
-    std::memcpy(stage, kIdentity34, sizeof(kIdentity34));
-    std::memcpy(stage + 12, rel_init, sizeof(double) * 12);
-    std::memcpy(stage + 24, kIdentity34, sizeof(kIdentity34));
-    if (rel_label) std::memcpy(stage + 36, rel_label, sizeof(double) * 12);
+    std::memcpy(stage, pose_i, sizeof(double) * 12);
+    std::memcpy(stage + 12, pose_j, sizeof(double) * 12);
+    if (label_i) {
+        std::memcpy(stage + 24, label_i, sizeof(double) * 12);
+        std::memcpy(stage + 36, label_j, sizeof(double) * 12);
+    }
     BT_CUDA(ws->stage.ensure(sizeof(stage)), "alloc stage");
     BT_CUDA(ws->items.ensure(sizeof(W::PrepItem)), "alloc items");
     const double* d = ws->stage.as<double>();
-    W::PrepItem it{ws->n_samples, 0, d, d + 12, rel_label ? d + 24 : nullptr, rel_label ? d + 36 : nullptr};
+    W::PrepItem it{ws->n_samples, 0, d, d + 12, label_i ? d + 24 : nullptr, label_i ? d + 36 : nullptr};
     BT_CUDA(cudaMemcpyAsync(ws->stage.p, stage, sizeof(stage), cudaMemcpyHostToDevice, s), "upload stage");
     BT_CUDA(cudaMemcpyAsync(ws->items.p, &it, sizeof(it), cudaMemcpyHostToDevice, s), "upload item");
     BT_CUDA(W::launch_prep(ws->samples.as<W::Sample>(), ws->items.as<W::PrepItem>(), 1, s), "launch prep");

@@ -66,7 +66,7 @@ SIZES = [1, 7, 63, 64, 65, 130, 257, 800]
 def _loaded(bt, sets, params):
     ws = bt.WarmStart(params)
     for p, q, M0, M in sets:
-        ws.add_set(p, q, M0, M)
+        ws.add_set(p, q, np.eye(4), M0, np.eye(4), M)
     return ws
 
 
@@ -235,7 +235,7 @@ def test_warmstart_errors(bt):
         ws.set_params(bad)
     ws.set_params(S.warmstart_init(0))
     with pytest.raises(bt.BTError):
-        ws.add_set(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32), np.eye(4))
+        ws.add_set(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32), np.eye(4), np.eye(4))
     with pytest.raises(bt.BTError):
         ws.predict([0])                       # no samples yet
     # a free node without any correspondence set: singular averaging system
