@@ -61,6 +61,8 @@ def parse_args():
     ap.add_argument("--workers", type=int, default=0, help="generator processes (0 = all cores)")
     ap.add_argument("--batch-graphs", type=int, default=64, help="graphs of the batched workload (0 = skip)")
     ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--learned-iters", type=int, default=2,
+                    help="Gauss-Newton iterations after the learned warm start (batched workload)")
     return ap.parse_args()
 
 
@@ -276,12 +278,13 @@ def run_batched(bt, graphs_b, stream, args):
     peak, peak_kind = hbm_peak()
     achieved = BYTES_PER_PIXEL_PAIR * px_pass / (us * 1e-6) / 1e9 if us > 0 else None
     nbytes = sum(r.depth.nbytes * 5 for g in graphs_b for r in g.renders)
-    batch.close()
-    for pg in pgs:
-        pg.close()
+    learned = run_learned(bt, pgs, batch, reset, plain_cost, t_plain, stream, args)
     storage = {"fp32": {"batched_solves_per_s": round(len(pgs) / t_batch, 2), "pass_us": round(us, 1),
                         "bytes_per_pixel_pair": BYTES_PER_PIXEL_PAIR,
                         "frac": round(achieved / peak, 4) if achieved else None}}
+    batch.close()
+    for pg in pgs:
+        pg.close()
     for name, code in (("fp16", bt.BT_FP16), ("bf16", bt.BT_BF16)):
         storage[name] = run_storage(bt, graphs_b, inits, stream, args, code, reps, peak)
     return {"workload": BATCH_WORKLOAD, "graphs": len(graphs_b),
@@ -297,7 +300,46 @@ def run_batched(bt, graphs_b, stream, args):
                                   "pixel_pairs_per_pass": int(px_pass),
                                   "pass_us": round(us, 1), "peak_kind": peak_kind},
             "pixel_pairs_per_s": round(px_pass * it / t_batch, 1),
+            "learned": learned,
             "storage": storage}
+
+
+def run_learned(bt, pgs, batch, reset, plain_cost, t_plain, stream, args):
+    """Learned warm start + batched Gauss-Newton (bt_batch_solve_warm) against
+    the plain per-graph solve at equal final cost: graphs more than 1 % above
+    the plain solve's cost are re-solved plainly inside the timed region.
+    Control: the batched solve with the same iteration count from the plain
+    start (no network)."""
+    import numpy as np
+    import torch
+    from paper_2108_00516_gb300.train_warmstart import DEFAULT_OUT
+    if not DEFAULT_OUT.exists():
+        return {"unavailable": "no trained weights at " + str(DEFAULT_OUT.relative_to(ROOT))}
+    K = args.learned_iters
+    ws = bt.WarmStart(np.load(DEFAULT_OUT)["params"], stream=stream)
+    for _ in range(2):                         # warm-up (captures the K-iteration graph)
+        reset()
+        batch.solve_warm(ws, K, args.iters, ref_costs=plain_cost, tol=0.01)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(args.batch_steps):
+        reset()
+        reps = batch.solve_warm(ws, K, args.iters, ref_costs=plain_cost, tol=0.01)
+    torch.cuda.synchronize()
+    t_learned = (time.perf_counter() - t0) / args.batch_steps
+    rel = [(r["cost_final"] - c) / c for r, c in zip(reps, plain_cost)]
+    reset()
+    ctrl = batch.solve(K)
+    ctrl_rel = [(r["cost_final"] - c) / c for r, c in zip(ctrl, plain_cost)]
+    ws.close()
+    return {"iters": K, "fallback_iters": args.iters,
+            "learned_batched_solves_per_s": round(len(pgs) / t_learned, 2),
+            "speedup_vs_plain": round(t_plain / t_learned, 3),
+            "fallbacks": int(sum(r["fell_back"] for r in reps)),
+            "equal_cost": {"max_rel_above_plain": float(max(rel)), "bound": 0.01, "ok": max(rel) <= 0.01},
+            "control_plain_start_same_iters": {
+                "graphs_above_1pct": int(sum(x > 0.01 for x in ctrl_rel)),
+                "max_rel_above_plain": float(max(ctrl_rel))}}
 
 
 def run_storage(bt, graphs_b, inits, stream, args, code, ref_reps, peak):

@@ -328,6 +328,18 @@ int bt_warmstart_apply(bt_warmstart* ws, bt_graph* g);
  * NULL or bt_batch_size() statuses.  Graphs that fail keep their poses. */
 int bt_warmstart_apply_batch(bt_warmstart* ws, bt_batch* b, int32_t* status_out);
 
+/* Warm-started batch solve with the plain solve as fallback: applies the
+ * warm start to every graph of b, runs `iters` Gauss-Newton iterations of the
+ * batch (bt_batch_solve), and re-solves with `fallback_iters` plain
+ * iterations (bt_solve, from the poses stored before the call) every graph
+ * whose solve failed or whose final cost exceeds (1 + tol) * ref_costs[k]
+ * (ref_costs: the plain solve's final costs, one per graph in batch order;
+ * NULL = fall back only on failure).  reps: NULL or bt_batch_size() reports
+ * with used_warmstart / fell_back set.  Synchronises the batch stream.
+ * Errors: BT_ERR_INVALID, BT_ERR_STATE, BT_ERR_SINGULAR, BT_ERR_CUDA, BT_ERR_OOM. */
+int bt_batch_solve_warm(bt_batch* b, bt_warmstart* ws, int32_t iters, int32_t fallback_iters,
+                        const double* ref_costs, double tol, bt_solve_report* reps);
+
 /* Profiling counters of one graph (the tracing facility; no paper
  * counterpart).  Launch counts are always kept; kernel durations are summed
  * from CUDA events recorded on the graph's stream around each launch of the

@@ -108,6 +108,8 @@ SIGNATURES = {
                                           C.POINTER(C.c_double)]),
     "bt_warmstart_apply": (C.c_int, [C.c_void_p, C.c_void_p]),
     "bt_warmstart_apply_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
+    "bt_batch_solve_warm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double),
+                                      C.c_double, C.POINTER(bt_solve_report)]),
     "bt_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "bt_profile_read": (C.c_int, [C.c_void_p, C.POINTER(bt_profile)]),
     "bt_pair_dense_energy_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(bt_intrinsics),
@@ -344,6 +346,31 @@ class Batch:
         if raise_on_error:
             _check(st, "bt_batch_solve")
         return [_report_dict(reps[k], reps[k].status) for k in range(n)]
+
+    def solve_warm(self, warmstart: "WarmStart", iters: int, fallback_iters: int, ref_costs=None,
+                   tol: float = 0.01, raise_on_error: bool = True):
+        """bt_batch_solve_warm: warm start + `iters` iterations, plain
+        `fallback_iters`-iteration solve where the final cost exceeds
+        (1 + tol) * ref_costs[k].  Returns report dicts with used_warmstart
+        and fell_back."""
+        n = len(self.graphs)
+        reps = (bt_solve_report * max(1, n))()
+        ref = None
+        if ref_costs is not None:
+            ref = np.ascontiguousarray(ref_costs, np.float64)
+            if ref.size != n:
+                raise ValueError("one reference cost per graph")
+        st = load().bt_batch_solve_warm(self._h, warmstart._h, int(iters), int(fallback_iters),
+                                        None if ref is None else ref.ctypes.data_as(C.POINTER(C.c_double)),
+                                        float(tol), reps)
+        if raise_on_error:
+            _check(st, "bt_batch_solve_warm")
+        out = []
+        for k in range(n):
+            d = _report_dict(reps[k], reps[k].status)
+            d.update(used_warmstart=reps[k].used_warmstart, fell_back=reps[k].fell_back)
+            out.append(d)
+        return out
 
     def close(self):
         if self._h:

@@ -546,4 +546,53 @@ int bt_warmstart_apply_batch(bt_warmstart* ws, bt_batch* b, int32_t* status_out)
     return apply_graphs(ws, b->graphs.data(), (int)b->graphs.size(), status_out);
 }
 
+int bt_batch_solve_warm(bt_batch* b, bt_warmstart* ws, int32_t iters, int32_t fallback_iters,
+                        const double* ref_costs, double tol, bt_solve_report* reps)
+{
+    last_error().clear();
+    int st = check_ready(ws, "bt_batch_solve_warm");
+    if (st != BT_OK) return st;
+    if (!b || b->graphs.empty()) return fail(BT_ERR_INVALID, "bt_batch_solve_warm: empty batch");
+    if (iters < 0 || iters > BT_MAX_REPORT_ITERS || fallback_iters < 0 || fallback_iters > BT_MAX_REPORT_ITERS ||
+        !(tol >= 0.0))
+        return fail(BT_ERR_INVALID, "bt_batch_solve_warm: bad iteration counts or tolerance");
+    const size_t G = b->graphs.size();
+    // the stored poses are the plain start and the fallback's start
+    std::vector<std::vector<double>> start(G);
+    for (size_t k = 0; k < G; ++k) {
+        bt_graph* g = b->graphs[k];
+        start[k].resize(16 * g->active.size());
+        for (size_t q = 0; q < g->active.size(); ++q)
+            std::memcpy(&start[k][16 * q], g->frames.at(g->active[q]).pose, sizeof(double) * 16);
+    }
+    std::vector<int> ws_status(G, BT_OK);
+    st = apply_graphs(ws, b->graphs.data(), (int)G, ws_status.data());
+    if (st != BT_OK && st != BT_ERR_SINGULAR) return st;
+    std::vector<bt_solve_report> r(G);
+    st = bt_batch_solve(b, iters, r.data());
+    if (st != BT_OK && st != BT_ERR_SINGULAR) return st;
+    int worst = BT_OK;
+    for (size_t k = 0; k < G; ++k) {
+        r[k].used_warmstart = ws_status[k] == BT_OK ? 1 : 0;
+        const bool bad = r[k].status != BT_OK ||
+                         (ref_costs && !(r[k].cost_final <= (1.0 + tol) * ref_costs[k]));
+        if (bad) {
+            bt_graph* g = b->graphs[k];
+            for (size_t q = 0; q < g->active.size(); ++q)
+                std::memcpy(g->frames.at(g->active[q]).pose, &start[k][16 * q], sizeof(double) * 16);
+            bt_solve_report plain{};
+            int s2 = bt_solve(g, fallback_iters, nullptr, &plain);
+            if (s2 != BT_OK && s2 != BT_ERR_SINGULAR) return s2;
+            plain.used_warmstart = r[k].used_warmstart;
+            plain.fell_back = 1;
+            r[k] = plain;
+        }
+        if (r[k].status != BT_OK) worst = r[k].status;
+    }
+    if (reps)
+        for (size_t k = 0; k < G; ++k) reps[k] = r[k];
+    if (worst != BT_OK) return fail(worst, "bt_batch_solve_warm: some graphs were singular; their poses are unchanged");
+    return BT_OK;
+}
+
 }  // extern "C"

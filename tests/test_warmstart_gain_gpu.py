@@ -1,0 +1,107 @@
+"""What the trained warm start gains over the plain start, and its fallback.
+
+Held-out graphs of the batched workload's distribution (ids outside the
+benchmark's 0..63) are solved by the plain GPU solver from the perturbed
+initial poses (10 iterations, the reference) and again from the warm start.
+The test reports, per graph, the pose error of each start against the
+converged poses and the number of Gauss-Newton iterations each needs to
+come within 1 % of the reference's final cost, and asserts that the warm
+start is closer and needs fewer iterations in total.  The fallback test runs
+an untrained network through bt_batch_solve_warm with the plain costs as
+reference: graphs it leaves more than 1 % worse are re-solved plainly and
+then match the plain solve exactly.
+"""
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+import synthgen as S
+
+pytestmark = pytest.mark.gpu
+
+WEIGHTS = Path(__file__).resolve().parent.parent / "paper_2108_00516_gb300" / "weights" / "warmstart.npz"
+HELDOUT_IDS = (1000, 1002, 1003, 1007, 1014, 1017)
+
+
+@pytest.fixture(scope="module")
+def bt():
+    from paper_2108_00516_gb300 import build as lbuild
+    lbuild.build()
+    from paper_2108_00516_gb300 import bt as _bt
+    _bt.load()
+    return _bt
+
+
+@pytest.fixture(scope="module")
+def graphs():
+    return [S.batched_graph(k) for k in HELDOUT_IDS]
+
+
+def _pose_err(A, B):
+    return max(np.degrees(S.rotation_angle(a[:3, :3] @ b[:3, :3].T)) for a, b in zip(A, B))
+
+
+def _iters_to(costs, target):
+    return next((k for k, c in enumerate(costs) if c <= target), len(costs))
+
+
+def test_trained_warm_start_gains_iterations(bt, graphs):
+    assert WEIGHTS.exists(), "trained warm-start weights missing (paper_2108_00516_gb300/train_warmstart.py)"
+    ws = bt.WarmStart(np.load(WEIGHTS)["params"])
+    rows = []
+    for k, g in zip(HELDOUT_IDS, graphs):
+        pg = bt.graph_from_synth(g)
+        P_ref, r_ref = pg.solve(10)
+        ref = r_ref["cost_final"]
+        plain_costs = list(r_ref["cost_per_iter"]) + [ref]
+        pw = bt.graph_from_synth(g)
+        ws.apply(pw)
+        start = pw.get_poses()
+        _, r_w = pw.solve(10)
+        warm_costs = list(r_w["cost_per_iter"]) + [r_w["cost_final"]]
+        rows.append(dict(graph=k, n=g.n, init_err_deg=_pose_err(g.pose_init, P_ref),
+                         warm_err_deg=_pose_err(start, P_ref),
+                         plain_iters=_iters_to(plain_costs, 1.01 * ref),
+                         warm_iters=_iters_to(warm_costs, 1.01 * ref),
+                         cost_ratio_start=warm_costs[0] / plain_costs[0],
+                         warm_final_rel=r_w["cost_final"] / ref - 1.0))
+        pg.close()
+        pw.close()
+    print("\n| graph | N | start error plain / warm (deg) | iterations to 1 % plain / warm | start cost warm/plain |")
+    print("|---|---|---|---|---|")
+    for r in rows:
+        print("| %d | %d | %.2f / %.2f | %d / %d | %.3f |" % (r["graph"], r["n"], r["init_err_deg"], r["warm_err_deg"],
+                                                            r["plain_iters"], r["warm_iters"], r["cost_ratio_start"]))
+    assert np.mean([r["warm_err_deg"] for r in rows]) < np.mean([r["init_err_deg"] for r in rows])
+    assert sum(r["warm_iters"] for r in rows) < sum(r["plain_iters"] for r in rows)
+    assert np.median([r["cost_ratio_start"] for r in rows]) < 1.0
+    # ten iterations from the warm start reach the plain solve's cost
+    assert all(r["warm_final_rel"] <= 0.01 for r in rows)
+
+
+def test_fallback_restores_the_plain_solve(bt, graphs):
+    gs = graphs[:3]
+    plain = []
+    for g in gs:
+        pg = bt.graph_from_synth(g)
+        plain.append(pg.solve(10))
+        pg.close()
+    ref = [r["cost_final"] for _, r in plain]
+    # an untrained network with large outputs: a poor start for some graphs
+    P = S.warmstart_init(7)
+    P[-6:] += 3.0
+    ws = bt.WarmStart(P)
+    pgs = [bt.graph_from_synth(g) for g in gs]
+    batch = bt.Batch()
+    for pg in pgs:
+        batch.add(pg)
+    reps = batch.solve_warm(ws, 1, 10, ref_costs=ref, tol=0.01)
+    assert all(r["used_warmstart"] == 1 for r in reps)
+    assert any(r["fell_back"] for r in reps)
+    for pg, r, (P_ref, r_ref) in zip(pgs, reps, plain):
+        if r["fell_back"]:
+            assert r["cost_final"] == r_ref["cost_final"]
+            assert np.array_equal(pg.get_poses(), P_ref)
+        else:
+            assert r["cost_final"] <= 1.01 * r_ref["cost_final"]
