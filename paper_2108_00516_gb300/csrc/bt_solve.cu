@@ -147,13 +147,27 @@ __device__ double sparse_block(const double* m, int which, int r, int c)
     return which == 2 ? -v : v;
 }
 
-// Second stage of an unordered pair {A < B}: FP64 sums of the tile partials of
-// both directions, K' = Ad_{T_dst}^T K Ad_{T_dst} and g' = Ad_{T_dst}^T g~ for
+// Second stage of an unordered pair {A < B}: sums of the tile partials of both
+// directions (compensated FP32, widened to FP64), K' = Ad_{T_dst}^T K Ad_{T_dst} and g' = Ad_{T_dst}^T g~ for
 // each (camera-j left blocks -> right perturbations), plus the pair's
 // correspondence set; written pre-combined:
 //   D_A = S + H_AA, D_B = S + H_BB, O_AB = -S + H_AB, g_A = gd + g_A^s,
 //   g_B = -gd + g_B^s with S = lambda_2 (K'_{A->B} + K'_{B->A}) and
 //   gd = lambda_2 (g'_{A->B} - g'_{B->A}).
+constexpr int kPairSmemDoubles = 1520;   // shared memory of the pair stage (doubles)
+
+// Neumaier-compensated accumulation in FP32: s + c is the running sum with
+// an error of order u^2 (u = 2^-24) per term instead of u.  On GB300 a
+// warp-wide FP64 instruction holds its sub-partition's DP unit for ~64
+// cycles, so long sums run on the FP32 pipes and only their results are
+// widened to FP64.
+__device__ __forceinline__ void comp_add(float& s, float& c, float x)
+{
+    const float t = s + x;
+    c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+}
+
 template <bool kFull>
 __device__ void reduce_upair(const SolveArgs& a, int u, double* sm)
 {
@@ -161,21 +175,85 @@ __device__ void reduce_upair(const SolveArgs& a, int u, double* sm)
     const int2 ab = a.upairs[u];
     const int A = ab.x, B = ab.y;
     const int e = a.upair_edge[u];
+    const bool has = e >= 0;
     const int tid = threadIdx.x;
-    const int dir = tid >> 7, v = tid & 31, grp = (tid >> 5) & 3;
+    float* fs = reinterpret_cast<float*>(sm);   // [2][16][32] (s, c) pairs
+    double* tot = sm + 1024;   // [2][32] tile sums of both directions
+    double* Ad = sm + 1088;    // [2][36]: Ad_{T_B} for A->B, Ad_{T_A} for B->A
+    double* K = sm + 1160;     // [2][36]: K, then Ad^T K Ad per direction
+    double* KA = sm + 1232;    // [2][36]
+    double* mo = sm + 1304;    // 40 sparse moments
+    double* gt = sm + 1344;    // [2][6] Ad^T g per direction
+    double* hs = sm + 1356;    // [3][36] sparse blocks (A,A), (B,B), (A,B)
+    double* ps = sm + 1464;    // [2][12] T_B, T_A
+    int* sfwd = reinterpret_cast<int*>(sm + 1488);
+    // loads that do not depend on the tile sums go out first
+    double pv = 0.0;
+    float mv = 0.f;
+    int ei = -1;
+    if (kFull && tid < 24) pv = __ldcg(a.pose + (tid < 12 ? B : A) * 12 + tid % 12);
+    if (has && tid >= 128 && tid < 128 + kSparseVals) mv = __ldcg(a.spart + (size_t)e * kSparseVals + tid - 128);
+    if (kFull && has && tid == 64) ei = __ldcg(&a.edges[e].i);
+    // tile sums: thread = (direction, one of 16 tile groups, 4 consecutive
+    // values); each thread reads every 16th tile of its direction as float4
+    // (independent loads), compensated FP32 sums, groups combined in a fixed
+    // order
+    const int dir = tid >> 7, v4 = tid & 7, grp = (tid >> 3) & 15;
     const int src = dir ? B : A, dst = dir ? A : B;
     const int jj = dst < src ? dst : dst - 1;
-    const NodeDev Ns = a.nodes[src];
-    double s = 0.0;
-    if (kFull || v == 27 || v == 28)
-        for (int t = Ns.tile0 + grp; t < Ns.tile0 + Ns.ntiles; t += 4)
-            s += (double)a.dpart[((size_t)t * (N - 1) + jj) * kDenseVals + v];
-    sm[tid] = s;
+    const int tile0 = a.nodes[src].tile0, ntiles = a.nodes[src].ntiles;
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+    if (kFull || v4 >= 6) {
+        const size_t stride = (size_t)(N - 1) * (kDenseVals / 4);
+        const float4* base =
+            reinterpret_cast<const float4*>(a.dpart + ((size_t)tile0 * (N - 1) + jj) * kDenseVals) + v4;
+        int t = grp;
+        for (; t + 112 < ntiles; t += 128) {
+            float4 x[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) x[q] = __ldcg(base + (size_t)(t + 16 * q) * stride);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                comp_add(s[0], c[0], x[q].x);
+                comp_add(s[1], c[1], x[q].y);
+                comp_add(s[2], c[2], x[q].z);
+                comp_add(s[3], c[3], x[q].w);
+            }
+        }
+        float4 x[7];
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {     // t + 112 >= ntiles: at most 7 tiles left
+            const int tq = t + 16 * q;
+            x[q] = tq < ntiles ? __ldcg(base + (size_t)tq * stride) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            comp_add(s[0], c[0], x[q].x);
+            comp_add(s[1], c[1], x[q].y);
+            comp_add(s[2], c[2], x[q].z);
+            comp_add(s[3], c[3], x[q].w);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int o = ((dir * 16 + grp) * 32 + 4 * v4 + k) * 2;
+        fs[o] = s[k];
+        fs[o + 1] = c[k];
+    }
+    if (kFull && tid < 24) ps[tid] = pv;
+    if (tid >= 128 && tid < 128 + kSparseVals) mo[tid - 128] = has ? (double)mv : 0.0;
+    if (tid == 64) *sfwd = ei;
     __syncthreads();
-    double* tot = sm + 256;   // [2][32]
     if (tid < 64) {
         const int d = tid >> 5, w = tid & 31;
-        tot[tid] = ((sm[d * 128 + w] + sm[d * 128 + 32 + w]) + sm[d * 128 + 64 + w]) + sm[d * 128 + 96 + w];
+        float S0 = 0.f, C0 = 0.f;
+#pragma unroll
+        for (int g = 0; g < 16; ++g) {
+            const int o = ((d * 16 + g) * 32 + w) * 2;
+            comp_add(S0, C0, fs[o]);
+            C0 += fs[o + 1];
+        }
+        tot[tid] = (double)S0 + (double)C0;
     }
     __syncthreads();
     double* out = a.upairblk + (size_t)u * kUPairBlk;
@@ -183,77 +261,69 @@ __device__ void reduce_upair(const SolveArgs& a, int u, double* sm)
     if (!kFull) {
         if (tid == 0) {
             out[90] = lg * (tot[27] + tot[32 + 27]);
-            out[91] = e >= 0 ? ls * (double)a.spart[(size_t)e * kSparseVals + 37] : 0.0;
+            out[91] = has ? ls * mo[37] : 0.0;
             out[92] = tot[28] + tot[32 + 28];
         }
         return;
     }
-    double* Ad = sm + 320;   // [2][36]: Ad_{T_B} for A->B, Ad_{T_A} for B->A
-    double* K = sm + 392;    // [2][36]
-    double* KA = sm + 464;   // [2][36]
-    double* mo = sm + 536;   // 40 sparse moments
-    double* S = sm + 576;    // [36]
-    double* gd = sm + 612;   // [6]
     if (tid < 72) {
-        const int d = tid / 36, q = tid % 36, r = q / 6, c = q % 6;
-        Ad[tid] = ad_entry(a.pose + (d ? A : B) * 12, r, c);
-        K[tid] = tot[d * 32 + sym_idx(r, c)];
-    } else if (tid >= 128 && tid < 128 + kSparseVals) {
-        mo[tid - 128] = e >= 0 ? (double)a.spart[(size_t)e * kSparseVals + tid - 128] : 0.0;
+        const int d = tid / 36, q = tid % 36, r = q / 6, cc = q % 6;
+        Ad[tid] = ad_entry(ps + d * 12, r, cc);
+        K[tid] = tot[d * 32 + sym_idx(r, cc)];
     }
     __syncthreads();
     if (tid < 72) {
-        const int d = tid / 36, q = tid % 36, r = q / 6, c = q % 6;
+        const int d = tid / 36, q = tid % 36, r = q / 6, cc = q % 6;
         double x = 0.0;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) x += K[d * 36 + r * 6 + k] * Ad[d * 36 + k * 6 + c];
+        for (int k = 0; k < 6; ++k) x += K[d * 36 + r * 6 + k] * Ad[d * 36 + k * 6 + cc];
         KA[tid] = x;
     }
     __syncthreads();
-    if (tid < 36) {
-        const int r = tid / 6, c = tid % 6;
-        if (c >= r) {
-            double x0 = 0.0, x1 = 0.0;
+    // K'_d = Ad_d^T K_d Ad_d and g'_d = Ad_d^T g_d per direction (threads
+    // 0-83), and the three sparse blocks (threads 128-235), side by side
+    if (tid < 72) {
+        const int d = tid / 36, q = tid % 36, r = q / 6, cc = q % 6;
+        double x = 0.0;
 #pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                x0 += Ad[k * 6 + r] * KA[k * 6 + c];
-                x1 += Ad[36 + k * 6 + r] * KA[36 + k * 6 + c];
-            }
-            S[r * 6 + c] = S[c * 6 + r] = lg * (x0 + x1);
-        }
-    } else if (tid < 42) {
-        const int r = tid - 36;
-        double g0 = 0.0, g1 = 0.0;
+        for (int k = 0; k < 6; ++k) x += Ad[d * 36 + k * 6 + r] * KA[d * 36 + k * 6 + cc];
+        K[tid] = x;
+    } else if (tid < 84) {
+        const int d = (tid - 72) / 6, r = (tid - 72) % 6;
+        double g = 0.0;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            g0 += Ad[k * 6 + r] * tot[21 + k];
-            g1 += Ad[36 + k * 6 + r] * tot[32 + 21 + k];
+        for (int k = 0; k < 6; ++k) g += Ad[d * 36 + k * 6 + r] * tot[d * 32 + 21 + k];
+        gt[tid - 72] = g;
+    } else if (tid >= 128 && tid < 128 + 108) {
+        const int w = (tid - 128) / 36, q = (tid - 128) % 36, r = q / 6, cc = q % 6;
+        const bool fwd = has && *sfwd == A;   // correspondence set stored as (A, B)
+        double h = 0.0;
+        if (has) {
+            if (w == 0) h = sparse_block(mo, fwd ? 0 : 1, r, cc);
+            else if (w == 1) h = sparse_block(mo, fwd ? 1 : 0, r, cc);
+            else h = fwd ? sparse_block(mo, 2, r, cc) : sparse_block(mo, 2, cc, r);
         }
-        gd[r] = lg * (g0 - g1);
+        hs[tid - 128] = ls * h;
     }
     __syncthreads();
-    const bool has = e >= 0;
-    const bool fwd = has && a.edges[e].i == A;   // correspondence set stored as (A, B)
     if (tid < 36) {
-        const int r = tid / 6, c = tid % 6;
-        double hAA = 0.0, hBB = 0.0, hAB = 0.0;
-        if (has) {
-            hAA = ls * sparse_block(mo, fwd ? 0 : 1, r, c);
-            hBB = ls * sparse_block(mo, fwd ? 1 : 0, r, c);
-            hAB = ls * (fwd ? sparse_block(mo, 2, r, c) : sparse_block(mo, 2, c, r));
+        const int r = tid / 6, cc = tid % 6;
+        const int q = (r < cc ? r : cc) * 6 + (r < cc ? cc : r);   // S is symmetric: one rounding for both halves
+        const double Sv = lg * (K[q] + K[36 + q]);
+        if (cc >= r) {
+            out[sym_idx(r, cc)] = Sv + hs[tid];
+            out[21 + sym_idx(r, cc)] = Sv + hs[36 + tid];
         }
-        if (c >= r) {
-            out[sym_idx(r, c)] = S[tid] + hAA;
-            out[21 + sym_idx(r, c)] = S[tid] + hBB;
-        }
-        out[42 + tid] = -S[tid] + hAB;
+        out[42 + tid] = -Sv + hs[72 + tid];
     } else if (tid < 42) {
         const int r = tid - 36;
+        const bool fwd = has && *sfwd == A;
+        const double gdv = lg * (gt[r] - gt[6 + r]);
         // g_i = -[sum w e; sum w a x e], g_j = [sum w e; sum w b x e]
         const double gi = has ? -ls * (r < 3 ? mo[28 + r] : mo[31 + r - 3]) : 0.0;
         const double gj = has ? ls * (r < 3 ? mo[28 + r] : mo[34 + r - 3]) : 0.0;
-        out[78 + r] = gd[r] + (fwd ? gi : gj);
-        out[84 + r] = -gd[r] + (fwd ? gj : gi);
+        out[78 + r] = gdv + (fwd ? gi : gj);
+        out[84 + r] = -gdv + (fwd ? gj : gi);
     } else if (tid == 42) {
         out[90] = lg * (tot[27] + tot[32 + 27]);
         out[91] = has ? ls * mo[37] : 0.0;
@@ -261,15 +331,18 @@ __device__ void reduce_upair(const SolveArgs& a, int u, double* sm)
     }
 }
 
-// SE(3) exponential of xi = (v, w) as a 3x4 matrix: R = I + A W + B W^2,
-// t = (I + B W + C W^2) v with A = sin(th)/th, B = (1 - cos th)/th^2,
-// C = (th - sin th)/th^3.  Below th = 0.1 the coefficients come from their
-// Taylor series through th^8 (truncation < 3e-18), which keeps the FP64
-// dependency chain short; above it from sincos.
-__device__ void se3_exp_d(const double* xi, double* E)
+// Entry (r, c) of the SE(3) exponential of xi = (v, w) as a 3x4 matrix:
+// R = I + A W + B W^2, t = (I + B W + C W^2) v with W = [w]x, W^2 = w w^T -
+// th^2 I, A = sin(th)/th, B = (1 - cos th)/th^2, C = (th - sin th)/th^3.  One
+// thread per entry: a warp-wide FP64 instruction costs its sub-partition
+// ~64 cycles whatever the number of active lanes, so the twelve entries of
+// each node are spread over lanes instead of running one node per lane.
+// Below th = 0.1 the coefficients come from their Taylor series through th^8
+// (truncation < 3e-18), which keeps the FP64 chain short; above it from sincos.
+__device__ double se3_exp_entry(const double* xi, int r, int c)
 {
-    const double wx = xi[3], wy = xi[4], wz = xi[5];
-    const double th2 = wx * wx + wy * wy + wz * wz;
+    const double w[3] = {xi[3], xi[4], xi[5]};
+    const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
     double A, B, C;
     if (th2 < 0.01) {
         A = 1.0 + th2 * (-1.0 / 6.0 + th2 * (1.0 / 120.0 + th2 * (-1.0 / 5040.0 + th2 * (1.0 / 362880.0))));
@@ -283,24 +356,18 @@ __device__ void se3_exp_d(const double* xi, double* E)
         B = (1.0 - cs) / th2;
         C = (th - sn) / (th2 * th);
     }
-    const double W[9] = {0.0, -wz, wy, wz, 0.0, -wx, -wy, wx, 0.0};
-    double W2[9];
+    auto Wm = [&](int i, int j) -> double {      // [w]x
+        if (i == j) return 0.0;
+        const int k = 3 - i - j;
+        const bool plus = (i + 1) % 3 == j;        // (0,1), (1,2), (2,0): -w_k
+        return plus ? -w[k] : w[k];
+    };
+    auto W2m = [&](int i, int j) -> double { return w[i] * w[j] - (i == j ? th2 : 0.0); };
+    if (c < 3) return (r == c ? 1.0 : 0.0) + A * Wm(r, c) + B * W2m(r, c);
+    double t = 0.0;
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-            W2[r * 3 + c] = W[r * 3 + 0] * W[0 * 3 + c] + W[r * 3 + 1] * W[1 * 3 + c] + W[r * 3 + 2] * W[2 * 3 + c];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        double t = 0.0;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const double id = r == c ? 1.0 : 0.0;
-            E[r * 4 + c] = id + A * W[r * 3 + c] + B * W2[r * 3 + c];
-            t += (id + B * W[r * 3 + c] + C * W2[r * 3 + c]) * xi[c];
-        }
-        E[r * 4 + 3] = t;
-    }
+    for (int k = 0; k < 3; ++k) t += ((r == k ? 1.0 : 0.0) + B * Wm(r, k) + C * W2m(r, k)) * xi[k];
+    return t;
 }
 
 // 1/d for a positive FP64 pivot: the hardware approximation (rcp.approx.f64)
@@ -329,13 +396,18 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
 {
     const int N = a.N, U = a.n_upairs;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
-    if (tid < 32) {
+    const int nf = a.n_free, n = 6 * nf;
+    const int status0 = kFull ? *(volatile int*)&a.ctrl->status : 0;
+    // energies of the iteration: from the staged pair blocks when a full
+    // solve stages them, else straight from global memory
+    const bool staged_costs = kFull && n > 0 && status0 == 0 && a.stage_blocks != 0;
+    auto write_costs = [&](const double* blocks, bool shared) {
         double ed = 0.0, es = 0.0, cnt = 0.0;
         for (int u = lane; u < U; u += 32) {
-            const double* o = a.upairblk + (size_t)u * kUPairBlk;
-            ed += __ldcg(o + 90);
-            es += __ldcg(o + 91);
-            cnt += __ldcg(o + 92);
+            const double* o = blocks + (size_t)u * kUPairBlk;
+            ed += shared ? o[90] : __ldcg(o + 90);
+            es += shared ? o[91] : __ldcg(o + 91);
+            cnt += shared ? o[92] : __ldcg(o + 92);
         }
 #pragma unroll
         for (int off = 16; off >= 1; off >>= 1) {
@@ -349,12 +421,9 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
             a.costs[iter * 4 + 2] = es;
             a.costs[iter * 4 + 3] = cnt;
         }
-    }
-    if (!kFull) return;
-    const int nf = a.n_free, n = 6 * nf;
-    if (n == 0) return;
-    const int status0 = *(volatile int*)&a.ctrl->status;
-    if (status0 != 0) return;
+    };
+    if (!staged_costs && tid < 32) write_costs(a.upairblk, false);
+    if (!kFull || n == 0 || status0 != 0) return;
     unsigned long long t0 = clock64();
     const int ld = n + 1;        // odd leading dimension: conflict-free FP64 rows
     double* H = sm;              // n*ld: lower triangle H, then L^T in the upper triangle
@@ -377,14 +446,26 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
     }
     for (int q = tid; q < 12 * N; q += nt) ps[q] = a.pose[q];
     if (tid == 0) s_fail = 0;
-    {
+    {   // pair blocks to shared memory, eight independent loads in flight per thread
         const double2* src = reinterpret_cast<const double2*>(a.upairblk);
         double2* dst = reinterpret_cast<double2*>(stage);
         const int n2 = (int)(stage_len / 2);
-#pragma unroll 4
-        for (int q = tid; q < n2; q += nt) dst[q] = __ldcg(src + q);
+        for (int q0 = tid; q0 < n2; q0 += 8 * nt) {
+            double2 v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int q = q0 + k * nt;
+                if (q < n2) v[k] = __ldcg(src + q);
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int q = q0 + k * nt;
+                if (q < n2) dst[q] = v[k];
+            }
+        }
     }
     __syncthreads();
+    if (staged_costs && tid < 32) write_costs(stage, true);
     const bool staged = a.stage_blocks != 0;
     auto blk = [&](size_t q) { return staged ? stage[q] : __ldcg(a.upairblk + q); };
     // diagonal blocks and gradient: one warp per free node, lanes 0-20 the
@@ -458,31 +539,41 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
         const double* ck = colb + (k & 1) * n;        // l_{i,k}
         double* cn = colb + ((k + 1) & 1) * n;        // l_{i,k+1}, written now
         if (warp == 0) {
+            // column p = k + 1, rows i = p .. n-1 in slots of 32: u_i = H_ip -
+            // l_ik H_pk (the pivot is u_p), then every lane forms 1 / u_p
+            // itself (no divergent branch, no second broadcast) and scales
             const int p = k + 1;
             const double hpk = H[p * ld + k];         // unscaled H_{k+1,k}
-            double rp = 0.0;
+            const int nq = (n - p + 31) >> 5;         // active slots (warp-uniform)
+            constexpr int kRows = (6 * (kMaxNodes - 1) + 31) / 32;
+            double hv[kRows], cv[kRows], u[kRows];
+#pragma unroll
+            for (int q = 0; q < kRows; ++q) {
+                if (q >= nq) break;
+                const int i = p + lane + 32 * q;
+                hv[q] = i < n ? H[i * ld + p] : 0.0;
+                cv[q] = i < n ? ck[i] : 0.0;
+            }
+#pragma unroll
+            for (int q = 0; q < kRows; ++q) {
+                if (q >= nq) break;
+                u[q] = hv[q] - cv[q] * hpk;
+            }
+            const double h = __shfl_sync(0xffffffffu, u[0], 0);
+            const bool ok = h > 0.0;
+            const double rp = ok ? rcp_fp64(h) : 0.0;
             if (lane == 0) {
-                const double h = H[p * ld + p] - ck[p] * hpk;
+                if (!ok) s_fail = 1;
                 H[p * ld + p] = h;
-                if (!(h > 0.0)) s_fail = 1; else rp = rcp_fp64(h);
                 rD[p] = rp;
             }
-            constexpr int kRows = (6 * (kMaxNodes - 1) + 31) / 32;
-            double u[kRows];
 #pragma unroll
             for (int q = 0; q < kRows; ++q) {
-                const int i = p + 1 + lane + 32 * q;
-                if (i < n) {
-                    u[q] = H[i * ld + p] - ck[i] * hpk;
-                    H[i * ld + p] = u[q];
-                }
-            }
-            rp = __shfl_sync(0xffffffffu, rp, 0);
-#pragma unroll
-            for (int q = 0; q < kRows; ++q) {
-                const int i = p + 1 + lane + 32 * q;
-                if (i < n) {
+                if (q >= nq) break;
+                const int i = p + lane + 32 * q;
+                if (i > p && i < n) {
                     const double l = u[q] * rp;
+                    H[i * ld + p] = u[q];
                     cn[i] = l;
                     H[p * ld + i] = l;
                 }
@@ -554,22 +645,26 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
     }
     __syncthreads();
     unsigned long long t3 = clock64();
-    // T_A <- T_A exp(dx_A)
-    if (tid < nf) {
-        const int A = node_of[tid];
-        double E[12], T[12];
-        se3_exp_d(y + 6 * tid, E);
-#pragma unroll
-        for (int k = 0; k < 12; ++k) T[k] = ps[A * 12 + k];
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                double s = T[r * 4 + 0] * E[0 * 4 + c] + T[r * 4 + 1] * E[1 * 4 + c] + T[r * 4 + 2] * E[2 * 4 + c];
-                if (c == 3) s += T[r * 4 + 3];
-                ps[A * 12 + r * 4 + c] = s;
-            }
+    // T_A <- T_A exp(dx_A): one thread per entry of exp(dx_A), then one per
+    // entry of the product (the look-ahead columns and tinv are free now)
+    {
+        double* E = colb;      // [nf][12]
+        double* P = tinv;      // [nf][12]
+        for (int q = tid; q < 12 * nf; q += nt) {
+            const int e = q % 12;
+            E[q] = se3_exp_entry(y + 6 * (q / 12), e >> 2, e & 3);
         }
+        __syncthreads();
+        for (int q = tid; q < 12 * nf; q += nt) {
+            const int f = q / 12, e = q % 12, r = e >> 2, c = e & 3;
+            const double* T = ps + node_of[f] * 12;
+            const double* Ef = E + f * 12;
+            double v = T[r * 4 + 0] * Ef[0 * 4 + c] + T[r * 4 + 1] * Ef[1 * 4 + c] + T[r * 4 + 2] * Ef[2 * 4 + c];
+            if (c == 3) v += T[r * 4 + 3];
+            P[q] = v;
+        }
+        __syncthreads();
+        for (int q = tid; q < 12 * nf; q += nt) ps[node_of[q / 12] * 12 + q % 12] = P[q];
     }
     __syncthreads();
     for (int q = tid; q < 12 * N; q += nt) a.pose[q] = ps[q];
@@ -584,7 +679,7 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
 }
 
 template <bool kFull>
-__global__ void __launch_bounds__(kThreads) reduce_kernel(SolveArgs a, int iter)
+__global__ void __launch_bounds__(kThreads, 1) reduce_kernel(SolveArgs a, int iter)
 {
     extern __shared__ double sm[];
     __shared__ int s_last;
@@ -611,7 +706,7 @@ static size_t reduce_smem_bytes_for(int n_free, int N, bool stage)
     const size_t tab_dbl = (n * (n + 1) / 2 + 1) / 2;
     size_t fin = (n * (n + 1) + 4 * n + 24 * (size_t)kMaxNodes + tab_dbl + 1 + sl) * sizeof(double) +
                  kMaxNodes * sizeof(int);
-    size_t ph1 = 640 * sizeof(double);
+    size_t ph1 = kPairSmemDoubles * sizeof(double);
     return fin > ph1 ? fin : ph1;
 }
 
@@ -656,7 +751,7 @@ template <bool kFull>
 __global__ void __launch_bounds__(kThreads) batch_pair_kernel(const SolveArgs* __restrict__ args,
                                                               const int2* __restrict__ work)
 {
-    __shared__ double sm[640];
+    __shared__ double sm[kPairSmemDoubles];
     __shared__ SolveArgs sa;
     const int2 w = work[blockIdx.x];
     if (threadIdx.x == 0) sa = args[w.x];
@@ -665,7 +760,7 @@ __global__ void __launch_bounds__(kThreads) batch_pair_kernel(const SolveArgs* _
 }
 
 template <bool kFull>
-__global__ void __launch_bounds__(kThreads) batch_solve_kernel(const SolveArgs* __restrict__ args, int iter)
+__global__ void __launch_bounds__(kThreads, 1) batch_solve_kernel(const SolveArgs* __restrict__ args, int iter)
 {
     extern __shared__ double smd[];
     __shared__ SolveArgs sa;
