@@ -228,12 +228,17 @@ int bt_batch_add(bt_batch* b, bt_graph* g);
 /* Number of graphs, or a negative status. */
 int bt_batch_size(const bt_batch* b);
 
-/* Fixes the residual CTA shape (0..3) or re-enables autotuning (-1, the
- * default).  Errors: BT_ERR_INVALID. */
+/* Residual-pass CTA shapes the autotuner chooses from (threads x source
+ * pixels per thread: 128x4, 128x2, 256x4, 64x4, 64x8, 32x16). */
+#define BT_NUM_SHAPES 6
+
+/* Fixes the residual CTA shape (0 .. BT_NUM_SHAPES-1) or re-enables
+ * autotuning (-1, the default).  Errors: BT_ERR_INVALID. */
 int bt_batch_set_shape(bt_batch* b, int32_t shape);
 
-/* The shape in use and the autotuner's measured time per shape (4 doubles,
- * microseconds of one full residual pass; 0 where not measured).  Either
+/* The shape in use and the autotuner's measured time per shape
+ * (BT_NUM_SHAPES doubles, microseconds of one full residual pass; 0 where
+ * not measured).  Either
  * pointer may be NULL.  Errors: BT_ERR_INVALID. */
 int bt_batch_tuning(const bt_batch* b, int32_t* shape_out, double* us_per_shape);
 

@@ -27,6 +27,7 @@ BT_BF16 = 1
 BT_FP16 = 2
 BT_MAX_NODES = 24
 BT_MAX_REPORT_ITERS = 64
+BT_NUM_SHAPES = 6
 
 LIB_PATH = Path(__file__).resolve().parent / "_build" / "libbt.so"
 
@@ -334,7 +335,7 @@ class Batch:
 
     def tuning(self):
         sh = C.c_int32()
-        us = (C.c_double * 4)()
+        us = (C.c_double * BT_NUM_SHAPES)()
         _check(load().bt_batch_tuning(self._h, C.byref(sh), us), "bt_batch_tuning")
         return sh.value, list(us)
 

@@ -22,6 +22,8 @@
 
 using namespace bthost;
 
+static_assert(bt::kNumShapes == BT_NUM_SHAPES, "shape count of the interface");
+
 std::string& bthost::last_error()
 {
     thread_local std::string s;

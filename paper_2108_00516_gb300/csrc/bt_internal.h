@@ -30,11 +30,15 @@ namespace bt {
 constexpr int kThreads = 256;                 // reduce CTAs, sparse CTAs, prep CTAs
 constexpr int kPixPerThread = 4;              // prep
 // Dense residual CTA shapes (threads x source pixels per thread); the tile of
-// a CTA is their product.  Shape 0 is the default of the single-graph path;
-// the batched solver's autotuner picks among all of them.
-constexpr int kNumShapes = 4;
-constexpr int kShapeThreads[kNumShapes] = {128, 128, 256, 64};
-constexpr int kShapePix[kNumShapes] = {4, 2, 4, 4};
+// a CTA is their product.  A thread takes its pixels of one target in
+// batches of up to 4 (the gathers of a batch are in flight together) and
+// reduces its sums across the warp once per target, so more pixels per
+// thread spread that reduction over more pixel pairs.  Shape 0 is the
+// default of the single-graph path; the batched solver's autotuner picks
+// among all of them.
+constexpr int kNumShapes = 6;     // BT_NUM_SHAPES
+constexpr int kShapeThreads[kNumShapes] = {128, 128, 256, 64, 64, 32};
+constexpr int kShapePix[kNumShapes] = {4, 2, 4, 4, 8, 16};
 constexpr int kResThreads = 128;              // sparse CTAs of the residual launch
 constexpr int kMaxTile = 1024;
 constexpr int kDenseVals = 32;                // 21 H + 6 g + cost + count + 3 pad

@@ -354,8 +354,9 @@ __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
     constexpr int kW = kT / 32;
     constexpr int kTile = kT * kB;
     constexpr int kResThreads = kT;
-    constexpr int kResBatch = kB;
-    constexpr int kResBatches = 1;
+    constexpr int kResBatch = kB < 4 ? kB : 4;
+    constexpr int kResBatches = kB / kResBatch;
+    static_assert(kResBatch * kResBatches == kB, "pixels per thread: 1, 2, 3 or a multiple of 4");
     const int N = a.N;
     const int i = a.tile_node[tile];
     const NodeDev Ni = a.nodes[i];
@@ -623,6 +624,8 @@ static void ensure_residual_attrs()
     set_residual_attrs<1>();
     set_residual_attrs<2>();
     set_residual_attrs<3>();
+    set_residual_attrs<4>();
+    set_residual_attrs<5>();
     done = true;
 }
 
@@ -654,6 +657,8 @@ cudaError_t launch_residual(const SolveArgs& a, bool full, cudaStream_t s, int s
     case 1: launch_residual_s<1>(a, full, grid, smem, s); break;
     case 2: launch_residual_s<2>(a, full, grid, smem, s); break;
     case 3: launch_residual_s<3>(a, full, grid, smem, s); break;
+    case 4: launch_residual_s<4>(a, full, grid, smem, s); break;
+    case 5: launch_residual_s<5>(a, full, grid, smem, s); break;
     default: launch_residual_s<0>(a, full, grid, smem, s); break;
     }
     return cudaGetLastError();
@@ -689,6 +694,8 @@ cudaError_t launch_batch_residual(const SolveArgs* args_dev, const int2* work_re
     case 1: launch_batch_residual_s<1>(args_dev, work_res, n_work, smem, full, precision, s); break;
     case 2: launch_batch_residual_s<2>(args_dev, work_res, n_work, smem, full, precision, s); break;
     case 3: launch_batch_residual_s<3>(args_dev, work_res, n_work, smem, full, precision, s); break;
+    case 4: launch_batch_residual_s<4>(args_dev, work_res, n_work, smem, full, precision, s); break;
+    case 5: launch_batch_residual_s<5>(args_dev, work_res, n_work, smem, full, precision, s); break;
     default: launch_batch_residual_s<0>(args_dev, work_res, n_work, smem, full, precision, s); break;
     }
     return cudaGetLastError();

@@ -66,3 +66,15 @@ def test_host_only_calls(lib):
     assert "Huber" in lib.bt_last_error().decode()
     assert lib.bt_solve(None, 1, None, None) == bt.BT_ERR_INVALID
     assert lib.bt_num_active(None) == bt.BT_ERR_INVALID
+
+
+def test_header_constants_match_binding(lib):
+    """Every numeric #define of bt.h has the same value in the binding."""
+    from paper_2108_00516_gb300 import bt
+    text = HEADER.read_text()
+    defs = dict(re.findall(r"#define\s+(BT_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", text))
+    assert {"BT_NUM_SHAPES", "BT_MAX_NODES", "BT_WS_NUM_PARAMS", "BT_ERR_SINGULAR"} <= set(defs)
+    for name, val in defs.items():
+        py = name.replace("BT_WS_NUM_PARAMS", "WS_NUM_PARAMS")
+        assert getattr(bt, py) == int(val), name
+    assert lib.bt_warmstart_num_params() == int(defs["BT_WS_NUM_PARAMS"])

@@ -63,7 +63,7 @@ def test_batch_autotuned_matches_oracle(bt):
         batch.add(pg)
     reps = batch.solve(7)
     shape, us = batch.tuning()
-    assert 0 <= shape < 4 and all(u > 0 for u in us)
+    assert 0 <= shape < bt.BT_NUM_SHAPES and len(us) == bt.BT_NUM_SHAPES and all(u > 0 for u in us)
     for g, pg, r in zip(gs, pgs, reps):
         # free-running comparison: the stated tolerance plus the motion of the
         # oracle's own next step (projective re-association keeps the iterate
@@ -86,7 +86,7 @@ def test_batch_replay_and_every_shape(bt):
     for pg in pgs:
         batch.add(pg)
     results = []
-    for shape in range(4):
+    for shape in range(bt.BT_NUM_SHAPES):
         batch.set_shape(shape)
         for g, pg in zip(gs, pgs):
             pg.set_poses(g.pose_init)
