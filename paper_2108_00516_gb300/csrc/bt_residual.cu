@@ -563,11 +563,11 @@ __device__ void sparse_edge(const SolveArgs& a, int e)
         if (lane == 0) sred[warp][k] = v;
     }
     __syncthreads();
-    if (threadIdx.x < kSparseVals && (kFull || threadIdx.x >= 37)) {
+    for (int k = threadIdx.x; k < kSparseVals; k += blockDim.x) {   // blocks of 32 threads too
+        if (!kFull && k < 37) continue;
         float s = 0.f;
-#pragma unroll
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sred[w][threadIdx.x];
-        a.spart[(size_t)e * kSparseVals + threadIdx.x] = s;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sred[w][k];
+        a.spart[(size_t)e * kSparseVals + k] = s;
     }
 }
 
