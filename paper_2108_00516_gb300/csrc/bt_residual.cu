@@ -35,10 +35,6 @@
 #include <math.h>
 #include <stdint.h>
 
-#ifndef BT_RESIDUAL_PIPELINE
-#define BT_RESIDUAL_PIPELINE 1
-#endif
-
 namespace bt {
 
 // ---------------------------------------------------------------------------
@@ -388,76 +384,76 @@ __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
     }
     __syncthreads();
     const float dmax2 = a.dmax2, cmin = a.cmin, hub = a.huber_dense;
-    // phases 1-2 of one batch: T_j T_i^-1 p, pi(.), nearest pixel, bounds,
-    // then the batch's target gathers, all in flight together
-    auto project = [&](const PairConst& c, int bb, float (&qx)[kResBatch], float (&qy)[kResBatch],
-                       float (&qz)[kResBatch], int (&pix)[kResBatch], float4 (&t)[kResBatch]) {
+    for (int jj = 0; jj < N - 1; ++jj) {
+        const int j = jj < i ? jj : jj + 1;
+        const PairConst& c = pc[j];
         const float m0 = c.m[0], m1 = c.m[1], m2 = c.m[2], m3 = c.m[3];
         const float m4 = c.m[4], m5 = c.m[5], m6 = c.m[6], m7 = c.m[7];
         const float m8 = c.m[8], m9 = c.m[9], m10 = c.m[10], m11 = c.m[11];
+        float acc[kDenseVals];
 #pragma unroll
-        for (int k = 0; k < kResBatch; ++k) {
-            const int s = (bb * kResBatch + k) * kResThreads + threadIdx.x;
-            const float4 p = sp[s];
-            qx[k] = __fmaf_rn(m2, p.z, __fmaf_rn(m1, p.y, __fmaf_rn(m0, p.x, m3)));
-            qy[k] = __fmaf_rn(m6, p.z, __fmaf_rn(m5, p.y, __fmaf_rn(m4, p.x, m7)));
-            qz[k] = __fmaf_rn(m10, p.z, __fmaf_rn(m9, p.y, __fmaf_rn(m8, p.x, m11)));
-            bool ok = s < nvalid && qz[k] > 0.f;
-            const float rz = __frcp_rn(qz[k]);
-            const float uh = __fadd_rn(__fmaf_rn(__fmul_rn(c.fx, qx[k]), rz, c.cx), 0.5f);
-            const float vh = __fadd_rn(__fmaf_rn(__fmul_rn(c.fy, qy[k]), rz, c.cy), 0.5f);
-            ok = ok && uh >= 0.f && uh < c.Wf && vh >= 0.f && vh < c.Hf;
-            pix[k] = ok ? (((int)floorf(vh)) << 16) | (int)floorf(uh) : -1;
-        }
+        for (int k = 0; k < kDenseVals; ++k) acc[k] = 0.f;
+#pragma unroll 1
+        for (int bb = 0; bb < kResBatches; ++bb) {
+            // phase 1: T_j T_i^-1 p, pi(.), nearest pixel, bounds
+            float qx[kResBatch], qy[kResBatch], qz[kResBatch];
+            int pix[kResBatch];
 #pragma unroll
-        for (int k = 0; k < kResBatch; ++k) {
-            const int iu = pix[k] & 0xffff, iv = pix[k] >> 16;
-            t[k] = pix[k] >= 0 ? load_target<P>(c.tgt, (size_t)iv * c.W + iu, c.zref)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    };
-    // phase 3: gates, residual, Jacobian, Huber, accumulation
-    auto finish = [&](const PairConst& c, int bb, const float (&qx)[kResBatch], const float (&qy)[kResBatch],
-                      const float (&qz)[kResBatch], const int (&pix)[kResBatch], const float4 (&t)[kResBatch],
-                      float (&acc)[kDenseVals]) {
-        const float m0 = c.m[0], m1 = c.m[1], m2 = c.m[2];
-        const float m4 = c.m[4], m5 = c.m[5], m6 = c.m[6];
-        const float m8 = c.m[8], m9 = c.m[9], m10 = c.m[10];
+            for (int k = 0; k < kResBatch; ++k) {
+                const int s = (bb * kResBatch + k) * kResThreads + threadIdx.x;
+                const float4 p = sp[s];
+                qx[k] = __fmaf_rn(m2, p.z, __fmaf_rn(m1, p.y, __fmaf_rn(m0, p.x, m3)));
+                qy[k] = __fmaf_rn(m6, p.z, __fmaf_rn(m5, p.y, __fmaf_rn(m4, p.x, m7)));
+                qz[k] = __fmaf_rn(m10, p.z, __fmaf_rn(m9, p.y, __fmaf_rn(m8, p.x, m11)));
+                bool ok = s < nvalid && qz[k] > 0.f;
+                const float rz = __frcp_rn(qz[k]);
+                const float uh = __fadd_rn(__fmaf_rn(__fmul_rn(c.fx, qx[k]), rz, c.cx), 0.5f);
+                const float vh = __fadd_rn(__fmaf_rn(__fmul_rn(c.fy, qy[k]), rz, c.cy), 0.5f);
+                ok = ok && uh >= 0.f && uh < c.Wf && vh >= 0.f && vh < c.Hf;
+                pix[k] = ok ? (((int)floorf(vh)) << 16) | (int)floorf(uh) : -1;
+            }
+            // phase 2: the gathers of the batch in flight together
+            float4 t[kResBatch];
 #pragma unroll
-        for (int k = 0; k < kResBatch; ++k) {
-            if (!(pix[k] >= 0 && t[k].x > 0.f)) continue;
-            const int iu = pix[k] & 0xffff, iv = pix[k] >> 16;
-            const float tz = t[k].x;
-            const float tx = __fmul_rn(__fmul_rn(__fsub_rn((float)iu, c.cx), tz), c.ifx);
-            const float ty = __fmul_rn(__fmul_rn(__fsub_rn((float)iv, c.cy), tz), c.ify);
-            const float dx = __fsub_rn(tx, qx[k]), dy = __fsub_rn(ty, qy[k]), dz = __fsub_rn(tz, qz[k]);
-            const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-            if (!(d2 <= dmax2)) continue;
-            const float4 n = sn[(bb * kResBatch + k) * kResThreads + threadIdx.x];
-            const float nx = __fmaf_rn(m2, n.z, __fmaf_rn(m1, n.y, __fmul_rn(m0, n.x)));
-            const float ny = __fmaf_rn(m6, n.z, __fmaf_rn(m5, n.y, __fmul_rn(m4, n.x)));
-            const float nz = __fmaf_rn(m10, n.z, __fmaf_rn(m9, n.y, __fmul_rn(m8, n.x)));
-            const float cs = __fmaf_rn(nz, t[k].w, __fmaf_rn(ny, t[k].z, __fmul_rn(nx, t[k].y)));
-            if (!(cs >= cmin)) continue;
-            // accepted: r = n_j . (q - T_j T_i^-1 p), the point-to-plane
-            // distance of Eq. 3 expressed in camera j; J~ = (n_j, q x n_j)
-            const float r = fmaf(nx, dx, fmaf(ny, dy, nz * dz));
-            const float ar = fabsf(r);
-            const bool inl = ar <= hub;
-            const float rho = inl ? 0.5f * r * r : hub * (ar - 0.5f * hub);
-            if constexpr (kFull) {
-                const float w = inl ? 1.f : __fdividef(hub, ar);
-                const float J[6] = {nx, ny, nz, fmaf(ty, nz, -tz * ny), fmaf(tz, nx, -tx * nz),
-                                    fmaf(tx, ny, -ty * nx)};
-                accumulate_pair(acc, J, w, r, rho);
-            } else {
-                acc[27] += rho;
-                acc[28] += 1.f;
+            for (int k = 0; k < kResBatch; ++k) {
+                const int iu = pix[k] & 0xffff, iv = pix[k] >> 16;
+                t[k] = pix[k] >= 0 ? load_target<P>(c.tgt, (size_t)iv * c.W + iu, c.zref)
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            // phase 3: gates, residual, Jacobian, Huber, accumulation
+#pragma unroll
+            for (int k = 0; k < kResBatch; ++k) {
+                if (!(pix[k] >= 0 && t[k].x > 0.f)) continue;
+                const int iu = pix[k] & 0xffff, iv = pix[k] >> 16;
+                const float tz = t[k].x;
+                const float tx = __fmul_rn(__fmul_rn(__fsub_rn((float)iu, c.cx), tz), c.ifx);
+                const float ty = __fmul_rn(__fmul_rn(__fsub_rn((float)iv, c.cy), tz), c.ify);
+                const float dx = __fsub_rn(tx, qx[k]), dy = __fsub_rn(ty, qy[k]), dz = __fsub_rn(tz, qz[k]);
+                const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+                if (!(d2 <= dmax2)) continue;
+                const float4 n = sn[(bb * kResBatch + k) * kResThreads + threadIdx.x];
+                const float nx = __fmaf_rn(m2, n.z, __fmaf_rn(m1, n.y, __fmul_rn(m0, n.x)));
+                const float ny = __fmaf_rn(m6, n.z, __fmaf_rn(m5, n.y, __fmul_rn(m4, n.x)));
+                const float nz = __fmaf_rn(m10, n.z, __fmaf_rn(m9, n.y, __fmul_rn(m8, n.x)));
+                const float cs = __fmaf_rn(nz, t[k].w, __fmaf_rn(ny, t[k].z, __fmul_rn(nx, t[k].y)));
+                if (!(cs >= cmin)) continue;
+                // accepted: r = n_j . (q - T_j T_i^-1 p), the point-to-plane
+                // distance of Eq. 3 expressed in camera j; J~ = (n_j, q x n_j)
+                const float r = fmaf(nx, dx, fmaf(ny, dy, nz * dz));
+                const float ar = fabsf(r);
+                const bool inl = ar <= hub;
+                const float rho = inl ? 0.5f * r * r : hub * (ar - 0.5f * hub);
+                if constexpr (kFull) {
+                    const float w = inl ? 1.f : __fdividef(hub, ar);
+                    const float J[6] = {nx, ny, nz, fmaf(ty, nz, -tz * ny), fmaf(tz, nx, -tx * nz),
+                                        fmaf(tx, ny, -ty * nx)};
+                    accumulate_pair(acc, J, w, r, rho);
+                } else {
+                    acc[27] += rho;
+                    acc[28] += 1.f;
+                }
             }
         }
-    };
-    // the warp's 32 sums of one target to shared memory
-    auto park = [&](int jj, float (&acc)[kDenseVals]) {
         float* slot = red + ((size_t)jj * kW + warp) * kDenseVals;
         if constexpr (kFull) {
             slot[lane] = warp_transpose_reduce(acc, lane);
@@ -472,48 +468,6 @@ __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
                 slot[27] = c0;
                 slot[28] = c1;
             }
-        }
-    };
-    if constexpr (kResBatches == 1 && BT_RESIDUAL_PIPELINE) {
-        // software pipeline over the targets: the gathers of target jj + 1
-        // are issued before the arithmetic of target jj, so their latency
-        // overlaps a whole target's phase 3
-        float cqx[kResBatch], cqy[kResBatch], cqz[kResBatch], nqx[kResBatch], nqy[kResBatch], nqz[kResBatch];
-        int cpix[kResBatch], npix[kResBatch];
-        float4 ct[kResBatch], nt[kResBatch];
-        if (N > 1) project(pc[i == 0 ? 1 : 0], 0, cqx, cqy, cqz, cpix, ct);
-        for (int jj = 0; jj < N - 1; ++jj) {
-            const int j = jj < i ? jj : jj + 1;
-            if (jj + 1 < N - 1) project(pc[jj + 1 < i ? jj + 1 : jj + 2], 0, nqx, nqy, nqz, npix, nt);
-            float acc[kDenseVals];
-#pragma unroll
-            for (int k = 0; k < kDenseVals; ++k) acc[k] = 0.f;
-            finish(pc[j], 0, cqx, cqy, cqz, cpix, ct, acc);
-            park(jj, acc);
-#pragma unroll
-            for (int k = 0; k < kResBatch; ++k) {
-                cqx[k] = nqx[k];
-                cqy[k] = nqy[k];
-                cqz[k] = nqz[k];
-                cpix[k] = npix[k];
-                ct[k] = nt[k];
-            }
-        }
-    } else {
-        for (int jj = 0; jj < N - 1; ++jj) {
-            const int j = jj < i ? jj : jj + 1;
-            float acc[kDenseVals];
-#pragma unroll
-            for (int k = 0; k < kDenseVals; ++k) acc[k] = 0.f;
-#pragma unroll 1
-            for (int bb = 0; bb < kResBatches; ++bb) {
-                float qx[kResBatch], qy[kResBatch], qz[kResBatch];
-                int pix[kResBatch];
-                float4 t[kResBatch];
-                project(pc[j], bb, qx, qy, qz, pix, t);
-                finish(pc[j], bb, qx, qy, qz, pix, t, acc);
-            }
-            park(jj, acc);
         }
     }
     __syncthreads();
