@@ -345,6 +345,26 @@ int bt_warmstart_apply_batch(bt_warmstart* ws, bt_batch* b, int32_t* status_out)
 int bt_batch_solve_warm(bt_batch* b, bt_warmstart* ws, int32_t iters, int32_t fallback_iters,
                         const double* ref_costs, double tol, bt_solve_report* reps);
 
+/* --------------------------------------------- memory pool (host only)
+ * Keyframe selection of Sec. IV-C and pool augmentation of Sec. IV-E.  Both
+ * read the rotation blocks of 4x4 row-major poses (host arrays) and do no
+ * GPU work.  The distance of two keyframes is the geodesic distance of their
+ * rotations, arccos((tr(R_a^T R_b) - 1) / 2). */
+
+/* Greedy minimum-H-subgraph selection: starts from pool entry 0 (I_0) and
+ * repeatedly adds the pool entry with the smallest summed distance to the
+ * current frame and to every entry selected so far (ties: the earlier entry),
+ * until min(K, n_pool) entries are selected.  Writes their pool indices in
+ * selection order to out[0 .. count) and returns count, or a negative status
+ * (BT_ERR_INVALID: negative size, NULL, non-finite pose). */
+int32_t bt_select_keyframes(const double* pool_poses, int32_t n_pool, const double* pose_current, int32_t K,
+                            int32_t* out);
+
+/* Pool augmentation rule: 1 when the current frame's distance to every pool
+ * entry exceeds min_deg degrees (the paper uses 10), else 0; a negative
+ * status on bad arguments. */
+int32_t bt_is_novel_view(const double* pool_poses, int32_t n_pool, const double* pose_current, double min_deg);
+
 /* Profiling counters of one graph (the tracing facility; no paper
  * counterpart).  Launch counts are always kept; kernel durations are summed
  * from CUDA events recorded on the graph's stream around each launch of the

@@ -111,6 +111,9 @@ SIGNATURES = {
     "bt_warmstart_apply_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
     "bt_batch_solve_warm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double),
                                       C.c_double, C.POINTER(bt_solve_report)]),
+    "bt_select_keyframes": (C.c_int32, [C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_double), C.c_int32,
+                                        C.POINTER(C.c_int32)]),
+    "bt_is_novel_view": (C.c_int32, [C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_double), C.c_double]),
     "bt_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "bt_profile_read": (C.c_int, [C.c_void_p, C.POINTER(bt_profile)]),
     "bt_pair_dense_energy_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(bt_intrinsics),
@@ -383,6 +386,39 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _poses16(poses) -> np.ndarray:
+    a = np.asarray(poses, dtype=np.float64)
+    if a.shape[-2:] == (3, 3):                     # rotations only: embed in 4x4 poses
+        T = np.zeros(a.shape[:-2] + (4, 4))
+        T[..., :3, :3] = a
+        T[..., 3, 3] = 1.0
+        a = T
+    return np.ascontiguousarray(a.reshape(-1, 16))
+
+
+def select_keyframes(pool_poses, pose_current, K: int) -> list:
+    """bt_select_keyframes: pool indices (selection order) of the greedy
+    keyframe selection of Sec. IV-C.  Poses as (n, 4, 4) or rotations (n, 3, 3)."""
+    P = _poses16(pool_poses)
+    cur = _poses16(pose_current)
+    out = np.zeros(max(1, int(K)), np.int32)
+    n = load().bt_select_keyframes(P.ctypes.data_as(C.POINTER(C.c_double)), len(P),
+                                   cur.ctypes.data_as(C.POINTER(C.c_double)), int(K),
+                                   out.ctypes.data_as(C.POINTER(C.c_int32)))
+    _check(min(n, 0), "bt_select_keyframes")
+    return out[:n].tolist()
+
+
+def is_novel_view(pool_poses, pose_current, min_deg: float = 10.0) -> bool:
+    """bt_is_novel_view: the pool augmentation rule of Sec. IV-E."""
+    P = _poses16(pool_poses)
+    cur = _poses16(pose_current)
+    r = load().bt_is_novel_view(P.ctypes.data_as(C.POINTER(C.c_double)), len(P),
+                                cur.ctypes.data_as(C.POINTER(C.c_double)), float(min_deg))
+    _check(min(r, 0), "bt_is_novel_view")
+    return bool(r)
 
 
 WS_NUM_PARAMS = 67590
