@@ -37,7 +37,8 @@ class _MatchSet(C.Structure):
 class _Params(C.Structure):
     _fields_ = [("huber_sparse", C.c_double), ("huber_dense", C.c_double),
                 ("dense_max_dist", C.c_double), ("dense_max_normal_deg", C.c_double),
-                ("lambda_sparse", C.c_double), ("lambda_dense", C.c_double)]
+                ("lambda_sparse", C.c_double), ("lambda_dense", C.c_double),
+                ("solver", C.c_int32), ("pcg_max_iters", C.c_int32), ("pcg_tol", C.c_double)]
 
 
 @dataclass
@@ -51,10 +52,14 @@ class Params:
     dense_max_normal_deg: float = 45.0
     lambda_sparse: float = 1.0
     lambda_dense: float = 1.0
+    solver: int = 0               # 0: Cholesky, 1: PCG with Jacobi preconditioner (Sec. IV-D)
+    pcg_max_iters: int = 500
+    pcg_tol: float = 1e-10
 
     def c(self) -> _Params:
         return _Params(self.huber_sparse, self.huber_dense, self.dense_max_dist,
-                       self.dense_max_normal_deg, self.lambda_sparse, self.lambda_dense)
+                       self.dense_max_normal_deg, self.lambda_sparse, self.lambda_dense,
+                       self.solver, self.pcg_max_iters, self.pcg_tol)
 
 
 _LIB = None
@@ -73,6 +78,8 @@ def lib():
         L.orc_se3_log.argtypes = [_dp, _dp]
         L.orc_cholesky_solve.restype = C.c_int
         L.orc_cholesky_solve.argtypes = [C.c_int, _dp, _dp]
+        L.orc_pcg_solve.restype = C.c_int
+        L.orc_pcg_solve.argtypes = [C.c_int, _dp, _dp, C.c_int, C.c_double, C.POINTER(C.c_int)]
         L.orc_associate.restype = C.c_int
         L.orc_associate.argtypes = [C.POINTER(_Frame), C.POINTER(_Frame), _dp, _dp,
                                     C.POINTER(_Params), _ip, _ip, C.c_int]
@@ -236,6 +243,18 @@ def cholesky_solve(A, b):
     st = lib().orc_cholesky_solve(len(b), _ptr(A, C.c_double), _ptr(b, C.c_double))
     return b, st
 
+
+
+def pcg_solve(A, b, max_iters: int = 500, tol: float = 1e-10):
+    """x of A x = b by Jacobi-preconditioned conjugate gradients, and the
+    iteration count (raises ValueError if A is not positive definite)."""
+    A = np.ascontiguousarray(A, np.float64)
+    x = np.ascontiguousarray(b, np.float64).copy()
+    it = C.c_int()
+    if lib().orc_pcg_solve(len(x), _ptr(A, C.c_double), _ptr(x, C.c_double), int(max_iters), float(tol),
+                           C.byref(it)) != 0:
+        raise ValueError("matrix not positive definite")
+    return x, it.value
 
 def huber_rho(r, delta):
     return lib().orc_huber_rho(float(r), float(delta))

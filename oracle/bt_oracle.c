@@ -217,6 +217,63 @@ int orc_cholesky_solve(int n, double* A, double* b)
     return 0;
 }
 
+/* Conjugate gradients with the diagonal preconditioner M = diag(A) (the
+ * inner solver of Sec. IV-D), textbook form: r = b - A x, z = M^-1 r,
+ * p = z; alpha = r.z / p.Ap, x += alpha p, r -= alpha Ap, beta = r'.z' / r.z,
+ * p = z' + beta p. */
+int orc_pcg_solve(int n, const double* A, double* b, int max_iters, double rel_tol, int* iters)
+{
+    double* x = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double* r = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double* z = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double* p = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double* q = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    int status = 0, it = 0;
+    if (!x || !r || !z || !p || !q) status = -2;
+    double bb = 0.0, rz = 0.0;
+    for (int i = 0; i < n && status == 0; ++i) {
+        if (!(A[i * n + i] > 0.0)) status = -1;
+        r[i] = b[i];
+        bb += b[i] * b[i];
+    }
+    for (int i = 0; i < n && status == 0; ++i) {
+        z[i] = r[i] / A[i * n + i];
+        p[i] = z[i];
+        rz += r[i] * z[i];
+    }
+    double rr = bb;
+    while (status == 0 && it < max_iters && rr > rel_tol * rel_tol * bb) {
+        double pq = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < n; ++j) s += A[i * n + j] * p[j];
+            q[i] = s;
+            pq += p[i] * s;
+        }
+        if (!(pq > 0.0)) { status = -1; break; }
+        const double alpha = rz / pq;
+        rr = 0.0;
+        for (int i = 0; i < n; ++i) {
+            x[i] += alpha * p[i];
+            r[i] -= alpha * q[i];
+            rr += r[i] * r[i];
+        }
+        double rz_new = 0.0;
+        for (int i = 0; i < n; ++i) {
+            z[i] = r[i] / A[i * n + i];
+            rz_new += r[i] * z[i];
+        }
+        const double beta = rz_new / rz;
+        rz = rz_new;
+        for (int i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+        ++it;
+    }
+    if (status == 0) memcpy(b, x, sizeof(double) * (size_t)n);
+    if (iters) *iters = it;
+    free(x); free(r); free(z); free(p); free(q);
+    return status;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Projective data association (Eq. 3 and the gating sentence after it)     */
 /* ------------------------------------------------------------------------ */
@@ -587,7 +644,8 @@ int orc_solve(const orc_frame* frames, int n_frames, double* poses, const int32_
                     for (int rc = 0; rc < 6; ++rc)
                         Hf[(6 * a + ra) * m + 6 * c + rc] = H[row * n6 + 6L * freeidx[c] + rc];
             }
-        if (orc_cholesky_solve(m, Hf, b) != 0) {
+        if ((prm->solver == 1 ? orc_pcg_solve(m, Hf, b, prm->pcg_max_iters, prm->pcg_tol, NULL)
+                              : orc_cholesky_solve(m, Hf, b)) != 0) {
             status = -1;
             break;
         }

@@ -50,6 +50,9 @@ typedef struct {
     double dense_max_normal_deg;  /* association gate: normal angle */
     double lambda_sparse;         /* lambda_1 of Eq. 1 */
     double lambda_dense;          /* lambda_2 of Eq. 1 */
+    int32_t solver;               /* 0: Cholesky, 1: PCG with Jacobi preconditioner */
+    int32_t pcg_max_iters;        /* PCG: iteration limit */
+    double pcg_tol;               /* PCG: stop when |r| <= pcg_tol |b| */
 } orc_params;
 
 /* Huber M-estimator rho and its IRLS weight rho'(r)/r. */
@@ -65,6 +68,14 @@ void orc_se3_log(const double T[16], double xi[6]);
  * overwritten; x returned in b).  Returns 0, or -1 if A is not positive
  * definite. */
 int orc_cholesky_solve(int n, double* A, double* b);
+
+/* Solve A x = b for symmetric positive-definite A (n x n, row-major, not
+ * modified) by the conjugate-gradient method with the diagonal (Jacobi)
+ * preconditioner, from x = 0, until |b - A x| <= rel_tol |b| or max_iters
+ * iterations; x returned in b, the iteration count in *iters (may be NULL).
+ * Returns 0, or -1 if a diagonal entry or a curvature p^T A p is not
+ * positive. */
+int orc_pcg_solve(int n, const double* A, double* b, int max_iters, double rel_tol, int* iters);
 
 /* Projective data association of Eq. 3 for the ordered pair (i -> j): every
  * valid masked pixel of frame i is projected into frame j, rounded to the
@@ -105,7 +116,8 @@ long orc_normal_equations(const orc_frame* frames, int n_frames, const double* p
                           int n_threads, double* H, double* g, double* energy);
 
 /* Iteratively re-weighted Gauss-Newton (Sec. IV-D): `iters` iterations of
- * associate -> normal equations -> Cholesky -> T_i <- exp(dxi_i) T_i for the
+ * associate -> normal equations -> Cholesky (or, with prm->solver == 1, the
+ * paper's preconditioned conjugate gradients) -> T_i <- exp(dxi_i) T_i for the
  * nodes with fixed[i] == 0, then the energy at the final poses.
  * cost_per_iter[k] = E before iteration k.  Returns 0, or -1 (poses
  * restored to their input values) if a system is not positive definite. */
