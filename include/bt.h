@@ -83,9 +83,16 @@ typedef struct {
  *   dense_max_dist = 0.02 m                (association gate on point-pair distance)
  *   dense_max_normal_deg = 45              (association gate on normal angle)
  *   lambda_sparse = lambda_dense = 1       (lambda_1, lambda_2 of Eq. 1)
- *   precision = BT_FP32, max_frames = 0 (no limit on stored frames).
+ *   precision = BT_FP32, max_frames = 0 (no limit on stored frames),
+ *   solver = BT_SOLVER_CHOLESKY, pcg_max_iters = 500, pcg_tol = 1e-10.
  * precision selects the storage of the per-pixel maps (BT_FP32 / BT_BF16 /
- * BT_FP16); it is fixed for the graph's lifetime. */
+ * BT_FP16); it is fixed for the graph's lifetime.  solver selects how each
+ * Gauss-Newton system H dx = -g is solved: BT_SOLVER_CHOLESKY, an exact FP64
+ * LDL^T factorisation, or BT_SOLVER_PCG, the paper's conjugate gradients
+ * with the diagonal (Jacobi) preconditioner (Sec. IV-D), in FP64 from
+ * dx = 0 until |H dx + g| <= pcg_tol |g| or pcg_max_iters iterations. */
+#define BT_SOLVER_CHOLESKY 0
+#define BT_SOLVER_PCG 1
 typedef struct {
     double huber_sparse;
     double huber_dense;
@@ -95,6 +102,9 @@ typedef struct {
     double lambda_dense;
     int32_t precision;
     int32_t max_frames;
+    int32_t solver;
+    int32_t pcg_max_iters;
+    double pcg_tol;
 } bt_config;
 
 /* Correspondences between a frame being added and an already stored frame

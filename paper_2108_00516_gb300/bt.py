@@ -28,6 +28,8 @@ BT_FP16 = 2
 BT_MAX_NODES = 24
 BT_MAX_REPORT_ITERS = 64
 BT_NUM_SHAPES = 6
+BT_SOLVER_CHOLESKY = 0
+BT_SOLVER_PCG = 1
 
 LIB_PATH = Path(__file__).resolve().parent / "_build" / "libbt.so"
 
@@ -41,7 +43,8 @@ class bt_config(C.Structure):
     _fields_ = [("huber_sparse", C.c_double), ("huber_dense", C.c_double),
                 ("dense_max_dist", C.c_double), ("dense_max_normal_deg", C.c_double),
                 ("lambda_sparse", C.c_double), ("lambda_dense", C.c_double),
-                ("precision", C.c_int32), ("max_frames", C.c_int32)]
+                ("precision", C.c_int32), ("max_frames", C.c_int32),
+                ("solver", C.c_int32), ("pcg_max_iters", C.c_int32), ("pcg_tol", C.c_double)]
 
 
 class bt_matches(C.Structure):

@@ -47,6 +47,10 @@ int validate_config(const bt_config& c)
     if (c.precision != BT_FP32 && c.precision != BT_BF16 && c.precision != BT_FP16)
         return fail(BT_ERR_INVALID, "config: precision must be BT_FP32, BT_BF16 or BT_FP16");
     if (c.max_frames < 0) return fail(BT_ERR_INVALID, "config: max_frames must be >= 0");
+    if (c.solver != BT_SOLVER_CHOLESKY && c.solver != BT_SOLVER_PCG)
+        return fail(BT_ERR_INVALID, "config: solver must be BT_SOLVER_CHOLESKY or BT_SOLVER_PCG");
+    if (c.pcg_max_iters < 0 || !std::isfinite(c.pcg_tol) || c.pcg_tol < 0.0)
+        return fail(BT_ERR_INVALID, "config: pcg_max_iters must be >= 0 and pcg_tol finite and >= 0");
     return BT_OK;
 }
 
@@ -206,6 +210,9 @@ int bthost::build_topology(bt_graph* g, int tile)
     a.huber_sparse = (float)c.huber_sparse;
     a.lambda_dense = c.lambda_dense;
     a.lambda_sparse = c.lambda_sparse;
+    a.solver = c.solver;
+    a.pcg_max_iters = c.pcg_max_iters;
+    a.pcg_tol2 = c.pcg_tol * c.pcg_tol;
     a.nodes = g->d_nodes.as<bt::NodeDev>();
     a.edges = g->d_edges.as<bt::EdgeDev>();
     a.tile_node = g->d_tile_node.as<int>();
@@ -320,6 +327,9 @@ void bt_config_default(bt_config* cfg)
     cfg->lambda_dense = 1.0;
     cfg->precision = BT_FP32;
     cfg->max_frames = 0;
+    cfg->solver = BT_SOLVER_CHOLESKY;
+    cfg->pcg_max_iters = 500;
+    cfg->pcg_tol = 1e-10;
 }
 
 int bt_graph_create(const bt_config* cfg, void* cuda_stream, bt_graph** out)

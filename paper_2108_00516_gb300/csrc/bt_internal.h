@@ -88,6 +88,9 @@ struct SolveArgs {
     int stage_blocks;       // 1: the last CTA copies the pair blocks to shared memory
     float dmax2, cmin, huber_dense, huber_sparse;
     double lambda_dense, lambda_sparse;
+    int solver;             // BT_SOLVER_CHOLESKY / BT_SOLVER_PCG
+    int pcg_max_iters;
+    double pcg_tol2;        // squared relative residual tolerance of PCG
     const NodeDev* nodes;
     const EdgeDev* edges;
     const int* tile_node;

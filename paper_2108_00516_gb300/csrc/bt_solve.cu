@@ -505,6 +505,92 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
     }
     __syncthreads();
     unsigned long long t1 = clock64();
+    double* colb = tinv + 12 * kMaxNodes;   // [2][n]
+    unsigned long long t2, t3;
+    if (a.solver == 1) {
+        // Conjugate gradients with the diagonal preconditioner (the paper's
+        // inner solver, Sec. IV-D), FP64, from dx = 0.  The matrix-vector
+        // product is split over (row, column chunk) pairs so that every
+        // thread has work: a warp-wide FP64 instruction costs its
+        // sub-partition the same whatever the number of active lanes.
+        double* xv = colb;           // dx
+        double* pv = colb + n;       // search direction
+        double* rv = y;              // residual, starts as -g
+        double* zv = rD;             // preconditioned residual
+        double* qv = tinv;           // H p
+        double* part = reinterpret_cast<double*>(node_of + kMaxNodes);   // [n * C]
+        double* red = part + 256;    // [8]
+        const int C = nt / n > 0 ? nt / n : 1;
+        const int w = (n + C - 1) / C;
+        auto block_sum = [&](double v) {
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if (lane == 0) red[warp] = v;
+            __syncthreads();
+            double t = 0.0;
+            for (int k = 0; k < nt / 32; ++k) t += red[k];
+            __syncthreads();
+            return t;
+        };
+        double bb = 0.0, rz = 0.0;
+        for (int i = tid; i < n; i += nt) {
+            const double d = H[i * ld + i];
+            if (!(d > 0.0)) s_fail = 1;
+            xv[i] = 0.0;
+            zv[i] = rv[i] / d;
+            pv[i] = zv[i];
+            bb += rv[i] * rv[i];
+            rz += rv[i] * zv[i];
+        }
+        bb = block_sum(bb);
+        rz = block_sum(rz);
+        double rr = bb;
+        for (int it = 0; !s_fail && it < a.pcg_max_iters && rr > a.pcg_tol2 * bb; ++it) {
+            if (tid < n * C) {
+                const int i = tid / C, c = tid % C;
+                const int j1 = (c + 1) * w < n ? (c + 1) * w : n;
+                double v = 0.0;
+                for (int j = c * w; j < j1; ++j) v += (j <= i ? H[i * ld + j] : H[j * ld + i]) * pv[j];
+                part[tid] = v;
+            }
+            __syncthreads();
+            double pq = 0.0;
+            for (int i = tid; i < n; i += nt) {
+                double v = 0.0;
+                for (int c = 0; c < C; ++c) v += part[i * C + c];
+                qv[i] = v;
+                pq += pv[i] * v;
+            }
+            pq = block_sum(pq);
+            if (!(pq > 0.0)) {
+                if (tid == 0) s_fail = 1;
+                __syncthreads();
+                break;
+            }
+            const double alpha = rz / pq;
+            double rrp = 0.0, rzp = 0.0;
+            for (int i = tid; i < n; i += nt) {
+                xv[i] += alpha * pv[i];
+                rv[i] -= alpha * qv[i];
+                zv[i] = rv[i] / H[i * ld + i];
+                rrp += rv[i] * rv[i];
+                rzp += rv[i] * zv[i];
+            }
+            rr = block_sum(rrp);
+            const double rz_new = block_sum(rzp);
+            const double beta = rz_new / rz;
+            rz = rz_new;
+            for (int i = tid; i < n; i += nt) pv[i] = zv[i] + beta * pv[i];
+            __syncthreads();
+        }
+        if (s_fail) {
+            if (tid == 0) a.ctrl->status = -4;
+            return;
+        }
+        for (int i = tid; i < n; i += nt) y[i] = xv[i];
+        __syncthreads();
+        t2 = t3 = clock64();
+    } else {
     // LDL^T with a one-column look-ahead, one barrier per column.  At step k
     // warp 0 prepares column k+1 -- its update by column k, the pivot
     // D_{k+1} and reciprocal, and the scaled l_{i,k+1} -- while warps
@@ -512,7 +598,6 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
     // trailing triangle of rows and columns >= k+2 and carry the forward
     // substitution.  The scaled column is double-buffered; L is stored
     // transposed in the upper triangle, L_ik at (k, i).
-    double* colb = tinv + 12 * kMaxNodes;   // [2][n]
     int* tab = reinterpret_cast<int*>(colb + 2 * n);
     for (int ip = tid; ip < n; ip += nt)
         for (int jp = 0; jp <= ip; ++jp) tab[ip * (ip + 1) / 2 + jp] = (ip << 16) | jp;
@@ -607,7 +692,7 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
     }
     for (int i = tid; i < n; i += nt) y[i] *= rD[i];   // D w = z
     __syncthreads();
-    unsigned long long t2 = clock64();
+    t2 = clock64();
     // L^T dx = w, unit diagonal (one warp; L_ki is stored at (i, k)).  Lane l
     // keeps w_i for i = l, l + 32, ... in registers; x_k is broadcast from its
     // owner with a shuffle, so each step is one shuffle and one FMA deep.
@@ -644,7 +729,8 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
         }
     }
     __syncthreads();
-    unsigned long long t3 = clock64();
+    t3 = clock64();
+    }
     // T_A <- T_A exp(dx_A): one thread per entry of exp(dx_A), then one per
     // entry of the product (the look-ahead columns and tinv are free now)
     {
@@ -704,7 +790,8 @@ static size_t reduce_smem_bytes_for(int n_free, int N, bool stage)
     const size_t U = (size_t)N * (N - 1) / 2;
     const size_t sl = stage ? U * kUPairBlk : 0;
     const size_t tab_dbl = (n * (n + 1) / 2 + 1) / 2;
-    size_t fin = (n * (n + 1) + 4 * n + 24 * (size_t)kMaxNodes + tab_dbl + 1 + sl) * sizeof(double) +
+    // ... + the PCG scratch after node_of: 256 partial sums + 8 warp sums
+    size_t fin = (n * (n + 1) + 4 * n + 24 * (size_t)kMaxNodes + tab_dbl + 1 + sl + 264) * sizeof(double) +
                  kMaxNodes * sizeof(int);
     size_t ph1 = kPairSmemDoubles * sizeof(double);
     return fin > ph1 ? fin : ph1;
