@@ -355,6 +355,37 @@ int bt_warmstart_apply_batch(bt_warmstart* ws, bt_batch* b, int32_t* status_out)
 int bt_batch_solve_warm(bt_batch* b, bt_warmstart* ws, int32_t iters, int32_t fallback_iters,
                         const double* ref_costs, double tol, bt_solve_report* reps);
 
+/* ------------------------------------------------- coarse registration
+ * Sec. IV-B: RANSAC over 3-point samples of a correspondence set, each
+ * hypothesis the closed-form least-squares rigid fit (Arun et al.; computed
+ * in quaternion form), an inlier a pair with |R p + t - q| < inlier_dist
+ * (the paper uses 5 mm; its normal-angle gate needs normals, which
+ * correspondence sets do not carry).  The result is the sample with the
+ * most inliers (ties: the earlier sample), refitted on its inliers when
+ * refine != 0 (the paper keeps the best sample's fit).  Sample h draws its
+ * indices from the counter-based SplitMix64 generator: value(c) =
+ * mix(seed + (c + 1) * 0x9E3779B97F4A7C15) for c = 16 h, 16 h + 1, ...,
+ * index = value % count, the first three distinct indices.  Inlier tests are
+ * evaluated in single precision with a fixed operation order. */
+
+/* Relative pose of one correspondence set: rel_out (4x4 row-major) maps
+ * camera i to camera j, q ~ rel_out p (pts_i, pts_j: count x 3 floats, host
+ * or device); inliers_out (may be NULL) gets the inlier count.  With fewer
+ * than 3 points or only degenerate samples rel_out is the identity and the
+ * count 0.  Enqueued on cuda_stream and synchronised.
+ * Errors: BT_ERR_INVALID, BT_ERR_CUDA, BT_ERR_OOM. */
+int bt_ransac(const float* pts_i, const float* pts_j, int32_t count, int32_t mem_kind, int32_t hypotheses,
+              uint64_t seed, double inlier_dist, int32_t refine, double* rel_out, int32_t* inliers_out,
+              void* cuda_stream);
+
+/* Coarse initialisation of a graph's free active nodes, as the paper
+ * initialises a new frame from the previous one: each free node j with a
+ * correspondence set to a fixed node f (the lowest-indexed such f) gets
+ * T_j = M T_f with M = T_j T_f^-1 estimated by bt_ransac on that set (all
+ * sets in one launch); other nodes keep their poses.
+ * Errors: BT_ERR_INVALID, BT_ERR_CUDA, BT_ERR_OOM. */
+int bt_ransac_init(bt_graph* g, int32_t hypotheses, uint64_t seed, double inlier_dist, int32_t refine);
+
 /* --------------------------------------------- memory pool (host only)
  * Keyframe selection of Sec. IV-C and pool augmentation of Sec. IV-E.  Both
  * read the rotation blocks of 4x4 row-major poses (host arrays) and do no

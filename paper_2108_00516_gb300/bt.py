@@ -114,6 +114,9 @@ SIGNATURES = {
     "bt_warmstart_apply_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
     "bt_batch_solve_warm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double),
                                       C.c_double, C.POINTER(bt_solve_report)]),
+    "bt_ransac": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.c_double,
+                            C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int32), C.c_void_p]),
+    "bt_ransac_init": (C.c_int, [C.c_void_p, C.c_int32, C.c_uint64, C.c_double, C.c_int32]),
     "bt_select_keyframes": (C.c_int32, [C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_double), C.c_int32,
                                         C.POINTER(C.c_int32)]),
     "bt_is_novel_view": (C.c_int32, [C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_double), C.c_double]),
@@ -299,6 +302,11 @@ class PoseGraph:
                  dense_inliers=rep.dense_inliers, dense_pixel_pairs=rep.dense_pixel_pairs)
         return out, r
 
+    def ransac_init(self, hypotheses: int = 256, seed: int = 0, inlier_dist: float = 0.005, refine: bool = False):
+        """bt_ransac_init: the paper's coarse initialisation of the free nodes."""
+        _check(load().bt_ransac_init(self._h, int(hypotheses), int(seed) & ((1 << 64) - 1), float(inlier_dist),
+                                     1 if refine else 0), "bt_ransac_init")
+
     def profile_enable(self, on: bool = True):
         _check(load().bt_profile_enable(self._h, int(bool(on))), "bt_profile_enable")
 
@@ -399,6 +407,22 @@ def _poses16(poses) -> np.ndarray:
         T[..., 3, 3] = 1.0
         a = T
     return np.ascontiguousarray(a.reshape(-1, 16))
+
+
+def ransac(pts_i, pts_j, hypotheses: int = 256, seed: int = 0, inlier_dist: float = 0.005, refine: bool = False,
+           stream=None):
+    """bt_ransac: (4x4 relative pose q ~ M p, inlier count) of one
+    correspondence set (numpy arrays or CUDA tensors)."""
+    pi, ki, kind = _ptr(pts_i, np.float32)
+    pj, kj, kind2 = _ptr(pts_j, np.float32)
+    if kind != kind2:
+        raise ValueError("both point arrays must live in the same memory")
+    M = np.zeros(16)
+    cnt = C.c_int32()
+    _check(load().bt_ransac(pi, pj, int(ki.shape[0]), kind, int(hypotheses), int(seed) & ((1 << 64) - 1),
+                            float(inlier_dist), 1 if refine else 0, M.ctypes.data_as(C.POINTER(C.c_double)),
+                            C.byref(cnt), _stream_handle(stream)), "bt_ransac")
+    return M.reshape(4, 4), cnt.value
 
 
 def select_keyframes(pool_poses, pose_current, K: int) -> list:
