@@ -55,20 +55,28 @@ int validate_config(const bt_config& c)
 }
 
 // Copies a count x 3 point list (host or device) into a new device array.
-int upload_points(const float* src, int count, int mem_kind, cudaStream_t s, float** out)
+// Copies a count x 3 point list (host or device) into a pooled device block.
+int upload_points(bt_graph* g, const float* src, int count, int mem_kind, float** out)
 {
     *out = nullptr;
     if (count == 0) return BT_OK;
     const size_t bytes = sizeof(float) * 3 * (size_t)count;
-    BT_CUDA(cudaMalloc(out, bytes), "cudaMalloc(matches)");
-    cudaError_t e = cudaMemcpyAsync(*out, src, bytes,
-                                    mem_kind == BT_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s);
+    void* p = nullptr;
+    BT_CUDA(g->pool.get(bytes, &p), "alloc(matches)");
+    cudaError_t e = cudaMemcpyAsync(p, src, bytes,
+                                    mem_kind == BT_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, g->stream);
     if (e != cudaSuccess) {
-        cudaFree(*out);
-        *out = nullptr;
+        g->pool.put(p, bytes);
         return cuda_fail(e, "cudaMemcpyAsync(matches)");
     }
+    *out = static_cast<float*>(p);
     return BT_OK;
+}
+
+void drop_matches(bt_graph* g, const MatchSet& m)
+{
+    g->pool.put(m.pa, sizeof(float) * 3 * (size_t)m.count);
+    g->pool.put(m.pb, sizeof(float) * 3 * (size_t)m.count);
 }
 
 int put_matches(bt_graph* g, int fa, int fb, int count, const float* pa, const float* pb, int mem_kind)
@@ -85,19 +93,17 @@ int put_matches(bt_graph* g, int fa, int fb, int count, const float* pa, const f
     ms.fa = fa;
     ms.fb = fb;
     ms.count = count;
-    int st = upload_points(pa, count, mem_kind, g->stream, &ms.pa);
+    int st = upload_points(g, pa, count, mem_kind, &ms.pa);
     if (st != BT_OK) return st;
-    st = upload_points(pb, count, mem_kind, g->stream, &ms.pb);
+    st = upload_points(g, pb, count, mem_kind, &ms.pb);
     if (st != BT_OK) {
-        cudaFree(ms.pa);
+        g->pool.put(ms.pa, sizeof(float) * 3 * (size_t)count);
         return st;
     }
     auto key = std::make_pair(fa, fb);
     auto it = g->matches.find(key);
     if (it != g->matches.end()) {
-        cudaStreamSynchronize(g->stream);
-        cudaFree(it->second.pa);
-        cudaFree(it->second.pb);
+        drop_matches(g, it->second);
         g->matches.erase(it);
     }
     if (count > 0) g->matches[key] = ms;
@@ -109,8 +115,30 @@ int put_matches(bt_graph* g, int fa, int fb, int count, const float* pa, const f
 // per-solve buffers.
 }  // namespace
 
+int bthost::resolve_pending(bt_graph* g)
+{
+    bool any = false;
+    for (auto& kv : g->frames) any |= kv.second.pending;
+    if (!any) return BT_OK;
+    BT_CUDA(cudaStreamSynchronize(g->stream), "read back frame preparation");
+    for (auto& kv : g->frames) {
+        Frame& f = kv.second;
+        if (!f.pending) continue;
+        f.M = g->pin_m2[2 * f.slot];
+        std::memcpy(&f.zref, &g->pin_m2[2 * f.slot + 1], sizeof(float));
+        g->free_slots.push_back(f.slot);
+        g->pool.put(f.dev_m2, 2 * sizeof(int));
+        f.dev_m2 = nullptr;
+        f.slot = -1;
+        f.pending = false;
+    }
+    return BT_OK;
+}
+
 int bthost::build_topology(bt_graph* g, int tile)
 {
+    int pst = resolve_pending(g);
+    if (pst != BT_OK) return pst;
     const int N = (int)g->active.size();
     if (N < 1) return fail(BT_ERR_INVALID, "solve: no active nodes");
     if (N > BT_MAX_NODES) return fail(BT_ERR_INVALID, "solve: more than BT_MAX_NODES active nodes");
@@ -396,36 +424,57 @@ int bt_add_frame(bt_graph* g, const float* depth, const float* normals, const ui
     const int P = g->cfg.precision;
     const size_t pb = bt::pixel_bytes(P);
     BT_CUDA(g->prep_blk.ensure(bt::prep_scratch_bytes(HW)), "alloc prep");
-    BT_CUDA(g->prep_src_p.ensure(pb * HW), "alloc prep");
-    BT_CUDA(g->prep_src_n.ensure(pb * HW), "alloc prep");
-    BT_CUDA(g->prep_M.ensure(2 * sizeof(int)), "alloc prep");
+    // a pinned host slot for the (M, zref) read-back, read at the next
+    // topology build instead of waiting here
+    if (g->free_slots.empty()) {
+        int st = resolve_pending(g);       // no copy may be in flight into the old slots
+        if (st != BT_OK) return st;
+        const int cap = std::max(64, 2 * g->pin_cap);
+        int* np = nullptr;
+        BT_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&np), sizeof(int) * 2 * (size_t)cap, cudaHostAllocDefault),
+                "cudaHostAlloc(read-back slots)");
+        if (g->pin_m2) cudaFreeHost(g->pin_m2);
+        g->pin_m2 = np;
+        for (int k = cap - 1; k >= g->pin_cap; --k) g->free_slots.push_back(k);
+        g->pin_cap = cap;
+    }
     Frame f;
-    BT_CUDA(cudaMalloc(&f.tgt, pb * HW), "cudaMalloc(target map)");
+    f.tgt_bytes = pb * HW;
+    f.src_bytes = pb * HW;
+    void *t = nullptr, *sp = nullptr, *sn = nullptr, *m2 = nullptr;
+    cudaError_t e = g->pool.get(f.tgt_bytes, &t);
+    if (e == cudaSuccess) e = g->pool.get(f.src_bytes, &sp);
+    if (e == cudaSuccess) e = g->pool.get(f.src_bytes, &sn);
+    if (e == cudaSuccess) e = g->pool.get(2 * sizeof(int), &m2);
+    f.tgt = t;
+    f.src_p = sp;
+    f.src_n = sn;
+    f.dev_m2 = static_cast<int*>(m2);
     const float ifx = 1.0f / K->fx, ify = 1.0f / K->fy;
-    cudaError_t e = bt::launch_prep(d_depth, d_normals, d_mask, W, H, K->cx, K->cy, ifx, ify, P, f.tgt,
-                                    g->prep_src_p.p, g->prep_src_n.p, g->prep_blk.p, g->prep_M.as<int>(), s);
+    if (e == cudaSuccess)
+        e = bt::launch_prep(d_depth, d_normals, d_mask, W, H, K->cx, K->cy, ifx, ify, P, f.tgt, f.src_p, f.src_n,
+                            g->prep_blk.p, f.dev_m2, s);
     g->prof.prep_launches += 3;
-    int out2[2] = {0, 0};
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out2, g->prep_M.p, sizeof(out2), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    const int M = out2[0];
-    if (e == cudaSuccess && M > 0) {
-        e = cudaMalloc(&f.src_p, pb * M);
-        if (e == cudaSuccess) e = cudaMalloc(&f.src_n, pb * M);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(f.src_p, g->prep_src_p.p, pb * M, cudaMemcpyDeviceToDevice, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(f.src_n, g->prep_src_n.p, pb * M, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) {
+        f.slot = g->free_slots.back();
+        g->free_slots.pop_back();
+        e = cudaMemcpyAsync(g->pin_m2 + 2 * f.slot, f.dev_m2, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+        f.pending = true;
+        if (e != cudaSuccess) {
+            g->free_slots.push_back(f.slot);
+            f.slot = -1;
+        }
     }
     if (e != cudaSuccess) {
-        cudaFree(f.tgt);
-        cudaFree(f.src_p);
-        cudaFree(f.src_n);
+        g->pool.put(f.tgt, f.tgt_bytes);
+        g->pool.put(f.src_p, f.src_bytes);
+        g->pool.put(f.src_n, f.src_bytes);
+        g->pool.put(f.dev_m2, 2 * sizeof(int));
         return cuda_fail(e, "bt_add_frame: preparation");
     }
-    std::memcpy(&f.zref, &out2[1], sizeof(float));
     f.id = g->next_id;
     f.K = *K;
     f.fixed = fixed ? 1 : 0;
-    f.M = M;
     std::memcpy(f.pose, pose_init, sizeof(double) * 16);
     g->frames[f.id] = f;
     g->next_id++;
@@ -460,15 +509,20 @@ int bt_remove_frame(bt_graph* g, int32_t frame_id)
     if (!g) return fail(BT_ERR_INVALID, "bt_remove_frame: NULL graph");
     auto it = g->frames.find(frame_id);
     if (it == g->frames.end()) return fail(BT_ERR_INVALID, "bt_remove_frame: unknown frame id");
-    cudaStreamSynchronize(g->stream);
-    cudaFree(it->second.tgt);
-    cudaFree(it->second.src_p);
-    cudaFree(it->second.src_n);
+    // blocks go back to the pool: later work that reuses them is enqueued
+    // after every earlier use on the same stream
+    Frame& f = it->second;
+    g->pool.put(f.tgt, f.tgt_bytes);
+    g->pool.put(f.src_p, f.src_bytes);
+    g->pool.put(f.src_n, f.src_bytes);
+    if (f.pending) {
+        g->pool.put(f.dev_m2, 2 * sizeof(int));
+        g->free_slots.push_back(f.slot);
+    }
     g->frames.erase(it);
     for (auto m = g->matches.begin(); m != g->matches.end();) {
         if (m->second.fa == frame_id || m->second.fb == frame_id) {
-            cudaFree(m->second.pa);
-            cudaFree(m->second.pb);
+            drop_matches(g, m->second);
             m = g->matches.erase(m);
         } else {
             ++m;

@@ -63,16 +63,60 @@ struct DevBuf {
     T* as() const { return static_cast<T*>(p); }
 };
 
+// Device blocks recycled within one graph: a freed buffer goes back to the
+// free list of its size class and is handed out again in stream order (all
+// of a graph's work runs on its stream, and batch and warm-start calls
+// synchronise before returning), so a steady turnover of frames and
+// correspondence sets neither allocates nor frees -- cudaFree would also
+// synchronise the whole device.
+struct DevPool {
+    std::multimap<size_t, void*> free_blocks;
+    std::vector<void*> owned;
+    static size_t size_class(size_t bytes)
+    {
+        const size_t q = bytes <= 65536 ? 256 : 65536;
+        return ((std::max<size_t>(bytes, 1) + q - 1) / q) * q;
+    }
+    cudaError_t get(size_t bytes, void** out)
+    {
+        const size_t c = size_class(bytes);
+        auto it = free_blocks.find(c);
+        if (it != free_blocks.end()) {
+            *out = it->second;
+            free_blocks.erase(it);
+            return cudaSuccess;
+        }
+        cudaError_t e = cudaMalloc(out, c);
+        if (e == cudaSuccess) owned.push_back(*out);
+        else *out = nullptr;
+        return e;
+    }
+    void put(void* p, size_t bytes)
+    {
+        if (p) free_blocks.emplace(size_class(bytes), p);
+    }
+    void release()
+    {
+        for (void* p : owned) cudaFree(p);
+        owned.clear();
+        free_blocks.clear();
+    }
+};
+
 struct Frame {
     int id = -1;
     bt_intrinsics K{};
     int fixed = 0;
     double pose[16];
     void* tgt = nullptr;     // target map, element size bt::pixel_bytes(precision)
-    void* src_p = nullptr;   // source points
+    void* src_p = nullptr;   // source points (room for every pixel; the first M are used)
     void* src_n = nullptr;   // source normals
+    size_t tgt_bytes = 0, src_bytes = 0;
     float zref = 0.f;        // reference depth of the 16-bit encodings
-    int M = 0;
+    int M = 0;               // valid source pixels (known once `pending` is resolved)
+    int* dev_m2 = nullptr;   // device (M, zref bits) written by the prep kernels
+    int slot = -1;           // pinned host slot receiving dev_m2
+    bool pending = false;    // M / zref not read back yet
 };
 
 struct MatchSet {
@@ -81,6 +125,7 @@ struct MatchSet {
     float* pa = nullptr;
     float* pb = nullptr;
 };
+
 
 inline bool finite_pose(const double* T)
 {
@@ -102,7 +147,11 @@ struct bt_graph {
     bool topo_dirty = true;
 
     // scratch for uploads and frame preparation
-    bthost::DevBuf up_depth, up_normals, up_mask, prep_blk, prep_src_p, prep_src_n, prep_M;
+    bthost::DevBuf up_depth, up_normals, up_mask, prep_blk;
+    bthost::DevPool pool;               // frame maps, source lists, correspondence sets
+    int* pin_m2 = nullptr;              // pinned host slots [cap][2] for (M, zref) read-backs
+    int pin_cap = 0;
+    std::vector<int> free_slots;
 
     // per-solve state
     bthost::DevBuf d_nodes, d_edges, d_tile_node, d_upairs, d_upair_edge, d_pose, d_xf, d_xinv, d_dpart,
@@ -122,19 +171,12 @@ struct bt_graph {
     {
         if (stream) cudaStreamSynchronize(stream);
         else cudaDeviceSynchronize();
-        for (auto& kv : frames) {
-            cudaFree(kv.second.tgt);
-            cudaFree(kv.second.src_p);
-            cudaFree(kv.second.src_n);
-        }
-        for (auto& kv : matches) {
-            cudaFree(kv.second.pa);
-            cudaFree(kv.second.pb);
-        }
+        pool.release();
+        if (pin_m2) cudaFreeHost(pin_m2);
         for (cudaEvent_t e : events) cudaEventDestroy(e);
-        for (bthost::DevBuf* b : {&up_depth, &up_normals, &up_mask, &prep_blk, &prep_src_p, &prep_src_n,
-                          &prep_M, &d_nodes, &d_edges, &d_tile_node, &d_upairs, &d_upair_edge,
-                          &d_pose, &d_xf, &d_xinv, &d_dpart, &d_spart, &d_upairblk, &d_ctrl, &d_costs})
+        for (bthost::DevBuf* b : {&up_depth, &up_normals, &up_mask, &prep_blk, &d_nodes, &d_edges, &d_tile_node,
+                          &d_upairs, &d_upair_edge, &d_pose, &d_xf, &d_xinv, &d_dpart, &d_spart, &d_upairblk,
+                          &d_ctrl, &d_costs})
             b->release();
     }
 };
@@ -171,6 +213,9 @@ namespace bthost {
 // Builds the graph's device tables (nodes, dense tiles of `tile` source
 // pixels, correspondence sets, node pairs) for its active nodes.
 int build_topology(bt_graph* g, int tile);
+// Reads back (M, zref) of every frame whose preparation is still pending
+// (one stream synchronisation for all of them).
+int resolve_pending(bt_graph* g);
 // Uploads the active nodes' stored poses, clears the control words and
 // launches the float transforms of a new solve.
 int upload_poses(bt_graph* g, std::vector<double>& staging);
