@@ -106,6 +106,41 @@ struct SolveArgs {
     double* costs;      // [iter][4]: total, dense, sparse, dense count
 };
 
+// Programmatic dependent launch.  The kernels of a solve form one chain per
+// stream (transforms -> residual -> reduce -> residual -> ...).  Each is
+// launched with programmatic stream serialisation: it may be scheduled
+// while its predecessor is still running, waits (griddepcontrol.wait) before
+// touching anything the predecessor writes, and at once allows its own
+// successor to be scheduled (griddepcontrol.launch_dependents), so the
+// launch latency of every kernel overlaps the tail of the previous one --
+// for the reduce kernel, its single-CTA solve stage.  The wait covers the
+// predecessor's completion and memory, and each predecessor waited for its
+// own, so every earlier kernel of the chain is complete as well.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait_and_release()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+#endif
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                  Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // K0 (frame preparation) for storage precision `precision`.  All launches
 // on `s`.  block_scratch must hold prep_scratch_bytes(W*H) bytes; out2[0]
 // receives the valid source count (int) and out2[1] the reference depth

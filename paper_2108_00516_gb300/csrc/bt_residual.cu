@@ -574,6 +574,7 @@ __device__ void sparse_edge(const SolveArgs& a, int e)
 template <bool kFull, int kT, int kB, int P>
 __global__ void __launch_bounds__(kT, 640 / kT) residual_kernel(SolveArgs a)
 {
+    pdl_wait_and_release();
     extern __shared__ __align__(16) unsigned char dsm[];
     if ((int)blockIdx.x < a.n_edges)
         sparse_edge<kFull>(a, blockIdx.x);
@@ -586,6 +587,7 @@ template <bool kFull, int kT, int kB, int P>
 __global__ void __launch_bounds__(kT, 640 / kT) batch_residual_kernel(const SolveArgs* __restrict__ args,
                                                                        const int2* __restrict__ work)
 {
+    pdl_wait_and_release();
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ SolveArgs sa;
     const int2 w = work[blockIdx.x];
@@ -630,21 +632,19 @@ static void ensure_residual_attrs()
 }
 
 template <int S, int P>
-static void launch_residual_shape(const SolveArgs& a, bool full, int grid, size_t smem, cudaStream_t s)
+static cudaError_t launch_residual_shape(const SolveArgs& a, bool full, int grid, size_t smem, cudaStream_t s)
 {
     constexpr int kT = kShapeThreads[S], kB = kShapePix[S];
-    if (full)
-        residual_kernel<true, kT, kB, P><<<grid, kT, smem, s>>>(a);
-    else
-        residual_kernel<false, kT, kB, P><<<grid, kT, smem, s>>>(a);
+    if (full) return launch_chained(residual_kernel<true, kT, kB, P>, dim3(grid), dim3(kT), smem, s, a);
+    return launch_chained(residual_kernel<false, kT, kB, P>, dim3(grid), dim3(kT), smem, s, a);
 }
 
 template <int S>
-static void launch_residual_s(const SolveArgs& a, bool full, int grid, size_t smem, cudaStream_t s)
+static cudaError_t launch_residual_s(const SolveArgs& a, bool full, int grid, size_t smem, cudaStream_t s)
 {
-    if (a.precision == 1) launch_residual_shape<S, 1>(a, full, grid, smem, s);
-    else if (a.precision == 2) launch_residual_shape<S, 2>(a, full, grid, smem, s);
-    else launch_residual_shape<S, 0>(a, full, grid, smem, s);
+    if (a.precision == 1) return launch_residual_shape<S, 1>(a, full, grid, smem, s);
+    if (a.precision == 2) return launch_residual_shape<S, 2>(a, full, grid, smem, s);
+    return launch_residual_shape<S, 0>(a, full, grid, smem, s);
 }
 
 cudaError_t launch_residual(const SolveArgs& a, bool full, cudaStream_t s, int shape)
@@ -654,34 +654,31 @@ cudaError_t launch_residual(const SolveArgs& a, bool full, cudaStream_t s, int s
     if (grid == 0) return cudaSuccess;
     const size_t smem = residual_smem_bytes(a.N, shape);
     switch (shape) {
-    case 1: launch_residual_s<1>(a, full, grid, smem, s); break;
-    case 2: launch_residual_s<2>(a, full, grid, smem, s); break;
-    case 3: launch_residual_s<3>(a, full, grid, smem, s); break;
-    case 4: launch_residual_s<4>(a, full, grid, smem, s); break;
-    case 5: launch_residual_s<5>(a, full, grid, smem, s); break;
-    default: launch_residual_s<0>(a, full, grid, smem, s); break;
+    case 1: return launch_residual_s<1>(a, full, grid, smem, s);
+    case 2: return launch_residual_s<2>(a, full, grid, smem, s);
+    case 3: return launch_residual_s<3>(a, full, grid, smem, s);
+    case 4: return launch_residual_s<4>(a, full, grid, smem, s);
+    case 5: return launch_residual_s<5>(a, full, grid, smem, s);
+    default: return launch_residual_s<0>(a, full, grid, smem, s);
     }
-    return cudaGetLastError();
 }
 
 template <int S, int P>
-static void launch_batch_residual_shape(const SolveArgs* args, const int2* work, int n, size_t smem, bool full,
-                                        cudaStream_t s)
+static cudaError_t launch_batch_residual_shape(const SolveArgs* args, const int2* work, int n, size_t smem,
+                                               bool full, cudaStream_t s)
 {
     constexpr int kT = kShapeThreads[S], kB = kShapePix[S];
-    if (full)
-        batch_residual_kernel<true, kT, kB, P><<<n, kT, smem, s>>>(args, work);
-    else
-        batch_residual_kernel<false, kT, kB, P><<<n, kT, smem, s>>>(args, work);
+    if (full) return launch_chained(batch_residual_kernel<true, kT, kB, P>, dim3(n), dim3(kT), smem, s, args, work);
+    return launch_chained(batch_residual_kernel<false, kT, kB, P>, dim3(n), dim3(kT), smem, s, args, work);
 }
 
 template <int S>
-static void launch_batch_residual_s(const SolveArgs* args, const int2* work, int n, size_t smem, bool full,
-                                    int precision, cudaStream_t s)
+static cudaError_t launch_batch_residual_s(const SolveArgs* args, const int2* work, int n, size_t smem, bool full,
+                                           int precision, cudaStream_t s)
 {
-    if (precision == 1) launch_batch_residual_shape<S, 1>(args, work, n, smem, full, s);
-    else if (precision == 2) launch_batch_residual_shape<S, 2>(args, work, n, smem, full, s);
-    else launch_batch_residual_shape<S, 0>(args, work, n, smem, full, s);
+    if (precision == 1) return launch_batch_residual_shape<S, 1>(args, work, n, smem, full, s);
+    if (precision == 2) return launch_batch_residual_shape<S, 2>(args, work, n, smem, full, s);
+    return launch_batch_residual_shape<S, 0>(args, work, n, smem, full, s);
 }
 
 cudaError_t launch_batch_residual(const SolveArgs* args_dev, const int2* work_res, int n_work, int max_N, bool full,
@@ -691,14 +688,13 @@ cudaError_t launch_batch_residual(const SolveArgs* args_dev, const int2* work_re
     if (n_work == 0) return cudaSuccess;
     const size_t smem = residual_smem_bytes(max_N, shape);
     switch (shape) {
-    case 1: launch_batch_residual_s<1>(args_dev, work_res, n_work, smem, full, precision, s); break;
-    case 2: launch_batch_residual_s<2>(args_dev, work_res, n_work, smem, full, precision, s); break;
-    case 3: launch_batch_residual_s<3>(args_dev, work_res, n_work, smem, full, precision, s); break;
-    case 4: launch_batch_residual_s<4>(args_dev, work_res, n_work, smem, full, precision, s); break;
-    case 5: launch_batch_residual_s<5>(args_dev, work_res, n_work, smem, full, precision, s); break;
-    default: launch_batch_residual_s<0>(args_dev, work_res, n_work, smem, full, precision, s); break;
+    case 1: return launch_batch_residual_s<1>(args_dev, work_res, n_work, smem, full, precision, s);
+    case 2: return launch_batch_residual_s<2>(args_dev, work_res, n_work, smem, full, precision, s);
+    case 3: return launch_batch_residual_s<3>(args_dev, work_res, n_work, smem, full, precision, s);
+    case 4: return launch_batch_residual_s<4>(args_dev, work_res, n_work, smem, full, precision, s);
+    case 5: return launch_batch_residual_s<5>(args_dev, work_res, n_work, smem, full, precision, s);
+    default: return launch_batch_residual_s<0>(args_dev, work_res, n_work, smem, full, precision, s);
     }
-    return cudaGetLastError();
 }
 
 void prepare_residual_attributes() { ensure_residual_attrs(); }

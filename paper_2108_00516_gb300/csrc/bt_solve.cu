@@ -60,14 +60,14 @@ __device__ void write_xforms(const SolveArgs& a, double* __restrict__ tinv, cons
 
 __global__ void xform_kernel(SolveArgs a)
 {
+    pdl_wait_and_release();
     __shared__ double tinv[12 * kMaxNodes];
     write_xforms(a, tinv, a.pose);
 }
 
 cudaError_t launch_xforms(const SolveArgs& a, cudaStream_t s)
 {
-    xform_kernel<<<1, kThreads, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_chained(xform_kernel, dim3(1), dim3(kThreads), 0, s, a);
 }
 
 // ---------------------------------------------------------------------------
@@ -769,6 +769,7 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
 template <bool kFull>
 __global__ void __launch_bounds__(kThreads, 1) reduce_kernel(SolveArgs a, int iter)
 {
+    pdl_wait_and_release();
     extern __shared__ double sm[];
     __shared__ int s_last;
     const int b = blockIdx.x;
@@ -817,10 +818,8 @@ cudaError_t launch_reduce(const SolveArgs& a, bool full, int iter, cudaStream_t 
     const int grid = a.n_upairs > 0 ? a.n_upairs : 1;
     const size_t smem = reduce_smem_bytes(a.n_free, a.N);
     if (full)
-        reduce_kernel<true><<<grid, kThreads, smem, s>>>(a, iter);
-    else
-        reduce_kernel<false><<<grid, kThreads, smem, s>>>(a, iter);
-    return cudaGetLastError();
+        return launch_chained(reduce_kernel<true>, dim3(grid), dim3(kThreads), smem, s, a, iter);
+    return launch_chained(reduce_kernel<false>, dim3(grid), dim3(kThreads), smem, s, a, iter);
 }
 
 // ---------------------------------------------------------------------------
@@ -829,6 +828,7 @@ cudaError_t launch_reduce(const SolveArgs& a, bool full, int iter, cudaStream_t 
 
 __global__ void batch_xform_kernel(const SolveArgs* __restrict__ args)
 {
+    pdl_wait_and_release();
     __shared__ double tinv[12 * kMaxNodes];
     __shared__ SolveArgs sa;
     if (threadIdx.x == 0) sa = args[blockIdx.x];
@@ -840,6 +840,7 @@ template <bool kFull>
 __global__ void __launch_bounds__(kThreads) batch_pair_kernel(const SolveArgs* __restrict__ args,
                                                               const int2* __restrict__ work)
 {
+    pdl_wait_and_release();
     __shared__ double sm[kPairSmemDoubles];
     __shared__ SolveArgs sa;
     const int2 w = work[blockIdx.x];
@@ -851,6 +852,7 @@ __global__ void __launch_bounds__(kThreads) batch_pair_kernel(const SolveArgs* _
 template <bool kFull>
 __global__ void __launch_bounds__(kThreads, 1) batch_solve_kernel(const SolveArgs* __restrict__ args, int iter)
 {
+    pdl_wait_and_release();
     extern __shared__ double smd[];
     __shared__ SolveArgs sa;
     if (threadIdx.x == 0) sa = args[blockIdx.x];
@@ -861,8 +863,7 @@ __global__ void __launch_bounds__(kThreads, 1) batch_solve_kernel(const SolveArg
 cudaError_t launch_batch_xforms(const SolveArgs* args_dev, int n_graphs, cudaStream_t s)
 {
     if (n_graphs == 0) return cudaSuccess;
-    batch_xform_kernel<<<n_graphs, kThreads, 0, s>>>(args_dev);
-    return cudaGetLastError();
+    return launch_chained(batch_xform_kernel, dim3(n_graphs), dim3(kThreads), 0, s, args_dev);
 }
 
 cudaError_t launch_batch_pairs(const SolveArgs* args_dev, const int2* work_pair, int n_work, bool full,
@@ -870,10 +871,8 @@ cudaError_t launch_batch_pairs(const SolveArgs* args_dev, const int2* work_pair,
 {
     if (n_work == 0) return cudaSuccess;
     if (full)
-        batch_pair_kernel<true><<<n_work, kThreads, 0, s>>>(args_dev, work_pair);
-    else
-        batch_pair_kernel<false><<<n_work, kThreads, 0, s>>>(args_dev, work_pair);
-    return cudaGetLastError();
+        return launch_chained(batch_pair_kernel<true>, dim3(n_work), dim3(kThreads), 0, s, args_dev, work_pair);
+    return launch_chained(batch_pair_kernel<false>, dim3(n_work), dim3(kThreads), 0, s, args_dev, work_pair);
 }
 
 cudaError_t launch_batch_solve(const SolveArgs* args_dev, int n_graphs, size_t smem, bool full, int iter,
@@ -887,10 +886,8 @@ cudaError_t launch_batch_solve(const SolveArgs* args_dev, int n_graphs, size_t s
     }
     if (n_graphs == 0) return cudaSuccess;
     if (full)
-        batch_solve_kernel<true><<<n_graphs, kThreads, smem, s>>>(args_dev, iter);
-    else
-        batch_solve_kernel<false><<<n_graphs, kThreads, smem, s>>>(args_dev, iter);
-    return cudaGetLastError();
+        return launch_chained(batch_solve_kernel<true>, dim3(n_graphs), dim3(kThreads), smem, s, args_dev, iter);
+    return launch_chained(batch_solve_kernel<false>, dim3(n_graphs), dim3(kThreads), smem, s, args_dev, iter);
 }
 
 void prepare_launch_attributes()
