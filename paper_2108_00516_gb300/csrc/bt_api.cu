@@ -193,34 +193,34 @@ int bthost::build_topology(bt_graph* g, int tile)
         upair_edge[a * N - a * (a + 1) / 2 + (b - a - 1)] = e;
     }
     cudaStream_t s = g->stream;
-    BT_CUDA(g->d_nodes.ensure(sizeof(bt::NodeDev) * N), "alloc nodes");
-    BT_CUDA(g->d_edges.ensure(sizeof(bt::EdgeDev) * std::max(E, 1)), "alloc edges");
-    BT_CUDA(g->d_tile_node.ensure(sizeof(int) * std::max(T, 1)), "alloc tiles");
-    BT_CUDA(g->d_pose.ensure(sizeof(double) * 12 * N), "alloc poses");
+    // one device block for the tables, staged through pinned memory
+    size_t off = 0;
+    auto take = [&off](size_t bytes) {
+        const size_t o = off;
+        off = align_up(o + std::max<size_t>(bytes, 1), 256);
+        return o;
+    };
+    const size_t o_nodes = take(sizeof(bt::NodeDev) * N), o_edges = take(sizeof(bt::EdgeDev) * E),
+                 o_tiles = take(sizeof(int) * T), o_upairs = take(sizeof(int2) * U),
+                 o_upair_edge = take(sizeof(int) * U), tab_bytes = off;
+    BT_CUDA(g->pin_tab.acquire(tab_bytes), "cudaHostAlloc(table staging)");
+    std::memcpy(g->pin_tab.at<char>(o_nodes), nodes.data(), sizeof(bt::NodeDev) * N);
+    if (E > 0) std::memcpy(g->pin_tab.at<char>(o_edges), edges.data(), sizeof(bt::EdgeDev) * E);
+    if (T > 0) std::memcpy(g->pin_tab.at<char>(o_tiles), tile_node.data(), sizeof(int) * T);
+    if (U > 0) {
+        std::memcpy(g->pin_tab.at<char>(o_upairs), upairs.data(), sizeof(int2) * U);
+        std::memcpy(g->pin_tab.at<char>(o_upair_edge), upair_edge.data(), sizeof(int) * U);
+    }
+    BT_CUDA(g->d_tab.ensure(tab_bytes), "alloc tables");
+    BT_CUDA(g->d_state.ensure(StateLayout(N).bytes), "alloc solve state");
     BT_CUDA(g->d_xf.ensure(sizeof(float) * 12 * N * N), "alloc xf");
     BT_CUDA(g->d_xinv.ensure(sizeof(float) * 12 * N), "alloc xinv");
     BT_CUDA(g->d_dpart.ensure(sizeof(float) * bt::kDenseVals * (size_t)std::max(T, 1) * std::max(N - 1, 1)),
             "alloc dpart");
     BT_CUDA(g->d_spart.ensure(sizeof(float) * bt::kSparseVals * std::max(E, 1)), "alloc spart");
-    BT_CUDA(g->d_upairs.ensure(sizeof(int2) * std::max(U, 1)), "alloc upairs");
-    BT_CUDA(g->d_upair_edge.ensure(sizeof(int) * std::max(U, 1)), "alloc upair edges");
     BT_CUDA(g->d_upairblk.ensure(sizeof(double) * bt::kUPairBlk * std::max(U, 1)), "alloc upairblk");
-    BT_CUDA(g->d_ctrl.ensure(sizeof(bt::Control)), "alloc ctrl");
-    BT_CUDA(g->d_costs.ensure(sizeof(double) * 4 * (BT_MAX_REPORT_ITERS + 1)), "alloc costs");
-    BT_CUDA(cudaMemcpyAsync(g->d_nodes.p, nodes.data(), sizeof(bt::NodeDev) * N, cudaMemcpyHostToDevice, s),
-            "upload nodes");
-    if (E > 0)
-        BT_CUDA(cudaMemcpyAsync(g->d_edges.p, edges.data(), sizeof(bt::EdgeDev) * E, cudaMemcpyHostToDevice, s),
-                "upload edges");
-    if (T > 0)
-        BT_CUDA(cudaMemcpyAsync(g->d_tile_node.p, tile_node.data(), sizeof(int) * T, cudaMemcpyHostToDevice, s),
-                "upload tiles");
-    if (U > 0) {
-        BT_CUDA(cudaMemcpyAsync(g->d_upairs.p, upairs.data(), sizeof(int2) * U, cudaMemcpyHostToDevice, s),
-                "upload pairs");
-        BT_CUDA(cudaMemcpyAsync(g->d_upair_edge.p, upair_edge.data(), sizeof(int) * U, cudaMemcpyHostToDevice, s),
-                "upload pair edges");
-    }
+    BT_CUDA(cudaMemcpyAsync(g->d_tab.p, g->pin_tab.p, tab_bytes, cudaMemcpyHostToDevice, s), "upload tables");
+    BT_CUDA(g->pin_tab.mark(s), "record table upload");
     bt::SolveArgs& a = g->args;
     a.N = N;
     a.n_tiles = T;
@@ -241,45 +241,74 @@ int bthost::build_topology(bt_graph* g, int tile)
     a.solver = c.solver;
     a.pcg_max_iters = c.pcg_max_iters;
     a.pcg_tol2 = c.pcg_tol * c.pcg_tol;
-    a.nodes = g->d_nodes.as<bt::NodeDev>();
-    a.edges = g->d_edges.as<bt::EdgeDev>();
-    a.tile_node = g->d_tile_node.as<int>();
-    a.upairs = g->d_upairs.as<int2>();
-    a.upair_edge = g->d_upair_edge.as<int>();
-    a.pose = g->d_pose.as<double>();
+    char* tab = g->d_tab.as<char>();
+    a.nodes = reinterpret_cast<bt::NodeDev*>(tab + o_nodes);
+    a.edges = reinterpret_cast<bt::EdgeDev*>(tab + o_edges);
+    a.tile_node = reinterpret_cast<int*>(tab + o_tiles);
+    a.upairs = reinterpret_cast<int2*>(tab + o_upairs);
+    a.upair_edge = reinterpret_cast<int*>(tab + o_upair_edge);
+    const StateLayout L(N);
+    char* state = g->d_state.as<char>();
+    a.ctrl = reinterpret_cast<bt::Control*>(state);
+    a.pose = reinterpret_cast<double*>(state + L.pose);
+    a.costs = reinterpret_cast<double*>(state + L.costs);
     a.xf = g->d_xf.as<float>();
     a.xinv = g->d_xinv.as<float>();
     a.dpart = g->d_dpart.as<float>();
     a.spart = g->d_spart.as<float>();
     a.upairblk = g->d_upairblk.as<double>();
-    a.ctrl = g->d_ctrl.as<bt::Control>();
-    a.costs = g->d_costs.as<double>();
     g->pixels_per_pass = px;
     int64_t sp = 0;
     for (const bt::EdgeDev& e : edges) sp += e.count;
     g->sparse_per_pass = sp;
-    // the tables above were copied from host vectors that go out of scope
-    BT_CUDA(cudaStreamSynchronize(s), "sync after table upload");
     g->topo_dirty = false;
     g->built_tile = tile;
     return BT_OK;
 }
 
-int bthost::upload_poses(bt_graph* g, std::vector<double>& staging)
+void bthost::stage_state(const bt_graph* g, char* blk)
 {
     const int N = (int)g->active.size();
-    staging.resize(12 * (size_t)N);
-    for (int k = 0; k < N; ++k) {
-        const Frame& f = g->frames.at(g->active[k]);
-        std::memcpy(&staging[12 * (size_t)k], f.pose, sizeof(double) * 12);
-    }
-    BT_CUDA(cudaMemcpyAsync(g->d_pose.p, staging.data(), sizeof(double) * 12 * N, cudaMemcpyHostToDevice,
-                            g->stream),
+    const StateLayout L(N);
+    std::memset(blk, 0, sizeof(bt::Control));
+    double* pose = reinterpret_cast<double*>(blk + L.pose);
+    for (int k = 0; k < N; ++k) std::memcpy(pose + 12 * (size_t)k, g->frames.at(g->active[k]).pose, sizeof(double) * 12);
+}
+
+int bthost::upload_poses(bt_graph* g)
+{
+    const StateLayout L((int)g->active.size());
+    BT_CUDA(g->pin_state.acquire(L.bytes), "cudaHostAlloc(state staging)");
+    stage_state(g, g->pin_state.at<char>(0));
+    BT_CUDA(cudaMemcpyAsync(g->d_state.p, g->pin_state.p, L.upload_bytes(), cudaMemcpyHostToDevice, g->stream),
             "upload poses");
-    BT_CUDA(cudaMemsetAsync(g->d_ctrl.p, 0, sizeof(bt::Control), g->stream), "reset control");
+    BT_CUDA(g->pin_state.mark(g->stream), "record state upload");
     BT_CUDA(bt::launch_xforms(g->args, g->stream), "launch xform");
     g->prof.xform_launches++;
     return BT_OK;
+}
+
+int bthost::fill_report(bt_graph* g, const char* blk, int iters, bt_solve_report* rep)
+{
+    const StateLayout L((int)g->active.size());
+    const bt::Control& ctrl = *reinterpret_cast<const bt::Control*>(blk);
+    const double* costs = reinterpret_cast<const double*>(blk + L.costs);
+    if (g->prof_on)
+        for (int k = 0; k < 4; ++k) g->prof.solve_phase_cycles[k] += (int64_t)ctrl.clk[k];
+    const int status = ctrl.status == -4 ? BT_ERR_SINGULAR : BT_OK;
+    if (rep) {
+        std::memset(rep, 0, sizeof(*rep));
+        rep->iters_run = iters;
+        rep->status = status;
+        rep->cost_init = iters > 0 ? costs[0] : costs[4 * iters];
+        rep->cost_final = costs[4 * iters + 0];
+        rep->dense_cost_final = costs[4 * iters + 1];
+        rep->sparse_cost_final = costs[4 * iters + 2];
+        rep->dense_inliers = (int64_t)std::llround(costs[4 * iters + 3]);
+        for (int k = 0; k < iters; ++k) rep->cost_per_iter[k] = costs[4 * k];
+        rep->dense_pixel_pairs = g->pixels_per_pass * iters;
+    }
+    return status;
 }
 
 namespace {
@@ -586,41 +615,28 @@ int bt_solve(bt_graph* g, int32_t iters, double* poses_out, bt_solve_report* rep
         int st = build_topology(g, bt::shape_tile(0));
         if (st != BT_OK) return st;
     }
-    std::vector<double> staging;
-    int st = upload_poses(g, staging);
+    int st = upload_poses(g);
     if (st != BT_OK) return st;
     cudaStream_t s = g->stream;
     const bt::SolveArgs& a = g->args;
     st = enqueue_passes(g, iters, true, iters);
     if (st != BT_OK) return st;
     const int N = a.N;
-    std::vector<double> pose(12 * (size_t)N), costs(4 * (size_t)(iters + 1));
-    bt::Control ctrl{};
-    BT_CUDA(cudaMemcpyAsync(pose.data(), a.pose, sizeof(double) * 12 * N, cudaMemcpyDeviceToHost, s), "read poses");
-    BT_CUDA(cudaMemcpyAsync(costs.data(), a.costs, sizeof(double) * 4 * (iters + 1), cudaMemcpyDeviceToHost, s),
-            "read costs");
-    BT_CUDA(cudaMemcpyAsync(&ctrl, a.ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost, s), "read status");
+    const StateLayout L(N);
+    // read back into the staging the upload came from (ordered after it on s)
+    BT_CUDA(cudaMemcpyAsync(g->pin_state.p, g->d_state.p, L.readback_bytes(iters), cudaMemcpyDeviceToHost, s),
+            "read solve state");
+    BT_CUDA(g->pin_state.mark(s), "record state read-back");
     BT_CUDA(cudaStreamSynchronize(s), "bt_solve: synchronize");
+    g->pin_state.busy = false;
     collect_events(g, iters + 1);
-    if (g->prof_on)
-        for (int k = 0; k < 4; ++k) g->prof.solve_phase_cycles[k] += (int64_t)ctrl.clk[k];
-    const int status = ctrl.status == -4 ? BT_ERR_SINGULAR : BT_OK;
-    if (rep) {
-        std::memset(rep, 0, sizeof(*rep));
-        rep->iters_run = iters;
-        rep->status = status;
-        rep->cost_init = iters > 0 ? costs[0] : costs[4 * iters];
-        rep->cost_final = costs[4 * iters + 0];
-        rep->dense_cost_final = costs[4 * iters + 1];
-        rep->sparse_cost_final = costs[4 * iters + 2];
-        rep->dense_inliers = (int64_t)std::llround(costs[4 * iters + 3]);
-        for (int k = 0; k < iters; ++k) rep->cost_per_iter[k] = costs[4 * k];
-        rep->dense_pixel_pairs = g->pixels_per_pass * iters;
-    }
+    const char* blk = g->pin_state.at<char>(0);
+    const int status = fill_report(g, blk, iters, rep);
+    const double* pose = reinterpret_cast<const double*>(blk + L.pose);
     if (status != BT_OK) return fail(status, "bt_solve: normal equations not positive definite; poses unchanged");
     for (int k = 0; k < N; ++k) {
         Frame& f = g->frames.at(g->active[k]);
-        std::memcpy(f.pose, &pose[12 * (size_t)k], sizeof(double) * 12);
+        std::memcpy(f.pose, pose + 12 * (size_t)k, sizeof(double) * 12);
         if (poses_out) std::memcpy(poses_out + 16 * (size_t)k, f.pose, sizeof(double) * 16);
     }
     return BT_OK;
@@ -635,15 +651,18 @@ int bt_eval_cost(bt_graph* g, double* cost_out, int64_t* dense_inliers)
         int st = build_topology(g, bt::shape_tile(0));
         if (st != BT_OK) return st;
     }
-    std::vector<double> staging;
-    int st = upload_poses(g, staging);
+    int st = upload_poses(g);
     if (st != BT_OK) return st;
     cudaStream_t s = g->stream;
     st = enqueue_passes(g, 0, true, 0);
     if (st != BT_OK) return st;
-    double c[4];
-    BT_CUDA(cudaMemcpyAsync(c, g->args.costs, sizeof(c), cudaMemcpyDeviceToHost, s), "read costs");
+    const StateLayout L(g->args.N);
+    BT_CUDA(cudaMemcpyAsync(g->pin_state.p, g->d_state.p, L.readback_bytes(0), cudaMemcpyDeviceToHost, s),
+            "read costs");
+    BT_CUDA(g->pin_state.mark(s), "record state read-back");
     BT_CUDA(cudaStreamSynchronize(s), "bt_eval_cost: synchronize");
+    g->pin_state.busy = false;
+    const double* c = g->pin_state.at<double>(L.costs);
     collect_events(g, 1);
     cost_out[0] = c[0];
     cost_out[1] = c[1];
@@ -708,6 +727,9 @@ int batch_build(bt_batch* b, int shape)
             int st = build_topology(g, tile);
             if (st != BT_OK) return st;
         }
+        // the graph's tables and frames were enqueued on its own stream
+        int st = order_streams(g->stream, b->stream);
+        if (st != BT_OK) return st;
         const bt::SolveArgs& a = g->args;
         args.push_back(a);
         for (int e = 0; e < a.n_edges; ++e) wres.push_back(make_int2((int)k, e));
@@ -718,19 +740,44 @@ int batch_build(bt_batch* b, int shape)
         b->pixels_per_pass += g->pixels_per_pass;
     }
     cudaStream_t s = b->stream;
-    BT_CUDA(b->d_args.ensure(sizeof(bt::SolveArgs) * std::max<size_t>(args.size(), 1)), "alloc batch args");
-    BT_CUDA(b->d_work_res.ensure(sizeof(int2) * std::max<size_t>(wres.size(), 1)), "alloc batch work");
-    BT_CUDA(b->d_work_pair.ensure(sizeof(int2) * std::max<size_t>(wpair.size(), 1)), "alloc batch work");
+    // every graph's solve state moves into one batch block (pointers in the
+    // batch's copy of its arguments)
+    const size_t G = b->graphs.size();
+    b->state_off.assign(G + 1, 0);
+    for (size_t k = 0; k < G; ++k) b->state_off[k + 1] = b->state_off[k] + StateLayout(args[k].N).bytes;
+    BT_CUDA(b->d_state.ensure(b->state_off[G]), "alloc batch state");
+    for (size_t k = 0; k < G; ++k) {
+        const StateLayout L(args[k].N);
+        char* blk = b->d_state.as<char>() + b->state_off[k];
+        args[k].ctrl = reinterpret_cast<bt::Control*>(blk);
+        args[k].pose = reinterpret_cast<double*>(blk + L.pose);
+        args[k].costs = reinterpret_cast<double*>(blk + L.costs);
+    }
+    b->h_args = args;
+    const size_t n_args = std::max<size_t>(args.size(), 1), n_res = std::max<size_t>(wres.size(), 1),
+                 n_pair = std::max<size_t>(wpair.size(), 1);
+    BT_CUDA(b->d_args.ensure(sizeof(bt::SolveArgs) * n_args), "alloc batch args");
+    BT_CUDA(b->d_work_res.ensure(sizeof(int2) * n_res), "alloc batch work");
+    BT_CUDA(b->d_work_pair.ensure(sizeof(int2) * n_pair), "alloc batch work");
+    const size_t o_res = align_up(sizeof(bt::SolveArgs) * n_args, 256),
+                 o_pair = o_res + align_up(sizeof(int2) * n_res, 256), tab_bytes = o_pair + sizeof(int2) * n_pair;
+    BT_CUDA(b->pin_tab.acquire(tab_bytes), "cudaHostAlloc(batch table staging)");
+    if (!args.empty()) std::memcpy(b->pin_tab.p, args.data(), sizeof(bt::SolveArgs) * args.size());
+    if (!wres.empty()) std::memcpy(b->pin_tab.at<char>(o_res), wres.data(), sizeof(int2) * wres.size());
+    if (!wpair.empty()) std::memcpy(b->pin_tab.at<char>(o_pair), wpair.data(), sizeof(int2) * wpair.size());
     if (!args.empty())
-        BT_CUDA(cudaMemcpyAsync(b->d_args.p, args.data(), sizeof(bt::SolveArgs) * args.size(), cudaMemcpyHostToDevice, s),
+        BT_CUDA(cudaMemcpyAsync(b->d_args.p, b->pin_tab.p, sizeof(bt::SolveArgs) * args.size(),
+                                cudaMemcpyHostToDevice, s),
                 "upload batch args");
     if (!wres.empty())
-        BT_CUDA(cudaMemcpyAsync(b->d_work_res.p, wres.data(), sizeof(int2) * wres.size(), cudaMemcpyHostToDevice, s),
+        BT_CUDA(cudaMemcpyAsync(b->d_work_res.p, b->pin_tab.at<char>(o_res), sizeof(int2) * wres.size(),
+                                cudaMemcpyHostToDevice, s),
                 "upload batch work");
     if (!wpair.empty())
-        BT_CUDA(cudaMemcpyAsync(b->d_work_pair.p, wpair.data(), sizeof(int2) * wpair.size(), cudaMemcpyHostToDevice, s),
+        BT_CUDA(cudaMemcpyAsync(b->d_work_pair.p, b->pin_tab.at<char>(o_pair), sizeof(int2) * wpair.size(),
+                                cudaMemcpyHostToDevice, s),
                 "upload batch work");
-    BT_CUDA(cudaStreamSynchronize(s), "sync after batch upload");
+    BT_CUDA(b->pin_tab.mark(s), "record batch table upload");
     b->n_work_res = (int)wres.size();
     b->n_work_pair = (int)wpair.size();
     if (b->exec) {
@@ -741,20 +788,22 @@ int batch_build(bt_batch* b, int shape)
     return BT_OK;
 }
 
-// Uploads the stored poses of every graph and clears its control words.
-int batch_upload_state(bt_batch* b)
+}  // namespace
+
+// Cleared control words and the stored poses of every graph, in one copy.
+int bthost::batch_upload_state(bt_batch* b)
 {
-    for (bt_graph* g : b->graphs) {
-        const int N = (int)g->active.size();
-        std::vector<double>& st = g->pose_stage;
-        st.resize(12 * (size_t)N);
-        for (int k = 0; k < N; ++k) std::memcpy(&st[12 * (size_t)k], g->frames.at(g->active[k]).pose, sizeof(double) * 12);
-        BT_CUDA(cudaMemcpyAsync(g->d_pose.p, st.data(), sizeof(double) * 12 * N, cudaMemcpyHostToDevice, b->stream),
-                "upload batch poses");
-        BT_CUDA(cudaMemsetAsync(g->d_ctrl.p, 0, sizeof(bt::Control), b->stream), "reset control");
-    }
+    const size_t G = b->graphs.size();
+    BT_CUDA(b->pin_state.acquire(b->state_off[G]), "cudaHostAlloc(batch state staging)");
+    for (size_t k = 0; k < G; ++k) stage_state(b->graphs[k], b->pin_state.at<char>(b->state_off[k]));
+    const size_t bytes = b->state_off[G - 1] + StateLayout(b->h_args[G - 1].N).upload_bytes();
+    BT_CUDA(cudaMemcpyAsync(b->d_state.p, b->pin_state.p, bytes, cudaMemcpyHostToDevice, b->stream),
+            "upload batch poses");
+    BT_CUDA(b->pin_state.mark(b->stream), "record batch state upload");
     return BT_OK;
 }
+
+namespace {
 
 // Enqueues the whole solve (xforms, iters full passes, one cost pass).
 int batch_enqueue(bt_batch* b, int iters, int shape)
@@ -818,6 +867,74 @@ int batch_autotune(bt_batch* b)
 }
 
 }  // namespace
+
+int bthost::batch_prepare(bt_batch* b, int iters)
+{
+    bt::prepare_launch_attributes();
+    bool topo_changed = b->dirty;
+    for (bt_graph* g : b->graphs) topo_changed |= g->topo_dirty;
+    if (topo_changed) {
+        b->dirty = false;
+        if (b->shape < 0) {
+            int st = batch_autotune(b);
+            if (st != BT_OK) return st;
+        }
+    }
+    const int shape = b->shape >= 0 ? b->shape : (b->tuned_shape >= 0 ? b->tuned_shape : 0);
+    if (topo_changed || b->exec_shape != shape) {
+        int st = batch_build(b, shape);
+        if (st != BT_OK) return st;
+    }
+    if (!b->exec || b->exec_iters != iters) {
+        if (b->exec) {
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+        cudaGraph_t graph;
+        BT_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        int st = batch_enqueue(b, iters, shape);
+        cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+        if (st != BT_OK) return st;
+        if (e != cudaSuccess) return cuda_fail(e, "end capture");
+        e = cudaGraphInstantiate(&b->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+        b->exec_iters = iters;
+    }
+    return BT_OK;
+}
+
+int bthost::batch_launch(bt_batch* b, int iters)
+{
+    const size_t G = b->graphs.size();
+    BT_CUDA(cudaGraphLaunch(b->exec, b->stream), "graph launch");
+    // read back into the staging the upload came from (stream order keeps
+    // the two copies apart; the host reads it after synchronising)
+    const size_t bytes = b->state_off[G - 1] + StateLayout(b->h_args[G - 1].N).readback_bytes(iters);
+    BT_CUDA(cudaMemcpyAsync(b->pin_state.p, b->d_state.p, bytes, cudaMemcpyDeviceToHost, b->stream),
+            "read batch state");
+    BT_CUDA(b->pin_state.mark(b->stream), "record batch state read-back");
+    return BT_OK;
+}
+
+int bthost::batch_collect(bt_batch* b, int iters, bt_solve_report* reps)
+{
+    int worst = BT_OK;
+    for (size_t k = 0; k < b->graphs.size(); ++k) {
+        bt_graph* g = b->graphs[k];
+        const char* blk = b->pin_state.at<char>(b->state_off[k]);
+        const StateLayout L(b->h_args[k].N);
+        const int status = fill_report(g, blk, iters, reps ? &reps[k] : nullptr);
+        if (status != BT_OK) {
+            worst = status;
+            continue;
+        }
+        const double* pose = reinterpret_cast<const double*>(blk + L.pose);
+        for (int q = 0; q < b->h_args[k].N; ++q)
+            std::memcpy(g->frames.at(g->active[q]).pose, pose + 12 * (size_t)q, sizeof(double) * 12);
+    }
+    return worst;
+}
 
 extern "C" {
 
@@ -892,83 +1009,14 @@ int bt_batch_solve(bt_batch* b, int32_t iters, bt_solve_report* reps)
     if (!b) return fail(BT_ERR_INVALID, "bt_batch_solve: NULL batch");
     if (iters < 0 || iters > BT_MAX_REPORT_ITERS) return fail(BT_ERR_INVALID, "bt_batch_solve: iters out of range");
     if (b->graphs.empty()) return fail(BT_ERR_INVALID, "bt_batch_solve: empty batch");
-    bt::prepare_launch_attributes();
-    bool topo_changed = b->dirty;
-    for (bt_graph* g : b->graphs) topo_changed |= g->topo_dirty;
-    if (topo_changed) {
-        b->dirty = false;
-        if (b->shape < 0) {
-            int st = batch_autotune(b);
-            if (st != BT_OK) return st;
-        }
-    }
-    const int shape = b->shape >= 0 ? b->shape : (b->tuned_shape >= 0 ? b->tuned_shape : 0);
-    if (topo_changed || b->exec_shape != shape) {
-        int st = batch_build(b, shape);
-        if (st != BT_OK) return st;
-    }
-    int st = batch_upload_state(b);
+    int st = batch_prepare(b, iters);
+    if (st == BT_OK) st = batch_upload_state(b);
+    if (st == BT_OK) st = batch_launch(b, iters);
     if (st != BT_OK) return st;
-    cudaStream_t s = b->stream;
-    if (!b->exec || b->exec_iters != iters) {
-        if (b->exec) {
-            cudaGraphExecDestroy(b->exec);
-            b->exec = nullptr;
-        }
-        cudaGraph_t graph;
-        BT_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
-        st = batch_enqueue(b, iters, shape);
-        cudaError_t e = cudaStreamEndCapture(s, &graph);
-        if (st != BT_OK) return st;
-        if (e != cudaSuccess) return cuda_fail(e, "end capture");
-        e = cudaGraphInstantiate(&b->exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
-        b->exec_iters = iters;
-    }
-    BT_CUDA(cudaGraphLaunch(b->exec, s), "graph launch");
-    const size_t G = b->graphs.size();
-    std::vector<std::vector<double>> poses(G), costs(G);
-    std::vector<bt::Control> ctrl(G);
-    for (size_t k = 0; k < G; ++k) {
-        bt_graph* g = b->graphs[k];
-        const int N = g->args.N;
-        poses[k].resize(12 * (size_t)N);
-        costs[k].resize(4 * (size_t)(iters + 1));
-        BT_CUDA(cudaMemcpyAsync(poses[k].data(), g->args.pose, sizeof(double) * 12 * N, cudaMemcpyDeviceToHost, s),
-                "read poses");
-        BT_CUDA(cudaMemcpyAsync(costs[k].data(), g->args.costs, sizeof(double) * 4 * (iters + 1),
-                                cudaMemcpyDeviceToHost, s),
-                "read costs");
-        BT_CUDA(cudaMemcpyAsync(&ctrl[k], g->args.ctrl, sizeof(bt::Control), cudaMemcpyDeviceToHost, s), "read status");
-    }
-    BT_CUDA(cudaStreamSynchronize(s), "bt_batch_solve: synchronize");
-    int worst = BT_OK;
-    for (size_t k = 0; k < G; ++k) {
-        bt_graph* g = b->graphs[k];
-        const int status = ctrl[k].status == -4 ? BT_ERR_SINGULAR : BT_OK;
-        if (reps) {
-            bt_solve_report* rep = &reps[k];
-            std::memset(rep, 0, sizeof(*rep));
-            const std::vector<double>& c = costs[k];
-            rep->iters_run = iters;
-            rep->status = status;
-            rep->cost_init = iters > 0 ? c[0] : c[4 * iters];
-            rep->cost_final = c[4 * iters + 0];
-            rep->dense_cost_final = c[4 * iters + 1];
-            rep->sparse_cost_final = c[4 * iters + 2];
-            rep->dense_inliers = (int64_t)std::llround(c[4 * iters + 3]);
-            for (int q = 0; q < iters; ++q) rep->cost_per_iter[q] = c[4 * q];
-            rep->dense_pixel_pairs = g->pixels_per_pass * iters;
-        }
-        if (status != BT_OK) {
-            worst = status;
-            continue;
-        }
-        for (int q = 0; q < g->args.N; ++q)
-            std::memcpy(g->frames.at(g->active[q]).pose, &poses[k][12 * (size_t)q], sizeof(double) * 12);
-    }
-    if (worst != BT_OK) return fail(worst, "bt_batch_solve: some graphs were singular; their poses are unchanged");
+    BT_CUDA(cudaStreamSynchronize(b->stream), "bt_batch_solve: synchronize");
+    b->pin_state.busy = false;
+    st = batch_collect(b, iters, reps);
+    if (st != BT_OK) return fail(st, "bt_batch_solve: some graphs were singular; their poses are unchanged");
     return BT_OK;
 }
 

@@ -7,6 +7,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -61,6 +62,87 @@ struct DevBuf {
     }
     template <class T>
     T* as() const { return static_cast<T*>(p); }
+};
+
+// Pinned host memory that stream-ordered copies read from or write to
+// asynchronously.  `mark` records an event after the last copy that uses the
+// memory; `acquire` waits for that event before the memory is written again
+// (or grown), so staging never races a copy still in flight.
+struct PinBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;
+    bool busy = false;
+    cudaError_t acquire(size_t bytes)
+    {
+        if (busy) {
+            cudaError_t e = cudaEventSynchronize(done);
+            if (e != cudaSuccess) return e;
+            busy = false;
+        }
+        if (bytes <= cap) return cudaSuccess;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        const size_t want = std::max<size_t>(bytes + bytes / 4, 4096);
+        cudaError_t e = cudaHostAlloc(&p, want, cudaHostAllocDefault);
+        if (e == cudaSuccess) cap = want;
+        else p = nullptr;
+        return e;
+    }
+    cudaError_t mark(cudaStream_t s)
+    {
+        if (!done) {
+            cudaError_t e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+            if (e != cudaSuccess) return e;
+        }
+        cudaError_t e = cudaEventRecord(done, s);
+        if (e == cudaSuccess) busy = true;
+        return e;
+    }
+    void release()
+    {
+        if (busy && done) cudaEventSynchronize(done);
+        busy = false;
+        if (done) cudaEventDestroy(done);
+        done = nullptr;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+    }
+    template <class T>
+    T* at(size_t off) const { return reinterpret_cast<T*>(static_cast<char*>(p) + off); }
+};
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Makes stream `to` wait for the work already enqueued on stream `from`.
+inline int order_streams(cudaStream_t from, cudaStream_t to)
+{
+    if (from == to) return BT_OK;
+    cudaEvent_t e;
+    BT_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+    cudaError_t r = cudaEventRecord(e, from);
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(to, e, 0);
+    cudaEventDestroy(e);
+    BT_CUDA(r, "order streams");
+    return BT_OK;
+}
+
+// One solve's state block on the device: control words, the 3x4 poses of the
+// N active nodes, then the energies of every pass (4 doubles each).  A solve
+// uploads the leading `upload_bytes` (cleared control words and the starting
+// poses) in one copy and reads `readback_bytes(iters)` back in one copy.
+struct StateLayout {
+    size_t pose = 0, costs = 0, bytes = 0;
+    explicit StateLayout(int N)
+    {
+        pose = align_up(sizeof(bt::Control), 64);
+        costs = align_up(pose + sizeof(double) * 12 * (size_t)N, 64);
+        bytes = align_up(costs + sizeof(double) * 4 * (BT_MAX_REPORT_ITERS + 1), 256);
+    }
+    size_t upload_bytes() const { return costs; }
+    size_t readback_bytes(int iters) const { return costs + sizeof(double) * 4 * (size_t)(iters + 1); }
 };
 
 // Device blocks recycled within one graph: a freed buffer goes back to the
@@ -153,14 +235,15 @@ struct bt_graph {
     int pin_cap = 0;
     std::vector<int> free_slots;
 
-    // per-solve state
-    bthost::DevBuf d_nodes, d_edges, d_tile_node, d_upairs, d_upair_edge, d_pose, d_xf, d_xinv, d_dpart,
-        d_spart, d_upairblk, d_ctrl, d_costs;
+    // per-solve state: the topology tables (nodes, edges, tile owners, node
+    // pairs, pair -> edge) in one device block staged through pinned memory,
+    // the solve state block (StateLayout) likewise, and the work buffers
+    bthost::DevBuf d_tab, d_state, d_xf, d_xinv, d_dpart, d_spart, d_upairblk;
+    bthost::PinBuf pin_tab, pin_state;
     bt::SolveArgs args{};
     int64_t pixels_per_pass = 0;
     int64_t sparse_per_pass = 0;
     int built_tile = 0;     // tile size the current tables were built for
-    std::vector<double> pose_stage;   // host staging of poses for batched uploads
 
     // profiling
     bt_profile prof{};
@@ -173,10 +256,11 @@ struct bt_graph {
         else cudaDeviceSynchronize();
         pool.release();
         if (pin_m2) cudaFreeHost(pin_m2);
+        pin_tab.release();
+        pin_state.release();
         for (cudaEvent_t e : events) cudaEventDestroy(e);
-        for (bthost::DevBuf* b : {&up_depth, &up_normals, &up_mask, &prep_blk, &d_nodes, &d_edges, &d_tile_node,
-                          &d_upairs, &d_upair_edge, &d_pose, &d_xf, &d_xinv, &d_dpart, &d_spart, &d_upairblk,
-                          &d_ctrl, &d_costs})
+        for (bthost::DevBuf* b : {&up_depth, &up_normals, &up_mask, &prep_blk, &d_tab, &d_state, &d_xf, &d_xinv,
+                                  &d_dpart, &d_spart, &d_upairblk})
             b->release();
     }
 };
@@ -190,6 +274,12 @@ struct bt_batch {
     int tuned_shape = -1;    // autotuner's choice for the current graph set
     bool dirty = true;       // graph set / topology changed since the last build
     bthost::DevBuf d_args, d_work_res, d_work_pair;
+    // solve state of every graph of the batch, one StateLayout block each at
+    // state_off[k]: one upload and one read-back per batched solve
+    bthost::DevBuf d_state;
+    bthost::PinBuf pin_state, pin_tab;
+    std::vector<size_t> state_off;
+    std::vector<bt::SolveArgs> h_args;   // host copy of d_args
     int n_work_res = 0, n_work_pair = 0, max_N = 1;
     size_t solve_smem = 0;
     int64_t pixels_per_pass = 0;
@@ -204,6 +294,9 @@ struct bt_batch {
         d_args.release();
         d_work_res.release();
         d_work_pair.release();
+        d_state.release();
+        pin_state.release();
+        pin_tab.release();
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
@@ -216,8 +309,26 @@ int build_topology(bt_graph* g, int tile);
 // Reads back (M, zref) of every frame whose preparation is still pending
 // (one stream synchronisation for all of them).
 int resolve_pending(bt_graph* g);
-// Uploads the active nodes' stored poses, clears the control words and
-// launches the float transforms of a new solve.
-int upload_poses(bt_graph* g, std::vector<double>& staging);
+// Uploads the active nodes' stored poses and cleared control words (one
+// copy from pinned staging) and launches the float transforms of a new solve.
+int upload_poses(bt_graph* g);
+// Writes cleared control words and the stored poses of g's active nodes into
+// a state block at `blk` (host memory laid out as StateLayout).
+void stage_state(const bt_graph* g, char* blk);
+// Fills `rep` (when not NULL) from a state block read back after `iters`
+// iterations and returns the solve's status (BT_OK or BT_ERR_SINGULAR).
+int fill_report(bt_graph* g, const char* blk, int iters, bt_solve_report* rep);
+
+// A batched solve in stages; bt_batch_solve runs them in order, the
+// warm-started solve enqueues its network between the upload and the launch.
+// Autotuning, tables and the captured CUDA graph (when out of date).
+int batch_prepare(bt_batch* b, int iters);
+// Cleared control words and the stored poses of every graph, one copy.
+int batch_upload_state(bt_batch* b);
+// The captured solve and the read-back of every graph's state, one copy.
+int batch_launch(bt_batch* b, int iters);
+// After the stream is synchronised: reports and the poses of the graphs
+// that were not singular; returns BT_OK or BT_ERR_SINGULAR.
+int batch_collect(bt_batch* b, int iters, bt_solve_report* reps);
 
 }  // namespace bthost

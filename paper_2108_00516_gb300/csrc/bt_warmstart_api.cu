@@ -27,6 +27,7 @@ struct bt_warmstart {
     // launch scratch
     DevBuf ids, y, cache, G, loss_per, grad, loss;
     DevBuf app_samples, app_y, app_graphs, app_scratch, app_status, app_items;
+    PinBuf pin_app, pin_status;   // staging of the apply tables and the per-graph status
 
     W::Net net() const
     {
@@ -40,6 +41,8 @@ struct bt_warmstart {
                           &loss_per, &grad, &loss, &app_samples, &app_y, &app_graphs, &app_scratch, &app_status,
                           &app_items})
             b->release();
+        pin_app.release();
+        pin_status.release();
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
@@ -162,11 +165,14 @@ int ensure_tables(bt_graph* g)
     return BT_OK;
 }
 
-// Predicts and applies the warm start to every graph in `gs` (one launch of
-// each kernel for all of them), then stores the new poses in the graphs.
-int apply_graphs(bt_warmstart* ws, bt_graph* const* gs, int n_graphs, int* status_out)
+// Enqueues on stream s the warm start of every graph in `gs` (one launch of
+// each kernel for all of them).  pose[k] holds the device poses of graph k's
+// active nodes: the network reads the starting relative poses from it and
+// the averaging writes the new poses into it.  Graph k's status lands in
+// app_status[k] (0 ok; 1 averaging system singular, poses left as they were).
+// The graphs' tables must be current.
+int enqueue_apply(bt_warmstart* ws, bt_graph* const* gs, int n_graphs, double* const* pose, cudaStream_t s)
 {
-    cudaStream_t s = ws->stream;
     std::vector<W::Sample> smp;
     std::vector<W::PrepItem> items;
     std::vector<W::AvgGraph> avg;
@@ -174,15 +180,6 @@ int apply_graphs(bt_warmstart* ws, bt_graph* const* gs, int n_graphs, int* statu
     int max_free = 0;
     for (int k = 0; k < n_graphs; ++k) {
         bt_graph* g = gs[k];
-        int st = ensure_tables(g);
-        if (st != BT_OK) return st;
-        if (g->stream != s) BT_CUDA(cudaStreamSynchronize(g->stream), "sync graph stream");
-        const int N = (int)g->active.size();
-        std::vector<double>& stg = g->pose_stage;
-        stg.resize(12 * (size_t)N);
-        for (int q = 0; q < N; ++q) std::memcpy(&stg[12 * (size_t)q], g->frames.at(g->active[q]).pose, sizeof(double) * 12);
-        BT_CUDA(cudaMemcpyAsync(g->d_pose.p, stg.data(), sizeof(double) * 12 * N, cudaMemcpyHostToDevice, s),
-                "upload poses");
         const std::vector<HostEdge> edges = graph_edges(g);
         if ((int)edges.size() != g->args.n_edges) return fail(BT_ERR_STATE, "warm start: edge table out of date");
         first[k] = (int)smp.size();
@@ -193,8 +190,8 @@ int apply_graphs(bt_warmstart* ws, bt_graph* const* gs, int n_graphs, int* statu
             x.n = e.count;
             W::PrepItem it{};
             it.sample = (int)smp.size();
-            it.Ti0 = g->args.pose + 12 * e.i;
-            it.Tj0 = g->args.pose + 12 * e.j;
+            it.Ti0 = pose[k] + 12 * e.i;
+            it.Tj0 = pose[k] + 12 * e.j;
             smp.push_back(x);
             items.push_back(it);
         }
@@ -218,44 +215,93 @@ int apply_graphs(bt_warmstart* ws, bt_graph* const* gs, int n_graphs, int* statu
         a.edges = g->args.edges;
         a.y = ws->app_y.as<float>() + (size_t)first[k] * W::kOut;
         a.smp = ws->app_samples.as<W::Sample>() + first[k];
-        a.pose = g->args.pose;
+        a.pose = pose[k];
         a.scratch = ws->app_scratch.as<double>() + (size_t)first[k] * 64;
         a.status = ws->app_status.as<int>() + k;
         avg.push_back(a);
     }
+    // the three tables go up from one pinned staging block
+    const size_t o_items = align_up(sizeof(W::Sample) * (size_t)S, 256),
+                 o_avg = o_items + align_up(sizeof(W::PrepItem) * (size_t)S, 256),
+                 bytes = o_avg + sizeof(W::AvgGraph) * (size_t)n_graphs;
+    BT_CUDA(ws->pin_app.acquire(bytes), "cudaHostAlloc(warm-start staging)");
     if (S > 0) {
-        BT_CUDA(cudaMemcpyAsync(ws->app_samples.p, smp.data(), sizeof(W::Sample) * S, cudaMemcpyHostToDevice, s),
+        std::memcpy(ws->pin_app.p, smp.data(), sizeof(W::Sample) * S);
+        std::memcpy(ws->pin_app.at<char>(o_items), items.data(), sizeof(W::PrepItem) * S);
+        BT_CUDA(cudaMemcpyAsync(ws->app_samples.p, ws->pin_app.p, sizeof(W::Sample) * S, cudaMemcpyHostToDevice, s),
                 "upload samples");
-        BT_CUDA(cudaMemcpyAsync(ws->app_items.p, items.data(), sizeof(W::PrepItem) * S, cudaMemcpyHostToDevice, s),
+        BT_CUDA(cudaMemcpyAsync(ws->app_items.p, ws->pin_app.at<char>(o_items), sizeof(W::PrepItem) * S,
+                                cudaMemcpyHostToDevice, s),
                 "upload items");
     }
-    BT_CUDA(cudaMemcpyAsync(ws->app_graphs.p, avg.data(), sizeof(W::AvgGraph) * n_graphs, cudaMemcpyHostToDevice, s),
+    std::memcpy(ws->pin_app.at<char>(o_avg), avg.data(), sizeof(W::AvgGraph) * n_graphs);
+    BT_CUDA(cudaMemcpyAsync(ws->app_graphs.p, ws->pin_app.at<char>(o_avg), sizeof(W::AvgGraph) * n_graphs,
+                            cudaMemcpyHostToDevice, s),
             "upload graphs");
+    BT_CUDA(ws->pin_app.mark(s), "record warm-start upload");
     W::Sample* d_smp = ws->app_samples.as<W::Sample>();
     BT_CUDA(W::launch_prep(d_smp, ws->app_items.as<W::PrepItem>(), S, s), "launch prep");
     BT_CUDA(W::launch_forward(ws->net(), d_smp, nullptr, S, ws->app_y.as<float>(), nullptr, s), "launch forward");
     BT_CUDA(W::launch_average(ws->app_graphs.as<W::AvgGraph>(), n_graphs, max_free, s), "launch average");
-    std::vector<std::vector<double>> poses(n_graphs);
-    std::vector<int> status(n_graphs, 0);
+    return BT_OK;
+}
+
+// Enqueues the read-back of the per-graph status words into pinned staging.
+int read_status(bt_warmstart* ws, int n_graphs, cudaStream_t s)
+{
+    BT_CUDA(ws->pin_status.acquire(sizeof(int) * (size_t)n_graphs), "cudaHostAlloc(status staging)");
+    BT_CUDA(cudaMemcpyAsync(ws->pin_status.p, ws->app_status.p, sizeof(int) * n_graphs, cudaMemcpyDeviceToHost, s),
+            "read status");
+    BT_CUDA(ws->pin_status.mark(s), "record status read-back");
+    return BT_OK;
+}
+
+// Predicts and applies the warm start to every graph in `gs`, then stores
+// the new poses in the graphs.
+int apply_graphs(bt_warmstart* ws, bt_graph* const* gs, int n_graphs, int* status_out)
+{
+    cudaStream_t s = ws->stream;
+    std::vector<double*> pose(n_graphs);
     for (int k = 0; k < n_graphs; ++k) {
-        poses[k].resize(12 * (size_t)gs[k]->args.N);
-        BT_CUDA(cudaMemcpyAsync(poses[k].data(), gs[k]->args.pose, sizeof(double) * 12 * gs[k]->args.N,
+        bt_graph* g = gs[k];
+        int st = ensure_tables(g);
+        if (st != BT_OK) return st;
+        st = order_streams(g->stream, s);
+        if (st != BT_OK) return st;
+        const StateLayout L((int)g->active.size());
+        BT_CUDA(g->pin_state.acquire(L.bytes), "cudaHostAlloc(state staging)");
+        stage_state(g, g->pin_state.at<char>(0));
+        BT_CUDA(cudaMemcpyAsync(g->d_state.p, g->pin_state.p, L.upload_bytes(), cudaMemcpyHostToDevice, s),
+                "upload poses");
+        pose[k] = g->args.pose;
+    }
+    int st = enqueue_apply(ws, gs, n_graphs, pose.data(), s);
+    if (st != BT_OK) return st;
+    for (int k = 0; k < n_graphs; ++k) {
+        bt_graph* g = gs[k];
+        const StateLayout L(g->args.N);
+        BT_CUDA(cudaMemcpyAsync(g->pin_state.at<char>(L.pose), g->args.pose, sizeof(double) * 12 * g->args.N,
                                 cudaMemcpyDeviceToHost, s),
                 "read poses");
+        BT_CUDA(g->pin_state.mark(s), "record pose read-back");
     }
-    BT_CUDA(cudaMemcpyAsync(status.data(), ws->app_status.p, sizeof(int) * n_graphs, cudaMemcpyDeviceToHost, s),
-            "read status");
+    st = read_status(ws, n_graphs, s);
+    if (st != BT_OK) return st;
     BT_CUDA(cudaStreamSynchronize(s), "warm start: synchronize");
+    ws->pin_status.busy = false;
     int worst = BT_OK;
     for (int k = 0; k < n_graphs; ++k) {
-        if (status_out) status_out[k] = status[k] ? BT_ERR_SINGULAR : BT_OK;
-        if (status[k]) {
+        bt_graph* g = gs[k];
+        g->pin_state.busy = false;
+        const int bad = ws->pin_status.at<int>(0)[k];
+        if (status_out) status_out[k] = bad ? BT_ERR_SINGULAR : BT_OK;
+        if (bad) {
             worst = BT_ERR_SINGULAR;
             continue;
         }
-        bt_graph* g = gs[k];
+        const double* P = g->pin_state.at<double>(StateLayout(g->args.N).pose);
         for (int q = 0; q < g->args.N; ++q)
-            std::memcpy(g->frames.at(g->active[q]).pose, &poses[k][12 * (size_t)q], sizeof(double) * 12);
+            std::memcpy(g->frames.at(g->active[q]).pose, P + 12 * (size_t)q, sizeof(double) * 12);
     }
     if (worst != BT_OK)
         return fail(worst, "warm start: averaging system not positive definite for some graph; its poses are unchanged");
@@ -565,12 +611,34 @@ int bt_batch_solve_warm(bt_batch* b, bt_warmstart* ws, int32_t iters, int32_t fa
         for (size_t q = 0; q < g->active.size(); ++q)
             std::memcpy(&start[k][16 * q], g->frames.at(g->active[q]).pose, sizeof(double) * 16);
     }
+    // one stream-ordered sequence: starting poses up, the network and the
+    // averaging write the warm start into the batch's state block, the
+    // captured solve runs from there, one read-back
+    cudaStream_t s = b->stream;
+    st = batch_prepare(b, iters);
+    if (st != BT_OK) return st;
+    for (bt_graph* g : b->graphs) {
+        st = ensure_tables(g);
+        if (st != BT_OK) return st;
+        st = order_streams(g->stream, s);
+        if (st != BT_OK) return st;
+    }
+    st = order_streams(ws->stream, s);
+    if (st == BT_OK) st = batch_upload_state(b);
+    if (st != BT_OK) return st;
+    std::vector<double*> pose(G);
+    for (size_t k = 0; k < G; ++k) pose[k] = b->h_args[k].pose;
+    st = enqueue_apply(ws, b->graphs.data(), (int)G, pose.data(), s);
+    if (st == BT_OK) st = read_status(ws, (int)G, s);
+    if (st == BT_OK) st = batch_launch(b, iters);
+    if (st != BT_OK) return st;
+    BT_CUDA(cudaStreamSynchronize(s), "bt_batch_solve_warm: synchronize");
+    b->pin_state.busy = false;
+    ws->pin_status.busy = false;
     std::vector<int> ws_status(G, BT_OK);
-    st = apply_graphs(ws, b->graphs.data(), (int)G, ws_status.data());
-    if (st != BT_OK && st != BT_ERR_SINGULAR) return st;
+    for (size_t k = 0; k < G; ++k) ws_status[k] = ws->pin_status.at<int>(0)[k] ? BT_ERR_SINGULAR : BT_OK;
     std::vector<bt_solve_report> r(G);
-    st = bt_batch_solve(b, iters, r.data());
-    if (st != BT_OK && st != BT_ERR_SINGULAR) return st;
+    batch_collect(b, iters, r.data());
     int worst = BT_OK;
     for (size_t k = 0; k < G; ++k) {
         r[k].used_warmstart = ws_status[k] == BT_OK ? 1 : 0;
