@@ -79,6 +79,17 @@ void drop_matches(bt_graph* g, const MatchSet& m)
     g->pool.put(m.pb, sizeof(float) * 3 * (size_t)m.count);
 }
 
+void unlink_partners(bt_graph* g, int fa, int fb)
+{
+    for (int k = 0; k < 2; ++k) {
+        auto it = g->partners.find(k == 0 ? fa : fb);
+        if (it == g->partners.end()) continue;
+        std::vector<int>& v = it->second;
+        v.erase(std::remove(v.begin(), v.end(), k == 0 ? fb : fa), v.end());
+        if (v.empty()) g->partners.erase(it);
+    }
+}
+
 int put_matches(bt_graph* g, int fa, int fb, int count, const float* pa, const float* pb, int mem_kind)
 {
     if (fa == fb) return fail(BT_ERR_INVALID, "matches: a frame cannot match itself");
@@ -105,8 +116,13 @@ int put_matches(bt_graph* g, int fa, int fb, int count, const float* pa, const f
     if (it != g->matches.end()) {
         drop_matches(g, it->second);
         g->matches.erase(it);
+        unlink_partners(g, fa, fb);
     }
-    if (count > 0) g->matches[key] = ms;
+    if (count > 0) {
+        g->matches[key] = ms;
+        g->partners[fa].push_back(fb);
+        g->partners[fb].push_back(fa);
+    }
     g->topo_dirty = true;
     return BT_OK;
 }
@@ -114,6 +130,24 @@ int put_matches(bt_graph* g, int fa, int fb, int count, const float* pa, const f
 // Rebuilds the node / tile / edge tables of the active set and sizes the
 // per-solve buffers.
 }  // namespace
+
+std::vector<ActiveEdge> bthost::active_edges(const bt_graph* g)
+{
+    const int N = (int)g->active.size();
+    std::vector<ActiveEdge> out;
+    for (int a = 0; a < N; ++a)
+        for (int b = a + 1; b < N; ++b) {
+            const int fa = g->active[a], fb = g->active[b];
+            auto it = g->matches.find(std::make_pair(std::min(fa, fb), std::max(fa, fb)));
+            if (it == g->matches.end() || it->second.count <= 0) continue;
+            const bool fwd = fa < fb;
+            out.push_back(ActiveEdge{fwd ? a : b, fwd ? b : a, &it->second});
+        }
+    std::sort(out.begin(), out.end(), [](const ActiveEdge& x, const ActiveEdge& y) {
+        return std::make_pair(x.m->fa, x.m->fb) < std::make_pair(y.m->fa, y.m->fb);
+    });
+    return out;
+}
 
 int bthost::resolve_pending(bt_graph* g)
 {
@@ -168,19 +202,14 @@ int bthost::build_topology(bt_graph* g, int tile)
         d.free_idx = f.fixed ? -1 : nfree++;
         px += (int64_t)f.M * (N - 1);
     }
-    std::map<int, int> node_of;
-    for (int k = 0; k < N; ++k) node_of[g->active[k]] = k;
     std::vector<bt::EdgeDev> edges;
-    for (auto& kv : g->matches) {
-        const MatchSet& m = kv.second;
-        auto ia = node_of.find(m.fa), ib = node_of.find(m.fb);
-        if (ia == node_of.end() || ib == node_of.end() || m.count <= 0) continue;
+    for (const ActiveEdge& ae : active_edges(g)) {
         bt::EdgeDev e;
-        e.i = ia->second;
-        e.j = ib->second;
-        e.count = m.count;
-        e.pa = m.pa;
-        e.pb = m.pb;
+        e.i = ae.i;
+        e.j = ae.j;
+        e.count = ae.m->count;
+        e.pa = ae.m->pa;
+        e.pb = ae.m->pb;
         edges.push_back(e);
     }
     const int T = (int)tile_node.size(), P = N * (N - 1), E = (int)edges.size(), U = N * (N - 1) / 2;
@@ -549,12 +578,16 @@ int bt_remove_frame(bt_graph* g, int32_t frame_id)
         g->free_slots.push_back(f.slot);
     }
     g->frames.erase(it);
-    for (auto m = g->matches.begin(); m != g->matches.end();) {
-        if (m->second.fa == frame_id || m->second.fb == frame_id) {
-            drop_matches(g, m->second);
-            m = g->matches.erase(m);
-        } else {
-            ++m;
+    auto pit = g->partners.find(frame_id);
+    if (pit != g->partners.end()) {
+        const std::vector<int> others = pit->second;
+        for (int o : others) {
+            auto m = g->matches.find(std::make_pair(std::min(o, frame_id), std::max(o, frame_id)));
+            if (m != g->matches.end()) {
+                drop_matches(g, m->second);
+                g->matches.erase(m);
+            }
+            unlink_partners(g, o, frame_id);
         }
     }
     g->active.erase(std::remove(g->active.begin(), g->active.end(), frame_id), g->active.end());

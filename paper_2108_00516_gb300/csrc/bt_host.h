@@ -225,6 +225,7 @@ struct bt_graph {
     int next_id = 0;
     std::map<int, bthost::Frame> frames;
     std::map<std::pair<int, int>, bthost::MatchSet> matches;
+    std::map<int, std::vector<int>> partners;   // frame -> frames it has a correspondence set with
     std::vector<int> active;
     bool topo_dirty = true;
 
@@ -302,6 +303,17 @@ struct bt_batch {
 };
 
 namespace bthost {
+
+// A correspondence set between two active nodes: i = node of m->fa, j = node
+// of m->fb.
+struct ActiveEdge {
+    int i, j;
+    const MatchSet* m;
+};
+// The non-empty correspondence sets among g's active nodes, ordered by their
+// frame-id pair (fa, fb).  Looks up the N (N - 1) / 2 active pairs only, so
+// the cost does not grow with the number of sets stored in the graph.
+std::vector<ActiveEdge> active_edges(const bt_graph* g);
 
 // Builds the graph's device tables (nodes, dense tiles of `tile` source
 // pixels, correspondence sets, node pairs) for its active nodes.

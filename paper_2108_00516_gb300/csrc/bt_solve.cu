@@ -599,7 +599,11 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
     // {1,2,3,5,6,7} (no FP64 pipe shared with warp 0) apply column k to the
     // trailing triangle of rows and columns >= k+2 and carry the forward
     // substitution.  The scaled column is double-buffered; L is stored
-    // transposed in the upper triangle, L_ik at (k, i).
+    // transposed in the upper triangle, L_ik at (k, i).  A failed pivot
+    // (not positive) sets s_fail and a zero reciprocal; the loop still runs
+    // to the end (same bounds, finite or discarded values) and the flag is
+    // read once afterwards, which keeps a shared-memory read and a branch
+    // off every column of the chain.
     int* tab = reinterpret_cast<int*>(colb + 2 * n);
     for (int ip = tid; ip < n; ip += nt)
         for (int jp = 0; jp <= ip; ++jp) tab[ip * (ip + 1) / 2 + jp] = (ip << 16) | jp;
@@ -622,7 +626,6 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
     const int nbulk = (nt / 32 >= 8 ? 6 : 0) * 32;
     const int bt = bulk ? (warp < 4 ? warp - 1 : warp - 2) * 32 + lane : -1;
     for (int k = 0; k < n - 1; ++k) {
-        if (s_fail) break;
         const double* ck = colb + (k & 1) * n;        // l_{i,k}
         double* cn = colb + ((k + 1) & 1) * n;        // l_{i,k+1}, written now
         if (warp == 0) {
@@ -647,7 +650,10 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
                 u[q] = hv[q] - cv[q] * hpk;
             }
             const double h = __shfl_sync(0xffffffffu, u[0], 0);
-            const bool ok = h > 0.0;
+            // h > 0 as an integer test on the bits (positive, not NaN): no
+            // FP64 compare on the chain
+            const long long hb = __double_as_longlong(h);
+            const bool ok = hb > 0ll && hb <= 0x7ff0000000000000ll;
             const double rp = ok ? rcp_fp64(h) : 0.0;
             if (lane == 0) {
                 if (!ok) s_fail = 1;

@@ -145,15 +145,8 @@ struct HostEdge {
 
 std::vector<HostEdge> graph_edges(const bt_graph* g)
 {
-    std::map<int, int> node_of;
-    for (size_t k = 0; k < g->active.size(); ++k) node_of[g->active[k]] = (int)k;
     std::vector<HostEdge> out;
-    for (auto& kv : g->matches) {
-        const MatchSet& m = kv.second;
-        auto ia = node_of.find(m.fa), ib = node_of.find(m.fb);
-        if (ia == node_of.end() || ib == node_of.end() || m.count <= 0) continue;
-        out.push_back(HostEdge{ia->second, ib->second, m.count, m.pa, m.pb});
-    }
+    for (const ActiveEdge& e : active_edges(g)) out.push_back(HostEdge{e.i, e.j, e.m->count, e.m->pa, e.m->pb});
     return out;
 }
 

@@ -227,6 +227,28 @@ def test_remove_frame(bt):
     assert rot <= ROT_TOL and tr <= TRANS_TOL
 
 
+def test_replaced_and_removed_sets(bt):
+    # a set given again in the other order replaces the stored one; an empty
+    # set removes the pair's set; removing a frame drops its sets -- the solve
+    # then matches the oracle on the graph without those sets
+    import dataclasses
+    g = S.tiny_graph(2)
+    pg = bt.graph_from_synth(g)
+    ids = pg.frame_ids
+    i0, j0, pa0, pb0 = g.matches[0]
+    pg.set_matches(ids[j0], ids[i0], pb0, pa0)
+    i1, j1, _, _ = g.matches[1]
+    empty = np.zeros((0, 3), np.float32)
+    pg.set_matches(ids[i1], ids[j1], empty, empty)
+    pg.remove_frame(ids[3])
+    Pg, rg = pg.solve(4)
+    kept = [m for k, m in enumerate(g.matches) if k != 1 and 3 not in (m[0], m[1])]
+    ro = O.solve(dataclasses.replace(g, matches=kept), 4, nodes=[0, 1, 2])
+    rot, tr = pose_err(Pg, ro["poses"])
+    assert rot <= ROT_TOL and tr <= TRANS_TOL
+    assert abs(rg["cost_final"] - ro["cost_final"]) <= COST_RTOL * ro["cost_final"]
+
+
 def test_invalid_arguments(bt):
     pg = bt.PoseGraph()
     with pytest.raises(bt.BTError):
