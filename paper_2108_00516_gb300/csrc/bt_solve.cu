@@ -26,7 +26,7 @@ namespace bt {
 // its rounding to single precision is reproducible bit for bit.
 // ---------------------------------------------------------------------------
 
-// Writes xf[i*N+j] = float(T_j T_i^-1) and xinv[i] = float(T_i^-1) with the
+// Writes xf[i*N+j] = float(T_j T_i^-1) (i != j) and xinv[i] = float(T_i^-1) with the
 // threads of one CTA, one matrix entry per thread (the FP64 inverse first, then
 // the products).  `tinv` is shared scratch of 12 * N doubles.
 __device__ void write_xforms(const SolveArgs& a, double* __restrict__ tinv, const double* __restrict__ pose)
@@ -46,15 +46,17 @@ __device__ void write_xforms(const SolveArgs& a, double* __restrict__ tinv, cons
         a.xinv[id] = __double2float_rn(v);
     }
     __syncthreads();
-    for (int id = tid; id < N * N * 12; id += nt) {
+    // pairs i != j only (the residual pass never reads xf[i*N+i])
+    const int M = N > 1 ? N - 1 : 0;
+    for (int id = tid; id < N * M * 12; id += nt) {
         const int pr = id / 12, e = id % 12, r = e / 4, c = e % 4;
-        const int i = pr / N, j = pr % N;
+        const int i = pr / M, jj = pr % M, j = jj < i ? jj : jj + 1;
         const double* A = pose + j * 12;     // T_j
         const double* B = tinv + i * 12;     // T_i^-1
         double s = __dadd_rn(__dadd_rn(__dmul_rn(A[r * 4 + 0], B[0 * 4 + c]), __dmul_rn(A[r * 4 + 1], B[1 * 4 + c])),
                              __dmul_rn(A[r * 4 + 2], B[2 * 4 + c]));
         if (c == 3) s = __dadd_rn(s, A[r * 4 + 3]);
-        a.xf[id] = __double2float_rn(s);
+        a.xf[(i * N + j) * 12 + e] = __double2float_rn(s);
     }
 }
 
@@ -701,39 +703,49 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
     for (int i = tid; i < n; i += nt) y[i] *= rD[i];   // D w = z
     __syncthreads();
     t2 = clock64();
-    // L^T dx = w, unit diagonal (one warp; L_ki is stored at (i, k)).  Lane l
-    // keeps w_i for i = l, l + 32, ... in registers; x_k is broadcast from its
-    // owner with a shuffle, so each step is one shuffle and one FMA deep.
-    if (tid < 32) {
-        constexpr int kSlots = (6 * (kMaxNodes - 1) + 31) / 32;
-        double w[kSlots];
-#pragma unroll
-        for (int q = 0; q < kSlots; ++q) {
-            const int i = lane + 32 * q;
-            w[q] = i < n ? y[i] : 0.0;
-        }
-        for (int k = n - 1; k >= 1; --k) {
-            const int slot = k >> 5, owner = k & 31;
-            double v;
-            switch (slot) {     // warp-uniform
-            case 0: v = w[0]; break;
-            case 1: v = w[1]; break;
-            case 2: v = w[2]; break;
-            case 3: v = w[3]; break;
-            default: v = w[kSlots - 1]; break;
+    // L^T dx = w, unit diagonal (L_ki is stored at (i, k)), in blocks of 32
+    // unknowns from the last block up.  Warp 0 runs the chain of one block
+    // with the block's values in registers, lane l holding row r0 + l: x_k
+    // is broadcast from its lane with a shuffle, so each step is one shuffle
+    // and one FP64 FMA deep, and a step issues one FP64 instruction whatever
+    // the size of the system.  The rows above the block then take the
+    // block's unknowns as dot products, split into column chunks over
+    // several warps (partial sums in shared memory, added per row).
+    {
+        double* part = reinterpret_cast<double*>(node_of + kMaxNodes);   // [chunks][r0], <= 256
+        for (int r0 = ((n - 1) >> 5) << 5; r0 >= 0; r0 -= 32) {
+            const int r1 = min(n, r0 + 32);
+            if (warp == 0) {
+                const int i = r0 + lane;
+                double wv = i < r1 ? y[i] : 0.0;
+                for (int k = r1 - 1; k > r0; --k) {
+                    const double hk = i < k ? H[i * ld + k] : 0.0;
+                    const double xk = __shfl_sync(0xffffffffu, wv, k - r0);
+                    if (i < k) wv = fma(-hk, xk, wv);
+                }
+                if (i < r1) y[i] = wv;
             }
-            const double xk = __shfl_sync(0xffffffffu, v, owner);
-#pragma unroll
-            for (int q = 0; q < kSlots; ++q) {
-                if (32 * q >= k) break;      // warp-uniform
-                const int i = lane + 32 * q;
-                if (i < k) w[q] -= H[i * ld + k] * xk;
+            __syncthreads();
+            if (r0 == 0) break;
+            const int chunks = min(4, 256 / r0);      // r0 <= 128: at least 2
+            if (tid < chunks * r0) {
+                const int i = tid % r0, c = tid / r0;
+                double s0 = 0.0, s1 = 0.0;
+                int k = r0 + c;
+                for (; k + chunks < r1; k += 2 * chunks) {
+                    s0 = fma(H[i * ld + k], y[k], s0);
+                    s1 = fma(H[i * ld + k + chunks], y[k + chunks], s1);
+                }
+                if (k < r1) s0 = fma(H[i * ld + k], y[k], s0);
+                part[c * r0 + i] = s0 + s1;
             }
-        }
-#pragma unroll
-        for (int q = 0; q < kSlots; ++q) {
-            const int i = lane + 32 * q;
-            if (i < n) y[i] = w[q];
+            __syncthreads();
+            for (int i = tid; i < r0; i += nt) {
+                double s = part[i];
+                for (int c = 1; c < chunks; ++c) s += part[c * r0 + i];
+                y[i] -= s;
+            }
+            __syncthreads();
         }
     }
     __syncthreads();
