@@ -60,7 +60,7 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="bounded oracle sample (CPU baseline)")
     ap.add_argument("--workers", type=int, default=0, help="generator processes (0 = all cores)")
     ap.add_argument("--batch-graphs", type=int, default=64, help="graphs of the batched workload (0 = skip)")
-    ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--learned-iters", type=int, default=2,
                     help="Gauss-Newton iterations after the learned warm start (batched workload)")
     return ap.parse_args()
