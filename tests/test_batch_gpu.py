@@ -135,3 +135,40 @@ def test_batched_workload_sample(bt):
         assert abs(r["cost_init"] - ro["cost_per_iter"][0]) <= 1e-6 * ro["cost_per_iter"][0]
         rot, tr = pose_err(pg.get_poses(), ro["poses"])
         assert rot <= ROT_TOL and tr <= TRANS_TOL
+
+
+def test_distinct_streams_give_identical_results(bt):
+    """Graphs, batch and warm start on three different streams: the work of
+    each is ordered after what the others enqueued before it (frame
+    preparation, table uploads, the network), so the results are bit for bit
+    those of the same calls on one stream."""
+    torch = pytest.importorskip("torch")
+    gs = _graphs()
+    params = S.warmstart_init(11)
+
+    def run(s_graph, s_batch, s_ws):
+        pgs = [bt.graph_from_synth(g, stream=s_graph) for g in gs]
+        batch = bt.Batch(stream=s_batch)
+        for pg in pgs:
+            batch.add(pg)
+        batch.set_shape(0)
+        plain = batch.solve(5)
+        P_plain = [pg.get_poses() for pg in pgs]
+        for pg, g in zip(pgs, gs):
+            pg.set_poses(g.pose_init)
+        ws = bt.WarmStart(params, stream=s_ws)
+        warm = batch.solve_warm(ws, 2, 5, raise_on_error=False)
+        P_warm = [pg.get_poses() for pg in pgs]
+        ws.close()
+        batch.close()
+        for pg in pgs:
+            pg.close()
+        return plain, P_plain, warm, P_warm
+
+    one = torch.cuda.Stream()
+    ref = run(one, one, one)
+    got = run(torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream())
+    for a, b in zip(ref[0] + ref[2], got[0] + got[2]):
+        assert a["cost_final"] == b["cost_final"] and a["dense_inliers"] == b["dense_inliers"]
+    for a, b in zip(ref[1] + ref[3], got[1] + got[3]):
+        assert np.array_equal(a, b)
