@@ -24,6 +24,7 @@ the same workload on the host cores.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -46,6 +47,18 @@ BYTES_PER_PIXEL_PAIR = 32      # source depth+normal 16 B + target depth+normal 
 HALF_BYTES_PER_PIXEL_PAIR = 16  # the same four values per side in 16 bits (BT_FP16 / BT_BF16 storage)
 BYTES_PER_SPARSE_PAIR = 24     # two FP32 3-vectors
 L2_FLUSH_BYTES = 512 << 20
+
+
+def gc_pause():
+    """Timed regions run with Python's cyclic collector paused, after one
+    collection: a full collection over the workload's host objects is a pause
+    of tens of milliseconds that is neither arm's work."""
+    gc.collect()
+    gc.disable()
+
+
+def gc_resume():
+    gc.enable()
 
 
 def parse_args():
@@ -251,11 +264,13 @@ def run_batched(bt, graphs_b, stream, args):
         for pg in pgs:
             pg.solve(it)
     torch.cuda.synchronize()
+    gc_pause()
     t0 = time.perf_counter()
     for s in range(args.batch_steps):
         reset()
         plain_cost = [pg.solve(it)[1]["cost_final"] for pg in pgs]
     torch.cuda.synchronize()
+    gc_resume()
     t_plain = (time.perf_counter() - t0) / args.batch_steps
     batch = bt.Batch(stream=stream)
     for pg in pgs:
@@ -265,11 +280,13 @@ def run_batched(bt, graphs_b, stream, args):
     reset()
     batch.solve(it)                            # warm-up replay
     torch.cuda.synchronize()
+    gc_pause()
     t0 = time.perf_counter()
     for s in range(args.batch_steps):
         reset()
         reps = batch.solve(it)
     torch.cuda.synchronize()
+    gc_resume()
     t_batch = (time.perf_counter() - t0) / args.batch_steps
     shape, tune_us = batch.tuning()
     px_pass = sum(r["dense_pixel_pairs"] for r in reps) / max(1, it)
@@ -321,12 +338,22 @@ def run_learned(bt, pgs, batch, reset, plain_cost, t_plain, stream, args):
         reset()
         batch.solve_warm(ws, K, args.iters, ref_costs=plain_cost, tol=0.01)
     torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.batch_steps)]
+    gc_pause()
     t0 = time.perf_counter()
+    walls = []
     for s in range(args.batch_steps):
+        w0 = time.perf_counter()
         reset()
+        ev[s][0].record(stream)
         reps = batch.solve_warm(ws, K, args.iters, ref_costs=plain_cost, tol=0.01)
+        ev[s][1].record(stream)
+        walls.append(time.perf_counter() - w0)
     torch.cuda.synchronize()
+    gc_resume()
     t_learned = (time.perf_counter() - t0) / args.batch_steps
+    span_ms = sum(a.elapsed_time(b) for a, b in ev) / args.batch_steps
     rel = [(r["cost_final"] - c) / c for r, c in zip(reps, plain_cost)]
     reset()
     ctrl = batch.solve(K)
@@ -334,6 +361,8 @@ def run_learned(bt, pgs, batch, reset, plain_cost, t_plain, stream, args):
     ws.close()
     return {"iters": K, "fallback_iters": args.iters,
             "learned_batched_solves_per_s": round(len(pgs) / t_learned, 2),
+            "ms_per_batch": {"wall": round(t_learned * 1e3, 3), "stream_span": round(span_ms, 3),
+                             "wall_min": round(min(walls) * 1e3, 3), "wall_max": round(max(walls) * 1e3, 3)},
             "speedup_vs_plain": round(t_plain / t_learned, 3),
             "fallbacks": int(sum(r["fell_back"] for r in reps)),
             "equal_cost": {"max_rel_above_plain": float(max(rel)), "bound": 0.01, "ok": max(rel) <= 0.01},
@@ -364,11 +393,13 @@ def run_storage(bt, graphs_b, inits, stream, args, code, ref_reps, peak):
     reset()
     batch.solve(it)
     torch.cuda.synchronize()
+    gc_pause()
     t0 = time.perf_counter()
     for s in range(args.batch_steps):
         reset()
         reps = batch.solve(it)
     torch.cuda.synchronize()
+    gc_resume()
     t = (time.perf_counter() - t0) / args.batch_steps
     shape, tune_us = batch.tuning()
     us = tune_us[shape]
@@ -444,6 +475,7 @@ def run_ours(args):
     clocks = ClockSampler(gpu_id)
     pg.profile_enable(True)
     px_total = 0
+    gc_pause()
     wall0 = time.perf_counter()
     for s in range(args.steps):
         flush_buf.fill_(float(s))               # L2 flush between timed steps (outside the events)
@@ -452,6 +484,7 @@ def run_ours(args):
         ev[s][1].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
+    gc_resume()
     prof = pg.profile_read()
     pg.profile_enable(False)
     clk = clocks.stop()
@@ -582,6 +615,7 @@ def run_e2e(bt, seq, graphs, pools, inits, stream, args, world):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
+    gc_pause()
     t0 = time.perf_counter()
     h2d = d2h = 0
     for _ in range(args.e2e_steps):
@@ -589,6 +623,7 @@ def run_e2e(bt, seq, graphs, pools, inits, stream, args, world):
         h2d += a
         d2h += b
     torch.cuda.synchronize()
+    gc_resume()
     el = max_over_ranks(time.perf_counter() - t0, world, "cuda")
     return {"value": round(job_throughput(len(graphs) * args.e2e_steps, world, el), 3), "unit": "solves/s",
             "h2d_bytes_per_step": h2d // args.e2e_steps, "d2h_bytes_per_step": d2h // args.e2e_steps,
@@ -629,11 +664,13 @@ def run_reference(args):
 
     for s in range(args.warmup):
         step(s)
+    gc_pause()
     t0 = time.perf_counter()
     done = 0
     for s in range(args.steps):
         done += step(args.warmup + s)
     el = time.perf_counter() - t0
+    gc_resume()
     value = done / el
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el * 1e3 / args.steps, 3),
