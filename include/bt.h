@@ -409,7 +409,9 @@ int32_t bt_is_novel_view(const double* pool_poses, int32_t n_pool, const double*
 /* Profiling counters of one graph (the tracing facility; no paper
  * counterpart).  Launch counts are always kept; kernel durations are summed
  * from CUDA events recorded on the graph's stream around each launch of the
- * residual and reduce kernels while profiling is enabled. */
+ * residual and reduce kernels of the timed solves (every solve, or every
+ * k-th: see bt_profile_enable); the pixel-pair and correspondence counts
+ * below cover the same timed launches. */
 typedef struct {
     int64_t prep_launches;      /* frame-preparation kernels (3 per frame) */
     int64_t xform_launches;
@@ -428,8 +430,12 @@ typedef struct {
     int64_t solve_phase_cycles[4];
 } bt_profile;
 
-/* Enables (on != 0) or disables event timing and resets every counter.
- * Errors: BT_ERR_INVALID, BT_ERR_CUDA. */
+/* Enables (on > 0) or disables (on == 0) event timing and resets every
+ * counter.  With on = k the events time every k-th bt_solve / bt_eval_cost
+ * from here on (the first included): recording events between the kernels
+ * of a solve costs host time and breaks the programmatic launch overlap of
+ * the timed solves, so sampling keeps the untimed ones at full speed.
+ * Errors: BT_ERR_INVALID (on < 0), BT_ERR_CUDA. */
 int bt_profile_enable(bt_graph* g, int32_t on);
 
 /* Copies the counters to *out (host).  Errors: BT_ERR_INVALID. */

@@ -307,8 +307,9 @@ class PoseGraph:
         _check(load().bt_ransac_init(self._h, int(hypotheses), int(seed) & ((1 << 64) - 1), float(inlier_dist),
                                      1 if refine else 0), "bt_ransac_init")
 
-    def profile_enable(self, on: bool = True):
-        _check(load().bt_profile_enable(self._h, int(bool(on))), "bt_profile_enable")
+    def profile_enable(self, on=True):
+        """on: False/0 off, True/1 time every solve, k > 1 every k-th solve."""
+        _check(load().bt_profile_enable(self._h, int(on)), "bt_profile_enable")
 
     def profile_read(self) -> dict:
         p = bt_profile()

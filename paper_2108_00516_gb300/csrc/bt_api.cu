@@ -360,18 +360,19 @@ int enqueue_passes(bt_graph* g, int iters, bool cost_pass, int cost_slot)
     cudaStream_t s = g->stream;
     const bt::SolveArgs& a = g->args;
     const int passes = iters + (cost_pass ? 1 : 0);
-    if (g->prof_on) {
+    g->prof_timed = g->prof_on && (g->prof_solves++ % g->prof_period) == 0;
+    if (g->prof_timed) {
         int st = ensure_events(g, passes);
         if (st != BT_OK) return st;
     }
     for (int p = 0; p < passes; ++p) {
         const bool full = p < iters;
         const int slot = full ? p : cost_slot;
-        if (g->prof_on) BT_CUDA(cudaEventRecord(g->events[4 * p + 0], s), "event");
+        if (g->prof_timed) BT_CUDA(cudaEventRecord(g->events[4 * p + 0], s), "event");
         BT_CUDA(bt::launch_residual(a, full, s), "launch residual");
-        if (g->prof_on) BT_CUDA(cudaEventRecord(g->events[4 * p + 1], s), "event");
+        if (g->prof_timed) BT_CUDA(cudaEventRecord(g->events[4 * p + 1], s), "event");
         BT_CUDA(bt::launch_reduce(a, full, slot, s), "launch reduce");
-        if (g->prof_on) BT_CUDA(cudaEventRecord(g->events[4 * p + 2], s), "event");
+        if (g->prof_timed) BT_CUDA(cudaEventRecord(g->events[4 * p + 2], s), "event");
         if (a.n_edges + a.n_tiles > 0) g->prof.residual_launches++;
         g->prof.reduce_launches++;
     }
@@ -381,7 +382,7 @@ int enqueue_passes(bt_graph* g, int iters, bool cost_pass, int cost_slot)
 // After the stream has been synchronised: fold the event times in.
 void collect_events(bt_graph* g, int passes)
 {
-    if (!g->prof_on) return;
+    if (!g->prof_timed) return;
     for (int p = 0; p < passes; ++p) {
         float t1 = 0.f, t2 = 0.f;
         if (cudaEventElapsedTime(&t1, g->events[4 * p + 0], g->events[4 * p + 1]) == cudaSuccess &&
@@ -708,8 +709,12 @@ int bt_profile_enable(bt_graph* g, int32_t on)
 {
     if (!g) return fail(BT_ERR_INVALID, "bt_profile_enable: NULL graph");
     BT_CUDA(g->stream ? cudaStreamSynchronize(g->stream) : cudaDeviceSynchronize(), "bt_profile_enable: sync");
+    if (on < 0) return fail(BT_ERR_INVALID, "bt_profile_enable: negative period");
     std::memset(&g->prof, 0, sizeof(g->prof));
     g->prof_on = on != 0;
+    g->prof_period = on > 0 ? on : 1;
+    g->prof_solves = 0;
+    g->prof_timed = false;
     return BT_OK;
 }
 

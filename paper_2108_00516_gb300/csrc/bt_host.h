@@ -249,6 +249,9 @@ struct bt_graph {
     // profiling
     bt_profile prof{};
     bool prof_on = false;
+    int prof_period = 1;      // event timing on every prof_period-th solve
+    int64_t prof_solves = 0;  // solves since profiling was enabled
+    bool prof_timed = false;  // the current solve records events
     std::vector<cudaEvent_t> events;
 
     ~bt_graph()
