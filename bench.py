@@ -588,16 +588,19 @@ def run_e2e(bt, seq, graphs, pools, inits, stream, args, world):
         ids = {}
         have = set()
 
-        def add(t):
+        def add(t, olds=()):
+            # the new frame with its correspondence sets to earlier frames
             nonlocal h2d
             d, n, m = frames_h[t]
-            ids[t] = pg.add_frame(d, n, m, seq.cam.as_tuple(), seq.poses_true[t], fixed=(t == 0))
-            h2d += d.nbytes + n.nbytes + m.nbytes
+            sets = [(ids[a],) + matches_h[(a, t)][::-1] for a in olds]
+            ids[t] = pg.add_frame(d, n, m, seq.cam.as_tuple(), seq.poses_true[t], fixed=(t == 0), matches=sets)
+            h2d += d.nbytes + n.nbytes + m.nbytes + sum(x.nbytes + y.nbytes for _, x, y in sets)
+            have.update((a, t) for a in olds)
 
         add(0)
         for k, nodes in enumerate(graphs):
             t = nodes[-1]
-            add(t)
+            add(t, [a for a in nodes if a < t and (a, t) not in have])
             for a in nodes:
                 for b in nodes:
                     if a < b and (a, b) not in have:
@@ -636,8 +639,9 @@ def run_e2e(bt, seq, graphs, pools, inits, stream, args, world):
     return {"value": round(job_throughput(len(graphs) * args.e2e_steps, world, el), 3), "unit": "solves/s",
             "h2d_bytes_per_step": h2d // args.e2e_steps, "d2h_bytes_per_step": d2h // args.e2e_steps,
             "steps": args.e2e_steps,
-            "note": "pinned host buffers through bt_add_frame / bt_set_matches / bt_solve; "
-                    "frames arrive one per solve; non-keyframes are removed after their solve"}
+            "note": "pinned host buffers through bt_add_frame (with the new frame's correspondence sets) / "
+                    "bt_set_matches / bt_solve; frames arrive one per solve; non-keyframes are removed after "
+                    "their solve"}
 
 
 # --------------------------------------------------------------------------- reference arm

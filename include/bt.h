@@ -441,6 +441,20 @@ int bt_profile_enable(bt_graph* g, int32_t on);
 /* Copies the counters to *out (host).  Errors: BT_ERR_INVALID. */
 int bt_profile_read(const bt_graph* g, bt_profile* out);
 
+/* Device memory cache (no paper counterpart).  Frames and correspondence
+ * sets live in blocks of a per-graph pool; a destroyed graph hands its
+ * blocks to a process-wide cache of idle blocks, from which later graphs
+ * take blocks of the same size class before allocating, so a series of
+ * graphs reuses device memory instead of allocating and freeing it (cudaFree
+ * synchronises the device).  Thread-safe.
+ *
+ * bt_device_cache_bytes: bytes of idle cached blocks.
+ * bt_device_cache_trim: frees the idle blocks above 64 KiB (the smaller
+ * ones share 2 MiB slabs that stay until the process exits) and returns the
+ * bytes freed. */
+int64_t bt_device_cache_bytes(void);
+int64_t bt_device_cache_trim(void);
+
 /* Dense energy of one frame pair without allocating device memory.
  *
  * The paper has no counterpart to this call; it exists for callers that

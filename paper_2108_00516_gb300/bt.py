@@ -122,6 +122,8 @@ SIGNATURES = {
     "bt_is_novel_view": (C.c_int32, [C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_double), C.c_double]),
     "bt_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "bt_profile_read": (C.c_int, [C.c_void_p, C.POINTER(bt_profile)]),
+    "bt_device_cache_bytes": (C.c_int64, []),
+    "bt_device_cache_trim": (C.c_int64, []),
     "bt_pair_dense_energy_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(bt_intrinsics),
                                                C.POINTER(C.c_double), C.c_void_p, C.c_void_p, C.c_void_p,
                                                C.POINTER(bt_intrinsics), C.POINTER(C.c_double),
@@ -424,6 +426,16 @@ def ransac(pts_i, pts_j, hypotheses: int = 256, seed: int = 0, inlier_dist: floa
                             float(inlier_dist), 1 if refine else 0, M.ctypes.data_as(C.POINTER(C.c_double)),
                             C.byref(cnt), _stream_handle(stream)), "bt_ransac")
     return M.reshape(4, 4), cnt.value
+
+
+def device_cache_bytes() -> int:
+    """Bytes of idle device blocks in the process-wide cache (bt_device_cache_bytes)."""
+    return int(load().bt_device_cache_bytes())
+
+
+def device_cache_trim() -> int:
+    """Frees the idle cached blocks above 64 KiB; returns the bytes freed."""
+    return int(load().bt_device_cache_trim())
 
 
 def select_keyframes(pool_poses, pose_current, K: int) -> list:

@@ -54,7 +54,6 @@ int validate_config(const bt_config& c)
     return BT_OK;
 }
 
-// Copies a count x 3 point list (host or device) into a new device array.
 // Copies a count x 3 point list (host or device) into a pooled device block.
 int upload_points(bt_graph* g, const float* src, int count, int mem_kind, float** out)
 {
@@ -75,6 +74,7 @@ int upload_points(bt_graph* g, const float* src, int count, int mem_kind, float*
 
 void drop_matches(bt_graph* g, const MatchSet& m)
 {
+    if (!m.owned) return;    // the points belong to a frame's block
     g->pool.put(m.pa, sizeof(float) * 3 * (size_t)m.count);
     g->pool.put(m.pb, sizeof(float) * 3 * (size_t)m.count);
 }
@@ -90,6 +90,8 @@ void unlink_partners(bt_graph* g, int fa, int fb)
     }
 }
 
+void store_matches(bt_graph* g, int fa, int fb, int count, float* pa, float* pb, bool owned);
+
 int put_matches(bt_graph* g, int fa, int fb, int count, const float* pa, const float* pb, int mem_kind)
 {
     if (fa == fb) return fail(BT_ERR_INVALID, "matches: a frame cannot match itself");
@@ -100,17 +102,81 @@ int put_matches(bt_graph* g, int fa, int fb, int count, const float* pa, const f
         std::swap(fa, fb);
         std::swap(pa, pb);
     }
+    float *da = nullptr, *db = nullptr;
+    int st = upload_points(g, pa, count, mem_kind, &da);
+    if (st != BT_OK) return st;
+    st = upload_points(g, pb, count, mem_kind, &db);
+    if (st != BT_OK) {
+        g->pool.put(da, sizeof(float) * 3 * (size_t)count);
+        return st;
+    }
+    store_matches(g, fa, fb, count, da, db, true);
+    return BT_OK;
+}
+
+// The correspondence sets given with a new frame f.  From host memory they
+// go up together: the points are packed into pinned staging and copied in
+// one transfer into one block owned by f (freed with f; the sets only point
+// into it).  Device-resident sets are copied one by one.
+int add_frame_matches(bt_graph* g, Frame& f, const bt_matches* matches, int n, int mem_kind)
+{
+    if (n <= 0) return BT_OK;
+    if (mem_kind != BT_HOST) {
+        for (int k = 0; k < n; ++k) {
+            int st = put_matches(g, f.id, matches[k].other_frame, matches[k].count, matches[k].pts_self,
+                                 matches[k].pts_other, mem_kind);
+            if (st != BT_OK) return st;
+        }
+        return BT_OK;
+    }
+    for (int k = 0; k < n; ++k)
+        if (matches[k].other_frame == f.id) return fail(BT_ERR_INVALID, "matches: a frame cannot match itself");
+    size_t total = 0;
+    for (int k = 0; k < n; ++k) total += 2 * sizeof(float) * 3 * (size_t)matches[k].count;
+    char* blk = nullptr;
+    if (total > 0) {
+        BT_CUDA(g->pin_match.acquire(total), "cudaHostAlloc(match staging)");
+        size_t off = 0;
+        for (int k = 0; k < n; ++k) {
+            const size_t b = sizeof(float) * 3 * (size_t)matches[k].count;
+            if (b == 0) continue;
+            std::memcpy(g->pin_match.at<char>(off), matches[k].pts_self, b);
+            std::memcpy(g->pin_match.at<char>(off + b), matches[k].pts_other, b);
+            off += 2 * b;
+        }
+        void* p = nullptr;
+        BT_CUDA(g->pool.get(total, &p), "alloc(matches)");
+        f.mblock = p;
+        f.mblock_bytes = total;
+        BT_CUDA(cudaMemcpyAsync(p, g->pin_match.p, total, cudaMemcpyHostToDevice, g->stream), "upload matches");
+        BT_CUDA(g->pin_match.mark(g->stream), "record match upload");
+        blk = static_cast<char*>(p);
+    }
+    size_t off = 0;
+    for (int k = 0; k < n; ++k) {
+        const int c = matches[k].count;
+        const size_t b = sizeof(float) * 3 * (size_t)c;
+        float* self = c > 0 ? reinterpret_cast<float*>(blk + off) : nullptr;
+        float* other = c > 0 ? reinterpret_cast<float*>(blk + off + b) : nullptr;
+        off += 2 * b;
+        const int fo = matches[k].other_frame;
+        if (fo < f.id) store_matches(g, fo, f.id, c, other, self, false);
+        else store_matches(g, f.id, fo, c, self, other, false);
+    }
+    return BT_OK;
+}
+
+// Stores (or, for count 0, removes) the set of the pair fa < fb whose
+// points are already on the device.
+void store_matches(bt_graph* g, int fa, int fb, int count, float* pa, float* pb, bool owned)
+{
     MatchSet ms;
     ms.fa = fa;
     ms.fb = fb;
     ms.count = count;
-    int st = upload_points(g, pa, count, mem_kind, &ms.pa);
-    if (st != BT_OK) return st;
-    st = upload_points(g, pb, count, mem_kind, &ms.pb);
-    if (st != BT_OK) {
-        g->pool.put(ms.pa, sizeof(float) * 3 * (size_t)count);
-        return st;
-    }
+    ms.pa = pa;
+    ms.pb = pb;
+    ms.owned = owned;
     auto key = std::make_pair(fa, fb);
     auto it = g->matches.find(key);
     if (it != g->matches.end()) {
@@ -124,7 +190,6 @@ int put_matches(bt_graph* g, int fa, int fb, int count, const float* pa, const f
         g->partners[fb].push_back(fa);
     }
     g->topo_dirty = true;
-    return BT_OK;
 }
 
 // Rebuilds the node / tile / edge tables of the active set and sizes the
@@ -537,16 +602,13 @@ int bt_add_frame(bt_graph* g, const float* depth, const float* normals, const ui
     std::memcpy(f.pose, pose_init, sizeof(double) * 16);
     g->frames[f.id] = f;
     g->next_id++;
-    for (int k = 0; k < n_matches; ++k) {
-        int st = put_matches(g, f.id, matches[k].other_frame, matches[k].count, matches[k].pts_self,
-                             matches[k].pts_other, mem_kind);
-        if (st != BT_OK) {
-            std::string msg = last_error();
-            bt_remove_frame(g, f.id);
-            g->next_id--;
-            last_error() = msg;
-            return st;
-        }
+    int st = add_frame_matches(g, g->frames[f.id], matches, n_matches, mem_kind);
+    if (st != BT_OK) {
+        std::string msg = last_error();
+        bt_remove_frame(g, f.id);
+        g->next_id--;
+        last_error() = msg;
+        return st;
     }
     g->active.push_back(f.id);
     g->topo_dirty = true;
@@ -578,6 +640,7 @@ int bt_remove_frame(bt_graph* g, int32_t frame_id)
         g->pool.put(f.dev_m2, 2 * sizeof(int));
         g->free_slots.push_back(f.slot);
     }
+    if (f.mblock) g->pool.put(f.mblock, f.mblock_bytes);
     g->frames.erase(it);
     auto pit = g->partners.find(frame_id);
     if (pit != g->partners.end()) {

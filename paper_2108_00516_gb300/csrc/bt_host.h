@@ -145,15 +145,23 @@ struct StateLayout {
     size_t readback_bytes(int iters) const { return costs + sizeof(double) * 4 * (size_t)(iters + 1); }
 };
 
+// Idle device blocks shared by every graph of the process (bt_memory.cu):
+// an idle block of size class `cls` on the current device, or a new one;
+// and the hand-over of an idle block (its stream synchronised) to the cache.
+cudaError_t cache_take(size_t cls, void** out);
+void cache_give(int device, size_t cls, void* p);
+
 // Device blocks recycled within one graph: a freed buffer goes back to the
 // free list of its size class and is handed out again in stream order (all
 // of a graph's work runs on its stream, and batch and warm-start calls
 // synchronise before returning), so a steady turnover of frames and
 // correspondence sets neither allocates nor frees -- cudaFree would also
-// synchronise the whole device.
+// synchronise the whole device.  New blocks come from the process-wide
+// cache, and a destroyed graph's blocks go back to it.
 struct DevPool {
     std::multimap<size_t, void*> free_blocks;
-    std::vector<void*> owned;
+    std::vector<std::pair<size_t, void*>> owned;   // (size class, block)
+    int device = -1;
     static size_t size_class(size_t bytes)
     {
         const size_t q = bytes <= 65536 ? 256 : 65536;
@@ -168,8 +176,12 @@ struct DevPool {
             free_blocks.erase(it);
             return cudaSuccess;
         }
-        cudaError_t e = cudaMalloc(out, c);
-        if (e == cudaSuccess) owned.push_back(*out);
+        if (device < 0) {
+            cudaError_t e = cudaGetDevice(&device);
+            if (e != cudaSuccess) return e;
+        }
+        cudaError_t e = cache_take(c, out);
+        if (e == cudaSuccess) owned.emplace_back(c, *out);
         else *out = nullptr;
         return e;
     }
@@ -177,9 +189,11 @@ struct DevPool {
     {
         if (p) free_blocks.emplace(size_class(bytes), p);
     }
+    // Every block back to the process-wide cache; the caller has synchronised
+    // the stream that used them.
     void release()
     {
-        for (void* p : owned) cudaFree(p);
+        for (auto& cb : owned) cache_give(device, cb.first, cb.second);
         owned.clear();
         free_blocks.clear();
     }
@@ -199,6 +213,8 @@ struct Frame {
     int* dev_m2 = nullptr;   // device (M, zref bits) written by the prep kernels
     int slot = -1;           // pinned host slot receiving dev_m2
     bool pending = false;    // M / zref not read back yet
+    void* mblock = nullptr;  // points of the correspondence sets given with the frame
+    size_t mblock_bytes = 0;
 };
 
 struct MatchSet {
@@ -206,6 +222,7 @@ struct MatchSet {
     int count = 0;
     float* pa = nullptr;
     float* pb = nullptr;
+    bool owned = true;      // pa, pb are pool blocks of their own; else inside a frame's mblock
 };
 
 
@@ -241,6 +258,7 @@ struct bt_graph {
     // the solve state block (StateLayout) likewise, and the work buffers
     bthost::DevBuf d_tab, d_state, d_xf, d_xinv, d_dpart, d_spart, d_upairblk;
     bthost::PinBuf pin_tab, pin_state;
+    bthost::PinBuf pin_match;           // staging of the correspondence sets given to bt_add_frame
     bt::SolveArgs args{};
     int64_t pixels_per_pass = 0;
     int64_t sparse_per_pass = 0;
@@ -262,6 +280,7 @@ struct bt_graph {
         if (pin_m2) cudaFreeHost(pin_m2);
         pin_tab.release();
         pin_state.release();
+        pin_match.release();
         for (cudaEvent_t e : events) cudaEventDestroy(e);
         for (bthost::DevBuf* b : {&up_depth, &up_normals, &up_mask, &prep_blk, &d_tab, &d_state, &d_xf, &d_xinv,
                                   &d_dpart, &d_spart, &d_upairblk})
