@@ -195,9 +195,10 @@ def hbm_peak():
         return 6800.0, "fallback"
 
 
-def ncu_traffic_per_pixel_pair():
-    """DRAM bytes per dense pixel-pair of the residual kernel from the committed
-    ncu summary, if it was taken from the current kernel source."""
+def ncu_summary():
+    """DRAM bytes per dense pixel-pair and L2 hit rate of the residual kernel
+    from the committed ncu summary, if it was taken from the current kernel
+    source (else None for both)."""
     summ = ROOT / "profiles" / "residual_kernel_paper_sequence.md"
     src = ROOT / "paper_2108_00516_gb300" / "csrc" / "bt_residual.cu"
     try:
@@ -205,11 +206,12 @@ def ncu_traffic_per_pixel_pair():
         sha = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
         m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
         m_b = re.search(r"dram_bytes_per_pixel_pair:\s*([0-9.eE+-]+)", text)
+        m_l2 = re.search(r"\| lts__t_sector_hit_rate \| ([0-9.]+) %", text)
         if m_sha and m_b and m_sha.group(1) == sha:
-            return float(m_b.group(1))
+            return float(m_b.group(1)), (float(m_l2.group(1)) / 100 if m_l2 else None)
     except Exception:
         pass
-    return None
+    return None, None
 
 
 def sample_order(n: int):
@@ -218,27 +220,67 @@ def sample_order(n: int):
     return [(k * stride) % n for k in range(n)]
 
 
-def cpu_baseline(seq, graphs, inits, seconds: float, iters: int):
-    """The FP64 oracle, as it stands, on a bounded sample of the same graphs."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in Path("/proc/cpuinfo").read_text().splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline(seq, graphs, inits, seconds: float, iters: int, tiny=None):
+    """The FP64 oracle, as it stands, on a bounded sample of the same graphs
+    (all host threads over ordered pairs, then one thread on a shorter
+    sample), and on the whole tiny workload (100 graphs, 7 iterations)."""
     import oracle as O
     n_threads = os.cpu_count() or 1
     order = sample_order(len(graphs))
-    done, t0 = 0, time.perf_counter()
-    k = 0
-    while True:
-        t = order[k % len(graphs)]
-        g = graph_view(seq, graphs[t], inits[t])
-        r = O.solve(g, iters, n_threads=n_threads)
-        if r["status"] != 0:
-            raise RuntimeError("oracle solve failed")
-        done += 1
-        k += 1
-        el = time.perf_counter() - t0
-        if el >= seconds:
-            break
-    return {"value": done / el, "unit": "solves/s", "cores": n_threads, "kind": "oracle",
-            "sample": f"{done} graphs spread over the sequence ({iters} GN iterations each, "
-                      f"{n_threads} threads over ordered pairs), {el:.1f} s", "seconds": el}
+
+    def run(limit, threads):
+        done, t0, k = 0, time.perf_counter(), 0
+        while True:
+            t = order[k % len(graphs)]
+            g = graph_view(seq, graphs[t], inits[t])
+            r = O.solve(g, iters, n_threads=threads)
+            if r["status"] != 0:
+                raise RuntimeError("oracle solve failed")
+            done += 1
+            k += 1
+            el = time.perf_counter() - t0
+            if el >= limit:
+                return done, el
+
+    done, el = run(seconds, n_threads)
+    done1, el1 = run(max(1.0, seconds / 4), 1)
+    out = {"value": done / el, "unit": "solves/s", "cores": n_threads, "kind": "oracle",
+           "sample": f"{done} graphs spread over the sequence ({iters} GN iterations each, "
+                     f"{n_threads} threads over ordered pairs), {el:.1f} s", "seconds": el,
+           "cpu_model": cpu_model(),
+           "single_thread": {"value": done1 / el1, "unit": "solves/s",
+                             "sample": f"{done1} graphs of the same order, 1 thread, {el1:.1f} s"}}
+    if tiny:
+        res = {}
+        for name, threads in (("threads", n_threads), ("single_thread", 1)):
+            t0 = time.perf_counter()
+            for g in tiny:
+                if O.solve(g, 7, n_threads=threads)["status"] != 0:
+                    raise RuntimeError("oracle solve failed")
+            res[name] = round(len(tiny) / (time.perf_counter() - t0), 3)
+        out["tiny_workload"] = {"graphs": len(tiny), "iters": 7, "unit": "solves/s",
+                                "value": res["threads"], "single_thread": res["single_thread"],
+                                "workload": "N=4, 160x120, 200 matches per pair (20% outliers)"}
+    return out
 
 
 # --------------------------------------------------------------------------- GPU arm
@@ -423,6 +465,10 @@ def run_ours(args):
     rank, world, local = dist_env()
     # all synthetic data is made before CUDA is touched (the generators fork)
     seq, graphs, pools, pairs, inits = build_workload(2000 + rank, args.frames, args.workers)
+    tiny = None
+    if rank == 0 and world == 1 and args.cpu_seconds > 0:
+        import synthgen as S
+        tiny = [S.tiny_graph(k) for k in range(100)]
     graphs_b = []
     if args.batch_graphs > 0:
         import synthgen as S
@@ -508,10 +554,11 @@ def run_ours(args):
                         BYTES_PER_SPARSE_PAIR * prof["sparse_pairs"]) / n_l
     achieved = bytes_per_launch / avg_s / 1e9
     peak, peak_kind = hbm_peak()
-    tpp = ncu_traffic_per_pixel_pair()
+    tpp, l2_hit = ncu_summary()
     traffic = tpp * prof["dense_pixel_pairs"] / n_l if tpp is not None else None
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
+                "l2_hit_rate_ncu": l2_hit,
                 "kernel": "residual_kernel<full> (dense tiles + sparse sets)",
                 "avg_launch_us": round(avg_s * 1e6, 2), "algorithmic_bytes_per_launch": round(bytes_per_launch),
                 "timed_launches": f"every {PROFILE_EVERY}th solve ({prof['timed_residual_launches']} of "
@@ -532,7 +579,7 @@ def run_ours(args):
 
     base = None
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
-        base = cpu_baseline(seq, graphs, inits, args.cpu_seconds, it)
+        base = cpu_baseline(seq, graphs, inits, args.cpu_seconds, it, tiny)
         base["value_pixel_pairs_per_s"] = None
 
     if rank == 0:
