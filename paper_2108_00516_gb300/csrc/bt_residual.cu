@@ -342,6 +342,12 @@ __device__ __forceinline__ void accumulate_pair(float (&acc)[kDenseVals], const 
     acc[28] += 1.f;
 }
 
+// Pixels per thread whose target gathers are issued together, and resident
+// threads per SM the residual kernels are compiled for, by storage precision
+// (FP32: six 128-thread CTAs, at most 80 registers a thread; 16-bit: five).
+constexpr int residual_batch(int P) { return P == 0 ? 2 : 4; }
+constexpr int residual_threads_per_sm(int P) { return P == 0 ? 768 : 640; }
+
 // One tile of source pixels of node i against every other node j.  Per target
 // each thread takes its kB pixels as one batch that goes through three
 // phases -- projection and bounds, the four target gathers (all
@@ -354,9 +360,14 @@ __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
     constexpr int kW = kT / 32;
     constexpr int kTile = kT * kB;
     constexpr int kResThreads = kT;
-    constexpr int kResBatch = kB < 4 ? kB : 4;
+    // FP32 maps: two pixels per batch, their gathers in flight together; the
+    // registers this leaves free buy a sixth resident 128-thread CTA per SM
+    // (768 threads), which hides the gathers' latency better than four pixels
+    // per batch at five CTAs.  16-bit maps (more registers for the widening)
+    // keep four pixels per batch at five CTAs.
+    constexpr int kResBatch = kB < residual_batch(P) ? kB : residual_batch(P);
     constexpr int kResBatches = kB / kResBatch;
-    static_assert(kResBatch * kResBatches == kB, "pixels per thread: 1, 2, 3 or a multiple of 4");
+    static_assert(kResBatch * kResBatches == kB, "pixels per thread: 1 or even");
     const int N = a.N;
     const int i = a.tile_node[tile];
     const NodeDev Ni = a.nodes[i];
@@ -571,8 +582,9 @@ __device__ void sparse_edge(const SolveArgs& a, int e)
     }
 }
 
+
 template <bool kFull, int kT, int kB, int P>
-__global__ void __launch_bounds__(kT, 640 / kT) residual_kernel(SolveArgs a)
+__global__ void __launch_bounds__(kT, residual_threads_per_sm(P) / kT) residual_kernel(SolveArgs a)
 {
     pdl_wait_and_release();
     extern __shared__ __align__(16) unsigned char dsm[];
@@ -584,7 +596,7 @@ __global__ void __launch_bounds__(kT, 640 / kT) residual_kernel(SolveArgs a)
 
 // Batched residual pass: CTA b takes work item work[b] = (graph, item).
 template <bool kFull, int kT, int kB, int P>
-__global__ void __launch_bounds__(kT, 640 / kT) batch_residual_kernel(const SolveArgs* __restrict__ args,
+__global__ void __launch_bounds__(kT, residual_threads_per_sm(P) / kT) batch_residual_kernel(const SolveArgs* __restrict__ args,
                                                                        const int2* __restrict__ work)
 {
     pdl_wait_and_release();
