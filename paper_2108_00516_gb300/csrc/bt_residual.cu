@@ -364,7 +364,8 @@ __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
     // registers this leaves free buy a sixth resident 128-thread CTA per SM
     // (768 threads), which hides the gathers' latency better than four pixels
     // per batch at five CTAs.  16-bit maps (more registers for the widening)
-    // keep four pixels per batch at five CTAs.
+    // keep four pixels per batch at five CTAs.  The batch loop is unrolled,
+    // so a batch's gathers may be issued while the previous batch computes.
     constexpr int kResBatch = kB < residual_batch(P) ? kB : residual_batch(P);
     constexpr int kResBatches = kB / kResBatch;
     static_assert(kResBatch * kResBatches == kB, "pixels per thread: 1 or even");
@@ -404,7 +405,7 @@ __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
         float acc[kDenseVals];
 #pragma unroll
         for (int k = 0; k < kDenseVals; ++k) acc[k] = 0.f;
-#pragma unroll 1
+#pragma unroll
         for (int bb = 0; bb < kResBatches; ++bb) {
             // phase 1: T_j T_i^-1 p, pi(.), nearest pixel, bounds
             float qx[kResBatch], qy[kResBatch], qz[kResBatch];
