@@ -246,9 +246,9 @@ cudaError_t launch_prep(const float* depth, const float* normals, const uint8_t*
 
 struct PairConst {
     float m[12];                         // camera i -> camera j (single)
-    float fx, fy, cx, cy, ifx, ify, Wf, Hf;
+    float fx, fy, cx, cy, ifx, ify;
     float zref;                          // target frame's reference depth (16-bit maps)
-    int W;
+    int W, H;
     const void* tgt;
 };
 
@@ -392,7 +392,7 @@ __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
 #pragma unroll
         for (int k = 0; k < 12; ++k) c.m[k] = a.xf[(i * N + j) * 12 + k];
         c.fx = Nj.fx; c.fy = Nj.fy; c.cx = Nj.cx; c.cy = Nj.cy; c.ifx = Nj.ifx; c.ify = Nj.ify;
-        c.Wf = (float)Nj.W; c.Hf = (float)Nj.H; c.W = Nj.W; c.tgt = Nj.tgt; c.zref = Nj.zref;
+        c.W = Nj.W; c.H = Nj.H; c.tgt = Nj.tgt; c.zref = Nj.zref;
     }
     __syncthreads();
     const float dmax2 = a.dmax2, cmin = a.cmin, hub = a.huber_dense;
@@ -421,8 +421,12 @@ __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
                 const float rz = __frcp_rn(qz[k]);
                 const float uh = __fadd_rn(__fmaf_rn(__fmul_rn(c.fx, qx[k]), rz, c.cx), 0.5f);
                 const float vh = __fadd_rn(__fmaf_rn(__fmul_rn(c.fy, qy[k]), rz, c.cy), 0.5f);
-                ok = ok && uh >= 0.f && uh < c.Wf && vh >= 0.f && vh < c.Hf;
-                pix[k] = ok ? (((int)floorf(vh)) << 16) | (int)floorf(uh) : -1;
+                // 0 <= uh < W and 0 <= vh < H, tested on floor(uh), floor(vh)
+                // as unsigned integers (the same decision for every float,
+                // NaN and infinities included: they convert out of range)
+                const int iu = __float2int_rd(uh), iv = __float2int_rd(vh);
+                ok = ok && (unsigned)iu < (unsigned)c.W && (unsigned)iv < (unsigned)c.H;
+                pix[k] = ok ? (iv << 16) | iu : -1;
             }
             // phase 2: the gathers of the batch in flight together
             float4 t[kResBatch];
