@@ -13,6 +13,7 @@
 // Perturbations are right perturbations, T_i <- T_i exp(d_i) (see
 // bt_residual.cu for why every iterate equals the left-perturbation one).
 #include "bt_internal.h"
+#include "bt_ldlt.h"
 
 #include <cuda_runtime.h>
 #include <math.h>
@@ -372,28 +373,10 @@ __device__ double se3_exp_entry(const double* xi, int r, int c)
     return t;
 }
 
-// 1/d for a positive FP64 pivot: the hardware approximation (rcp.approx.f64,
-// relative error below 1e-6 on GB300) refined by one Newton step
-// r <- r + r (1 - d r), which leaves a relative error below 1e-12 (measured
-// on 1M pivots spanning 1e-6 .. 1e6) -- ample for a factorisation whose
-// results are compared at 1e-5, and two dependent FP64 operations shorter
-// than the correctly rounded reciprocal on the column chain.
-__device__ __forceinline__ double rcp_fp64(double d)
-{
-    double r;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
-    const double e = fma(-d, r, 1.0);
-    return fma(r, e, r);
-}
-
-// Last CTA: energies, then (full) assembly of H and g over the free nodes and
-// the FP64 solve of H dx = -g by the square-root-free Cholesky factorisation
-// H = L D L^T (right-looking, two barriers per column, the forward
-// substitution L z = -g carried along), D w = z, L^T dx = w, and finally
-// T <- T exp(dx).  On GB300 a dependent FP64 operation costs ~64 cycles, so
-// the loop is arranged for short dependency chains: each pivot reciprocal is
-// formed by the thread that finishes that diagonal entry, and the column is
-// scaled while a copy of its unscaled values feeds the trailing update.
+// Last CTA: energies, then (full) assembly of H and g over the free nodes,
+// the FP64 solve of H dx = -g (square-root-free Cholesky with a one-column
+// look-ahead, bt_ldlt.h; or PCG, the paper's inner solver), and finally
+// T <- T exp(dx).
 template <bool kFull>
 __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
 {
@@ -595,158 +578,17 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
         __syncthreads();
         t2 = t3 = clock64();
     } else {
-    // LDL^T with a one-column look-ahead, one barrier per column.  At step k
-    // warp 0 prepares column k+1 -- its update by column k, the pivot
-    // D_{k+1} and reciprocal, and the scaled l_{i,k+1} -- while warps
-    // {1,2,3,5,6,7} (no FP64 pipe shared with warp 0) apply column k to the
-    // trailing triangle of rows and columns >= k+2 and carry the forward
-    // substitution.  The scaled column is double-buffered; L is stored
-    // transposed in the upper triangle, L_ik at (k, i).  A failed pivot
-    // (not positive) sets s_fail and a zero reciprocal; the loop still runs
-    // to the end (same bounds, finite or discarded values) and the flag is
-    // read once afterwards, which keeps a shared-memory read and a branch
-    // off every column of the chain.
-    int* tab = reinterpret_cast<int*>(colb + 2 * n);
-    for (int ip = tid; ip < n; ip += nt)
-        for (int jp = 0; jp <= ip; ++jp) tab[ip * (ip + 1) / 2 + jp] = (ip << 16) | jp;
-    if (warp == 0) {
-        double r = 0.0;
-        if (lane == 0) {
-            const double d = H[0];
-            if (!(d > 0.0)) s_fail = 1; else r = rcp_fp64(d);
-            rD[0] = r;
-        }
-        r = __shfl_sync(0xffffffffu, r, 0);
-        for (int i = 1 + lane; i < n; i += 32) {
-            const double l = H[i * ld] * r;
-            colb[i] = l;
-            H[i] = l;
-        }
-    }
-    __syncthreads();
-    const bool bulk = warp != 0 && warp != 4 && warp < 8;
-    const int nbulk = (nt / 32 >= 8 ? 6 : 0) * 32;
-    const int bt = bulk ? (warp < 4 ? warp - 1 : warp - 2) * 32 + lane : -1;
-    for (int k = 0; k < n - 1; ++k) {
-        const double* ck = colb + (k & 1) * n;        // l_{i,k}
-        double* cn = colb + ((k + 1) & 1) * n;        // l_{i,k+1}, written now
-        if (warp == 0) {
-            // column p = k + 1, rows i = p .. n-1 in slots of 32: u_i = H_ip -
-            // l_ik H_pk (the pivot is u_p), then every lane forms 1 / u_p
-            // itself (no divergent branch, no second broadcast) and scales
-            const int p = k + 1;
-            const double hpk = H[p * ld + k];         // unscaled H_{k+1,k}
-            const int nq = (n - p + 31) >> 5;         // active slots (warp-uniform)
-            constexpr int kRows = (6 * (kMaxNodes - 1) + 31) / 32;
-            double hv[kRows], cv[kRows], u[kRows];
-#pragma unroll
-            for (int q = 0; q < kRows; ++q) {
-                if (q >= nq) break;
-                const int i = p + lane + 32 * q;
-                hv[q] = i < n ? H[i * ld + p] : 0.0;
-                cv[q] = i < n ? ck[i] : 0.0;
-            }
-#pragma unroll
-            for (int q = 0; q < kRows; ++q) {
-                if (q >= nq) break;
-                u[q] = hv[q] - cv[q] * hpk;
-            }
-            const double h = __shfl_sync(0xffffffffu, u[0], 0);
-            // h > 0 as an integer test on the bits (positive, not NaN): no
-            // FP64 compare on the chain
-            const long long hb = __double_as_longlong(h);
-            const bool ok = hb > 0ll && hb <= 0x7ff0000000000000ll;
-            const double rp = ok ? rcp_fp64(h) : 0.0;
-            if (lane == 0) {
-                if (!ok) s_fail = 1;
-                H[p * ld + p] = h;
-                rD[p] = rp;
-            }
-#pragma unroll
-            for (int q = 0; q < kRows; ++q) {
-                if (q >= nq) break;
-                const int i = p + lane + 32 * q;
-                if (i > p && i < n) {
-                    const double l = u[q] * rp;
-                    H[i * ld + p] = u[q];
-                    cn[i] = l;
-                    H[p * ld + i] = l;
-                }
-            }
-        } else if (bulk) {
-            const int m1 = n - k - 2, tri = m1 * (m1 + 1) / 2;
-            const double zk = y[k];
-            for (int i = k + 1 + bt; i < n; i += nbulk) y[i] -= ck[i] * zk;
-            int t = bt;
-            for (; t + nbulk < tri; t += 2 * nbulk) {
-                const int e0 = tab[t], e1 = tab[t + nbulk];
-                const int i0 = k + 2 + (e0 >> 16), j0 = k + 2 + (e0 & 0xffff);
-                const int i1 = k + 2 + (e1 >> 16), j1 = k + 2 + (e1 & 0xffff);
-                const double a0 = H[i0 * ld + j0], a1 = H[i1 * ld + j1];
-                const double l0 = ck[i0], l1 = ck[i1];
-                const double b0 = H[j0 * ld + k], b1 = H[j1 * ld + k];
-                H[i0 * ld + j0] = a0 - l0 * b0;
-                H[i1 * ld + j1] = a1 - l1 * b1;
-            }
-            for (; t < tri; t += nbulk) {
-                const int e = tab[t];
-                const int i = k + 2 + (e >> 16), j = k + 2 + (e & 0xffff);
-                H[i * ld + j] -= ck[i] * H[j * ld + k];
-            }
-        }
-        __syncthreads();
-    }
+    // LDL^T with a one-column look-ahead, D w = z, blocked L^T dx = w
+    // (bt_ldlt.h); the forward substitution of -g is carried along
+    LdltScratch sc;
+    sc.rD = rD;
+    sc.colb = colb;
+    sc.tab = reinterpret_cast<int*>(colb + 2 * n);
+    sc.part = reinterpret_cast<double*>(node_of + kMaxNodes);
+    ldlt_solve(H, ld, n, y, sc, &s_fail, t2);
     if (s_fail) {
         if (tid == 0) a.ctrl->status = -4;
         return;
-    }
-    for (int i = tid; i < n; i += nt) y[i] *= rD[i];   // D w = z
-    __syncthreads();
-    t2 = clock64();
-    // L^T dx = w, unit diagonal (L_ki is stored at (i, k)), in blocks of 32
-    // unknowns from the last block up.  Warp 0 runs the chain of one block
-    // with the block's values in registers, lane l holding row r0 + l: x_k
-    // is broadcast from its lane with a shuffle, so each step is one shuffle
-    // and one FP64 FMA deep, and a step issues one FP64 instruction whatever
-    // the size of the system.  The rows above the block then take the
-    // block's unknowns as dot products, split into column chunks over
-    // several warps (partial sums in shared memory, added per row).
-    {
-        double* part = reinterpret_cast<double*>(node_of + kMaxNodes);   // [chunks][r0], <= 256
-        for (int r0 = ((n - 1) >> 5) << 5; r0 >= 0; r0 -= 32) {
-            const int r1 = min(n, r0 + 32);
-            if (warp == 0) {
-                const int i = r0 + lane;
-                double wv = i < r1 ? y[i] : 0.0;
-                for (int k = r1 - 1; k > r0; --k) {
-                    const double hk = i < k ? H[i * ld + k] : 0.0;
-                    const double xk = __shfl_sync(0xffffffffu, wv, k - r0);
-                    if (i < k) wv = fma(-hk, xk, wv);
-                }
-                if (i < r1) y[i] = wv;
-            }
-            __syncthreads();
-            if (r0 == 0) break;
-            const int chunks = min(4, 256 / r0);      // r0 <= 128: at least 2
-            if (tid < chunks * r0) {
-                const int i = tid % r0, c = tid / r0;
-                double s0 = 0.0, s1 = 0.0;
-                int k = r0 + c;
-                for (; k + chunks < r1; k += 2 * chunks) {
-                    s0 = fma(H[i * ld + k], y[k], s0);
-                    s1 = fma(H[i * ld + k + chunks], y[k + chunks], s1);
-                }
-                if (k < r1) s0 = fma(H[i * ld + k], y[k], s0);
-                part[c * r0 + i] = s0 + s1;
-            }
-            __syncthreads();
-            for (int i = tid; i < r0; i += nt) {
-                double s = part[i];
-                for (int c = 1; c < chunks; ++c) s += part[c * r0 + i];
-                y[i] -= s;
-            }
-            __syncthreads();
-        }
     }
     __syncthreads();
     t3 = clock64();

@@ -13,6 +13,7 @@
 // Backward pass: only the rows that hold a channel's maximum receive
 // gradient, so layer 1 and layer 2 gradients are outer products over at most
 // 256 rows, recomputed from the inputs with the forward pass's arithmetic.
+#include "bt_ldlt.h"
 #include "bt_ws.h"
 
 #include <cuda_bf16.h>
@@ -28,6 +29,7 @@ namespace {
 constexpr int kFwdThreads = 256;
 constexpr int kChunk = 64;      // points per layer-2 tile
 constexpr int kLd = 136;        // padded row length (BF16) of W2 and the h1 tile in shared memory
+constexpr int kLd3 = 258;       // padded row length (BF16) of the layer-3 weights (odd word stride)
 
 __device__ __forceinline__ float bf2f(__nv_bfloat16 b) { return __bfloat162float(b); }
 
@@ -47,6 +49,28 @@ __device__ __forceinline__ void point_features(const float* __restrict__ p, cons
     x[3] = __fmul_rn(__fsub_rn(qx, ux), kInvSR);
     x[4] = __fmul_rn(__fsub_rn(qy, uy), kInvSR);
     x[5] = __fmul_rn(__fsub_rn(qz, uz), kInvSR);
+}
+
+// Offset (floats) of layer-1 unit u's packed weights in the forward kernel's
+// shared memory: 8 floats a unit, each block of 32 units skewed by 16 bytes,
+// so that the four threads of a row, which take the blocks u / 32 = 0..3,
+// read four different bank groups.
+__device__ __forceinline__ int w1_at(int u) { return u * 8 + (u >> 5) * 4; }
+
+// z1_unit with the unit's weights and bias packed as w[0..5], w[6] = bias
+// (two 16-byte shared-memory loads); the same operations in the same order.
+__device__ __forceinline__ float z1_unit8(const float* w8, const float x[6])
+{
+    const float4 a = *reinterpret_cast<const float4*>(w8);
+    const float4 b = *reinterpret_cast<const float4*>(w8 + 4);
+    float z = b.z;
+    z = __fmaf_rn(a.x, x[0], z);
+    z = __fmaf_rn(a.y, x[1], z);
+    z = __fmaf_rn(a.z, x[2], z);
+    z = __fmaf_rn(a.w, x[3], z);
+    z = __fmaf_rn(b.x, x[4], z);
+    z = __fmaf_rn(b.y, x[5], z);
+    return z;
 }
 
 // Layer-1 pre-activation of one unit (weights w[6], bias b), fixed order.
@@ -79,10 +103,9 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
 struct Fwd {
     static constexpr size_t W2 = 0;                                          // bf16 [256][kLd]
     static constexpr size_t H1 = W2 + 2 * (size_t)kH2 * kLd;                 // bf16 [64][kLd]
-    static constexpr size_t W3 = H1 + 2 * (size_t)kChunk * kLd;              // bf16 [128][256]
-    static constexpr size_t W1 = W3 + 2 * (size_t)kH3 * kH2;                 // float [128][6]
-    static constexpr size_t B1 = W1 + 4 * (size_t)kH1 * kIn;                 // float [128]
-    static constexpr size_t B2 = B1 + 4 * (size_t)kH1;                       // float [256]
+    static constexpr size_t W3 = H1 + 2 * (size_t)kChunk * kLd;              // bf16 [128][kLd3]
+    static constexpr size_t W1 = W3 + ((2 * (size_t)kH3 * kLd3 + 15) / 16) * 16;   // float [128][8] + skew (w1_at)
+    static constexpr size_t B2 = W1 + 4 * ((size_t)kH1 * 8 + 16);            // float [256]
     static constexpr size_t B3 = B2 + 4 * (size_t)kH2;                       // float [128]
     static constexpr size_t W4 = B3 + 4 * (size_t)kH3;                       // float [6][128]
     static constexpr size_t B4 = W4 + 4 * (size_t)kOut * kH3;                // float [8]
@@ -96,6 +119,7 @@ struct Fwd {
     static constexpr size_t Total = MC + 64;
 };
 static_assert(Fwd::H1 % 16 == 0 && Fwd::W3 % 16 == 0 && Fwd::W1 % 16 == 0, "alignment");
+static_assert(kFwdThreads == 2 * kH3 && kFwdThreads == kH2, "head mapping: two threads per layer-3 unit");
 
 template <bool kTrain>
 __global__ void __launch_bounds__(kFwdThreads, 1)
@@ -105,9 +129,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     extern __shared__ __align__(16) unsigned char sm[];
     __nv_bfloat16* sW2 = reinterpret_cast<__nv_bfloat16*>(sm + Fwd::W2);
     __nv_bfloat16* sH1 = reinterpret_cast<__nv_bfloat16*>(sm + Fwd::H1);
-    __nv_bfloat16* sW3 = reinterpret_cast<__nv_bfloat16*>(sm + Fwd::W3);
-    float* sW1 = reinterpret_cast<float*>(sm + Fwd::W1);
-    float* sB1 = reinterpret_cast<float*>(sm + Fwd::B1);
+    __nv_bfloat16* sW3 = reinterpret_cast<__nv_bfloat16*>(sm + Fwd::W3);    // layer 3: [unit][kLd3]
+    float* sW1 = reinterpret_cast<float*>(sm + Fwd::W1);     // unit u at w1_at(u): weights [0..5], bias [6]
     float* sB2 = reinterpret_cast<float*>(sm + Fwd::B2);
     float* sB3 = reinterpret_cast<float*>(sm + Fwd::B3);
     float* sW4 = reinterpret_cast<float*>(sm + Fwd::W4);
@@ -127,16 +150,27 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         *reinterpret_cast<uint4*>(sW2 + row * kLd + c8) =
             *reinterpret_cast<const uint4*>(net.wb + bW2 + row * kH1 + c8);
     }
-    for (int k = tid; k < kH3 * kH2 / 8; k += kFwdThreads)
-        reinterpret_cast<uint4*>(sW3)[k] = reinterpret_cast<const uint4*>(net.wb + bW3)[k];
-    for (int k = tid; k < kH1 * kIn; k += kFwdThreads) sW1[k] = bf2f(net.wb[bW1 + k]);
+    for (int k = tid; k < kH3 * kH2 / 2; k += kFwdThreads) {   // bf16 pairs, rows padded to kLd3
+        const int o = k / (kH2 / 2), c2 = (k % (kH2 / 2)) * 2;
+        *reinterpret_cast<uint32_t*>(sW3 + o * kLd3 + c2) =
+            *reinterpret_cast<const uint32_t*>(net.wb + bW3 + o * kH2 + c2);
+    }
+    for (int k = tid; k < kH1 * 8; k += kFwdThreads) {
+        const int u = k >> 3, e = k & 7;
+        sW1[w1_at(u) + e] = e < kIn ? bf2f(net.wb[bW1 + u * kIn + e]) : (e == kIn ? net.master[ob1 + u] : 0.f);
+    }
     for (int k = tid; k < kOut * kH3; k += kFwdThreads) sW4[k] = bf2f(net.wb[bW4 + k]);
-    for (int k = tid; k < kH1; k += kFwdThreads) sB1[k] = net.master[ob1 + k];
     for (int k = tid; k < kH2; k += kFwdThreads) sB2[k] = net.master[ob2 + k];
     for (int k = tid; k < kH3; k += kFwdThreads) sB3[k] = net.master[ob3 + k];
     if (tid < kOut) sB4[tid] = net.master[ob4 + tid];
 
     const int wm = warp & 1, wn = warp >> 1;     // warp tile: rows wm*32 .. +32, columns wn*64 .. +64
+    __syncthreads();
+    float b2[16];                                // layer-2 bias of the thread's 16 columns
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) b2[2 * nt + e] = sB2[wn * 64 + nt * 8 + 2 * (lane & 3) + e];
     for (int s = blockIdx.x; s < n_sets; s += gridDim.x) {
         const int sid = ids ? ids[s] : s;
         const Sample* S = smp + sid;
@@ -166,8 +200,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                     const int u = q4 * 32 + 2 * k;
-                    const float h0 = fmaxf(z1_unit(sW1 + u * 6, sB1[u], x), 0.f);
-                    const float h1 = fmaxf(z1_unit(sW1 + (u + 1) * 6, sB1[u + 1], x), 0.f);
+                    const float h0 = fmaxf(z1_unit8(sW1 + w1_at(u), x), 0.f);
+                    const float h1 = fmaxf(z1_unit8(sW1 + w1_at(u + 1), x), 0.f);
                     __nv_bfloat162 b2 = __floats2bfloat162_rn(h0, h1);
                     packed[k] = *reinterpret_cast<uint32_t*>(&b2);
                 }
@@ -213,8 +247,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                         for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
                             for (int e = 0; e < 2; ++e) {
-                                const int col = wn * 64 + nt * 8 + 2 * (lane & 3) + e;
-                                const float v = fmaxf(acc[mt][nt][2 * h + e] + sB2[col], 0.f);
+                                const float v = fmaxf(acc[mt][nt][2 * h + e] + b2[2 * nt + e], 0.f);
                                 if (v > best[2 * nt + e]) {
                                     best[2 * nt + e] = v;
                                     bestr[2 * nt + e] = row;
@@ -258,19 +291,21 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             sR[tid] = r;
         }
         __syncthreads();
-        {   // head layer 3: two threads per unit, halves of the 256 inputs
-            const int o = tid >> 1, half = tid & 1;
-            const __nv_bfloat16* w = sW3 + o * kH2 + half * 128;
+        {   // head layer 3: unit tid % 128, input half tid / 128; the odd row
+            // stride kLd3 / 2 words puts the 32 units of a warp in 32 banks
+            const int o = tid & (kH3 - 1), half = tid >> 7;
+            const __nv_bfloat16* w = sW3 + o * kLd3 + half * 128;
             const float* g = sG + half * 128;
             float a = 0.f;
 #pragma unroll 8
             for (int k = 0; k < 128; ++k) a = __fmaf_rn(bf2f(w[k]), g[k], a);
-            const float other = __shfl_xor_sync(0xffffffffu, a, 1);
-            const float z = sB3[o] + (half == 0 ? a + other : other + a);
-            if (half == 0) {
-                sZ3[o] = z;
-                sH3[o] = fmaxf(z, 0.f);
-            }
+            sRV[tid] = a;      // the max-pool scratch is free again
+        }
+        __syncthreads();
+        if (tid < kH3) {
+            const float z = sB3[tid] + (sRV[tid] + sRV[kH3 + tid]);
+            sZ3[tid] = z;
+            sH3[tid] = fmaxf(z, 0.f);
         }
         __syncthreads();
         if (warp < kOut) {   // head layer 4: one warp per output
@@ -655,8 +690,13 @@ __global__ void __launch_bounds__(kAvgThreads) average_kernel(const AvgGraph* __
     double* sT = sT0 + 12 * N;               // [N][12]
     double* H = sT + 12 * N;                 // [n][ld]
     double* b = H + (size_t)n * ld;          // [n]
-    int* eof = reinterpret_cast<int*>(b + n);   // [N][N]
+    LdltScratch sc;                          // the solve's scratch (bt_ldlt.h)
+    sc.rD = b + n;                           // [n]
+    sc.colb = sc.rD + n;                     // [2n]
+    sc.part = sc.colb + 2 * n;               // [256]
+    int* eof = reinterpret_cast<int*>(sc.part + 256);   // [N][N]
     int* freenode = eof + N * N;             // [nf]
+    sc.tab = freenode + nf;                  // [n (n + 1) / 2]
     const double Wd[6] = {1.0 / (kSU * kSU), 1.0 / (kSU * kSU), 1.0 / (kSU * kSU),
                           1.0 / (kSW * kSW), 1.0 / (kSW * kSW), 1.0 / (kSW * kSW)};
     if (tid == 0) s_sing = 0;
@@ -768,47 +808,20 @@ __global__ void __launch_bounds__(kAvgThreads) average_kernel(const AvgGraph* __
         b[r] = v;
     }
     __syncthreads();
-    // 4. Cholesky H = L L^T in place (lower triangle)
-    for (int k = 0; k < n; ++k) {
-        if (tid == 0) {
-            const double d = H[k * ld + k];
-            if (!(d > 0.0) || !isfinite(d)) s_sing = 1;
-            else H[k * ld + k] = sqrt(d);
-        }
-        __syncthreads();
-        if (s_sing) break;
-        const double inv = 1.0 / H[k * ld + k];
-        for (int i = k + 1 + tid; i < n; i += kAvgThreads) H[i * ld + k] *= inv;
-        __syncthreads();
-        const int m = n - k - 1;
-        for (int idx = tid; idx < m * m; idx += kAvgThreads) {
-            const int i = k + 1 + idx / m, j = k + 1 + idx % m;
-            if (j <= i) H[i * ld + j] -= H[i * ld + k] * H[j * ld + k];
-        }
+    // 4-5. H d = b by LDL^T with a one-column look-ahead (bt_ldlt.h); a
+    // pivot that is not positive, or a solution that is not finite, leaves
+    // the poses as they were
+    if (n > 0) {
+        unsigned long long t_unused;
+        ldlt_solve(H, ld, n, b, sc, &s_sing, t_unused);
+        for (int i = tid; i < n; i += kAvgThreads)
+            if (!isfinite(b[i])) s_sing = 1;
         __syncthreads();
     }
     if (s_sing) {
         if (tid == 0) *G.status = 1;
         return;
     }
-    // 5. L z = b, L^T d = z (warp 0)
-    if (tid < 32) {
-        for (int k = 0; k < n; ++k) {
-            double s = 0.0;
-            for (int m = tid; m < k; m += 32) s += H[k * ld + m] * b[m];
-            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-            if (tid == 0) b[k] = (b[k] - s) / H[k * ld + k];
-            __syncwarp();
-        }
-        for (int k = n - 1; k >= 0; --k) {
-            double s = 0.0;
-            for (int m = k + 1 + tid; m < n; m += 32) s += H[m * ld + k] * b[m];
-            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-            if (tid == 0) b[k] = (b[k] - s) / H[k * ld + k];
-            __syncwarp();
-        }
-    }
-    __syncthreads();
     // 6. T_j <- exp(d_j) T_j for the free nodes
     for (int j = tid; j < N; j += kAvgThreads) {
         const int f = G.nodes[j].free_idx;
@@ -878,8 +891,8 @@ cudaError_t launch_adam(Net net, const float* grad, float lr, float beta1, float
 size_t average_smem_bytes(int max_free, int max_N)
 {
     const size_t n = 6 * (size_t)max_free;
-    return sizeof(double) * (24 * (size_t)max_N + n * (n + 1) + n) + sizeof(int) * ((size_t)max_N * max_N + max_free) +
-           16;
+    return sizeof(double) * (24 * (size_t)max_N + n * (n + 1) + 4 * n + 256) +
+           sizeof(int) * ((size_t)max_N * max_N + max_free + n * (n + 1) / 2) + 16;
 }
 
 cudaError_t launch_average(const AvgGraph* graphs, int n_graphs, int max_free, cudaStream_t s)
