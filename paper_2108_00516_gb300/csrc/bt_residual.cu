@@ -635,17 +635,19 @@ static void set_residual_attrs()
     set_residual_attrs_p<S, 2>();
 }
 
+// Once per process (a function-local static: thread-safe initialisation).
 static void ensure_residual_attrs()
 {
-    static bool done = false;
-    if (done) return;
-    set_residual_attrs<0>();
-    set_residual_attrs<1>();
-    set_residual_attrs<2>();
-    set_residual_attrs<3>();
-    set_residual_attrs<4>();
-    set_residual_attrs<5>();
-    done = true;
+    static const bool done = [] {
+        set_residual_attrs<0>();
+        set_residual_attrs<1>();
+        set_residual_attrs<2>();
+        set_residual_attrs<3>();
+        set_residual_attrs<4>();
+        set_residual_attrs<5>();
+        return true;
+    }();
+    (void)done;
 }
 
 template <int S, int P>

@@ -669,12 +669,12 @@ size_t reduce_smem_bytes(int n_free, int N)
 
 cudaError_t launch_reduce(const SolveArgs& a, bool full, int iter, cudaStream_t s)
 {
-    static bool attr_set = false;
-    if (!attr_set) {
+    static const bool attr_set = [] {      // once per process, thread-safe
         cudaFuncSetAttribute(reduce_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReduceSmemMax);
         cudaFuncSetAttribute(reduce_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReduceSmemMax);
-        attr_set = true;
-    }
+        return true;
+    }();
+    (void)attr_set;
     const int grid = a.n_upairs > 0 ? a.n_upairs : 1;
     const size_t smem = reduce_smem_bytes(a.n_free, a.N);
     if (full)
@@ -738,12 +738,12 @@ cudaError_t launch_batch_pairs(const SolveArgs* args_dev, const int2* work_pair,
 cudaError_t launch_batch_solve(const SolveArgs* args_dev, int n_graphs, size_t smem, bool full, int iter,
                                cudaStream_t s)
 {
-    static bool attr_set = false;
-    if (!attr_set) {
+    static const bool attr_set = [] {      // once per process, thread-safe
         cudaFuncSetAttribute(batch_solve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReduceSmemMax);
         cudaFuncSetAttribute(batch_solve_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReduceSmemMax);
-        attr_set = true;
-    }
+        return true;
+    }();
+    (void)attr_set;
     if (n_graphs == 0) return cudaSuccess;
     if (full)
         return launch_chained(batch_solve_kernel<true>, dim3(n_graphs), dim3(kThreads), smem, s, args_dev, iter);

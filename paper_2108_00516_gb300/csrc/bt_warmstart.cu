@@ -332,24 +332,23 @@ template <bool kTrain>
 struct ForwardAttr {
     static void set()
     {
-        static bool done = false;
-        if (!done) {
+        static const bool done = [] {      // once per process, thread-safe
             cudaFuncSetAttribute(forward_kernel<kTrain>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Fwd::Total);
-            done = true;
-        }
+            return true;
+        }();
+        (void)done;
     }
 };
 
 int num_sms()
 {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
+    static const int n = [] {             // once per process, thread-safe
+        int dev = 0, v = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v > 0 ? v : 1;
+    }();
     return n;
 }
 
@@ -899,12 +898,12 @@ cudaError_t launch_average(const AvgGraph* graphs, int n_graphs, int max_free, c
 {
     if (n_graphs <= 0) return cudaSuccess;
     const size_t smem = average_smem_bytes(max_free, kMaxNodes);
-    static bool attr = false;
-    if (!attr) {
+    static const bool attr = [] {         // once per process, thread-safe
         cudaFuncSetAttribute(average_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)average_smem_bytes(kMaxNodes - 1, kMaxNodes));
-        attr = true;
-    }
+        return true;
+    }();
+    (void)attr;
     average_kernel<<<n_graphs, kAvgThreads, smem, s>>>(graphs);
     return cudaGetLastError();
 }
