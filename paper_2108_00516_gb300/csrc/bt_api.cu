@@ -356,6 +356,7 @@ int bthost::build_topology(bt_graph* g, int tile)
     for (const bt::EdgeDev& e : edges) sp += e.count;
     g->sparse_per_pass = sp;
     g->topo_dirty = false;
+    g->topo_version++;
     g->built_tile = tile;
     return BT_OK;
 }
@@ -855,6 +856,8 @@ int batch_build(bt_batch* b, int shape)
         args[k].costs = reinterpret_cast<double*>(blk + L.costs);
     }
     b->h_args = args;
+    b->topo_versions.clear();
+    for (bt_graph* g : b->graphs) b->topo_versions.push_back(g->topo_version);
     const size_t n_args = std::max<size_t>(args.size(), 1), n_res = std::max<size_t>(wres.size(), 1),
                  n_pair = std::max<size_t>(wpair.size(), 1);
     BT_CUDA(b->d_args.ensure(sizeof(bt::SolveArgs) * n_args), "alloc batch args");
@@ -974,6 +977,11 @@ int bthost::batch_prepare(bt_batch* b, int iters)
     bt::prepare_launch_attributes();
     bool topo_changed = b->dirty;
     for (bt_graph* g : b->graphs) topo_changed |= g->topo_dirty;
+    // tables rebuilt outside the batch (a single-graph solve at another tile
+    // size, e.g. the warm-started solve's fallback) moved or rewrote what the
+    // batch's arguments point to
+    bool moved = b->topo_versions.size() != b->graphs.size();
+    for (size_t k = 0; !moved && k < b->graphs.size(); ++k) moved = b->graphs[k]->topo_version != b->topo_versions[k];
     if (topo_changed) {
         b->dirty = false;
         if (b->shape < 0) {
@@ -982,7 +990,7 @@ int bthost::batch_prepare(bt_batch* b, int iters)
         }
     }
     const int shape = b->shape >= 0 ? b->shape : (b->tuned_shape >= 0 ? b->tuned_shape : 0);
-    if (topo_changed || b->exec_shape != shape) {
+    if (topo_changed || moved || b->exec_shape != shape) {
         int st = batch_build(b, shape);
         if (st != BT_OK) return st;
     }

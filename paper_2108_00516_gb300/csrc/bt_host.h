@@ -263,6 +263,7 @@ struct bt_graph {
     int64_t pixels_per_pass = 0;
     int64_t sparse_per_pass = 0;
     int built_tile = 0;     // tile size the current tables were built for
+    uint64_t topo_version = 0;   // incremented by every build of the tables
 
     // profiling
     bt_profile prof{};
@@ -303,6 +304,7 @@ struct bt_batch {
     bthost::PinBuf pin_state, pin_tab;
     std::vector<size_t> state_off;
     std::vector<bt::SolveArgs> h_args;   // host copy of d_args
+    std::vector<uint64_t> topo_versions; // the graphs' table versions h_args was built from
     int n_work_res = 0, n_work_pair = 0, max_N = 1;
     size_t solve_smem = 0;
     int64_t pixels_per_pass = 0;

@@ -172,3 +172,28 @@ def test_distinct_streams_give_identical_results(bt):
         assert a["cost_final"] == b["cost_final"] and a["dense_inliers"] == b["dense_inliers"]
     for a, b in zip(ref[1] + ref[3], got[1] + got[3]):
         assert np.array_equal(a, b)
+
+
+def test_batch_after_single_solve_at_another_tile(bt):
+    """A single-graph solve rebuilds a graph's tables at its own tile size
+    (512 pixels); the batch (here 64x4 CTAs: 256-pixel tiles) notices and
+    rebuilds its arguments: the next batched solve equals the first."""
+    gs = _graphs()
+    pgs = [bt.graph_from_synth(g) for g in gs]
+    batch = bt.Batch()
+    for pg in pgs:
+        batch.add(pg)
+    batch.set_shape(3)
+    first = batch.solve(4)
+    P_first = [pg.get_poses() for pg in pgs]
+    pgs[0].set_poses(gs[0].pose_init)
+    pgs[0].solve(2)                          # tables of graph 0 rebuilt at 512-pixel tiles
+    for pg, g in zip(pgs, gs):
+        pg.set_poses(g.pose_init)
+    again = batch.solve(4)
+    for a, b_, pg, P in zip(first, again, pgs, P_first):
+        assert a["cost_final"] == b_["cost_final"]
+        assert np.array_equal(pg.get_poses(), P)
+    batch.close()
+    for pg in pgs:
+        pg.close()
