@@ -455,28 +455,27 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
     if (staged_costs && warp == (nt >> 5) - 1) write_costs(stage, true);
     const bool staged = a.stage_blocks != 0;
     auto blk = [&](size_t q) { return staged ? stage[q] : __ldcg(a.upairblk + q); };
-    // diagonal blocks and gradient: one warp per free node, lanes 0-20 the
-    // unique block entries, lanes 21-26 the gradient entries
-    for (int f = warp; f < nf; f += nt / 32) {
+    // diagonal blocks and gradient: one thread per (free node, value), values
+    // 0-20 the unique block entries, 21-26 the gradient entries (all the
+    // warps' FP64 pipes at once rather than one warp per node)
+    for (int q = tid; q < nf * 27; q += nt) {
+        const int f = q / 27, v = q - 27 * f;
         const int A = node_of[f];
-        if (lane < 27) {
-            double s0 = 0.0, s1 = 0.0;
-            for (int k = 0; k < N; ++k) {
-                if (k == A) continue;
-                const int u = A < k ? upair_index(A, k, N) : upair_index(k, A, N);
-                const size_t off = (size_t)u * kUPairBlk +
-                                   (lane < 21 ? (A < k ? 0 : 21) + lane : (A < k ? 78 : 84) + lane - 21);
-                if (k & 1) s1 += blk(off); else s0 += blk(off);
-            }
-            const double s = s0 + s1;
-            if (lane < 21) {
-                int r = 0, q = lane;
-                while (q >= 6 - r) { q -= 6 - r; ++r; }
-                const int c = r + q;     // (r, c), c >= r, of the 6x6 block
-                H[(6 * f + c) * ld + 6 * f + r] = s;
-            } else {
-                y[6 * f + lane - 21] = -s;   // right-hand side of H dx = -g
-            }
+        double s0 = 0.0, s1 = 0.0;
+        for (int k = 0; k < N; ++k) {
+            if (k == A) continue;
+            const int u = A < k ? upair_index(A, k, N) : upair_index(k, A, N);
+            const size_t off = (size_t)u * kUPairBlk + (v < 21 ? (A < k ? 0 : 21) + v : (A < k ? 78 : 84) + v - 21);
+            if (k & 1) s1 += blk(off); else s0 += blk(off);
+        }
+        const double s = s0 + s1;
+        if (v < 21) {
+            int r = 0, e = v;
+            while (e >= 6 - r) { e -= 6 - r; ++r; }
+            const int c = r + e;     // (r, c), c >= r, of the 6x6 block
+            H[(6 * f + c) * ld + 6 * f + r] = s;
+        } else {
+            y[6 * f + v - 21] = -s;   // right-hand side of H dx = -g
         }
     }
     // off-diagonal blocks (fa > fb)
