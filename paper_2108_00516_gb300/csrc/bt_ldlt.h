@@ -159,9 +159,9 @@ __device__ __forceinline__ void ldlt_solve(double* __restrict__ H, int ld, int n
     // L^T x = w, unit diagonal (L_ki is stored at (i, k)), in blocks of 32
     // unknowns from the last block up.  Warp 0 runs the chain of one block
     // with the block's values in registers, lane l holding row r0 + l: x_k
-    // is broadcast from its lane with a shuffle, so each step is one shuffle
-    // and one FP64 FMA deep, and a step issues one FP64 instruction whatever
-    // the size of the system.  The rows above the block then take the
+    // is broadcast from its lane with a shuffle, and the FP64 instructions
+    // issued do not grow with the size of the system.  The rows above the
+    // block then take the
     // block's unknowns as dot products, split into column chunks over
     // several warps (partial sums in shared memory, added per row).
     double* part = sc.part;
@@ -170,7 +170,23 @@ __device__ __forceinline__ void ldlt_solve(double* __restrict__ H, int ld, int n
         if (warp == 0) {
             const int i = r0 + lane;
             double wv = i < r1 ? y[i] : 0.0;
-            for (int k = r1 - 1; k > r0; --k) {
+            int k = r1 - 1;
+            // two unknowns a step: x_k is final; every lane forms
+            // x_{k-1} = w_{k-1} - L_{k,k-1} x_k itself from the broadcast
+            // values (the same FMA its owner would apply), so the chain is
+            // one shuffle and two FMAs deep per two unknowns; each row takes
+            // x_k, then x_{k-1}, exactly as in the one-at-a-time order
+            for (; k > r0 + 1; k -= 2) {
+                const double hk = i < k ? H[i * ld + k] : 0.0;
+                const double hk1 = i < k - 1 ? H[i * ld + k - 1] : 0.0;
+                const double lk = H[(k - 1) * ld + k];        // L_{k,k-1}
+                const double xk = __shfl_sync(0xffffffffu, wv, k - r0);
+                const double wk1 = __shfl_sync(0xffffffffu, wv, k - 1 - r0);
+                const double xk1 = fma(-lk, xk, wk1);
+                if (i < k) wv = fma(-hk, xk, wv);
+                if (i < k - 1) wv = fma(-hk1, xk1, wv);
+            }
+            if (k == r0 + 1) {
                 const double hk = i < k ? H[i * ld + k] : 0.0;
                 const double xk = __shfl_sync(0xffffffffu, wv, k - r0);
                 if (i < k) wv = fma(-hk, xk, wv);
