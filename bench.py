@@ -698,10 +698,17 @@ def run_reference(args):
     if rank != 0:
         return
     import synthgen as S
-    from paper_2108_00516_gb300 import keyframes as KF
     import oracle as O
+    import oracle.keyframes as OK
     seq = S.paper_sequence(seed=2000, n_frames=args.frames)
-    graphs, _ = KF.plan_sequence(seq.poses_true[:, :3, :3], max_nodes=10)
+    # the same keyframe plan as the GPU arm (the library's selection is
+    # tested equal to this oracle's), made without the library
+    R = seq.poses_true[:, :3, :3]
+    graphs, pool = [], [0]
+    for t in range(1, len(R)):
+        graphs.append([pool[k] for k in OK.select(R[pool], R[t], 9)] + [t])
+        if OK.is_novel(R[pool], R[t], 10.0):
+            pool.append(t)
     inits = [[seq.init_pose(f, t + 1) for f in g] for t, g in enumerate(graphs)]
     n_threads = os.cpu_count() or 1
     # each step: the oracle solves a bounded sample of the sequence's graphs
