@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -856,6 +857,8 @@ int batch_build(bt_batch* b, int shape)
         args[k].costs = reinterpret_cast<double*>(blk + L.costs);
     }
     b->h_args = args;
+    static std::atomic<uint64_t> next_build_id{0};
+    b->build_id = ++next_build_id;
     b->topo_versions.clear();
     for (bt_graph* g : b->graphs) b->topo_versions.push_back(g->topo_version);
     const size_t n_args = std::max<size_t>(args.size(), 1), n_res = std::max<size_t>(wres.size(), 1),

@@ -305,6 +305,7 @@ struct bt_batch {
     std::vector<size_t> state_off;
     std::vector<bt::SolveArgs> h_args;   // host copy of d_args
     std::vector<uint64_t> topo_versions; // the graphs' table versions h_args was built from
+    uint64_t build_id = 0;               // unique per batch_build in the process (never 0 once built)
     int n_work_res = 0, n_work_pair = 0, max_N = 1;
     size_t solve_smem = 0;
     int64_t pixels_per_pass = 0;

@@ -28,6 +28,10 @@ struct bt_warmstart {
     DevBuf ids, y, cache, G, loss_per, grad, loss;
     DevBuf app_samples, app_y, app_graphs, app_scratch, app_status, app_items;
     PinBuf pin_app, pin_status;   // staging of the apply tables and the per-graph status
+    // the apply tables on the device were built for this batch build (0:
+    // none); a warm-started batched solve of an unchanged batch reuses them
+    uint64_t app_build = 0;
+    int app_S = 0, app_max_free = 0;
 
     W::Net net() const
     {
@@ -164,8 +168,11 @@ int ensure_tables(bt_graph* g)
 // the averaging writes the new poses into it.  Graph k's status lands in
 // app_status[k] (0 ok; 1 averaging system singular, poses left as they were).
 // The graphs' tables must be current.
+int launch_apply(bt_warmstart* ws, int S, int n_graphs, int max_free, cudaStream_t s);
+
 int enqueue_apply(bt_warmstart* ws, bt_graph* const* gs, int n_graphs, double* const* pose, cudaStream_t s)
 {
+    ws->app_build = 0;     // the tables are rewritten below
     std::vector<W::Sample> smp;
     std::vector<W::PrepItem> items;
     std::vector<W::AvgGraph> avg;
@@ -232,6 +239,16 @@ int enqueue_apply(bt_warmstart* ws, bt_graph* const* gs, int n_graphs, double* c
                             cudaMemcpyHostToDevice, s),
             "upload graphs");
     BT_CUDA(ws->pin_app.mark(s), "record warm-start upload");
+    ws->app_S = S;
+    ws->app_max_free = max_free;
+    return launch_apply(ws, S, n_graphs, max_free, s);
+}
+
+// The three launches of a warm start over the apply tables already on the
+// device: relative poses and centres from the current poses, the network,
+// the averaging.
+int launch_apply(bt_warmstart* ws, int S, int n_graphs, int max_free, cudaStream_t s)
+{
     W::Sample* d_smp = ws->app_samples.as<W::Sample>();
     BT_CUDA(W::launch_prep(d_smp, ws->app_items.as<W::PrepItem>(), S, s), "launch prep");
     BT_CUDA(W::launch_forward(ws->net(), d_smp, nullptr, S, ws->app_y.as<float>(), nullptr, s), "launch forward");
@@ -621,7 +638,14 @@ int bt_batch_solve_warm(bt_batch* b, bt_warmstart* ws, int32_t iters, int32_t fa
     if (st != BT_OK) return st;
     std::vector<double*> pose(G);
     for (size_t k = 0; k < G; ++k) pose[k] = b->h_args[k].pose;
-    st = enqueue_apply(ws, b->graphs.data(), (int)G, pose.data(), s);
+    // the apply tables depend only on the batch build (edges, point sets,
+    // pointers into the batch's state block): rebuilt only when it changed
+    if (ws->app_build != 0 && ws->app_build == b->build_id) {
+        st = launch_apply(ws, ws->app_S, (int)G, ws->app_max_free, s);
+    } else {
+        st = enqueue_apply(ws, b->graphs.data(), (int)G, pose.data(), s);
+        if (st == BT_OK) ws->app_build = b->build_id;
+    }
     if (st == BT_OK) st = read_status(ws, (int)G, s);
     if (st == BT_OK) st = batch_launch(b, iters);
     if (st != BT_OK) return st;

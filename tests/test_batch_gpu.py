@@ -197,3 +197,57 @@ def test_batch_after_single_solve_at_another_tile(bt):
     batch.close()
     for pg in pgs:
         pg.close()
+
+
+def test_warm_started_batch_reuses_and_rebuilds_its_tables(bt):
+    """Repeated warm-started solves of an unchanged batch reuse the network's
+    input tables; a changed correspondence set rebuilds them.  Each result
+    equals the same solve on a fresh batch."""
+    gs = _graphs()
+    params = S.warmstart_init(5)
+
+    def fresh(graphs):
+        pgs = [bt.graph_from_synth(g) for g in graphs]
+        b = bt.Batch()
+        for pg in pgs:
+            b.add(pg)
+        b.set_shape(0)
+        ws = bt.WarmStart(params)
+        reps = b.solve_warm(ws, 2, 4, raise_on_error=False)
+        out = ([r["cost_final"] for r in reps], [pg.get_poses() for pg in pgs])
+        ws.close()
+        b.close()
+        for pg in pgs:
+            pg.close()
+        return out
+
+    pgs = [bt.graph_from_synth(g) for g in gs]
+    batch = bt.Batch()
+    for pg in pgs:
+        batch.add(pg)
+    batch.set_shape(0)
+    ws = bt.WarmStart(params)
+    ref = fresh(gs)
+    for _ in range(2):                     # the second call reuses the tables
+        for pg, g in zip(pgs, gs):
+            pg.set_poses(g.pose_init)
+        reps = batch.solve_warm(ws, 2, 4, raise_on_error=False)
+        assert [r["cost_final"] for r in reps] == ref[0]
+        assert all(np.array_equal(pg.get_poses(), P) for pg, P in zip(pgs, ref[1]))
+    # drop the first correspondence set of graph 3 (N = 5): tables rebuilt
+    i, j, pi, pj = gs[3].matches[0]
+    empty = np.zeros((0, 3), np.float32)
+    pgs[3].set_matches(pgs[3].frame_ids[i], pgs[3].frame_ids[j], empty, empty)
+    changed = list(gs)
+    import dataclasses
+    changed[3] = dataclasses.replace(gs[3], matches=gs[3].matches[1:])
+    ref2 = fresh(changed)
+    for pg, g in zip(pgs, gs):
+        pg.set_poses(g.pose_init)
+    reps = batch.solve_warm(ws, 2, 4, raise_on_error=False)
+    assert [r["cost_final"] for r in reps] == ref2[0]
+    assert all(np.array_equal(pg.get_poses(), P) for pg, P in zip(pgs, ref2[1]))
+    ws.close()
+    batch.close()
+    for pg in pgs:
+        pg.close()
