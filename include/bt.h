@@ -14,8 +14,8 @@
  *
  * Conventions used by every call:
  *   - pose: 4x4 row-major double, maps OBJECT coordinates to CAMERA
- *     coordinates of that frame (Sec. III, "the object pose in the camera's
- *     frame"); the last row must be 0 0 0 1;
+ *     coordinates of that frame (the node poses of Sec. IV-D: the object's
+ *     pose expressed in each camera); the last row must be 0 0 0 1;
  *   - pixel (u, v): u = column, v = row, pixel centres at integer coordinates;
  *     pinhole model u = fx X/Z + cx, v = fy Y/Z + cy;
  *   - depth: metres along the optical axis, row-major H x W float; values
