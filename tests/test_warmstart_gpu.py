@@ -246,3 +246,43 @@ def test_warmstart_errors(bt):
         ws.apply(pg2)
     assert e.value.status == bt.BT_ERR_SINGULAR
     assert np.array_equal(pg2.get_poses(), g.pose_init)
+
+
+def test_largest_graph_solve_and_average(bt):
+    """BT_MAX_NODES = 24 nodes (6 x 23 = 138 unknowns, the largest system of
+    both FP64 solves): the Gauss-Newton solve against the oracle, the batch
+    against the single graph bit for bit, and the warm start's averaging
+    against the oracle's."""
+    g = S.random_graph(777, bt.BT_MAX_NODES, S.TINY_CAMERA, 60, 0.2)
+    pg = bt.graph_from_synth(g)
+    P_gpu, rep = pg.solve(2)
+    ro = O.solve(g, 2)
+    assert rep["status"] == 0 and ro["status"] == 0
+    assert abs(rep["cost_final"] - ro["cost_final"]) <= 1e-5 * ro["cost_final"]
+    for a, b_ in zip(P_gpu, ro["poses"]):
+        assert S.rotation_angle(a[:3, :3] @ b_[:3, :3].T) <= 1e-5 and np.abs(a[:3, 3] - b_[:3, 3]).max() <= 1e-6
+    pb = bt.graph_from_synth(g)
+    batch = bt.Batch()
+    batch.add(pb)
+    batch.set_shape(0)
+    r_b = batch.solve(2)[0]
+    assert r_b["cost_final"] == rep["cost_final"] and np.array_equal(pb.get_poses(), P_gpu)
+    batch.close()
+    P = _params(8)
+    ws = bt.WarmStart(P)
+    pw = bt.graph_from_synth(g)
+    ws.apply(pw)
+    got = pw.get_poses()
+    D = {}
+    for (i, j, pi, pj) in g.matches:
+        M0 = g.pose_init[j] @ np.linalg.inv(g.pose_init[i])
+        x, c = W.features(pi, pj, M0)
+        y, _ = W.forward(P.astype(np.float64), x)
+        D[(i, j)] = W.increment(y, c)
+    ref = W.average(list(g.pose_init), list(g.fixed), D)
+    for k in range(g.n):
+        rot = S.rotation_angle(got[k][:3, :3] @ ref[k][:3, :3].T)
+        assert rot < 1e-4 and np.max(np.abs(got[k][:3, 3] - ref[k][:3, 3])) < 1e-5, k
+    ws.close()
+    for h in (pg, pb, pw):
+        h.close()
