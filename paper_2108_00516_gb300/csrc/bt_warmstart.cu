@@ -33,13 +33,13 @@ constexpr int kLd3 = 258;       // padded row length (BF16) of the layer-3 weigh
 
 __device__ __forceinline__ float bf2f(__nv_bfloat16 b) { return __bfloat162float(b); }
 
-// Features of point k of a set, FP32 with a fixed operation order (the
-// backward pass recomputes them bit for bit).
-__device__ __forceinline__ void point_features(const float* __restrict__ p, const float* __restrict__ q,
-                                               const float* m, const float* c, int k, float x[6])
+// Features of one point pair (p in camera i, q in camera j: v = px py pz qx
+// qy qz), FP32 with a fixed operation order (the backward pass recomputes
+// them bit for bit).
+__device__ __forceinline__ void features_from(const float v[6], const float* m, const float* c, float x[6])
 {
-    const float px = p[3 * k], py = p[3 * k + 1], pz = p[3 * k + 2];
-    const float qx = q[3 * k], qy = q[3 * k + 1], qz = q[3 * k + 2];
+    const float px = v[0], py = v[1], pz = v[2];
+    const float qx = v[3], qy = v[4], qz = v[5];
     const float ux = __fmaf_rn(m[0], px, __fmaf_rn(m[1], py, __fmaf_rn(m[2], pz, m[3])));
     const float uy = __fmaf_rn(m[4], px, __fmaf_rn(m[5], py, __fmaf_rn(m[6], pz, m[7])));
     const float uz = __fmaf_rn(m[8], px, __fmaf_rn(m[9], py, __fmaf_rn(m[10], pz, m[11])));
@@ -49,6 +49,32 @@ __device__ __forceinline__ void point_features(const float* __restrict__ p, cons
     x[3] = __fmul_rn(__fsub_rn(qx, ux), kInvSR);
     x[4] = __fmul_rn(__fsub_rn(qy, uy), kInvSR);
     x[5] = __fmul_rn(__fsub_rn(qz, uz), kInvSR);
+}
+
+// Point pair k of a set (zeros when k >= n).
+__device__ __forceinline__ void load_pair(const float* __restrict__ p, const float* __restrict__ q, int k, int n,
+                                          float v[6])
+{
+    if (k < n) {
+        v[0] = p[3 * k];
+        v[1] = p[3 * k + 1];
+        v[2] = p[3 * k + 2];
+        v[3] = q[3 * k];
+        v[4] = q[3 * k + 1];
+        v[5] = q[3 * k + 2];
+    } else {
+#pragma unroll
+        for (int e = 0; e < 6; ++e) v[e] = 0.f;
+    }
+}
+
+// Features of point k of a set.
+__device__ __forceinline__ void point_features(const float* __restrict__ p, const float* __restrict__ q,
+                                               const float* m, const float* c, int k, float x[6])
+{
+    float v[6];
+    load_pair(p, q, k, k + 1, v);
+    features_from(v, m, c, x);
 }
 
 // Offset (floats) of layer-1 unit u's packed weights in the forward kernel's
@@ -191,11 +217,14 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             best[k] = -1.f;
             bestr[k] = 0;
         }
+        const int lrow = tid >> 2, q4 = tid & 3;  // layer 1: thread = (row, quarter of the 128 units)
+        float pq[6];                             // the point pair of this thread's row of the chunk
+        load_pair(P, Q, lrow, n, pq);
         for (int r0 = 0; r0 < n; r0 += kChunk) {
-            {   // layer 1: thread = (row, quarter of the 128 units)
-                const int row = tid >> 2, q4 = tid & 3, gr = r0 + row;
+            {
+                const int gr = r0 + lrow;
                 float x[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                if (gr < n) point_features(P, Q, sMC, sMC + 12, gr, x);
+                if (gr < n) features_from(pq, sMC, sMC + 12, x);
                 uint32_t packed[16];
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
@@ -205,12 +234,14 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                     __nv_bfloat162 b2 = __floats2bfloat162_rn(h0, h1);
                     packed[k] = *reinterpret_cast<uint32_t*>(&b2);
                 }
-                uint4* dst = reinterpret_cast<uint4*>(sH1 + row * kLd + q4 * 32);
+                uint4* dst = reinterpret_cast<uint4*>(sH1 + lrow * kLd + q4 * 32);
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
                     dst[k] = make_uint4(packed[4 * k], packed[4 * k + 1], packed[4 * k + 2], packed[4 * k + 3]);
             }
             __syncthreads();
+            // the next chunk's point pair: the loads are in flight during layer 2
+            load_pair(P, Q, r0 + kChunk + lrow, n, pq);
             float acc[2][8][4];
 #pragma unroll
             for (int a = 0; a < 2; ++a)
