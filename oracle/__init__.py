@@ -83,6 +83,13 @@ def lib():
         L.orc_associate.restype = C.c_int
         L.orc_associate.argtypes = [C.POINTER(_Frame), C.POINTER(_Frame), _dp, _dp,
                                     C.POINTER(_Params), _ip, _ip, C.c_int]
+        L.orc_associate_classify.restype = C.c_int
+        L.orc_associate_classify.argtypes = [C.POINTER(_Frame), C.POINTER(_Frame), _dp, _dp,
+                                             C.POINTER(_Params), _ip, _ip, _ip, _dp, C.c_int]
+        L.orc_normal_equations_frozen.restype = C.c_long
+        L.orc_normal_equations_frozen.argtypes = [C.POINTER(_Frame), C.c_int, _dp, C.POINTER(_MatchSet),
+                                                  C.c_int, C.POINTER(_Params), C.POINTER(_ip),
+                                                  C.POINTER(_ip), _ip, C.c_int, _dp, _dp, _dp]
         L.orc_dense_terms.argtypes = [C.POINTER(_Frame), C.POINTER(_Frame), _dp, _dp, _ip, _ip,
                                       C.c_int, _dp, _dp]
         L.orc_sparse_terms.argtypes = [C.POINTER(_MatchSet), _dp, _dp, _dp, _dp]
@@ -191,6 +198,126 @@ def associate(graph, i: int, j: int, poses, params: Params | None = None):
                             _ptr(X[j], C.c_double), C.byref(prm), _ptr(sp, C.c_int32),
                             _ptr(tp, C.c_int32), cap)
     return sp[:n].copy(), tp[:n].copy()
+
+
+@dataclass
+class Classified:
+    """Association decisions of one ordered pair, one entry per valid masked
+    source pixel (increasing pixel order): ``src`` the pixel, ``nominal`` the
+    oracle's single-precision decision (target pixel or -1), ``alt`` (n, 4)
+    the other outcomes single-precision rounding admits (-1 = dropped, -2 =
+    none), ``slack`` the largest change of that pixel's Huber cost (Eq. 3,
+    before lambda_2) over them."""
+    src: np.ndarray
+    nominal: np.ndarray
+    alt: np.ndarray
+    slack: np.ndarray
+
+    @property
+    def ambiguous(self) -> np.ndarray:
+        return (self.alt != -2).any(axis=1)
+
+    def admits(self, outcome: np.ndarray) -> np.ndarray:
+        """Per entry: is `outcome` (target pixel or -1) the nominal decision
+        or one of the admissible alternatives?"""
+        outcome = np.asarray(outcome)
+        return (outcome == self.nominal) | (self.alt == outcome[:, None]).any(axis=1)
+
+    def count_range(self):
+        """(fewest, most) accepted associations over the admissible outcomes."""
+        acc_nom = self.nominal >= 0
+        acc_alt = (self.alt >= 0).any(axis=1)
+        rej_alt = (self.alt == -1).any(axis=1)
+        lo = int(np.sum(acc_nom & ~rej_alt))
+        hi = int(np.sum(acc_nom | acc_alt))
+        return lo, hi
+
+
+def associate_classified(graph, i: int, j: int, poses, params: Params | None = None) -> Classified:
+    """Every association decision of the ordered pair i -> j with the outcomes
+    that single-precision rounding admits (FP64 classification)."""
+    P = Problem(graph)
+    prm = (params or Params()).c()
+    X = np.ascontiguousarray(poses, np.float64)
+    cap = graph.cams[i].width * graph.cams[i].height
+    sp = np.zeros(cap, np.int32)
+    nom = np.zeros(cap, np.int32)
+    alt = np.zeros((cap, 4), np.int32)
+    sl = np.zeros(cap)
+    n = lib().orc_associate_classify(C.byref(P.frames[i]), C.byref(P.frames[j]), _ptr(X[i], C.c_double),
+                                     _ptr(X[j], C.c_double), C.byref(prm), _ptr(sp, C.c_int32),
+                                     _ptr(nom, C.c_int32), _ptr(alt, C.c_int32), _ptr(sl, C.c_double), cap)
+    return Classified(sp[:n].copy(), nom[:n].copy(), alt[:n].copy(), sl[:n].copy())
+
+
+def energy_bounds(graph, poses, params: Params | None = None, nodes=None):
+    """Over every ordered pair of the graph (or of `nodes`): the fewest and
+    most dense associations single-precision rounding admits, the largest
+    change of the dense energy (lambda_2 included) that the admissible
+    alternatives can make, and the number of ambiguous pixels."""
+    prm = params or Params()
+    nodes = list(range(len(graph.renders))) if nodes is None else list(nodes)
+    lo = hi = 0
+    slack = 0.0
+    amb = 0
+    total = 0
+    for a in nodes:
+        for b in nodes:
+            if a == b:
+                continue
+            c = associate_classified(graph, a, b, poses if len(poses) == len(graph.renders)
+                                     else _expand(poses, nodes, len(graph.renders)), prm)
+            l, h = c.count_range()
+            lo += l
+            hi += h
+            slack += prm.lambda_dense * float(np.sum(c.slack))
+            amb += int(c.ambiguous.sum())
+            total += len(c.src)
+    return dict(count_lo=lo, count_hi=hi, slack=slack, ambiguous=amb, pixels=total)
+
+
+def _expand(poses, nodes, n_all):
+    X = np.tile(np.eye(4), (n_all, 1, 1))
+    for k, f in enumerate(nodes):
+        X[f] = poses[k]
+    return X
+
+
+def normal_equations_frozen(graph, poses, assoc, params: Params | None = None, n_threads: int | None = None):
+    """orc_normal_equations with the association given instead of computed:
+    assoc[(i, j)] = (source pixels, target pixels) of every ordered pair.
+    Returns the full 6N x 6N H, 6N g, the energy and the dense term count."""
+    P = Problem(graph)
+    prm = (params or Params()).c()
+    N = P.n
+    X = np.ascontiguousarray(poses, np.float64)
+    keep = []
+    srcs = (_ip * max(1, N * (N - 1)))()
+    tgts = (_ip * max(1, N * (N - 1)))()
+    cnt = np.zeros(max(1, N * (N - 1)), np.int32)
+    for i in range(N):
+        for j in range(N):
+            if i == j:
+                continue
+            k = i * (N - 1) + (j if j < i else j - 1)
+            s, t = assoc[(i, j)]
+            s = np.ascontiguousarray(s, np.int32)
+            t = np.ascontiguousarray(t, np.int32)
+            if len(s) != len(t):
+                raise ValueError("source and target lists differ in length")
+            keep += [s, t]
+            srcs[k] = _ptr(s, C.c_int32)
+            tgts[k] = _ptr(t, C.c_int32)
+            cnt[k] = len(s)
+    H = np.zeros((6 * N, 6 * N))
+    g = np.zeros(6 * N)
+    E = np.zeros(1)
+    n = lib().orc_normal_equations_frozen(P.frames, N, _ptr(X, C.c_double), P.sets, P.n_sets, C.byref(prm),
+                                          srcs, tgts, _ptr(cnt, C.c_int32), n_threads or default_threads(),
+                                          _ptr(H, C.c_double), _ptr(g, C.c_double), _ptr(E, C.c_double))
+    if n < 0:
+        raise ValueError("association holds a pixel index out of range")
+    return H, g, float(E[0]), int(n)
 
 
 def dense_terms(graph, i: int, j: int, poses, src, tgt):

@@ -27,12 +27,17 @@
  *     Jacobian is formed (no derivative of the depth lookup) and recomputed
  *     at the start of every iteration.
  *   - The accept/reject decision of the association produces integers (pixel
- *     indices, keep/drop).  It is evaluated in IEEE single precision, the
- *     precision of the GPU's residual pass, with the operation order spelled
- *     out below (fused multiply-adds exactly where written, fmaf, and nowhere
- *     else), so that both implementations take the same decisions from the
- *     same single-precision inputs.  Residuals,
- *     Jacobians, weights and everything after are FP64.
+ *     indices, keep/drop).  It is taken in IEEE single precision (the
+ *     precision of the GPU's residual pass; the paper fixes none) straight
+ *     from the definition: each operation of the formula rounded on its
+ *     own, in the order written, no fused multiply-add.  A GPU kernel may
+ *     order and fuse its operations otherwise, so its decision may differ
+ *     from this one for a pixel lying within single-precision rounding of
+ *     a decision boundary (the half-pixel edge of the nearest pixel, the
+ *     image edge, the distance gate, the angle gate).  orc_associate_classify
+ *     evaluates every pixel in FP64 and lists the outcomes that such
+ *     rounding admits.  Residuals, Jacobians, weights and everything after
+ *     are FP64.
  *   - Gauss-Newton step: solve H dxi = -g exactly (Cholesky, no damping) over
  *     the nodes not flagged fixed (the gauge: frame I_0 is held constant),
  *     then T_i <- exp(dxi_i) T_i.
@@ -289,65 +294,217 @@ static int pixel_valid(const orc_frame* f, long pix)
     return isfinite(n[0]) && isfinite(n[1]) && isfinite(n[2]);
 }
 
+/* The decision for one source pixel (u, v) of frame i, taken in IEEE single
+ * precision -- the precision of the GPU's residual pass; the paper fixes
+ * none -- straight from the definition, every operation rounded on its own
+ * in the order written (the library is compiled without contraction):
+ *   p  = pi_D^-1(u, v)                      back-projection in camera i
+ *   q  = B p, B = T_j T_i^-1                p seen from camera j
+ *   u' = floor(pi(q) + 1/2)                 nearest pixel of the projection
+ *   t  = pi_D^-1(u')                        the looked-up target point
+ *   keep if q_z > 0, u' inside the image, u' valid, |t - q| <= d_max and
+ *   n_i . R_B^T n_j >= cos(theta_max)       (unit normals: the angle gate)
+ * |t - q| equals |T_i T_j^-1 t - p| of Eq. 3 (a rigid motion keeps
+ * distances) and n_i . R_B^T n_j the cosine of the angle between n_i and the
+ * target normal brought into camera i.  Bf: B rounded to single, row-major
+ * 3x4.  Returns the target pixel, or -1. */
+static long decide_f32(const orc_frame* fi, const orc_frame* fj, const float Bf[12], float dmax, float cmin,
+                       int u, int v)
+{
+    const long pix = (long)v * fi->width + u;
+    const float z = fi->depth[pix];
+    const float p[3] = {((float)u - fi->cx) * z / fi->fx, ((float)v - fi->cy) * z / fi->fy, z};
+    float q[3];
+    for (int r = 0; r < 3; ++r) q[r] = Bf[4 * r] * p[0] + Bf[4 * r + 1] * p[1] + Bf[4 * r + 2] * p[2] + Bf[4 * r + 3];
+    if (!(q[2] > 0.0f)) return -1;
+    const float fu = floorf(fj->fx * q[0] / q[2] + fj->cx + 0.5f);
+    const float fv = floorf(fj->fy * q[1] / q[2] + fj->cy + 0.5f);
+    if (!(fu >= 0.0f && fu < (float)fj->width && fv >= 0.0f && fv < (float)fj->height)) return -1;
+    const int iu = (int)fu, iv = (int)fv;
+    const long tp = (long)iv * fj->width + iu;
+    if (!pixel_valid(fj, tp)) return -1;
+    const float zt = fj->depth[tp];
+    const float t[3] = {((float)iu - fj->cx) * zt / fj->fx, ((float)iv - fj->cy) * zt / fj->fy, zt};
+    const float d[3] = {t[0] - q[0], t[1] - q[1], t[2] - q[2]};
+    if (!(sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) <= dmax)) return -1;
+    const float* ni = fi->normals + 3 * pix;
+    const float* nj = fj->normals + 3 * tp;
+    float nb[3]; /* R_B^T n_j: the target normal in camera i */
+    for (int r = 0; r < 3; ++r) nb[r] = Bf[r] * nj[0] + Bf[4 + r] * nj[1] + Bf[8 + r] * nj[2];
+    if (!(ni[0] * nb[0] + ni[1] * nb[1] + ni[2] * nb[2] >= cmin)) return -1;
+    return tp;
+}
+
+static void pair_transforms(const double Ti[16], const double Tj[16], double B[16], double A[16], float Bf[12])
+{
+    double Tiinv[16], Tjinv[16];
+    pose_inv(Ti, Tiinv);
+    pose_inv(Tj, Tjinv);
+    pose_mul(Tj, Tiinv, B); /* camera i -> camera j */
+    pose_mul(Ti, Tjinv, A); /* camera j -> camera i */
+    for (int k = 0; k < 12; ++k) Bf[k] = (float)B[k];
+}
+
 int orc_associate(const orc_frame* fi, const orc_frame* fj, const double Ti[16],
                   const double Tj[16], const orc_params* prm,
                   int32_t* src_pix, int32_t* tgt_pix, int cap)
 {
-    /* M = T_j T_i^-1 maps camera i to camera j; rounded once to single. */
-    double Tiinv[16], M[16];
-    pose_inv(Ti, Tiinv);
-    pose_mul(Tj, Tiinv, M);
-    float m[12];
-    for (int k = 0; k < 12; ++k) m[k] = (float)M[k];
-    const float dmax2 = (float)(prm->dense_max_dist * prm->dense_max_dist);
+    double B[16], A[16];
+    float Bf[12];
+    pair_transforms(Ti, Tj, B, A, Bf);
+    const float dmax = (float)prm->dense_max_dist;
     const float cmin = (float)cos(prm->dense_max_normal_deg * ORC_PI / 180.0);
-    const float Wf = (float)fj->width, Hf = (float)fj->height;
-    /* reciprocal focal lengths, one IEEE single division each */
-    const float ifx_i = 1.0f / fi->fx, ify_i = 1.0f / fi->fy;
-    const float ifx_j = 1.0f / fj->fx, ify_j = 1.0f / fj->fy;
     int n = 0;
     for (int v = 0; v < fi->height; ++v) {
         for (int u = 0; u < fi->width; ++u) {
             long pix = (long)v * fi->width + u;
             if (!pixel_valid(fi, pix)) continue;
-            /* source point p = pi_D^-1(x) in camera i (single precision) */
-            float z = fi->depth[pix];
-            float px = (((float)u - fi->cx) * z) * ifx_i;
-            float py = (((float)v - fi->cy) * z) * ify_i;
-            float pz = z;
-            /* T_j T_i^-1 p: one fused multiply-add chain per row */
-            float qjx = fmaf(m[2], pz, fmaf(m[1], py, fmaf(m[0], px, m[3])));
-            float qjy = fmaf(m[6], pz, fmaf(m[5], py, fmaf(m[4], px, m[7])));
-            float qjz = fmaf(m[10], pz, fmaf(m[9], py, fmaf(m[8], px, m[11])));
-            if (!(qjz > 0.0f)) continue;
-            /* pi(.) with one correctly rounded reciprocal, then the nearest pixel */
-            float rz = 1.0f / qjz;
-            float uh = fmaf(fj->fx * qjx, rz, fj->cx) + 0.5f;
-            float vh = fmaf(fj->fy * qjy, rz, fj->cy) + 0.5f;
-            if (!(uh >= 0.0f && uh < Wf && vh >= 0.0f && vh < Hf)) continue;
-            int iu = (int)floorf(uh), iv = (int)floorf(vh);
-            long tp = (long)iv * fj->width + iu;
-            if (!pixel_valid(fj, tp)) continue;
-            /* pi_D^-1 at the looked-up pixel, camera j */
-            float zt = fj->depth[tp];
-            float tx = (((float)iu - fj->cx) * zt) * ifx_j;
-            float ty = (((float)iv - fj->cy) * zt) * ify_j;
-            float tz = zt;
-            /* gate 1: point-pair distance */
-            float dx = tx - qjx, dy = ty - qjy, dz = tz - qjz;
-            float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            if (!(d2 <= dmax2)) continue;
-            /* gate 2: angle between the rotated source normal and the target normal */
-            const float* ns = fi->normals + 3 * pix;
-            const float* nt = fj->normals + 3 * tp;
-            float nx = fmaf(m[2], ns[2], fmaf(m[1], ns[1], m[0] * ns[0]));
-            float ny = fmaf(m[6], ns[2], fmaf(m[5], ns[1], m[4] * ns[0]));
-            float nz = fmaf(m[10], ns[2], fmaf(m[9], ns[1], m[8] * ns[0]));
-            float c = fmaf(nz, nt[2], fmaf(ny, nt[1], nx * nt[0]));
-            if (!(c >= cmin)) continue;
+            long tp = decide_f32(fi, fj, Bf, dmax, cmin, u, v);
+            if (tp < 0) continue;
             if (n < cap) {
                 src_pix[n] = (int32_t)pix;
                 tgt_pix[n] = (int32_t)tp;
+            }
+            ++n;
+        }
+    }
+    return n;
+}
+
+/* FP64 gate quantities of source point p (camera i, normal ni) against
+ * target pixel tp of frame j: distance |A t - p| of the pair, cosine of the
+ * angle between ni and R_A n_j, and the point-to-plane residual
+ * r = ni . (A t - p) of Eq. 3.  Returns 0 when tp cannot be a target. */
+static int target_terms(const orc_frame* fj, const double A[16], long tp, const double p[3], const double ni[3],
+                        double* d, double* c, double* r)
+{
+    if (!pixel_valid(fj, tp)) return 0;
+    const int iu = (int)(tp % fj->width), iv = (int)(tp / fj->width);
+    const double zt = fj->depth[tp];
+    const double t[3] = {((double)iu - fj->cx) * zt / fj->fx, ((double)iv - fj->cy) * zt / fj->fy, zt};
+    double ti[3], nr[3];
+    apply(A, t, ti);
+    const double nj[3] = {fj->normals[3 * tp], fj->normals[3 * tp + 1], fj->normals[3 * tp + 2]};
+    for (int k = 0; k < 3; ++k) nr[k] = A[k * 4 + 0] * nj[0] + A[k * 4 + 1] * nj[1] + A[k * 4 + 2] * nj[2];
+    const double e[3] = {ti[0] - p[0], ti[1] - p[1], ti[2] - p[2]};
+    *d = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+    *c = ni[0] * nr[0] + ni[1] * nr[1] + ni[2] * nr[2];
+    *r = ni[0] * e[0] + ni[1] * e[1] + ni[2] * e[2];
+    return 1;
+}
+
+/* Admissible outcomes of every decision (see the header).  Error model of a
+ * single-precision evaluation: unit roundoff u = 2^-24, every input and
+ * intermediate carrying at most K = 16 roundings of its own magnitude
+ * (the back-projection, the rounding of B, a three-term sum, a reciprocal
+ * or divide, a product and a sum -- about six -- with a factor of more than
+ * two to spare, for any order or fusion of the operations):
+ *   q_r      : dq_r = 2 K u (|B_r0 p_0| + |B_r1 p_1| + |B_r2 p_2| + |B_r3|)
+ *   u' edge  : e_u  = (f_x dq_0 + |u^ - c_x| dq_2) / q_2 + K u (|u^| + 1)
+ *   distance : e_d  = dq_0 + dq_1 + dq_2 + K u (|t|_1 + d_max)
+ *   cosine   : e_c  = 8 K u
+ * where u^ = pi(q) + 1/2 in FP64.  Every nearest-pixel candidate within
+ * e_u of u^ on each axis is examined; a candidate whose distance or cosine
+ * lies within e_d / e_c of its gate may be kept or dropped. */
+int orc_associate_classify(const orc_frame* fi, const orc_frame* fj, const double Ti[16],
+                           const double Tj[16], const orc_params* prm, int32_t* src_pix,
+                           int32_t* nominal, int32_t* alt, double* slack, int cap)
+{
+    double B[16], A[16];
+    float Bf[12];
+    pair_transforms(Ti, Tj, B, A, Bf);
+    const float dmax_f = (float)prm->dense_max_dist;
+    const double cmin = cos(prm->dense_max_normal_deg * ORC_PI / 180.0);
+    const float cmin_f = (float)cmin;
+    const double dmax = prm->dense_max_dist, hub = prm->huber_dense;
+    const double K = 16.0, u32 = ldexp(1.0, -24);
+    int n = 0;
+    for (int v = 0; v < fi->height; ++v) {
+        for (int u = 0; u < fi->width; ++u) {
+            const long pix = (long)v * fi->width + u;
+            if (!pixel_valid(fi, pix)) continue;
+            const long nom = decide_f32(fi, fj, Bf, dmax_f, cmin_f, u, v);
+            /* admissible outcomes: up to four candidate pixels and "dropped" */
+            long adm[5];
+            double arho[5];
+            int na = 0;
+            int reject_ok = 0;
+            const double z = fi->depth[pix];
+            const double p[3] = {((double)u - fi->cx) * z / fi->fx, ((double)v - fi->cy) * z / fi->fy, z};
+            const double ni[3] = {fi->normals[3 * pix], fi->normals[3 * pix + 1], fi->normals[3 * pix + 2]};
+            double q[3], dq[3];
+            for (int r = 0; r < 3; ++r) {
+                q[r] = B[4 * r] * p[0] + B[4 * r + 1] * p[1] + B[4 * r + 2] * p[2] + B[4 * r + 3];
+                dq[r] = 2.0 * K * u32 * (fabs(B[4 * r] * p[0]) + fabs(B[4 * r + 1] * p[1]) +
+                                         fabs(B[4 * r + 2] * p[2]) + fabs(B[4 * r + 3]));
+            }
+            if (!(q[2] > dq[2])) {
+                /* behind (or within rounding of) camera j: only a projection
+                 * far outside the image could come out, i.e. dropped */
+                reject_ok = 1;
+            }
+            if (q[2] > 0.0) {
+                const double uh = fj->fx * q[0] / q[2] + fj->cx + 0.5;
+                const double vh = fj->fy * q[1] / q[2] + fj->cy + 0.5;
+                const double eu = (fj->fx * dq[0] + fabs(uh - 0.5 - fj->cx) * dq[2]) / q[2] + K * u32 * (fabs(uh) + 1.0);
+                const double ev = (fj->fy * dq[1] + fabs(vh - 0.5 - fj->cy) * dq[2]) / q[2] + K * u32 * (fabs(vh) + 1.0);
+                const double cu[2] = {floor(uh - eu), floor(uh + eu)};
+                const double cv[2] = {floor(vh - ev), floor(vh + ev)};
+                for (int a = 0; a < 2; ++a) {
+                    if (a == 1 && cu[1] == cu[0]) continue;
+                    for (int b = 0; b < 2; ++b) {
+                        if (b == 1 && cv[1] == cv[0]) continue;
+                        if (!(cu[a] >= 0.0 && cu[a] < fj->width && cv[b] >= 0.0 && cv[b] < fj->height)) {
+                            reject_ok = 1;
+                            continue;
+                        }
+                        const long tp = (long)cv[b] * fj->width + (long)cu[a];
+                        double d, c, r;
+                        if (!target_terms(fj, A, tp, p, ni, &d, &c, &r)) {
+                            reject_ok = 1;
+                            continue;
+                        }
+                        const int iu = (int)(tp % fj->width), iv = (int)(tp / fj->width);
+                        const double zt = fj->depth[tp];
+                        const double tl1 = fabs(((double)iu - fj->cx) * zt / fj->fx) +
+                                           fabs(((double)iv - fj->cy) * zt / fj->fy) + zt;
+                        const double ed = dq[0] + dq[1] + dq[2] + K * u32 * (tl1 + dmax);
+                        const double ec = 8.0 * K * u32;
+                        const int fail = d > dmax + ed || c < cmin - ec;
+                        const int pass = d <= dmax - ed && c >= cmin + ec;
+                        if (!fail) {
+                            adm[na] = tp;
+                            arho[na] = orc_huber_rho(r, hub);
+                            ++na;
+                        }
+                        if (!pass) reject_ok = 1;
+                    }
+                }
+            }
+            if (reject_ok) {
+                adm[na] = -1;
+                arho[na] = 0.0;
+                ++na;
+            }
+            /* the single-precision decision must itself be admissible; if it
+             * is not, report it as its own (inconsistent) outcome with an
+             * infinite slack so that every test sees the failure */
+            double rho_nom = NAN;
+            for (int k = 0; k < na; ++k)
+                if (adm[k] == nom) rho_nom = arho[k];
+            if (n < cap) {
+                src_pix[n] = (int32_t)pix;
+                nominal[n] = (int32_t)nom;
+                int m = 0;
+                double s = 0.0;
+                for (int k = 0; k < na; ++k) {
+                    if (adm[k] == nom) continue;
+                    if (m < 4) alt[4 * n + m++] = (int32_t)adm[k];
+                    const double ds = fabs(arho[k] - rho_nom);
+                    if (!(ds <= s)) s = ds; /* NaN (inconsistent nominal) propagates */
+                }
+                for (; m < 4; ++m) alt[4 * n + m] = -2;
+                slack[n] = isnan(rho_nom) ? INFINITY : s;
             }
             ++n;
         }
@@ -442,6 +599,11 @@ typedef struct {
     const orc_params* prm;
     int n_threads, tid;
     int want_system;  /* 0: energy only */
+    /* frozen association (NULL: associate): lists per ordered pair
+     * k = i (N-1) + (j < i ? j : j - 1) */
+    const int32_t* const* fz_src;
+    const int32_t* const* fz_tgt;
+    const int32_t* fz_n;
     double* H;        /* 6N x 6N (thread private) */
     double* g;        /* 6N */
     double e_dense, e_sparse;
@@ -489,10 +651,22 @@ static void* worker(void* arg)
             const double* Ti = w->poses + 16 * i;
             const double* Tj = w->poses + 16 * j;
             int cap = fi->width * fi->height;
+            int n;
             int32_t* sp = (int32_t*)malloc(sizeof(int32_t) * (size_t)(cap > 0 ? cap : 1));
             int32_t* tp = (int32_t*)malloc(sizeof(int32_t) * (size_t)(cap > 0 ? cap : 1));
             if (!sp || !tp) { free(sp); free(tp); w->failed = 1; continue; }
-            int n = orc_associate(fi, fj, Ti, Tj, prm, sp, tp, cap);
+            if (w->fz_src) {
+                n = w->fz_n[it];
+                if (n < 0 || n > cap) { free(sp); free(tp); w->failed = 1; continue; }
+                for (int k = 0; k < n; ++k) {
+                    sp[k] = w->fz_src[it][k];
+                    tp[k] = w->fz_tgt[it][k];
+                    if (sp[k] < 0 || sp[k] >= cap || tp[k] < 0 || tp[k] >= fj->width * fj->height) w->failed = 1;
+                }
+                if (w->failed) { free(sp); free(tp); continue; }
+            } else {
+                n = orc_associate(fi, fj, Ti, Tj, prm, sp, tp, cap);
+            }
             double* r = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
             double* J = (double*)malloc(sizeof(double) * 12 * (size_t)(n > 0 ? n : 1));
             if (!r || !J) { free(sp); free(tp); free(r); free(J); w->failed = 1; continue; }
@@ -531,7 +705,8 @@ static void* worker(void* arg)
 
 static int run_workers(const orc_frame* frames, int n_frames, const double* poses,
                        const orc_match_set* sets, int n_sets, const orc_params* prm,
-                       int n_threads, int want_system, double* H, double* g, double out[5])
+                       int n_threads, int want_system, double* H, double* g, double out[5],
+                       const int32_t* const* fz_src, const int32_t* const* fz_tgt, const int32_t* fz_n)
 {
     if (n_threads < 1) n_threads = 1;
     if (n_threads > 256) n_threads = 256;
@@ -545,6 +720,7 @@ static int run_workers(const orc_frame* frames, int n_frames, const double* pose
         w->frames = frames; w->n_frames = n_frames; w->poses = poses;
         w->sets = sets; w->n_sets = n_sets; w->prm = prm;
         w->n_threads = n_threads; w->tid = t; w->want_system = want_system;
+        w->fz_src = fz_src; w->fz_tgt = fz_tgt; w->fz_n = fz_n;
         if (want_system) {
             w->H = (double*)calloc((size_t)(n6 * n6), sizeof(double));
             w->g = (double*)calloc((size_t)n6, sizeof(double));
@@ -587,7 +763,7 @@ void orc_energy(const orc_frame* frames, int n_frames, const double* poses,
                 const orc_match_set* sets, int n_sets, const orc_params* prm,
                 int n_threads, double out[5])
 {
-    if (run_workers(frames, n_frames, poses, sets, n_sets, prm, n_threads, 0, NULL, NULL, out) != 0)
+    if (run_workers(frames, n_frames, poses, sets, n_sets, prm, n_threads, 0, NULL, NULL, out, NULL, NULL, NULL) != 0)
         out[0] = out[1] = out[2] = NAN;
 }
 
@@ -596,7 +772,22 @@ long orc_normal_equations(const orc_frame* frames, int n_frames, const double* p
                           int n_threads, double* H, double* g, double* energy)
 {
     double out[5];
-    if (run_workers(frames, n_frames, poses, sets, n_sets, prm, n_threads, 1, H, g, out) != 0) {
+    if (run_workers(frames, n_frames, poses, sets, n_sets, prm, n_threads, 1, H, g, out, NULL, NULL, NULL) != 0) {
+        *energy = NAN;
+        return -1;
+    }
+    *energy = out[0];
+    return (long)out[3];
+}
+
+long orc_normal_equations_frozen(const orc_frame* frames, int n_frames, const double* poses,
+                                 const orc_match_set* sets, int n_sets, const orc_params* prm,
+                                 const int32_t* const* src_pix, const int32_t* const* tgt_pix,
+                                 const int32_t* counts, int n_threads, double* H, double* g, double* energy)
+{
+    double out[5];
+    if (run_workers(frames, n_frames, poses, sets, n_sets, prm, n_threads, 1, H, g, out, src_pix, tgt_pix,
+                    counts) != 0) {
         *energy = NAN;
         return -1;
     }

@@ -82,11 +82,30 @@ int orc_pcg_solve(int n, const double* A, double* b, int max_iters, double rel_t
  * nearest pixel, and kept if that pixel is valid and passes the distance and
  * normal-angle gates.  Writes up to `cap` (source pixel, target pixel)
  * indices in increasing source-pixel order and returns the number kept.  The
- * accept/reject decision is evaluated in IEEE single precision (see the
- * source for the exact operation order). */
+ * accept/reject decision is taken in IEEE single precision, straight from
+ * the definition (see the source for the formula and its order). */
 int orc_associate(const orc_frame* fi, const orc_frame* fj, const double Ti[16],
                   const double Tj[16], const orc_params* prm,
                   int32_t* src_pix, int32_t* tgt_pix, int cap);
+
+/* Classification of the association decisions of the ordered pair (i -> j)
+ * against single-precision rounding.  For every valid masked pixel of frame
+ * i (increasing pixel order; k-th entry), evaluated in FP64:
+ *   src_pix[k]     the source pixel;
+ *   nominal[k]     orc_associate's decision: target pixel, or -1 (dropped);
+ *   alt[4k..4k+3]  the other outcomes that a single-precision evaluation
+ *                  may reach -- a neighbouring nearest pixel when the
+ *                  projection lies within rounding of a half-pixel edge, or
+ *                  -1 when a gate or the image edge is within rounding --
+ *                  padded with -2;
+ *   slack[k]       max |rho(outcome) - rho(nominal)| (Huber cost of Eq. 3,
+ *                  rho = 0 when dropped) over those outcomes; +inf when the
+ *                  single-precision decision is itself not admissible.
+ * The rounding bound is stated in the source.  Returns the number of valid
+ * source pixels (entries beyond cap are counted, not written). */
+int orc_associate_classify(const orc_frame* fi, const orc_frame* fj, const double Ti[16],
+                           const double Tj[16], const orc_params* prm, int32_t* src_pix,
+                           int32_t* nominal, int32_t* alt, double* slack, int cap);
 
 /* Dense point-to-plane residual of Eq. 3 for a frozen association, with its
  * Jacobian with respect to left perturbations of T_i (columns 0-5) and T_j
@@ -114,6 +133,16 @@ void orc_energy(const orc_frame* frames, int n_frames, const double* poses,
 long orc_normal_equations(const orc_frame* frames, int n_frames, const double* poses,
                           const orc_match_set* sets, int n_sets, const orc_params* prm,
                           int n_threads, double* H, double* g, double* energy);
+
+/* orc_normal_equations with a given association instead of Eq. 3's
+ * (protocol: the same terms of an association computed elsewhere).
+ * src_pix[k], tgt_pix[k], counts[k]: the accepted pairs of the ordered pair
+ * k = i (N-1) + (j < i ? j : j - 1).  Returns the number of dense terms, or
+ * -1 on a pixel index out of range. */
+long orc_normal_equations_frozen(const orc_frame* frames, int n_frames, const double* poses,
+                                 const orc_match_set* sets, int n_sets, const orc_params* prm,
+                                 const int32_t* const* src_pix, const int32_t* const* tgt_pix,
+                                 const int32_t* counts, int n_threads, double* H, double* g, double* energy);
 
 /* Iteratively re-weighted Gauss-Newton (Sec. IV-D): `iters` iterations of
  * associate -> normal equations -> Cholesky (or, with prm->solver == 1, the

@@ -79,6 +79,26 @@ def test_p1_association_matches_visibility(clean_box):
     visible &= (uj >= 0) & (uj < cam.width) & (vj >= 0) & (vj < cam.height)
     n_vis = int(visible.sum())
     assert 0.9 * n_vis <= len(sp) <= n_vis
+    # exactly which: a visible pixel is kept when its nearest target pixel
+    # images the same box face (analytic normals of the renderer agree) within
+    # d_max (clean FP64 depths); only decisions within single-precision
+    # rounding of a boundary may go either way
+    src_all = np.flatnonzero(g.mask(i).ravel())
+    tgt = (vj * cam.width + uj).astype(np.int64)
+    tgt[~visible] = 0
+    nt_true = g.renders[j].normals_true.reshape(-1, 3)[tgt]
+    ns_true = g.renders[i].normals_true.reshape(-1, 3)[src_all] @ Tji[:3, :3].T
+    tv2, tu2 = np.divmod(tgt, cam.width)
+    zt2 = g.renders[j].depth_clean.ravel()[tgt]
+    Qt = np.stack([(tu2 - cam.cx) * zt2 / cam.fx, (tv2 - cam.cy) * zt2 / cam.fy, zt2], -1)
+    expect = visible & (g.mask(j).ravel()[tgt] > 0) & ((ns_true * nt_true).sum(-1) > 0.999) & \
+        (np.linalg.norm(Qt - Xj, axis=1) <= PARAMS.dense_max_dist)
+    c = O.associate_classified(g, i, j, P, PARAMS)
+    assert np.array_equal(c.src, src_all)
+    got = c.nominal >= 0
+    differ = got != expect
+    assert not (differ & ~c.ambiguous).any(), int((differ & ~c.ambiguous).sum())
+    assert np.array_equal(c.nominal[got & expect], tgt[got & expect])
     # geometric check of every kept pair (independent back-projection)
     tv, tu = np.divmod(tp, cam.width)
     zt = g.renders[j].depth_clean[tv, tu]
