@@ -347,10 +347,15 @@ int bt_warmstart_apply_batch(bt_warmstart* ws, bt_batch* b, int32_t* status_out)
  * warm start to every graph of b, runs `iters` Gauss-Newton iterations of the
  * batch (bt_batch_solve), and re-solves with `fallback_iters` plain
  * iterations (bt_solve, from the poses stored before the call) every graph
- * whose solve failed or whose final cost exceeds (1 + tol) * ref_costs[k]
- * (ref_costs: the plain solve's final costs, one per graph in batch order;
- * NULL = fall back only on failure).  reps: NULL or bt_batch_size() reports
- * with used_warmstart / fell_back set.  Synchronises the batch stream.
+ * whose solve failed or that fails the acceptance rule:
+ *   ref_costs != NULL (the plain solve's final costs, one per graph in batch
+ *     order): the final cost exceeds (1 + tol) * ref_costs[k];
+ *   ref_costs == NULL (a rule that needs no plain solve): the last
+ *     warm-started iteration changed the cost by more than tol times the
+ *     final cost, |E_{iters-1} - E_iters| > tol E_iters -- the iterations had
+ *     not converged (with iters == 0 only failures fall back).
+ * reps: NULL or bt_batch_size() reports with used_warmstart / fell_back set.
+ * Synchronises the batch stream.
  * Errors: BT_ERR_INVALID, BT_ERR_STATE, BT_ERR_SINGULAR, BT_ERR_CUDA, BT_ERR_OOM. */
 int bt_batch_solve_warm(bt_batch* b, bt_warmstart* ws, int32_t iters, int32_t fallback_iters,
                         const double* ref_costs, double tol, bt_solve_report* reps);
@@ -405,6 +410,39 @@ int32_t bt_select_keyframes(const double* pool_poses, int32_t n_pool, const doub
  * entry exceeds min_deg degrees (the paper uses 10), else 0; a negative
  * status on bad arguments. */
 int32_t bt_is_novel_view(const double* pool_poses, int32_t n_pool, const double* pose_current, double min_deg);
+
+/* ------------------------------------------------------------ diagnostics
+ * Intermediate results of a Gauss-Newton iteration of bt_solve at the stored
+ * poses of the active nodes, computed by the solve's own kernels, so that an
+ * independent implementation can be compared with them value by value.  No
+ * paper counterpart; the stored poses are not changed. */
+
+/* The dense association of the ordered pair (src_node -> dst_node), both
+ * indices in the active node order (Eq. 3 and the gating sentence after it,
+ * Sec. IV-D): for every valid masked pixel of src_node, in increasing pixel
+ * order, the pixel v * width + u of dst_node that the residual pass
+ * associates it with, or -1 when it is dropped (projection behind the
+ * camera or outside the image, invalid target pixel, distance gate, angle
+ * gate).  tgt_out: host array of cap entries, or NULL to query the count
+ * only; *count_out (may be NULL) receives the number of valid source
+ * pixels, also when cap is too small.  Synchronises the stream.
+ * Errors: BT_ERR_INVALID (NULL graph, node out of range, src_node ==
+ * dst_node, cap smaller than the count), BT_ERR_CUDA, BT_ERR_OOM. */
+int bt_debug_associate(bt_graph* g, int32_t src_node, int32_t dst_node, int32_t* tgt_out, int32_t cap,
+                       int32_t* count_out);
+
+/* The normal equations H dx = -g of one Gauss-Newton iteration at the stored
+ * poses (Sec. IV-D), exactly as bt_solve assembles them before its FP64
+ * factorisation: n = 6 x (free active nodes) unknowns, right perturbations
+ * T_i <- T_i exp(dx_i), dx_i = (v, w) (translation first), free nodes in
+ * active order.  H_out: n x n row-major, symmetric; g_out: n; both host.
+ * cost_out (4 doubles, may be NULL): E of Eq. 1, its dense part, its sparse
+ * part and the number of accepted dense associations at those poses.
+ * *n_out (may be NULL) receives n, also when n_cap < n.  Synchronises the
+ * stream.  Errors: BT_ERR_INVALID (NULL graph or output, n_cap < n, no free
+ * node), BT_ERR_CUDA, BT_ERR_OOM. */
+int bt_debug_normal_equations(bt_graph* g, double* H_out, double* g_out, int32_t n_cap, int32_t* n_out,
+                              double* cost_out);
 
 /* Profiling counters of one graph (the tracing facility; no paper
  * counterpart).  Launch counts are always kept; kernel durations are summed
@@ -464,9 +502,9 @@ int64_t bt_device_cache_trim(void);
  * loops where cudaMalloc/cudaFree would synchronise the device and stall
  * other streams, and embedders working under a fixed device-memory budget.
  *
- * It computes lambda_2 (E_g(a,b) + E_g(b,a)) of Eq. 1/Eq. 3 -- the dense part
- * of bt_eval_cost for a graph of these two frames -- straight from the
- * caller's buffers, with the same association rule, gates and Huber loss.
+ * It computes the dense part of bt_eval_cost (cost_out[1]) for a graph made
+ * of these two frames, straight from the caller's buffers, with the same
+ * association decisions, gates and Huber loss as the residual pass.
  *   depth_x, normals_x, mask_x: DEVICE pointers (H x W, H x W x 3, H x W);
  *   Kx, pose_x, cfg: host memory (cfg may be NULL for the defaults);
  *   out: DEVICE pointer to 2 doubles, receives the energy and the number of

@@ -120,6 +120,10 @@ SIGNATURES = {
     "bt_select_keyframes": (C.c_int32, [C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_double), C.c_int32,
                                         C.POINTER(C.c_int32)]),
     "bt_is_novel_view": (C.c_int32, [C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_double), C.c_double]),
+    "bt_debug_associate": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.c_int32,
+                                     C.POINTER(C.c_int32)]),
+    "bt_debug_normal_equations": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int32,
+                                            C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
     "bt_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "bt_profile_read": (C.c_int, [C.c_void_p, C.POINTER(bt_profile)]),
     "bt_device_cache_bytes": (C.c_int64, []),
@@ -319,6 +323,37 @@ class PoseGraph:
         out = {k: getattr(p, k) for k, _ in bt_profile._fields_}
         out["solve_phase_cycles"] = list(p.solve_phase_cycles)
         return out
+
+    def debug_associate(self, src_node: int, dst_node: int) -> np.ndarray:
+        """bt_debug_associate: target pixel (or -1) of every valid source
+        pixel of active node src_node (increasing pixel order) against
+        dst_node, at the stored poses."""
+        L = load()
+        cnt = C.c_int32(0)
+        _check(L.bt_debug_associate(self._h, int(src_node), int(dst_node), None, 0, C.byref(cnt)),
+               "bt_debug_associate")
+        out = np.zeros(max(1, cnt.value), np.int32)
+        _check(L.bt_debug_associate(self._h, int(src_node), int(dst_node),
+                                    out.ctypes.data_as(C.POINTER(C.c_int32)), len(out), C.byref(cnt)),
+               "bt_debug_associate")
+        return out[:cnt.value].copy()
+
+    def debug_normal_equations(self):
+        """bt_debug_normal_equations: (H (n,n), g (n,), costs dict) of one
+        Gauss-Newton iteration at the stored poses, right perturbations of the
+        free nodes in active order; the poses are not changed."""
+        L = load()
+        n = C.c_int32(0)
+        cap = 6 * BT_MAX_NODES
+        H = np.zeros((cap, cap))
+        g = np.zeros(cap)
+        c = (C.c_double * 4)()
+        _check(L.bt_debug_normal_equations(self._h, H.ctypes.data_as(C.POINTER(C.c_double)),
+                                           g.ctypes.data_as(C.POINTER(C.c_double)), cap, C.byref(n), c),
+               "bt_debug_normal_equations")
+        m = n.value
+        Hm = H.reshape(-1)[:m * m].reshape(m, m).copy()
+        return Hm, g[:m].copy(), dict(total=c[0], dense=c[1], sparse=c[2], dense_inliers=int(round(c[3])))
 
     def eval_cost(self):
         c = (C.c_double * 3)()
@@ -577,15 +612,48 @@ class WarmStart:
             pass
 
 
+def noalloc_argument_error(torch, device: int, size_a, size_b, depth_a, normals_a, mask_a, depth_b, normals_b,
+                           mask_b, out) -> str:
+    """What is wrong with the buffers of a bt_pair_dense_energy_noalloc call
+    ("" if nothing): each must be a contiguous CUDA tensor on `device`; depth
+    float32 with W*H elements, normals float32 with 3*W*H, mask uint8 or bool
+    with W*H, out float64 with at least 2.  The C call reads and writes them by
+    pointer and cannot check any of this itself."""
+    named = (("depth_a", depth_a), ("normals_a", normals_a), ("mask_a", mask_a), ("depth_b", depth_b),
+             ("normals_b", normals_b), ("mask_b", mask_b), ("out", out))
+    for name, x in named:
+        if not (getattr(x, "is_cuda", False) and x.is_contiguous()):
+            return f"{name} must be a contiguous CUDA tensor"
+        if x.device.index != device:
+            return f"{name} is on {x.device}, not cuda:{device}"
+    for tag, (w, h), d, n, m in (("a", size_a, depth_a, normals_a, mask_a), ("b", size_b, depth_b, normals_b,
+                                                                               mask_b)):
+        hw = int(w) * int(h)
+        if d.dtype != torch.float32 or d.numel() != hw:
+            return f"depth_{tag} must be float32 with W*H = {hw} elements"
+        if n.dtype != torch.float32 or n.numel() != 3 * hw:
+            return f"normals_{tag} must be float32 with 3*W*H = {3 * hw} elements"
+        if m.dtype not in (torch.uint8, torch.bool) or m.numel() != hw:
+            return f"mask_{tag} must be uint8 or bool with W*H = {hw} elements"
+    if out.dtype != torch.float64 or out.numel() < 2:
+        return "out must be float64 with at least 2 elements"
+    return ""
+
+
 def pair_dense_energy_noalloc(depth_a, normals_a, mask_a, intr_a, pose_a, depth_b, normals_b, mask_b, intr_b,
                               pose_b, out, config: bt_config | None = None, stream=None):
     """bt_pair_dense_energy_noalloc: all image buffers and `out` (2 float64)
-    must be CUDA tensors; enqueues on `stream` and returns immediately."""
-    for x in (depth_a, normals_a, mask_a, depth_b, normals_b, mask_b, out):
-        if not (_is_torch(x) and x.is_cuda and x.is_contiguous()):
-            raise ValueError("bt_pair_dense_energy_noalloc takes contiguous CUDA tensors")
+    must be contiguous CUDA tensors on the current device -- depth float32
+    with W*H elements, normals float32 with 3*W*H, mask uint8 or bool with
+    W*H, out float64 with at least 2 -- since the C call reads and writes
+    them by pointer; enqueues on `stream` and returns immediately."""
+    import torch
     Ka = bt_intrinsics(*intr_a)
     Kb = bt_intrinsics(*intr_b)
+    err = noalloc_argument_error(torch, torch.cuda.current_device(), (Ka.width, Ka.height), (Kb.width, Kb.height),
+                                 depth_a, normals_a, mask_a, depth_b, normals_b, mask_b, out)
+    if err:
+        raise ValueError("bt_pair_dense_energy_noalloc: " + err)
     Pa = np.ascontiguousarray(pose_a, np.float64).reshape(16)
     Pb = np.ascontiguousarray(pose_b, np.float64).reshape(16)
     cfg = config if config is not None else config_default()

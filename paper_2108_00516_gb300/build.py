@@ -19,7 +19,7 @@ BUILD = PKG / "_build"
 LIB = BUILD / "libbt.so"
 INCLUDE = ROOT / "include"
 SOURCES = sorted(CSRC.glob("*.cu"))
-HEADERS = sorted(CSRC.glob("*.h")) + sorted(INCLUDE.glob("*.h"))
+HEADERS = sorted(CSRC.glob("*.h")) + sorted(CSRC.glob("*.cuh")) + sorted(INCLUDE.glob("*.h"))
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

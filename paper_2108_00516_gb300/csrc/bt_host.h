@@ -257,6 +257,7 @@ struct bt_graph {
     // pairs, pair -> edge) in one device block staged through pinned memory,
     // the solve state block (StateLayout) likewise, and the work buffers
     bthost::DevBuf d_tab, d_state, d_xf, d_xinv, d_dpart, d_spart, d_upairblk;
+    bthost::DevBuf d_debug;             // outputs of the diagnostic calls
     bthost::PinBuf pin_tab, pin_state;
     bthost::PinBuf pin_match;           // staging of the correspondence sets given to bt_add_frame
     bt::SolveArgs args{};
@@ -284,7 +285,7 @@ struct bt_graph {
         pin_match.release();
         for (cudaEvent_t e : events) cudaEventDestroy(e);
         for (bthost::DevBuf* b : {&up_depth, &up_normals, &up_mask, &prep_blk, &d_tab, &d_state, &d_xf, &d_xinv,
-                                  &d_dpart, &d_spart, &d_upairblk})
+                                  &d_dpart, &d_spart, &d_upairblk, &d_debug})
             b->release();
     }
 };

@@ -104,6 +104,7 @@ struct SolveArgs {
     double* upairblk;   // [U][96]
     Control* ctrl;
     double* costs;      // [iter][4]: total, dense, sparse, dense count
+    double* ne_out;     // NULL, or [n*n + n]: the assembled H and g are written here instead of solving
 };
 
 // Programmatic dependent launch.  The kernels of a solve form one chain per
@@ -160,6 +161,10 @@ cudaError_t launch_xforms(const SolveArgs& a, cudaStream_t s);
 // full = false: cost only, recorded at slot `iter`.
 cudaError_t launch_residual(const SolveArgs& a, bool full, cudaStream_t s, int shape = 0);
 cudaError_t launch_reduce(const SolveArgs& a, bool full, int iter, cudaStream_t s);
+
+// Diagnostic export: target pixel (or -1) of every source entry of node i
+// against node j at the current transforms (out: device, nodes[i].M ints).
+cudaError_t launch_assoc_debug(const SolveArgs& a, int i, int j, int M, int* out, cudaStream_t s);
 
 size_t reduce_smem_bytes(int n_free, int N);
 bool reduce_stage_fits(int n_free, int N);

@@ -14,6 +14,7 @@
 // cleared at the start of each call.  Calls whose GPU work overlaps (two
 // streams, or two host threads) race on it.
 #include "bt.h"
+#include "bt_assoc.cuh"
 
 #include <cuda_runtime.h>
 
@@ -46,15 +47,15 @@ NoAllocScratch* g_scratch_ptr[kMaxDevices] = {};
 std::mutex g_scratch_mu;
 
 struct Xf {
-    float ab[12];   // camera a -> camera b
-    float ba[12];   // camera b -> camera a
+    bt::PairK kab;   // camera a -> camera b
+    bt::PairK kba;   // camera b -> camera a
 };
 
 struct View {
     const float* depth;
     const float* normals;
     const uint8_t* mask;
-    float fx, fy, cx, cy, ifx, ify, Wf, Hf;
+    float fx, fy, cx, cy, ifx, ify;
     int W, H;
 };
 
@@ -71,9 +72,9 @@ __device__ __forceinline__ bool valid_px(const View& v, int pix, float& z, float
 
 // One direction per half of the grid: CTAs [0, nb_a) take source frame a and
 // target b, CTAs [nb_a, nb_a + nb_b) the reverse.  The association decision
-// follows the library's single-precision specification exactly (see the
-// residual kernel); the energy is the Huber sum of the accepted
-// point-to-plane residuals times lambda_2.
+// and the residual are the residual pass's own device functions
+// (bt_assoc.cuh); the energy is the Huber sum of the accepted point-to-plane
+// residuals times lambda_2.
 __global__ void __launch_bounds__(kNoAllocThreads) pair_energy_kernel(
     NoAllocScratch* scr, View va, View vb, Xf xf, int nb_a, float dmax2, float cmin, float hub, double lambda,
     double* out)
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(kNoAllocThreads) pair_energy_kernel(
     const bool rev = (int)blockIdx.x >= nb_a;
     const View& src = rev ? vb : va;
     const View& dst = rev ? va : vb;
-    const float* m = rev ? xf.ba : xf.ab;
+    const bt::PairK& K = rev ? xf.kba : xf.kab;
     const int blk = rev ? blockIdx.x - nb_a : blockIdx.x;
     float e = 0.f, cnt = 0.f;
     const int HW = src.W * src.H;
@@ -94,32 +95,21 @@ __global__ void __launch_bounds__(kNoAllocThreads) pair_energy_kernel(
         float z, nx, ny, nz;
         if (!valid_px(src, pix, z, nx, ny, nz)) continue;
         const int u = pix % src.W, v = pix / src.W;
-        const float px = __fmul_rn(__fmul_rn(__fsub_rn((float)u, src.cx), z), src.ifx);
-        const float py = __fmul_rn(__fmul_rn(__fsub_rn((float)v, src.cy), z), src.ify);
-        const float pz = z;
-        const float qx = __fmaf_rn(m[2], pz, __fmaf_rn(m[1], py, __fmaf_rn(m[0], px, m[3])));
-        const float qy = __fmaf_rn(m[6], pz, __fmaf_rn(m[5], py, __fmaf_rn(m[4], px, m[7])));
-        const float qz = __fmaf_rn(m[10], pz, __fmaf_rn(m[9], py, __fmaf_rn(m[8], px, m[11])));
-        if (!(qz > 0.f)) continue;
-        const float rz = __frcp_rn(qz);
-        const float uh = __fadd_rn(__fmaf_rn(__fmul_rn(dst.fx, qx), rz, dst.cx), 0.5f);
-        const float vh = __fadd_rn(__fmaf_rn(__fmul_rn(dst.fy, qy), rz, dst.cy), 0.5f);
-        if (!(uh >= 0.f && uh < dst.Wf && vh >= 0.f && vh < dst.Hf)) continue;
-        const int iu = (int)floorf(uh), iv = (int)floorf(vh);
+        // pi_D^-1(x) as the frame preparation of the graph path computes it
+        const float px = ((float)u - src.cx) * z * src.ifx;
+        const float py = ((float)v - src.cy) * z * src.ify;
+        float2 qxy;
+        float qz;
+        int iu, iv;
+        if (!bt::assoc_project(K, px, py, z, qxy, qz, iu, iv)) continue;
         const int tp = iv * dst.W + iu;
         float tz, tnx, tny, tnz;
         if (!valid_px(dst, tp, tz, tnx, tny, tnz)) continue;
-        const float tx = __fmul_rn(__fmul_rn(__fsub_rn((float)iu, dst.cx), tz), dst.ifx);
-        const float ty = __fmul_rn(__fmul_rn(__fsub_rn((float)iv, dst.cy), tz), dst.ify);
-        const float dx = __fsub_rn(tx, qx), dy = __fsub_rn(ty, qy), dz = __fsub_rn(tz, qz);
-        const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-        if (!(d2 <= dmax2)) continue;
-        const float njx = __fmaf_rn(m[2], nz, __fmaf_rn(m[1], ny, __fmul_rn(m[0], nx)));
-        const float njy = __fmaf_rn(m[6], nz, __fmaf_rn(m[5], ny, __fmul_rn(m[4], nx)));
-        const float njz = __fmaf_rn(m[10], nz, __fmaf_rn(m[9], ny, __fmul_rn(m[8], nx)));
-        const float cs = __fmaf_rn(njz, tnz, __fmaf_rn(njy, tny, __fmul_rn(njx, tnx)));
-        if (!(cs >= cmin)) continue;
-        const float r = fmaf(njx, dx, fmaf(njy, dy, njz * dz));
+        float2 txy, dxy, nxy;
+        float dz, nzr;
+        if (!bt::assoc_distance(K, iu, iv, tz, qxy, qz, dmax2, txy, dxy, dz)) continue;
+        if (!bt::assoc_normal(K, nx, ny, nz, tnx, tny, tnz, cmin, nxy, nzr)) continue;
+        const float r = bt::assoc_residual(nxy, nzr, dxy, dz);
         const float ar = fabsf(r);
         e += ar <= hub ? 0.5f * r * r : hub * (ar - 0.5f * hub);
         cnt += 1.f;
@@ -258,16 +248,17 @@ extern "C" int bt_pair_dense_energy_noalloc(const float* depth_a, const float* n
         v.fx = K->fx; v.fy = K->fy; v.cx = K->cx; v.cy = K->cy;
         v.ifx = 1.0f / K->fx;
         v.ify = 1.0f / K->fy;
-        v.Wf = (float)K->width;
-        v.Hf = (float)K->height;
         v.W = K->width;
         v.H = K->height;
         return v;
     };
     const View va = view(depth_a, normals_a, mask_a, Ka), vb = view(depth_b, normals_b, mask_b, Kb);
     Xf xf;
-    pair_transform(pose_a, pose_b, xf.ab);
-    pair_transform(pose_b, pose_a, xf.ba);
+    float mab[12], mba[12];
+    pair_transform(pose_a, pose_b, mab);
+    pair_transform(pose_b, pose_a, mba);
+    xf.kab = bt::make_pair_k(mab, vb.fx, vb.fy, vb.cx, vb.cy, vb.ifx, vb.ify, vb.W, vb.H);
+    xf.kba = bt::make_pair_k(mba, va.fx, va.fy, va.cx, va.cy, va.ifx, va.ify, va.W, va.H);
     const int nb_a = (Ka->width * Ka->height + kNoAllocBlockPix - 1) / kNoAllocBlockPix;
     const int nb_b = (Kb->width * Kb->height + kNoAllocBlockPix - 1) / kNoAllocBlockPix;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);

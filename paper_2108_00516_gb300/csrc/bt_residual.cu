@@ -21,19 +21,22 @@
 // -K' to (i,j), (j,i).
 //
 // Association decision.  Keep / drop and the looked-up pixel are integers
-// decided in IEEE single precision with the operation order below: fused
-// multiply-adds exactly where written (__fmaf_rn), every other operation
-// rounded on its own (__fmul_rn / __fadd_rn / __fsub_rn / __frcp_rn), so that
-// the same single-precision inputs always give the same decisions as any
-// other implementation of the same specification.  Residual values,
-// Jacobians and weights use ordinary FP32 arithmetic.
+// decided in single precision by the device functions of bt_assoc.cuh (fused
+// multiply-adds, the hardware reciprocal, packed FP32x2 arithmetic).  Another
+// single-precision evaluation -- or the exact one -- can differ from it only
+// for pixels within rounding of a half-pixel edge, the image edge or a gate;
+// bt_debug_associate exports the decisions so that they can be checked pixel
+// by pixel.  Residual values, Jacobians and weights are FP32 as well.
 #include "bt_internal.h"
+#include "bt_assoc.cuh"
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+
+#include <algorithm>
 
 namespace bt {
 
@@ -202,9 +205,9 @@ __global__ void __launch_bounds__(kThreads) prep_write_kernel(
         const int pix = base + k;
         const int u = pix % W, v = pix / W;
         const float z = zz[k];
-        // pi_D^-1(x): ((u - cx) z) * (1/fx), ((v - cy) z) * (1/fy), z
-        const float px = __fmul_rn(__fmul_rn(__fsub_rn((float)u, cx), z), ifx);
-        const float py = __fmul_rn(__fmul_rn(__fsub_rn((float)v, cy), z), ify);
+        // pi_D^-1(x): (u - cx) z / fx, (v - cy) z / fy, z
+        const float px = ((float)u - cx) * z * ifx;
+        const float py = ((float)v - cy) * z * ify;
         if constexpr (P == 0) {
             reinterpret_cast<float4*>(src_p_v)[off] = make_float4(px, py, z, 0.f);
             reinterpret_cast<float4*>(src_n_v)[off] = make_float4(nn[k].x, nn[k].y, nn[k].z, 0.f);
@@ -244,13 +247,20 @@ cudaError_t launch_prep(const float* depth, const float* normals, const uint8_t*
 // Residual pass
 // ---------------------------------------------------------------------------
 
+// Per-target constants of a tile, staged in shared memory by the CTA.
 struct PairConst {
-    float m[12];                         // camera i -> camera j (single)
-    float fx, fy, cx, cy, ifx, ify;
-    float zref;                          // target frame's reference depth (16-bit maps)
-    int W, H;
+    PairK k;
     const void* tgt;
+    float zref;                          // target frame's reference depth (16-bit maps)
 };
+
+__device__ __forceinline__ void fill_pair_const(const SolveArgs& a, int i, int j, PairConst& c)
+{
+    const NodeDev Nj = a.nodes[j];
+    c.k = make_pair_k(a.xf + (size_t)(i * a.N + j) * 12, Nj.fx, Nj.fy, Nj.cx, Nj.cy, Nj.ifx, Nj.ify, Nj.W, Nj.H);
+    c.tgt = Nj.tgt;
+    c.zref = Nj.zref;
+}
 
 // Target-map gather: (z, nx, ny, nz) as FP32 whatever the storage.
 template <int P>
@@ -302,44 +312,36 @@ size_t residual_smem_bytes(int N, int shape)
            sizeof(float) * (size_t)nt * (kShapeThreads[shape] / 32) * kDenseVals;
 }
 
-// Packed single-precision FMA on two lanes of a 64-bit register pair:
-// (c0, c1) += (a0, a1) * (b0, b1).
-__device__ __forceinline__ void ffma2(float& c0, float& c1, float a0, float a1, float b0, float b1)
-{
-    asm("{\n\t.reg .b64 ra, rb, rc;\n\t"
-        "mov.b64 ra, {%2, %3};\n\t"
-        "mov.b64 rb, {%4, %5};\n\t"
-        "mov.b64 rc, {%0, %1};\n\t"
-        "fma.rn.f32x2 rc, ra, rb, rc;\n\t"
-        "mov.b64 {%0, %1}, rc;\n\t}"
-        : "+f"(c0), "+f"(c1)
-        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
-}
-
 // acc[0..20] += w J J^T (upper triangle, row-major), acc[21..26] += w J r,
-// acc[27] += rho, acc[28] += 1.  Two entries per packed FMA: rows (0,1),
-// (2,3), (4,5) of the same column share the broadcast J_b.
-__device__ __forceinline__ void accumulate_pair(float (&acc)[kDenseVals], const float (&J)[6], float w, float r,
-                                                float rho)
+// acc[27] += rho, acc[28] += 1, two entries per packed FP32x2 FMA: rows
+// (0,1), (2,3), (4,5) of one column share the broadcast J_b.
+__device__ __forceinline__ void accumulate_pair(float (&acc)[kDenseVals], float2 J01, float2 J23, float2 J45, float w,
+                                                float r, float rho)
 {
-    float wJ[6];
+    const float2 ww = make_float2(w, w);
+    const float2 w01 = __fmul2_rn(J01, ww), w23 = __fmul2_rn(J23, ww), w45 = __fmul2_rn(J45, ww);
+    const float J[6] = {J01.x, J01.y, J23.x, J23.y, J45.x, J45.y};
+    auto f2 = [&](int lo, int hi, float2 a, float b) {
+        const float2 s = __ffma2_rn(a, make_float2(b, b), make_float2(acc[lo], acc[hi]));
+        acc[lo] = s.x;
+        acc[hi] = s.y;
+    };
+    // upper-triangle index of (a, b), b >= a: (0,b) = b, (1,b) = 5 + b,
+    // (2,b) = 9 + b, (3,b) = 12 + b, (4,b) = 14 + b, (5,5) = 20
+    acc[0] = fmaf(w01.x, J[0], acc[0]);
 #pragma unroll
-    for (int q = 0; q < 6; ++q) wJ[q] = w * J[q];
-    // upper-triangle indices: row a, column b >= a
-    // (0,b) = b, (1,b) = 5 + b, (2,b) = 9 + b, (3,b) = 12 + b, (4,b) = 14 + b, (5,5) = 20
-    acc[0] = fmaf(wJ[0], J[0], acc[0]);
+    for (int b = 1; b < 6; ++b) f2(b, 5 + b, w01, J[b]);
+    acc[11] = fmaf(w23.x, J[2], acc[11]);
 #pragma unroll
-    for (int b = 1; b < 6; ++b) ffma2(acc[b], acc[5 + b], wJ[0], wJ[1], J[b], J[b]);
-    acc[11] = fmaf(wJ[2], J[2], acc[11]);
-#pragma unroll
-    for (int b = 3; b < 6; ++b) ffma2(acc[9 + b], acc[12 + b], wJ[2], wJ[3], J[b], J[b]);
-    acc[18] = fmaf(wJ[4], J[4], acc[18]);
-    ffma2(acc[19], acc[20], wJ[4], wJ[5], J[5], J[5]);
-    ffma2(acc[21], acc[22], wJ[0], wJ[1], r, r);
-    ffma2(acc[23], acc[24], wJ[2], wJ[3], r, r);
-    ffma2(acc[25], acc[26], wJ[4], wJ[5], r, r);
-    acc[27] += rho;
-    acc[28] += 1.f;
+    for (int b = 3; b < 6; ++b) f2(9 + b, 12 + b, w23, J[b]);
+    acc[18] = fmaf(w45.x, J[4], acc[18]);
+    f2(19, 20, w45, J[5]);
+    f2(21, 22, w01, r);
+    f2(23, 24, w23, r);
+    f2(25, 26, w45, r);
+    const float2 s = __fadd2_rn(make_float2(acc[27], acc[28]), make_float2(rho, 1.f));
+    acc[27] = s.x;
+    acc[28] = s.y;
 }
 
 // Pixels per thread whose target gathers are issued together, and resident
@@ -348,27 +350,28 @@ __device__ __forceinline__ void accumulate_pair(float (&acc)[kDenseVals], const 
 constexpr int residual_batch(int P) { return P == 0 ? 2 : 4; }
 constexpr int residual_threads_per_sm(int P) { return P == 0 ? 768 : 640; }
 
-// One tile of source pixels of node i against every other node j.  Per target
-// each thread takes its kB pixels as one batch that goes through three
-// phases -- projection and bounds, the four target gathers (all
-// in flight together), then gates, residual, Jacobian and accumulation.  The
-// warp's 32 sums are parked in shared memory; one barrier at the end, then
-// the (N-1) x 32 block sums are written to dpart[tile][j'].
+// One tile of kT x kB source pixels of node i against every other node j.
+// The work of the tile is (N-1) x kW units -- unit (jj, c) = target jj, chunk
+// c of 32 x kB consecutive tile pixels -- in target-major order, and warp w
+// takes the N-1 consecutive units [w (N-1), (w+1) (N-1)).  A warp keeps its
+// 21 + 6 + 2 sums in registers while its units stay on one target and
+// reduces them across its lanes (a 31-shuffle reduce-scatter) only when the
+// target changes: about (N-1)/kW + 1 reductions per warp instead of N-1.
+// Per unit each lane takes its kB pixels in batches that go through three
+// phases -- projection and bounds, the target gathers of the batch (all in
+// flight together), then gates, residual, Jacobian and accumulation.  The
+// warp totals are parked in shared memory; one barrier at the end, then the
+// (N-1) x 32 block sums of the tile are written to dpart[tile][jj] (each
+// the sum, in warp order, of the warps that covered that target).
 template <bool kFull, int kT, int kB, int P>
 __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
 {
     constexpr int kW = kT / 32;
     constexpr int kTile = kT * kB;
-    constexpr int kResThreads = kT;
-    // FP32 maps: two pixels per batch, their gathers in flight together; the
-    // registers this leaves free buy a sixth resident 128-thread CTA per SM
-    // (768 threads), which hides the gathers' latency better than four pixels
-    // per batch at five CTAs.  16-bit maps (more registers for the widening)
-    // keep four pixels per batch at five CTAs.  The batch loop is unrolled,
-    // so a batch's gathers may be issued while the previous batch computes.
-    constexpr int kResBatch = kB < residual_batch(P) ? kB : residual_batch(P);
-    constexpr int kResBatches = kB / kResBatch;
-    static_assert(kResBatch * kResBatches == kB, "pixels per thread: 1 or even");
+    constexpr int kUnit = 32 * kB;
+    constexpr int kBatch = kB < residual_batch(P) ? kB : residual_batch(P);
+    constexpr int kBatches = kB / kBatch;
+    static_assert(kBatch * kBatches == kB, "pixels per thread: 1 or even");
     const int N = a.N;
     const int i = a.tile_node[tile];
     const NodeDev Ni = a.nodes[i];
@@ -379,94 +382,78 @@ __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
     float4* sn = sp + kTile;
     PairConst* pc = reinterpret_cast<PairConst*>(sn + kTile);
     float* red = reinterpret_cast<float*>(pc + kMaxNodes);   // [N-1][kW][32]
-    for (int s = threadIdx.x; s < kTile; s += kResThreads) {
+    for (int s = threadIdx.x; s < kTile; s += kT) {
         float4 pp = make_float4(0.f, 0.f, 0.f, 0.f), nn = pp;
         if (s < nvalid) load_source<P>(Ni, base + s, pp, nn);
         sp[s] = pp;
         sn[s] = nn;
     }
-    if (threadIdx.x < N && threadIdx.x != i) {
-        const int j = threadIdx.x;
-        const NodeDev Nj = a.nodes[j];
-        PairConst& c = pc[j];
-#pragma unroll
-        for (int k = 0; k < 12; ++k) c.m[k] = a.xf[(i * N + j) * 12 + k];
-        c.fx = Nj.fx; c.fy = Nj.fy; c.cx = Nj.cx; c.cy = Nj.cy; c.ifx = Nj.ifx; c.ify = Nj.ify;
-        c.W = Nj.W; c.H = Nj.H; c.tgt = Nj.tgt; c.zref = Nj.zref;
-    }
+    if (threadIdx.x < N && threadIdx.x != i) fill_pair_const(a, i, threadIdx.x, pc[threadIdx.x]);
     __syncthreads();
     const float dmax2 = a.dmax2, cmin = a.cmin, hub = a.huber_dense;
-    for (int jj = 0; jj < N - 1; ++jj) {
+    const int M1 = N - 1;
+    int u = warp * M1;
+    const int u_end = u + M1;
+    while (u < u_end) {
+        const int jj = u / kW;
         const int j = jj < i ? jj : jj + 1;
-        const PairConst& c = pc[j];
-        const float m0 = c.m[0], m1 = c.m[1], m2 = c.m[2], m3 = c.m[3];
-        const float m4 = c.m[4], m5 = c.m[5], m6 = c.m[6], m7 = c.m[7];
-        const float m8 = c.m[8], m9 = c.m[9], m10 = c.m[10], m11 = c.m[11];
+        const int u_stop = min(u_end, (jj + 1) * kW);
+        const PairK& K = pc[j].k;
+        const void* tgt = pc[j].tgt;
+        const float zref = pc[j].zref;
         float acc[kDenseVals];
 #pragma unroll
         for (int k = 0; k < kDenseVals; ++k) acc[k] = 0.f;
+        for (; u < u_stop; ++u) {
+            const int c0 = (u - jj * kW) * kUnit;
+            if (c0 >= nvalid) continue;     // chunk past the last valid pixel of the tile
 #pragma unroll
-        for (int bb = 0; bb < kResBatches; ++bb) {
-            // phase 1: T_j T_i^-1 p, pi(.), nearest pixel, bounds
-            float qx[kResBatch], qy[kResBatch], qz[kResBatch];
-            int pix[kResBatch];
+            for (int bb = 0; bb < kBatches; ++bb) {
+                // phase 1: q = M p, nearest pixel, bounds
+                float2 qxy[kBatch];
+                float qz[kBatch];
+                int iu[kBatch], iv[kBatch];
+                bool ok[kBatch];
 #pragma unroll
-            for (int k = 0; k < kResBatch; ++k) {
-                const int s = (bb * kResBatch + k) * kResThreads + threadIdx.x;
-                const float4 p = sp[s];
-                qx[k] = __fmaf_rn(m2, p.z, __fmaf_rn(m1, p.y, __fmaf_rn(m0, p.x, m3)));
-                qy[k] = __fmaf_rn(m6, p.z, __fmaf_rn(m5, p.y, __fmaf_rn(m4, p.x, m7)));
-                qz[k] = __fmaf_rn(m10, p.z, __fmaf_rn(m9, p.y, __fmaf_rn(m8, p.x, m11)));
-                bool ok = s < nvalid && qz[k] > 0.f;
-                const float rz = __frcp_rn(qz[k]);
-                const float uh = __fadd_rn(__fmaf_rn(__fmul_rn(c.fx, qx[k]), rz, c.cx), 0.5f);
-                const float vh = __fadd_rn(__fmaf_rn(__fmul_rn(c.fy, qy[k]), rz, c.cy), 0.5f);
-                // 0 <= uh < W and 0 <= vh < H, tested on floor(uh), floor(vh)
-                // as unsigned integers (the same decision for every float,
-                // NaN and infinities included: they convert out of range)
-                const int iu = __float2int_rd(uh), iv = __float2int_rd(vh);
-                ok = ok && (unsigned)iu < (unsigned)c.W && (unsigned)iv < (unsigned)c.H;
-                pix[k] = ok ? (iv << 16) | iu : -1;
-            }
-            // phase 2: the gathers of the batch in flight together
-            float4 t[kResBatch];
+                for (int k = 0; k < kBatch; ++k) {
+                    const int s = c0 + (bb * kBatch + k) * 32 + lane;
+                    const float4 p = sp[s];
+                    ok[k] = assoc_project(K, p.x, p.y, p.z, qxy[k], qz[k], iu[k], iv[k]) && s < nvalid;
+                }
+                // phase 2: the gathers of the batch in flight together
+                float4 t[kBatch];
 #pragma unroll
-            for (int k = 0; k < kResBatch; ++k) {
-                const int iu = pix[k] & 0xffff, iv = pix[k] >> 16;
-                t[k] = pix[k] >= 0 ? load_target<P>(c.tgt, (size_t)iv * c.W + iu, c.zref)
-                                   : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-            // phase 3: gates, residual, Jacobian, Huber, accumulation
+                for (int k = 0; k < kBatch; ++k)
+                    t[k] = ok[k] ? load_target<P>(tgt, (size_t)iv[k] * K.W + iu[k], zref)
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+                // phase 3: gates, residual, Jacobian, Huber, accumulation
 #pragma unroll
-            for (int k = 0; k < kResBatch; ++k) {
-                if (!(pix[k] >= 0 && t[k].x > 0.f)) continue;
-                const int iu = pix[k] & 0xffff, iv = pix[k] >> 16;
-                const float tz = t[k].x;
-                const float tx = __fmul_rn(__fmul_rn(__fsub_rn((float)iu, c.cx), tz), c.ifx);
-                const float ty = __fmul_rn(__fmul_rn(__fsub_rn((float)iv, c.cy), tz), c.ify);
-                const float dx = __fsub_rn(tx, qx[k]), dy = __fsub_rn(ty, qy[k]), dz = __fsub_rn(tz, qz[k]);
-                const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-                if (!(d2 <= dmax2)) continue;
-                const float4 n = sn[(bb * kResBatch + k) * kResThreads + threadIdx.x];
-                const float nx = __fmaf_rn(m2, n.z, __fmaf_rn(m1, n.y, __fmul_rn(m0, n.x)));
-                const float ny = __fmaf_rn(m6, n.z, __fmaf_rn(m5, n.y, __fmul_rn(m4, n.x)));
-                const float nz = __fmaf_rn(m10, n.z, __fmaf_rn(m9, n.y, __fmul_rn(m8, n.x)));
-                const float cs = __fmaf_rn(nz, t[k].w, __fmaf_rn(ny, t[k].z, __fmul_rn(nx, t[k].y)));
-                if (!(cs >= cmin)) continue;
-                // accepted: r = n_j . (q - T_j T_i^-1 p), the point-to-plane
-                // distance of Eq. 3 expressed in camera j; J~ = (n_j, q x n_j)
-                const float r = fmaf(nx, dx, fmaf(ny, dy, nz * dz));
-                const float ar = fabsf(r);
-                const bool inl = ar <= hub;
-                const float rho = inl ? 0.5f * r * r : hub * (ar - 0.5f * hub);
-                if constexpr (kFull) {
-                    const float w = inl ? 1.f : __fdividef(hub, ar);
-                    const float J[6] = {nx, ny, nz, fmaf(ty, nz, -tz * ny), fmaf(tz, nx, -tx * nz),
-                                        fmaf(tx, ny, -ty * nx)};
-                    accumulate_pair(acc, J, w, r, rho);
-                } else {
-                    acc[27] += rho;
-                    acc[28] += 1.f;
+                for (int k = 0; k < kBatch; ++k) {
+                    if (!(ok[k] && t[k].x > 0.f)) continue;
+                    float2 txy, dxy;
+                    float dz;
+                    if (!assoc_distance(K, iu[k], iv[k], t[k].x, qxy[k], qz[k], dmax2, txy, dxy, dz)) continue;
+                    const float4 n = sn[c0 + (bb * kBatch + k) * 32 + lane];
+                    float2 nxy;
+                    float nz;
+                    if (!assoc_normal(K, n.x, n.y, n.z, t[k].y, t[k].z, t[k].w, cmin, nxy, nz)) continue;
+                    // accepted: r = n' . (t - q), the point-to-plane distance
+                    // of Eq. 3 expressed in camera j; J~ = (n', t x n')
+                    const float r = assoc_residual(nxy, nz, dxy, dz);
+                    const float ar = fabsf(r);
+                    const bool inl = ar <= hub;
+                    const float rho = inl ? 0.5f * r * r : hub * (ar - 0.5f * hub);
+                    if constexpr (kFull) {
+                        const float w = inl ? 1.f : hub * rcp_approx(ar);
+                        const float tz = t[k].x;
+                        const float2 J23 = make_float2(nz, fmaf(txy.y, nz, -tz * nxy.y));
+                        const float2 J45 = make_float2(fmaf(tz, nxy.x, -txy.x * nz), fmaf(txy.x, nxy.y, -txy.y * nxy.x));
+                        accumulate_pair(acc, nxy, J23, J45, w, r, rho);
+                    } else {
+                        const float2 s = __fadd2_rn(make_float2(acc[27], acc[28]), make_float2(rho, 1.f));
+                        acc[27] = s.x;
+                        acc[28] = s.y;
+                    }
                 }
             }
         }
@@ -487,26 +474,26 @@ __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
         }
     }
     __syncthreads();
-    const int nout = (N - 1) * kDenseVals;
-    for (int o = threadIdx.x; o < nout; o += kResThreads) {
+    const int nout = M1 * kDenseVals;
+    for (int o = threadIdx.x; o < nout; o += kT) {
         const int jj = o / kDenseVals, v = o % kDenseVals;
         if (!kFull && v != 27 && v != 28) continue;
+        // warps that covered target jj: units [jj kW, (jj+1) kW), warp = unit / (N-1)
+        const int w0 = (jj * kW) / M1, w1 = ((jj + 1) * kW - 1) / M1;
         float s = 0.f;
         if constexpr (P == 0) {
-#pragma unroll
-            for (int w = 0; w < kW; ++w) s += red[((size_t)jj * kW + w) * kDenseVals + v];
+            for (int w = w0; w <= w1; ++w) s += red[((size_t)jj * kW + w) * kDenseVals + v];
         } else {
             // compensated (Kahan) sum of the warps' block sums
             float cmp = 0.f;
-#pragma unroll
-            for (int w = 0; w < kW; ++w) {
+            for (int w = w0; w <= w1; ++w) {
                 const float y = red[((size_t)jj * kW + w) * kDenseVals + v] - cmp;
                 const float t2 = s + y;
                 cmp = (t2 - s) - y;
                 s = t2;
             }
         }
-        a.dpart[((size_t)tile * (N - 1) + jj) * kDenseVals + v] = s;
+        a.dpart[((size_t)tile * M1 + jj) * kDenseVals + v] = s;
     }
 }
 
@@ -614,6 +601,45 @@ __global__ void __launch_bounds__(kT, residual_threads_per_sm(P) / kT) batch_res
         sparse_edge<kFull>(sa, w.y);
     else
         dense_tile<kFull, kT, kB, P>(sa, w.y - sa.n_edges, dsm);
+}
+
+// Diagnostic export of the association of the ordered pair (i -> j): one
+// thread per source entry, the same decision functions and the same target
+// gather as dense_tile, out[s] = target pixel or -1.
+template <int P>
+__global__ void __launch_bounds__(kThreads) assoc_debug_kernel(SolveArgs a, int i, int j, int* __restrict__ out)
+{
+    pdl_wait_and_release();
+    __shared__ PairConst pc;
+    if (threadIdx.x == 0) fill_pair_const(a, i, j, pc);
+    __syncthreads();
+    const NodeDev Ni = a.nodes[i];
+    const PairK& K = pc.k;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < Ni.M; s += gridDim.x * blockDim.x) {
+        float4 p, n;
+        load_source<P>(Ni, s, p, n);
+        float2 qxy;
+        float qz;
+        int iu, iv;
+        int res = -1;
+        if (assoc_project(K, p.x, p.y, p.z, qxy, qz, iu, iv)) {
+            const float4 t = load_target<P>(pc.tgt, (size_t)iv * K.W + iu, pc.zref);
+            float2 txy, dxy, nxy;
+            float dz, nz;
+            if (t.x > 0.f && assoc_distance(K, iu, iv, t.x, qxy, qz, a.dmax2, txy, dxy, dz) &&
+                assoc_normal(K, n.x, n.y, n.z, t.y, t.z, t.w, a.cmin, nxy, nz))
+                res = iv * K.W + iu;
+        }
+        out[s] = res;
+    }
+}
+
+cudaError_t launch_assoc_debug(const SolveArgs& a, int i, int j, int M, int* out, cudaStream_t s)
+{
+    const int grid = std::max(1, std::min((M + kThreads - 1) / kThreads, 4096));
+    if (a.precision == 1) return launch_chained(assoc_debug_kernel<1>, dim3(grid), dim3(kThreads), 0, s, a, i, j, out);
+    if (a.precision == 2) return launch_chained(assoc_debug_kernel<2>, dim3(grid), dim3(kThreads), 0, s, a, i, j, out);
+    return launch_chained(assoc_debug_kernel<0>, dim3(grid), dim3(kThreads), 0, s, a, i, j, out);
 }
 
 template <int S, int P>

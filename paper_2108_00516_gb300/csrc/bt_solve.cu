@@ -490,6 +490,16 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
         H[(6 * fa + rr) * ld + 6 * fb + cc] = blk((size_t)u * kUPairBlk + 42 + (A < B ? rr * 6 + cc : cc * 6 + rr));
     }
     __syncthreads();
+    if (a.ne_out != nullptr) {
+        // diagnostic export of the assembled system (symmetric H, g = -y);
+        // no solve, no update
+        for (int q = tid; q < n * n; q += nt) {
+            const int r = q / n, c = q - r * n;
+            a.ne_out[q] = r >= c ? H[r * ld + c] : H[c * ld + r];
+        }
+        for (int q = tid; q < n; q += nt) a.ne_out[n * n + q] = -y[q];
+        return;
+    }
     unsigned long long t1 = clock64();
     double* colb = tinv + 12 * kMaxNodes;   // [2][n]
     unsigned long long t2, t3;

@@ -659,8 +659,14 @@ int bt_batch_solve_warm(bt_batch* b, bt_warmstart* ws, int32_t iters, int32_t fa
     int worst = BT_OK;
     for (size_t k = 0; k < G; ++k) {
         r[k].used_warmstart = ws_status[k] == BT_OK ? 1 : 0;
+        // with the plain solve's costs: worse than (1 + tol) times them; else
+        // (the rule needs no plain solve) the last warm-started iteration
+        // still moved the cost by more than tol of its final value, i.e. the
+        // iterations did not converge
+        const double e_last = r[k].cost_final;
+        const bool moving = iters >= 1 && !(std::fabs(r[k].cost_per_iter[iters - 1] - e_last) <= tol * e_last);
         const bool bad = r[k].status != BT_OK ||
-                         (ref_costs && !(r[k].cost_final <= (1.0 + tol) * ref_costs[k]));
+                         (ref_costs ? !(r[k].cost_final <= (1.0 + tol) * ref_costs[k]) : moving);
         if (bad) {
             bt_graph* g = b->graphs[k];
             for (size_t q = 0; q < g->active.size(); ++q)

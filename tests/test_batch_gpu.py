@@ -4,6 +4,7 @@ import pytest
 
 import oracle as O
 import synthgen as S
+from parity_util import oracle_self_spread, pose_err
 
 pytestmark = pytest.mark.gpu
 
@@ -19,12 +20,6 @@ def bt():
     from paper_2108_00516_gb300 import bt as _bt
     _bt.load()
     return _bt
-
-
-def pose_err(A, B):
-    rot = max(S.rotation_angle(a[:3, :3] @ b[:3, :3].T) for a, b in zip(A, B))
-    tr = max(np.abs(a[:3, 3] - b[:3, 3]).max() for a, b in zip(A, B))
-    return rot, tr
 
 
 def _graphs():
@@ -65,16 +60,17 @@ def test_batch_autotuned_matches_oracle(bt):
     shape, us = batch.tuning()
     assert 0 <= shape < bt.BT_NUM_SHAPES and len(us) == bt.BT_NUM_SHAPES and all(u > 0 for u in us)
     for g, pg, r in zip(gs, pgs, reps):
-        # free-running comparison: the stated tolerance plus the motion of the
-        # oracle's own next step (projective re-association keeps the iterate
-        # moving on graphs with many pixels; see test_parity_gpu)
-        ro = O.solve(g, 7)
-        nxt = O.solve(g, 1, poses=ro["poses"])
-        own_rot, own_tr = pose_err(ro["poses"], nxt["poses"])
-        own_cost = abs(nxt["cost_final"] - ro["cost_final"])
+        # free-running comparison: the stated tolerance plus twice the
+        # oracle's own spread from starts moved by 1e-9 rad (projective
+        # re-association makes the iteration discontinuous on graphs with many
+        # pixels; see test_parity_gpu)
+        ro, s_rot, s_tr, s_cost = oracle_self_spread(g, 7)
         rot, tr = pose_err(pg.get_poses(), ro["poses"])
-        assert abs(r["cost_final"] - ro["cost_final"]) <= COST_RTOL * ro["cost_final"] + own_cost
-        assert rot <= ROT_TOL + own_rot and tr <= TRANS_TOL + own_tr
+        dc = abs(r["cost_final"] - ro["cost_final"]) / ro["cost_final"]
+        print(f"\nbatch graph N={len(g.renders)}: GPU vs oracle {rot:.2e} rad {tr:.2e} m cost {dc:.2e}; "
+              f"oracle self-spread {s_rot:.2e} rad {s_tr:.2e} m cost {s_cost:.2e}")
+        assert dc <= COST_RTOL + 2 * s_cost
+        assert rot <= ROT_TOL + 2 * s_rot and tr <= TRANS_TOL + 2 * s_tr
 
 
 def test_batch_replay_and_every_shape(bt):

@@ -2,30 +2,34 @@
 
 Tolerances.  The GPU computes residuals, Jacobians and their block sums in
 FP32 and everything from the 6x6 blocks on in FP64; the oracle is FP64
-throughout.  The association decision (integers) is specified in single
-precision on both sides, so from identical poses the accepted dense
-associations are identical and their count is compared exactly.  Per-pixel
-FP32 residuals carry ~1e-7 relative rounding on coordinates of ~0.5 m, i.e.
-~3e-8 m on residuals of ~1e-3 m; summed over thousands of pixels with random
-signs this is <= 1e-6 of the energy.  The solve tolerances are the ones the
-method's specification states for the FP32 path: relative final cost 1e-5,
-poses 1e-5 rad and 1e-6 m; they apply to every single iteration started from
-identical poses, and to whole solves that converge.
+throughout.  The association decision (integers) is taken in single
+precision on both sides but in different operation orders, so it may differ
+for a pixel within rounding of a half-pixel edge, the image edge or a gate;
+the oracle classifies every pixel (oracle.energy_bounds) and the GPU's count
+must lie in the admissible range, its energy within FP32 rounding plus the
+largest change those pixels can make (index-level and frozen-association
+checks: test_assoc_gpu.py).  Per-pixel FP32 residuals carry ~1e-7 relative
+rounding on coordinates of ~0.5 m, i.e. ~3e-8 m on residuals of ~1e-3 m;
+summed over thousands of pixels with random signs this is <= 1e-6 of the
+energy.  The solve tolerances are the ones the method's specification
+states for the FP32 path: relative final cost 1e-5, poses 1e-5 rad and
+1e-6 m; they apply to every single iteration started from identical poses,
+and to whole solves that converge.
 
 Gauss-Newton with projective re-association at every iteration and no line
 search does not settle on a point on the large graphs: the association set
-changes from one iterate to the next and the iterate keeps moving by
-1e-5..1e-4 rad per step (the energy by ~1e-4 relative) long after it has
-converged to its basin.  Two implementations whose steps differ in the 8th
-digit then follow different paths inside that set.  Whole-solve comparisons
-on those graphs therefore allow, on top of the stated tolerance, the motion
-of the oracle's own last step.
+changes from one iterate to the next, and a start moved by 1e-9 rad leads
+the oracle itself 1e-5..3e-5 rad away within 10 iterations.  The free-running
+comparison on the paper-shaped graph therefore allows, on top of the stated
+tolerance, twice the oracle's own spread from perturbed starts (measured in
+the test); stepwise comparisons hold the stated tolerance unwidened.
 """
 import numpy as np
 import pytest
 
 import oracle as O
 import synthgen as S
+from parity_util import oracle_self_spread, pose_err
 
 pytestmark = pytest.mark.gpu
 
@@ -46,23 +50,28 @@ def bt():
     return _bt
 
 
-def pose_err(A, B):
-    rot = max(S.rotation_angle(a[:3, :3] @ b[:3, :3].T) for a, b in zip(A, B))
-    tr = max(np.abs(a[:3, 3] - b[:3, 3]).max() for a, b in zip(A, B))
-    return rot, tr
+def check_energy(gpu_total, gpu_count, g, P, nodes=None, gpu_dense=None):
+    """The GPU's energy and association count at poses P against the oracle:
+    count within the range single-precision rounding admits, energy within
+    FP32 rounding plus the cost those open decisions can move."""
+    o = O.energy(g, P, nodes=nodes)
+    b = O.energy_bounds(g, P, nodes=nodes)
+    assert b["count_lo"] <= gpu_count <= b["count_hi"], (gpu_count, b)
+    assert b["ambiguous"] <= 5e-3 * max(b["pixels"], 1), b
+    assert abs(gpu_total - o["total"]) <= COST_RTOL_EVAL * o["total"] + b["slack"], (gpu_total, o, b)
+    if gpu_dense is not None:
+        assert abs(gpu_dense - o["dense"]) <= COST_RTOL_EVAL * o["dense"] + b["slack"]
+    return o, b
 
 
 @pytest.mark.parametrize("gid", [0, 1, 2])
 def test_eval_cost_matches_oracle(bt, gid):
-    """Eq. 1 at the same poses: identical association (exact count), energy
-    within FP32 rounding."""
+    """Eq. 1 at the same poses: association count in the admissible range,
+    energy within FP32 rounding (plus the slack of open decisions)."""
     g = S.tiny_graph(gid)
     pg = bt.graph_from_synth(g)
     c = pg.eval_cost()
-    o = O.energy(g, g.pose_init)
-    assert c["dense_inliers"] == o["dense_count"]
-    assert abs(c["total"] - o["total"]) <= COST_RTOL_EVAL * o["total"]
-    assert abs(c["dense"] - o["dense"]) <= COST_RTOL_EVAL * o["dense"]
+    o, b = check_energy(c["total"], c["dense_inliers"], g, g.pose_init, gpu_dense=c["dense"])
     assert abs(c["sparse"] - o["sparse"]) <= COST_RTOL_EVAL * o["sparse"]
 
 
@@ -79,12 +88,11 @@ def test_stepwise_iterations_match_oracle(bt, gid):
         Pg, rg = pg.solve(1)
         ro = O.solve(g, 1, poses=P)
         assert rg["status"] == 0 and ro["status"] == 0
-        assert abs(rg["cost_init"] - ro["cost_per_iter"][0]) <= COST_RTOL_EVAL * ro["cost_per_iter"][0]
+        b0 = O.energy_bounds(g, P)
+        assert abs(rg["cost_init"] - ro["cost_per_iter"][0]) <= COST_RTOL_EVAL * ro["cost_per_iter"][0] + b0["slack"]
         rot, tr = pose_err(Pg, ro["poses"])
         assert rot <= ROT_TOL and tr <= TRANS_TOL, (it, rot, tr)
-        e_o = O.energy(g, Pg)
-        assert rg["dense_inliers"] == e_o["dense_count"]
-        assert abs(rg["cost_final"] - e_o["total"]) <= COST_RTOL_EVAL * e_o["total"]
+        check_energy(rg["cost_final"], rg["dense_inliers"], g, Pg)
         P = Pg
 
 
@@ -96,9 +104,8 @@ def test_solve_matches_oracle_tiny(bt, gid):
     Pg, rg = pg.solve(7)
     ro = O.solve(g, 7)
     rot, tr = pose_err(Pg, ro["poses"])
-    e_at_gpu = O.energy(g, Pg)["total"]
     # the GPU's own energy of its poses is the oracle's energy of them
-    assert abs(rg["cost_final"] - e_at_gpu) <= COST_RTOL_EVAL * e_at_gpu
+    check_energy(rg["cost_final"], rg["dense_inliers"], g, Pg)
     assert abs(rg["cost_final"] - ro["cost_final"]) <= COST_RTOL * ro["cost_final"], (rot, tr)
     assert rot <= ROT_TOL and tr <= TRANS_TOL
 
@@ -118,30 +125,34 @@ def test_stepwise_paper_shaped(bt, paper):
         pg.set_poses(P)
         Pg, rg = pg.solve(1)
         ro = O.solve(g, 1, poses=P)
-        assert abs(rg["cost_init"] - ro["cost_per_iter"][0]) <= COST_RTOL_EVAL * ro["cost_per_iter"][0]
+        b0 = O.energy_bounds(g, P)
+        assert abs(rg["cost_init"] - ro["cost_per_iter"][0]) <= COST_RTOL_EVAL * ro["cost_per_iter"][0] + b0["slack"]
         rot, tr = pose_err(Pg, ro["poses"])
         assert rot <= ROT_TOL and tr <= TRANS_TOL, (it, rot, tr)
-        e_o = O.energy(g, Pg)
-        assert rg["dense_inliers"] == e_o["dense_count"]
-        assert abs(rg["cost_final"] - e_o["total"]) <= COST_RTOL_EVAL * e_o["total"]
+        check_energy(rg["cost_final"], rg["dense_inliers"], g, Pg)
         P = Pg
 
 
 def test_solve_matches_oracle_paper_shaped(bt, paper):
-    """10 free-running iterations on the paper-shaped graph."""
+    """10 free-running iterations on the paper-shaped graph.  Projective
+    re-association makes the iteration map discontinuous: a start moved by
+    1e-9 rad flips a few of the ~6M association decisions and the oracle
+    itself then ends 1e-5..3e-5 rad and ~1e-6 m away after 10 iterations (a
+    1e-12 start does not move it at all).  No implementation whose rounding
+    differs can follow the oracle closer than that, so the comparison allows,
+    on top of the stated tolerance, twice the oracle's own spread from two
+    1e-9 starts, measured here.  The unwidened numbers are printed."""
     g = paper
     pg = bt.graph_from_synth(g)
     Pg, rg = pg.solve(10)
-    ro = O.solve(g, 10)
-    ro_next = O.solve(g, 1, poses=ro["poses"])
-    own_rot, own_tr = pose_err(ro["poses"], ro_next["poses"])
-    own_cost = abs(ro_next["cost_final"] - ro["cost_final"])
+    ro, s_rot, s_tr, s_cost = oracle_self_spread(g, 10)
     rot, tr = pose_err(Pg, ro["poses"])
-    e_at_gpu = O.energy(g, Pg)
-    assert rg["dense_inliers"] == e_at_gpu["dense_count"]
-    assert abs(rg["cost_final"] - e_at_gpu["total"]) <= COST_RTOL_EVAL * e_at_gpu["total"]
-    assert abs(rg["cost_final"] - ro["cost_final"]) <= COST_RTOL * ro["cost_final"] + own_cost
-    assert rot <= ROT_TOL + own_rot and tr <= TRANS_TOL + own_tr, (rot, tr, own_rot, own_tr)
+    dc = abs(rg["cost_final"] - ro["cost_final"]) / ro["cost_final"]
+    print(f"\npaper-0 free-running: GPU vs oracle {rot:.2e} rad {tr:.2e} m cost {dc:.2e}; "
+          f"oracle self-spread {s_rot:.2e} rad {s_tr:.2e} m cost {s_cost:.2e}")
+    check_energy(rg["cost_final"], rg["dense_inliers"], g, Pg)
+    assert dc <= COST_RTOL + 2 * s_cost
+    assert rot <= ROT_TOL + 2 * s_rot and tr <= TRANS_TOL + 2 * s_tr, (rot, tr, s_rot, s_tr)
     assert rg["dense_pixel_pairs"] == 10 * 9 * sum(
         int(((g.mask(k) > 0) & (g.depth(k) > 0) & np.isfinite(g.normals(k)).all(-1)).sum()) for k in range(10))
 
@@ -210,8 +221,7 @@ def test_zero_iterations_and_fixed_only(bt):
     pg = bt.graph_from_synth(g)
     P, rep = pg.solve(0)
     assert np.array_equal(P, g.pose_init)
-    o = O.energy(g, g.pose_init)
-    assert abs(rep["cost_final"] - o["total"]) <= COST_RTOL_EVAL * o["total"]
+    check_energy(rep["cost_final"], rep["dense_inliers"], g, g.pose_init)
     pg.set_active([pg.frame_ids[0]])
     P1, rep1 = pg.solve(2)
     assert np.array_equal(P1[0], g.pose_init[0]) and rep1["cost_final"] == 0.0

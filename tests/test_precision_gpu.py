@@ -4,23 +4,27 @@ oracle run on the original FP32 inputs.
 The arithmetic stays FP32 / FP64; only the stored points and normals are
 rounded (depth as an offset from the frame's mean valid depth).  FP16 keeps 11
 significand bits (~5e-4 relative: ~0.03-0.07 mm on the stored coordinates),
-BF16 8 bits (~4e-3: ~0.2-0.6 mm), against 1 mm depth noise, so the final
-energy moves by well under the noise floor for FP16 and by a visible fraction
-for BF16.  The bounds below are sanity bounds; the measured errors are printed
-as a table (run pytest with -s).
+BF16 8 bits (~4e-3: ~0.2-0.6 mm), against 1 mm depth noise.  Measured on
+GB300 (tiny graphs / the paper-shaped graph): FP16 moves the final cost by
+<= 3.5e-5, the poses by <= 6.5e-5 rad and 4.1e-6 m; BF16 by <= 3.7e-4, 3.3e-4
+rad and 1.7e-5 m.  The bounds below are about five times those errors, so a
+change that makes a storage format markedly worse fails; FP32 storage on the
+tiny graphs is held to the specified tolerance.  The table is printed (-s).
 """
 import numpy as np
 import pytest
 
 import oracle as O
 import synthgen as S
+from parity_util import pose_err
 
 pytestmark = pytest.mark.gpu
 
 BOUNDS = {  # dtype: (rel cost, rad, m)
-    "fp16": (0.02, 2e-3, 2e-4),
-    "bf16": (0.5, 2e-2, 2e-3),
+    "fp16": (2e-4, 3e-4, 2e-5),
+    "bf16": (2e-3, 2e-3, 1e-4),
 }
+FP32_TINY = (1e-5, 1e-5, 1e-6)      # the specified FP32 tolerance (paper-shaped: test_parity_gpu)
 
 
 @pytest.fixture(scope="module")
@@ -30,12 +34,6 @@ def bt():
     from paper_2108_00516_gb300 import bt as _bt
     _bt.load()
     return _bt
-
-
-def pose_err(A, B):
-    rot = max(S.rotation_angle(a[:3, :3] @ b[:3, :3].T) for a, b in zip(A, B))
-    tr = max(np.abs(a[:3, 3] - b[:3, 3]).max() for a, b in zip(A, B))
-    return rot, tr
 
 
 @pytest.fixture(scope="module")
@@ -56,8 +54,8 @@ def test_precision_error_table(bt, cases):
             rel = abs(rep["cost_final"] - ro["cost_final"]) / ro["cost_final"]
             rot, tr = pose_err(P, ro["poses"])
             rows.append((name, dtype, rel, rot, tr))
-            if dtype in BOUNDS:
-                b = BOUNDS[dtype]
+            b = BOUNDS.get(dtype) or (FP32_TINY if name.startswith("tiny") else None)
+            if b is not None:
                 assert rel <= b[0] and rot <= b[1] and tr <= b[2], (name, dtype, rel, rot, tr)
     print("\n| graph | storage | rel. final cost vs FP64 oracle | pose rad | pose m |")
     print("|---|---|---|---|---|")
