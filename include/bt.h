@@ -241,6 +241,10 @@ int bt_batch_size(const bt_batch* b);
 /* Residual-pass CTA shapes the autotuner chooses from (threads x source
  * pixels per thread: 128x4, 128x2, 256x4, 64x4, 64x8, 32x16). */
 #define BT_NUM_SHAPES 6
+/* The shape of the single-graph solve (bt_solve, bt_eval_cost): 256 x 4,
+ * 1024-pixel tiles.  A batch fixed to this shape reproduces bt_solve bit for
+ * bit. */
+#define BT_SINGLE_GRAPH_SHAPE 2
 
 /* Fixes the residual CTA shape (0 .. BT_NUM_SHAPES-1) or re-enables
  * autotuning (-1, the default).  Errors: BT_ERR_INVALID. */
@@ -443,6 +447,15 @@ int bt_debug_associate(bt_graph* g, int32_t src_node, int32_t dst_node, int32_t*
  * node), BT_ERR_CUDA, BT_ERR_OOM. */
 int bt_debug_normal_equations(bt_graph* g, double* H_out, double* g_out, int32_t n_cap, int32_t* n_out,
                               double* cost_out);
+
+/* Makes the library's next n device or pinned host allocations fail as if
+ * memory were exhausted -- the calls that needed them return BT_ERR_OOM and
+ * leave their objects as they were -- so that a caller can exercise its
+ * out-of-memory handling without exhausting a GPU; n = 0 cancels.  Process
+ * wide (every thread and graph).  Returns the number of injected failures
+ * that were still pending.  Allocations the device-memory cache can serve
+ * from idle blocks are not allocations and do not consume one. */
+int32_t bt_debug_fail_allocations(int32_t n);
 
 /* Profiling counters of one graph (the tracing facility; no paper
  * counterpart).  Launch counts are always kept; kernel durations are summed

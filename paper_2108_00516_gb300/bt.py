@@ -28,6 +28,7 @@ BT_FP16 = 2
 BT_MAX_NODES = 24
 BT_MAX_REPORT_ITERS = 64
 BT_NUM_SHAPES = 6
+BT_SINGLE_GRAPH_SHAPE = 2
 BT_SOLVER_CHOLESKY = 0
 BT_SOLVER_PCG = 1
 
@@ -124,6 +125,7 @@ SIGNATURES = {
                                      C.POINTER(C.c_int32)]),
     "bt_debug_normal_equations": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int32,
                                             C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
+    "bt_debug_fail_allocations": (C.c_int32, [C.c_int32]),
     "bt_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "bt_profile_read": (C.c_int, [C.c_void_p, C.POINTER(bt_profile)]),
     "bt_device_cache_bytes": (C.c_int64, []),
@@ -461,6 +463,12 @@ def ransac(pts_i, pts_j, hypotheses: int = 256, seed: int = 0, inlier_dist: floa
                             float(inlier_dist), 1 if refine else 0, M.ctypes.data_as(C.POINTER(C.c_double)),
                             C.byref(cnt), _stream_handle(stream)), "bt_ransac")
     return M.reshape(4, 4), cnt.value
+
+
+def debug_fail_allocations(n: int) -> int:
+    """bt_debug_fail_allocations: the library's next n device or pinned host
+    allocations fail as out of memory (0 cancels); returns the pending count."""
+    return int(load().bt_debug_fail_allocations(int(n)))
 
 
 def device_cache_bytes() -> int:

@@ -512,6 +512,7 @@ int bt_add_frame(bt_graph* g, const float* depth, const float* normals, const ui
                  const bt_intrinsics* K, const double pose_init[16], int32_t fixed,
                  const bt_matches* matches, int32_t n_matches, int32_t mem_kind, int32_t* frame_id_out)
 {
+    NvtxRange nvtx_range("bt_add_frame");
     last_error().clear();
     if (!g || !depth || !normals || !mask || !K || !pose_init)
         return fail(BT_ERR_INVALID, "bt_add_frame: NULL argument");
@@ -557,7 +558,9 @@ int bt_add_frame(bt_graph* g, const float* depth, const float* normals, const ui
         if (st != BT_OK) return st;
         const int cap = std::max(64, 2 * g->pin_cap);
         int* np = nullptr;
-        BT_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&np), sizeof(int) * 2 * (size_t)cap, cudaHostAllocDefault),
+        BT_CUDA(alloc_should_fail() ? cudaErrorMemoryAllocation
+                                    : cudaHostAlloc(reinterpret_cast<void**>(&np), sizeof(int) * 2 * (size_t)cap,
+                                                    cudaHostAllocDefault),
                 "cudaHostAlloc(read-back slots)");
         if (g->pin_m2) cudaFreeHost(g->pin_m2);
         g->pin_m2 = np;
@@ -621,6 +624,7 @@ int bt_add_frame(bt_graph* g, const float* depth, const float* normals, const ui
 int bt_set_matches(bt_graph* g, int32_t frame_a, int32_t frame_b, int32_t count, const float* pts_a,
                    const float* pts_b, int32_t mem_kind)
 {
+    NvtxRange nvtx_range("bt_set_matches");
     last_error().clear();
     if (!g) return fail(BT_ERR_INVALID, "bt_set_matches: NULL graph");
     if (mem_kind != BT_HOST && mem_kind != BT_DEVICE) return fail(BT_ERR_INVALID, "bt_set_matches: bad mem_kind");
@@ -706,12 +710,13 @@ int bt_get_poses(const bt_graph* g, double* poses)
 
 int bt_solve(bt_graph* g, int32_t iters, double* poses_out, bt_solve_report* rep)
 {
+    NvtxRange nvtx_range("bt_solve");
     last_error().clear();
     if (!g) return fail(BT_ERR_INVALID, "bt_solve: NULL graph");
     if (iters < 0 || iters > BT_MAX_REPORT_ITERS) return fail(BT_ERR_INVALID, "bt_solve: iters out of range");
     if (g->active.empty()) return fail(BT_ERR_INVALID, "bt_solve: no active nodes");
-    if (g->topo_dirty || g->built_tile != bt::shape_tile(0)) {
-        int st = build_topology(g, bt::shape_tile(0));
+    if (g->topo_dirty || g->built_tile != bt::shape_tile(bt::kSingleShape)) {
+        int st = build_topology(g, bt::shape_tile(bt::kSingleShape));
         if (st != BT_OK) return st;
     }
     int st = upload_poses(g);
@@ -743,11 +748,12 @@ int bt_solve(bt_graph* g, int32_t iters, double* poses_out, bt_solve_report* rep
 
 int bt_eval_cost(bt_graph* g, double* cost_out, int64_t* dense_inliers)
 {
+    NvtxRange nvtx_range("bt_eval_cost");
     last_error().clear();
     if (!g || !cost_out) return fail(BT_ERR_INVALID, "bt_eval_cost: NULL argument");
     if (g->active.empty()) return fail(BT_ERR_INVALID, "bt_eval_cost: no active nodes");
-    if (g->topo_dirty || g->built_tile != bt::shape_tile(0)) {
-        int st = build_topology(g, bt::shape_tile(0));
+    if (g->topo_dirty || g->built_tile != bt::shape_tile(bt::kSingleShape)) {
+        int st = build_topology(g, bt::shape_tile(bt::kSingleShape));
         if (st != BT_OK) return st;
     }
     int st = upload_poses(g);
@@ -1117,6 +1123,7 @@ int bt_batch_tuning(const bt_batch* b, int32_t* shape_out, double* us_per_shape)
 
 int bt_batch_solve(bt_batch* b, int32_t iters, bt_solve_report* reps)
 {
+    NvtxRange nvtx_range("bt_batch_solve");
     last_error().clear();
     if (!b) return fail(BT_ERR_INVALID, "bt_batch_solve: NULL batch");
     if (iters < 0 || iters > BT_MAX_REPORT_ITERS) return fail(BT_ERR_INVALID, "bt_batch_solve: iters out of range");

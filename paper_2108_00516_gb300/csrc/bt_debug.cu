@@ -15,8 +15,8 @@ namespace {
 int prepare(bt_graph* g)
 {
     if (g->active.empty()) return fail(BT_ERR_INVALID, "no active nodes");
-    if (g->topo_dirty || g->built_tile != bt::shape_tile(0)) {
-        int st = build_topology(g, bt::shape_tile(0));
+    if (g->topo_dirty || g->built_tile != bt::shape_tile(bt::kSingleShape)) {
+        int st = build_topology(g, bt::shape_tile(bt::kSingleShape));
         if (st != BT_OK) return st;
     }
     return upload_poses(g);
@@ -29,6 +29,7 @@ extern "C" {
 int bt_debug_associate(bt_graph* g, int32_t src_node, int32_t dst_node, int32_t* tgt_out, int32_t cap,
                        int32_t* count_out)
 {
+    NvtxRange nvtx_range("bt_debug_associate");
     last_error().clear();
     if (!g) return fail(BT_ERR_INVALID, "bt_debug_associate: NULL graph");
     const int N = (int)g->active.size();
@@ -55,11 +56,12 @@ int bt_debug_associate(bt_graph* g, int32_t src_node, int32_t dst_node, int32_t*
 int bt_debug_normal_equations(bt_graph* g, double* H_out, double* g_out, int32_t n_cap, int32_t* n_out,
                               double* cost_out)
 {
+    NvtxRange nvtx_range("bt_debug_normal_equations");
     last_error().clear();
     if (!g || !H_out || !g_out) return fail(BT_ERR_INVALID, "bt_debug_normal_equations: NULL argument");
     if (g->active.empty()) return fail(BT_ERR_INVALID, "bt_debug_normal_equations: no active nodes");
-    if (g->topo_dirty || g->built_tile != bt::shape_tile(0)) {
-        int st = build_topology(g, bt::shape_tile(0));
+    if (g->topo_dirty || g->built_tile != bt::shape_tile(bt::kSingleShape)) {
+        int st = build_topology(g, bt::shape_tile(bt::kSingleShape));
         if (st != BT_OK) return st;
     }
     const int n = 6 * g->args.n_free;

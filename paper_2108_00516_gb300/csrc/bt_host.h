@@ -6,6 +6,7 @@
 #include "bt_internal.h"
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -20,6 +21,22 @@ namespace bthost {
 
 // Message of the calling thread's last failure (returned by bt_last_error).
 std::string& last_error();
+
+// Allocation-failure injection (bt_debug_fail_allocations): true when the
+// allocation about to be made is to fail as out of memory (consumes one
+// pending failure).  Every device and pinned host allocation of the library
+// asks first.
+bool alloc_should_fail();
+
+// A named NVTX range over the rest of the enclosing scope (the library's
+// entry points), so that profilers can attribute GPU work to the call that
+// enqueued it; costs one test of a function pointer when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 
 inline int fail(int code, const std::string& msg)
@@ -50,6 +67,7 @@ struct DevBuf {
         p = nullptr;
         cap = 0;
         size_t want = std::max<size_t>(bytes, 256);
+        if (alloc_should_fail()) return cudaErrorMemoryAllocation;
         cudaError_t e = cudaMalloc(&p, want);
         if (e == cudaSuccess) cap = want;
         return e;
@@ -85,6 +103,7 @@ struct PinBuf {
         p = nullptr;
         cap = 0;
         const size_t want = std::max<size_t>(bytes + bytes / 4, 4096);
+        if (alloc_should_fail()) return cudaErrorMemoryAllocation;
         cudaError_t e = cudaHostAlloc(&p, want, cudaHostAllocDefault);
         if (e == cudaSuccess) cap = want;
         else p = nullptr;

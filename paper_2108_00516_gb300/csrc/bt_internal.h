@@ -22,6 +22,8 @@
 //     FP64 contributions to H and g), control words.
 #pragma once
 
+#include "bt.h"
+
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -33,10 +35,11 @@ constexpr int kPixPerThread = 4;              // prep
 // a CTA is their product.  A thread takes its pixels of one target in
 // batches of up to 4 (the gathers of a batch are in flight together) and
 // reduces its sums across the warp once per target, so more pixels per
-// thread spread that reduction over more pixel pairs.  Shape 0 is the
-// default of the single-graph path; the batched solver's autotuner picks
-// among all of them.
+// thread spread that reduction over more pixel pairs.  Shape
+// BT_SINGLE_GRAPH_SHAPE (256 x 4) is the single-graph path's; the batched
+// solver's autotuner picks among all of them.
 constexpr int kNumShapes = 6;     // BT_NUM_SHAPES
+constexpr int kSingleShape = BT_SINGLE_GRAPH_SHAPE;   // CTA shape of the single-graph solve (bt_solve)
 constexpr int kShapeThreads[kNumShapes] = {128, 128, 256, 64, 64, 32};
 constexpr int kShapePix[kNumShapes] = {4, 2, 4, 4, 8, 16};
 constexpr int kResThreads = 128;              // sparse CTAs of the residual launch
@@ -79,7 +82,7 @@ struct Control {
     unsigned long long clk[4];
 };
 
-constexpr size_t kReduceSmemMax = 200 * 1024;
+constexpr size_t kReduceSmemMax = 226 * 1024;   // of the 227 KB a CTA may opt into (1 KB left for static shared memory)
 
 struct SolveArgs {
     int N, n_tiles, n_pairs, n_edges, n_free, n_upairs;
@@ -159,7 +162,7 @@ cudaError_t launch_xforms(const SolveArgs& a, cudaStream_t s);
 // One residual pass (dense tiles + sparse edges) and one reduce/solve pass.
 // full = true: Gauss-Newton iteration `iter` (records E before the update);
 // full = false: cost only, recorded at slot `iter`.
-cudaError_t launch_residual(const SolveArgs& a, bool full, cudaStream_t s, int shape = 0);
+cudaError_t launch_residual(const SolveArgs& a, bool full, cudaStream_t s, int shape = kSingleShape);
 cudaError_t launch_reduce(const SolveArgs& a, bool full, int iter, cudaStream_t s);
 
 // Diagnostic export: target pixel (or -1) of every source entry of node i

@@ -29,8 +29,11 @@ __device__ __forceinline__ double rcp_fp64(double d)
     return fma(r, e, r);
 }
 
-// Largest system: 6 unknowns per free node.
+// Largest system: 6 unknowns per free node.  The back substitution splits
+// the rows above a block of 32 unknowns into min(4, 256 / r0) column chunks
+// (256 threads), which needs r0 < n <= 256.
 constexpr int kLdltMaxN = 6 * (kMaxNodes - 1);
+static_assert(kLdltMaxN <= 256, "ldlt_solve: at most 256 unknowns for one 256-thread CTA");
 
 // Shared-memory scratch of ldlt_solve for an n x n system.
 struct LdltScratch {

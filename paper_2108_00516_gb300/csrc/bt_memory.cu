@@ -14,6 +14,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -56,10 +57,11 @@ cudaError_t bthost::cache_take(size_t cls, void** out)
         c.idle_bytes -= (int64_t)cls;
         return cudaSuccess;
     }
-    if (cls > kSmallMax) return cudaMalloc(out, cls);
+    if (cls > kSmallMax) return alloc_should_fail() ? cudaErrorMemoryAllocation : cudaMalloc(out, cls);
     auto& s = c.slab[dev];
     if (!s.first || s.second + cls > kSlabBytes) {
         void* p = nullptr;
+        if (alloc_should_fail()) return cudaErrorMemoryAllocation;
         e = cudaMalloc(&p, kSlabBytes);
         if (e != cudaSuccess) return e;
         c.slabs.push_back(p);
@@ -110,3 +112,21 @@ int64_t bt_device_cache_trim(void)
 }
 
 }  // extern "C"
+
+namespace {
+std::atomic<int> g_fail_allocs{0};
+}
+
+bool bthost::alloc_should_fail()
+{
+    int n = g_fail_allocs.load(std::memory_order_relaxed);
+    while (n > 0) {
+        if (g_fail_allocs.compare_exchange_weak(n, n - 1, std::memory_order_relaxed)) return true;
+    }
+    return false;
+}
+
+extern "C" int32_t bt_debug_fail_allocations(int32_t n)
+{
+    return g_fail_allocs.exchange(n > 0 ? n : 0);
+}

@@ -166,34 +166,22 @@ int fail(int code, const std::string& msg)
     return code;
 }
 
-// M = T_dst T_src^-1 in FP64, products and sums in the library's fixed order,
-// each operation rounded on its own (the volatile temporaries keep the host
-// compiler from fusing them), rounded once to single precision -- the same
-// bits the solve kernels derive on the device.
+// M = T_dst T_src^-1 in FP64 with fused multiply-adds in the library's fixed
+// order (std::fma is the correctly rounded fused operation, as on the
+// device), rounded once to single precision -- the same bits the solve
+// kernels derive on the device.
 void pair_transform(const double* Tsrc, const double* Tdst, float* m)
 {
     double inv[12];
     for (int r = 0; r < 3; ++r) {
         for (int c = 0; c < 3; ++c) inv[r * 4 + c] = Tsrc[c * 4 + r];
-        volatile double p0 = Tsrc[0 * 4 + r] * Tsrc[3];
-        volatile double p1 = Tsrc[1 * 4 + r] * Tsrc[7];
-        volatile double p2 = Tsrc[2 * 4 + r] * Tsrc[11];
-        volatile double s01 = p0 + p1;
-        volatile double s = s01 + p2;
-        inv[r * 4 + 3] = -s;
+        inv[r * 4 + 3] = -std::fma(Tsrc[2 * 4 + r], Tsrc[11], std::fma(Tsrc[1 * 4 + r], Tsrc[7], Tsrc[0 * 4 + r] * Tsrc[3]));
     }
     for (int r = 0; r < 3; ++r) {
         for (int c = 0; c < 4; ++c) {
-            volatile double p0 = Tdst[r * 4 + 0] * inv[0 * 4 + c];
-            volatile double p1 = Tdst[r * 4 + 1] * inv[1 * 4 + c];
-            volatile double p2 = Tdst[r * 4 + 2] * inv[2 * 4 + c];
-            volatile double s01 = p0 + p1;
-            volatile double s = s01 + p2;
-            double v = s;
-            if (c == 3) {
-                volatile double w = v + Tdst[r * 4 + 3];
-                v = w;
-            }
+            double v = std::fma(Tdst[r * 4 + 2], inv[2 * 4 + c],
+                                std::fma(Tdst[r * 4 + 1], inv[1 * 4 + c], Tdst[r * 4 + 0] * inv[0 * 4 + c]));
+            if (c == 3) v += Tdst[r * 4 + 3];
             m[r * 4 + c] = (float)v;
         }
     }

@@ -409,6 +409,7 @@ int bt_ransac(const float* pts_i, const float* pts_j, int32_t count, int32_t mem
               uint64_t seed, double inlier_dist, int32_t refine, double* rel_out, int32_t* inliers_out,
               void* cuda_stream)
 {
+    NvtxRange nvtx_range("bt_ransac");
     last_error().clear();
     if (!rel_out || (count > 0 && (!pts_i || !pts_j))) return fail(BT_ERR_INVALID, "bt_ransac: NULL argument");
     if (count < 0 || hypotheses < 1 || hypotheses > (1 << 20) || !(inlier_dist > 0.0) || !std::isfinite(inlier_dist))
@@ -419,8 +420,8 @@ int bt_ransac(const float* pts_i, const float* pts_j, int32_t count, int32_t mem
     float* dq = nullptr;
     const size_t bytes = sizeof(float) * 3 * (size_t)(count > 0 ? count : 1);
     if (mem_kind == BT_HOST) {
-        BT_CUDA(cudaMalloc(&dp, bytes), "cudaMalloc(ransac points)");
-        cudaError_t e = cudaMalloc(&dq, bytes);
+        BT_CUDA(alloc_should_fail() ? cudaErrorMemoryAllocation : cudaMalloc(&dp, bytes), "cudaMalloc(ransac points)");
+        cudaError_t e = alloc_should_fail() ? cudaErrorMemoryAllocation : cudaMalloc(&dq, bytes);
         if (e == cudaSuccess && count > 0) e = cudaMemcpyAsync(dp, pts_i, bytes, cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess && count > 0) e = cudaMemcpyAsync(dq, pts_j, bytes, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) {
@@ -447,6 +448,7 @@ int bt_ransac(const float* pts_i, const float* pts_j, int32_t count, int32_t mem
 
 int bt_ransac_init(bt_graph* g, int32_t hypotheses, uint64_t seed, double inlier_dist, int32_t refine)
 {
+    NvtxRange nvtx_range("bt_ransac_init");
     last_error().clear();
     if (!g) return fail(BT_ERR_INVALID, "bt_ransac_init: NULL graph");
     if (hypotheses < 1 || hypotheses > (1 << 20) || !(inlier_dist > 0.0) || !std::isfinite(inlier_dist))

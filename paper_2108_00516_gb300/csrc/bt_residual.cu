@@ -347,8 +347,14 @@ __device__ __forceinline__ void accumulate_pair(float (&acc)[kDenseVals], float2
 // Pixels per thread whose target gathers are issued together, and resident
 // threads per SM the residual kernels are compiled for, by storage precision
 // (FP32: six 128-thread CTAs, at most 80 registers a thread; 16-bit: five).
-constexpr int residual_batch(int P) { return P == 0 ? 2 : 4; }
-constexpr int residual_threads_per_sm(int P) { return P == 0 ? 768 : 640; }
+#ifndef BT_RES_BATCH_F32
+#define BT_RES_BATCH_F32 2
+#endif
+#ifndef BT_RES_THREADS_F32
+#define BT_RES_THREADS_F32 768
+#endif
+constexpr int residual_batch(int P) { return P == 0 ? BT_RES_BATCH_F32 : 4; }
+constexpr int residual_threads_per_sm(int P) { return P == 0 ? BT_RES_THREADS_F32 : 640; }
 
 // One tile of kT x kB source pixels of node i against every other node j.
 // The work of the tile is (N-1) x kW units -- unit (jj, c) = target jj, chunk
@@ -409,30 +415,33 @@ __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
             if (c0 >= nvalid) continue;     // chunk past the last valid pixel of the tile
 #pragma unroll
             for (int bb = 0; bb < kBatches; ++bb) {
-                // phase 1: q = M p, nearest pixel, bounds
+                // phase 1: q = M p, nearest pixel (packed (v << 16) | u, or -1
+                // when dropped: sides are at most 32767), bounds
                 float2 qxy[kBatch];
                 float qz[kBatch];
-                int iu[kBatch], iv[kBatch];
-                bool ok[kBatch];
+                int pk[kBatch];
 #pragma unroll
                 for (int k = 0; k < kBatch; ++k) {
                     const int s = c0 + (bb * kBatch + k) * 32 + lane;
                     const float4 p = sp[s];
-                    ok[k] = assoc_project(K, p.x, p.y, p.z, qxy[k], qz[k], iu[k], iv[k]) && s < nvalid;
+                    int iu, iv;
+                    const bool ok = assoc_project(K, p.x, p.y, p.z, qxy[k], qz[k], iu, iv) && s < nvalid;
+                    pk[k] = ok ? (iv << 16) | iu : -1;
                 }
                 // phase 2: the gathers of the batch in flight together
                 float4 t[kBatch];
 #pragma unroll
                 for (int k = 0; k < kBatch; ++k)
-                    t[k] = ok[k] ? load_target<P>(tgt, (size_t)iv[k] * K.W + iu[k], zref)
-                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+                    t[k] = pk[k] >= 0 ? load_target<P>(tgt, (size_t)(pk[k] >> 16) * K.W + (pk[k] & 0xffff), zref)
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
                 // phase 3: gates, residual, Jacobian, Huber, accumulation
 #pragma unroll
                 for (int k = 0; k < kBatch; ++k) {
-                    if (!(ok[k] && t[k].x > 0.f)) continue;
+                    if (!(pk[k] >= 0 && t[k].x > 0.f)) continue;
                     float2 txy, dxy;
                     float dz;
-                    if (!assoc_distance(K, iu[k], iv[k], t[k].x, qxy[k], qz[k], dmax2, txy, dxy, dz)) continue;
+                    if (!assoc_distance(K, pk[k] & 0xffff, pk[k] >> 16, t[k].x, qxy[k], qz[k], dmax2, txy, dxy, dz))
+                        continue;
                     const float4 n = sn[c0 + (bb * kBatch + k) * 32 + lane];
                     float2 nxy;
                     float nz;

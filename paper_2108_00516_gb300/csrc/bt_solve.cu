@@ -23,8 +23,10 @@ namespace bt {
 
 // ---------------------------------------------------------------------------
 // Single-precision transforms of the FP64 poses.  M = T_j T_i^-1 is formed in
-// FP64 without FMA contraction, products and sums in a fixed order, so that
-// its rounding to single precision is reproducible bit for bit.
+// FP64 with fused multiply-adds in a fixed order (fma(a2, b2, fma(a1, b1,
+// a0 * b0)), plus the translation) and rounded once to single precision, so
+// its bits are reproducible (the no-alloc call forms the same bits on the
+// host with std::fma).
 // ---------------------------------------------------------------------------
 
 // Writes xf[i*N+j] = float(T_j T_i^-1) (i != j) and xinv[i] = float(T_i^-1) with the
@@ -40,8 +42,7 @@ __device__ void write_xforms(const SolveArgs& a, double* __restrict__ tinv, cons
         if (c < 3) {
             v = T[c * 4 + r];
         } else {
-            v = -__dadd_rn(__dadd_rn(__dmul_rn(T[0 * 4 + r], T[3]), __dmul_rn(T[1 * 4 + r], T[7])),
-                           __dmul_rn(T[2 * 4 + r], T[11]));
+            v = -fma(T[2 * 4 + r], T[11], fma(T[1 * 4 + r], T[7], T[0 * 4 + r] * T[3]));
         }
         tinv[id] = v;
         a.xinv[id] = __double2float_rn(v);
@@ -54,9 +55,8 @@ __device__ void write_xforms(const SolveArgs& a, double* __restrict__ tinv, cons
         const int i = pr / M, jj = pr % M, j = jj < i ? jj : jj + 1;
         const double* A = pose + j * 12;     // T_j
         const double* B = tinv + i * 12;     // T_i^-1
-        double s = __dadd_rn(__dadd_rn(__dmul_rn(A[r * 4 + 0], B[0 * 4 + c]), __dmul_rn(A[r * 4 + 1], B[1 * 4 + c])),
-                             __dmul_rn(A[r * 4 + 2], B[2 * 4 + c]));
-        if (c == 3) s = __dadd_rn(s, A[r * 4 + 3]);
+        double s = fma(A[r * 4 + 2], B[2 * 4 + c], fma(A[r * 4 + 1], B[1 * 4 + c], A[r * 4 + 0] * B[0 * 4 + c]));
+        if (c == 3) s += A[r * 4 + 3];
         a.xf[(i * N + j) * 12 + e] = __double2float_rn(s);
     }
 }

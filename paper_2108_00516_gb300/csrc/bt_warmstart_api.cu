@@ -59,7 +59,7 @@ int grow(DevBuf& b, size_t bytes, size_t keep, cudaStream_t s, void** old_out = 
     if (old_out) *old_out = b.p;
     if (bytes <= b.cap) return BT_OK;
     void* p = nullptr;
-    BT_CUDA(cudaMalloc(&p, bytes), "cudaMalloc(warm-start data)");
+    BT_CUDA(alloc_should_fail() ? cudaErrorMemoryAllocation : cudaMalloc(&p, bytes), "cudaMalloc(warm-start data)");
     if (keep) BT_CUDA(cudaMemcpyAsync(p, b.p, keep, cudaMemcpyDeviceToDevice, s), "copy warm-start data");
     BT_CUDA(cudaStreamSynchronize(s), "sync warm-start growth");
     if (b.p) cudaFree(b.p);
@@ -158,7 +158,7 @@ int ensure_tables(bt_graph* g)
 {
     if (g->active.empty()) return fail(BT_ERR_INVALID, "warm start: graph has no active nodes");
     if (g->topo_dirty || g->built_tile == 0)
-        return build_topology(g, g->built_tile > 0 ? g->built_tile : bt::shape_tile(0));
+        return build_topology(g, g->built_tile > 0 ? g->built_tile : bt::shape_tile(bt::kSingleShape));
     return BT_OK;
 }
 
@@ -511,6 +511,7 @@ int bt_warmstart_clear_samples(bt_warmstart* ws)
 
 int bt_warmstart_predict(bt_warmstart* ws, const int32_t* ids, int32_t n, float* y_out)
 {
+    NvtxRange nvtx_range("bt_warmstart_predict");
     last_error().clear();
     int st = check_ready(ws, "bt_warmstart_predict");
     if (st != BT_OK) return st;
@@ -545,6 +546,7 @@ int bt_warmstart_get_sample(const bt_warmstart* ws, int32_t id, float* centre, f
 
 int bt_warmstart_gradient(bt_warmstart* ws, const int32_t* ids, int32_t n, float* grad_out, double* loss_out)
 {
+    NvtxRange nvtx_range("bt_warmstart_gradient");
     last_error().clear();
     int st = check_ready(ws, "bt_warmstart_gradient");
     if (st != BT_OK) return st;
@@ -562,6 +564,7 @@ int bt_warmstart_gradient(bt_warmstart* ws, const int32_t* ids, int32_t n, float
 
 int bt_warmstart_train_step(bt_warmstart* ws, const int32_t* ids, int32_t n, float lr, double* loss_out)
 {
+    NvtxRange nvtx_range("bt_warmstart_train_step");
     last_error().clear();
     int st = check_ready(ws, "bt_warmstart_train_step");
     if (st != BT_OK) return st;
@@ -584,6 +587,7 @@ int bt_warmstart_train_step(bt_warmstart* ws, const int32_t* ids, int32_t n, flo
 
 int bt_warmstart_apply(bt_warmstart* ws, bt_graph* g)
 {
+    NvtxRange nvtx_range("bt_warmstart_apply");
     last_error().clear();
     int st = check_ready(ws, "bt_warmstart_apply");
     if (st != BT_OK) return st;
@@ -595,6 +599,7 @@ int bt_warmstart_apply(bt_warmstart* ws, bt_graph* g)
 
 int bt_warmstart_apply_batch(bt_warmstart* ws, bt_batch* b, int32_t* status_out)
 {
+    NvtxRange nvtx_range("bt_warmstart_apply_batch");
     last_error().clear();
     int st = check_ready(ws, "bt_warmstart_apply_batch");
     if (st != BT_OK) return st;
@@ -605,6 +610,7 @@ int bt_warmstart_apply_batch(bt_warmstart* ws, bt_batch* b, int32_t* status_out)
 int bt_batch_solve_warm(bt_batch* b, bt_warmstart* ws, int32_t iters, int32_t fallback_iters,
                         const double* ref_costs, double tol, bt_solve_report* reps)
 {
+    NvtxRange nvtx_range("bt_batch_solve_warm");
     last_error().clear();
     int st = check_ready(ws, "bt_batch_solve_warm");
     if (st != BT_OK) return st;

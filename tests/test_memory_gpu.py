@@ -65,3 +65,34 @@ def test_destroyed_graphs_feed_the_cache(bt):
     pg.close()
     freed = bt.device_cache_trim()
     assert freed > 0 and bt.device_cache_bytes() == idle - freed
+
+
+def test_injected_out_of_memory_leaves_state(bt):
+    """bt_debug_fail_allocations makes the next allocation fail as if the GPU
+    were out of memory: the call reports BT_ERR_OOM, the graph keeps its
+    frames and poses, and the same calls succeed once the injection is used
+    up, with the results of a graph that never failed."""
+    g = S.tiny_graph(9)
+    r, c = g.renders[0], g.cams[0]
+    pg = bt.PoseGraph()
+    assert bt.debug_fail_allocations(1) == 0
+    with pytest.raises(bt.BTError) as e:
+        pg.add_frame(r.depth, r.normals, r.mask, c.as_tuple(), g.pose_init[0], True)
+    assert e.value.status == bt.BT_ERR_OOM
+    assert pg.num_active == 0
+    assert bt.debug_fail_allocations(0) == 0          # consumed by that call
+    pg.close()
+    ref = bt.graph_from_synth(g)
+    P_ref, r_ref = ref.solve(3)
+    ref.close()
+    pg = bt.graph_from_synth(g)
+    P0 = pg.get_poses()
+    bt.debug_fail_allocations(1)                      # the solve's first table allocation fails
+    with pytest.raises(bt.BTError) as e:
+        pg.solve(3)
+    assert e.value.status == bt.BT_ERR_OOM
+    assert np.array_equal(pg.get_poses(), P0)
+    assert bt.debug_fail_allocations(0) == 0
+    P, rep = pg.solve(3)
+    assert np.array_equal(P, P_ref) and rep["cost_final"] == r_ref["cost_final"]
+    pg.close()

@@ -68,7 +68,7 @@ def test_pcg_in_a_batch(bt):
     batch = bt.Batch()
     for pg in pgs:
         batch.add(pg)
-    batch.set_shape(0)
+    batch.set_shape(bt.BT_SINGLE_GRAPH_SHAPE)
     batch.solve(4)
     for pg, P in zip(pgs, singles):
         assert np.array_equal(pg.get_poses(), P)

@@ -72,7 +72,7 @@ def test_half_storage_batches_and_rejects_mixing(bt):
     batch = bt.Batch()
     batch.add(a)
     batch.add(b)
-    batch.set_shape(0)
+    batch.set_shape(bt.BT_SINGLE_GRAPH_SHAPE)
     reps = batch.solve(4)
     single = bt.graph_from_synth(g, config=cfg)
     P, rep = single.solve(4)

@@ -116,3 +116,50 @@ def test_fallback_restores_the_plain_solve(bt, graphs):
             assert np.array_equal(pg.get_poses(), P_ref)
         else:
             assert r["cost_final"] <= 1.01 * r_ref["cost_final"]
+
+
+def test_runtime_fallback_rule(bt, graphs):
+    """bt_batch_solve_warm without the plain costs (the rule a deployment can
+    run): a graph falls back exactly when its last warm-started iteration
+    moved the cost by more than tol of the final cost.  With the trained
+    network and two iterations no held-out graph falls back and every one
+    ends within 1 % of the plain solve; with a corrupted network and one
+    iteration the graphs that did not converge are re-solved plainly and
+    then equal the plain solve."""
+    assert WEIGHTS.exists()
+    plain = []
+    for g in graphs:
+        pg = bt.graph_from_synth(g)
+        plain.append(pg.solve(10))
+        pg.close()
+
+    def run(params, iters):
+        ws = bt.WarmStart(params)
+        pgs = [bt.graph_from_synth(g) for g in graphs]
+        batch = bt.Batch()
+        for pg in pgs:
+            batch.add(pg)
+        reps = batch.solve_warm(ws, iters, 10, ref_costs=None, tol=0.01)
+        poses = [pg.get_poses() for pg in pgs]
+        ws.close()
+        batch.close()
+        for pg in pgs:
+            pg.close()
+        return reps, poses
+
+    reps, _ = run(np.load(WEIGHTS)["params"], 2)
+    assert not any(r["fell_back"] for r in reps)
+    for r, (_, r_ref) in zip(reps, plain):
+        assert r["used_warmstart"] == 1
+        assert abs(r["cost_per_iter"][-1] - r["cost_final"]) <= 0.01 * r["cost_final"]
+        assert r["cost_final"] <= 1.01 * r_ref["cost_final"]
+
+    bad = S.warmstart_init(7)
+    bad[-6:] += 3.0
+    reps, poses = run(bad, 1)
+    assert any(r["fell_back"] for r in reps)
+    for r, P, (P_ref, r_ref) in zip(reps, poses, plain):
+        if r["fell_back"]:
+            assert r["cost_final"] == r_ref["cost_final"] and np.array_equal(P, P_ref)
+        else:
+            assert abs(r["cost_per_iter"][-1] - r["cost_final"]) <= 0.01 * r["cost_final"]

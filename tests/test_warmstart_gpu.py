@@ -264,7 +264,7 @@ def test_largest_graph_solve_and_average(bt):
     pb = bt.graph_from_synth(g)
     batch = bt.Batch()
     batch.add(pb)
-    batch.set_shape(0)
+    batch.set_shape(bt.BT_SINGLE_GRAPH_SHAPE)
     r_b = batch.solve(2)[0]
     assert r_b["cost_final"] == rep["cost_final"] and np.array_equal(pb.get_poses(), P_gpu)
     batch.close()
