@@ -306,6 +306,16 @@ int bt_warmstart_set_params(bt_warmstart* ws, const float* params, int32_t mem_k
  * (no parameters set), BT_ERR_CUDA. */
 int bt_warmstart_get_params(const bt_warmstart* ws, float* params, int32_t mem_kind);
 
+/* Training state for a checkpoint: the Adam first and second moments
+ * (BT_WS_NUM_PARAMS floats each, host or device) and the number of steps
+ * taken.  A training run resumed from get_params + get_adam (set_params,
+ * then set_adam) continues exactly as the uninterrupted run would.
+ * set_params clears this state.  Errors: BT_ERR_INVALID (NULL, negative
+ * step, non-finite or negative second moment), BT_ERR_STATE (no
+ * parameters set), BT_ERR_CUDA. */
+int bt_warmstart_get_adam(const bt_warmstart* ws, float* m, float* v, int32_t* step, int32_t mem_kind);
+int bt_warmstart_set_adam(bt_warmstart* ws, const float* m, const float* v, int32_t step, int32_t mem_kind);
+
 /* Appends one training sample: count > 0 point pairs (pts_i in camera i,
  * pts_j in camera j: count x 3 float, host or device), the initial poses of
  * the two frames (4x4 row-major; M0 = T_j T_i^-1) and, optionally, the poses

@@ -99,6 +99,8 @@ SIGNATURES = {
     "bt_warmstart_num_params": (C.c_int32, []),
     "bt_warmstart_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "bt_warmstart_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "bt_warmstart_get_adam": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32), C.c_int32]),
+    "bt_warmstart_set_adam": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32]),
     "bt_warmstart_add_set": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_double),
                                        C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                        C.c_int32]),
@@ -539,6 +541,23 @@ class WarmStart:
         _check(load().bt_warmstart_get_params(self._h, C.c_void_p(out.ctypes.data), BT_HOST),
                "bt_warmstart_get_params")
         return out
+
+    def get_adam(self):
+        """(first moments, second moments, step) of the Adam optimiser."""
+        m = np.empty(WS_NUM_PARAMS, np.float32)
+        v = np.empty(WS_NUM_PARAMS, np.float32)
+        t = C.c_int32()
+        _check(load().bt_warmstart_get_adam(self._h, C.c_void_p(m.ctypes.data), C.c_void_p(v.ctypes.data),
+                                            C.byref(t), BT_HOST), "bt_warmstart_get_adam")
+        return m, v, t.value
+
+    def set_adam(self, m, v, step: int):
+        m = np.ascontiguousarray(np.asarray(m, np.float32).ravel())
+        v = np.ascontiguousarray(np.asarray(v, np.float32).ravel())
+        if m.size != WS_NUM_PARAMS or v.size != WS_NUM_PARAMS:
+            raise ValueError("moments: %d floats each" % WS_NUM_PARAMS)
+        _check(load().bt_warmstart_set_adam(self._h, C.c_void_p(m.ctypes.data), C.c_void_p(v.ctypes.data),
+                                            int(step), BT_HOST), "bt_warmstart_set_adam")
 
     def add_set(self, pts_i, pts_j, pose_i, pose_j, label_i=None, label_j=None):
         """One training sample: point pairs and the two frames' initial poses

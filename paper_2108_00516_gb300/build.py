@@ -17,6 +17,7 @@ ROOT = PKG.parent
 CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = BUILD / "libbt.so"
+LIB_CHECKED = BUILD / "libbt_checked.so"
 INCLUDE = ROOT / "include"
 SOURCES = sorted(CSRC.glob("*.cu"))
 HEADERS = sorted(CSRC.glob("*.h")) + sorted(CSRC.glob("*.cuh")) + sorted(INCLUDE.glob("*.h"))
@@ -38,17 +39,22 @@ def _flags(ptxas_verbose: bool):
     return f
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False) -> Path:
-    BUILD.mkdir(exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False, checked: bool = False) -> Path:
+    """Compile libbt.so, or with checked=True libbt_checked.so: the same
+    library with every index of the residual pass tested before use
+    (-DBT_CHECKED; a failed test is reported as BT_ERR_INVALID)."""
+    out_dir = BUILD / "checked" if checked else BUILD
+    lib = LIB_CHECKED if checked else LIB
+    out_dir.mkdir(parents=True, exist_ok=True)
     newest = max(p.stat().st_mtime for p in SOURCES + HEADERS + [Path(__file__)])
-    if LIB.exists() and not force and not ptxas_verbose and LIB.stat().st_mtime >= newest:
-        return LIB
+    if lib.exists() and not force and not ptxas_verbose and lib.stat().st_mtime >= newest:
+        return lib
     cc = nvcc()
-    objs = []
+    extra = ["-DBT_CHECKED"] if checked else []
 
     def compile_one(src: Path):
-        obj = BUILD / (src.stem + ".o")
-        cmd = [cc, *_flags(ptxas_verbose), "-c", str(src), "-o", str(obj)]
+        obj = out_dir / (src.stem + ".o")
+        cmd = [cc, *_flags(ptxas_verbose), *extra, "-c", str(src), "-o", str(obj)]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -60,14 +66,14 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB.with_suffix(f".so.tmp{os.getpid()}")
+    tmp = lib.with_suffix(f".so.tmp{os.getpid()}")
     cmd = [cc, *ARCH, "-shared", "-Xcompiler", "-fPIC", *map(str, objs), "-o", str(tmp)]
     if verbose:
         print(" ".join(cmd), flush=True)
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force=True, verbose=True, ptxas_verbose="-v" in sys.argv))
+    print(build(force=True, verbose=True, ptxas_verbose="-v" in sys.argv, checked="--checked" in sys.argv))

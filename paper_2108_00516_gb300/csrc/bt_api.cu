@@ -391,7 +391,7 @@ int bthost::fill_report(bt_graph* g, const char* blk, int iters, bt_solve_report
     const double* costs = reinterpret_cast<const double*>(blk + L.costs);
     if (g->prof_on)
         for (int k = 0; k < 4; ++k) g->prof.solve_phase_cycles[k] += (int64_t)ctrl.clk[k];
-    const int status = ctrl.status == -4 ? BT_ERR_SINGULAR : BT_OK;
+    const int status = ctrl.checked != 0u ? BT_ERR_INVALID : ctrl.status == -4 ? BT_ERR_SINGULAR : BT_OK;
     if (rep) {
         std::memset(rep, 0, sizeof(*rep));
         rep->iters_run = iters;
@@ -737,6 +737,8 @@ int bt_solve(bt_graph* g, int32_t iters, double* poses_out, bt_solve_report* rep
     const char* blk = g->pin_state.at<char>(0);
     const int status = fill_report(g, blk, iters, rep);
     const double* pose = reinterpret_cast<const double*>(blk + L.pose);
+    if (status == BT_ERR_INVALID)
+        return fail(status, "bt_solve: an index check of the bounds-checked build failed; poses unchanged");
     if (status != BT_OK) return fail(status, "bt_solve: normal equations not positive definite; poses unchanged");
     for (int k = 0; k < N; ++k) {
         Frame& f = g->frames.at(g->active[k]);
@@ -769,6 +771,8 @@ int bt_eval_cost(bt_graph* g, double* cost_out, int64_t* dense_inliers)
     g->pin_state.busy = false;
     const double* c = g->pin_state.at<double>(L.costs);
     collect_events(g, 1);
+    if (g->pin_state.at<bt::Control>(0)->checked != 0u)
+        return fail(BT_ERR_INVALID, "bt_eval_cost: an index check of the bounds-checked build failed");
     cost_out[0] = c[0];
     cost_out[1] = c[1];
     cost_out[2] = c[2];

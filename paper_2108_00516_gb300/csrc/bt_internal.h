@@ -75,7 +75,8 @@ struct EdgeDev {
 struct Control {
     unsigned int counter;   // last-block detection of the reduce kernel
     int status;             // 0 ok, -4 singular (sticky for the solve)
-    int pad[2];
+    unsigned checked;       // BT_CHECKED builds: bits of the index checks that failed (kChk*)
+    int pad;
     // SM clock cycles spent by the last CTA, summed over the solve's
     // iterations: [0] gather + assembly, [1] factorisation (with forward
     // substitution), [2] back substitution, [3] pose update + transforms
@@ -109,6 +110,29 @@ struct SolveArgs {
     double* costs;      // [iter][4]: total, dense, sparse, dense count
     double* ne_out;     // NULL, or [n*n + n]: the assembled H and g are written here instead of solving
 };
+
+// Bounds-checked build (compiled with -DBT_CHECKED: libbt_checked.so).  The
+// residual pass tests every shared-memory, gather and output index it forms
+// before the access; a failed test skips the access and sets a bit in the
+// solve's control block, which the host reports as BT_ERR_INVALID.  Nothing
+// traps.  In the normal build the tests compile to nothing.
+constexpr unsigned kChkSourceTile = 1u;    // staged source pixel / normal
+constexpr unsigned kChkPipeSlot = 2u;      // per-lane pipeline slot
+constexpr unsigned kChkGather = 4u;        // target-map pixel
+constexpr unsigned kChkRedSlot = 8u;       // per-warp reduction slot
+constexpr unsigned kChkOutput = 16u;       // dpart / spart entry
+#ifdef BT_CHECKED
+#ifdef __CUDACC__
+__device__ __forceinline__ bool index_check(bool ok, unsigned bit, Control* ctrl)
+{
+    if (!ok) atomicOr(&ctrl->checked, bit);
+    return ok;
+}
+#endif
+#define BT_CHECK_IDX(cond, bit, ctrl) (::bt::index_check((cond), (bit), (ctrl)))
+#else
+#define BT_CHECK_IDX(cond, bit, ctrl) true
+#endif
 
 // Programmatic dependent launch.  The kernels of a solve form one chain per
 // stream (transforms -> residual -> reduce -> residual -> ...).  Each is

@@ -29,6 +29,12 @@ __device__ __forceinline__ double rcp_fp64(double d)
     return fma(r, e, r);
 }
 
+// Trailing rows from which warp 4 joins the bulk update (see ldlt_solve).
+#ifndef BT_LDLT_WIDE_ROWS
+#define BT_LDLT_WIDE_ROWS 30
+#endif
+constexpr int kWideBulkRows = BT_LDLT_WIDE_ROWS;
+
 // Largest system: 6 unknowns per free node.  The back substitution splits
 // the rows above a block of 32 unknowns into min(4, 256 / r0) column chunks
 // (256 threads), which needs r0 < n <= 256.
@@ -84,12 +90,19 @@ __device__ __forceinline__ void ldlt_solve(double* __restrict__ H, int ld, int n
         }
     }
     __syncthreads();
-    const bool bulk = warp != 0 && warp != 4 && warp < 8;
-    constexpr int nbulk = 6 * 32;
-    const int bt = bulk ? (warp < 4 ? warp - 1 : warp - 2) * 32 + lane : -1;
+    // bulk warps: {1,2,3,5,6,7}, and also warp 4 while the trailing triangle
+    // is large (the early columns, where the bulk update and not warp 0's
+    // chain sets the pace; warp 4 shares warp 0's FP64 unit, which has slack
+    // there)
+    const int bt6 = (warp != 0 && warp != 4 && warp < 8) ? (warp < 4 ? warp - 1 : warp - 2) * 32 + lane : -1;
+    const int bt7 = (warp != 0 && warp < 8) ? (warp - 1) * 32 + lane : -1;
     for (int k = 0; k < n - 1; ++k) {
         const double* ck = colb + (k & 1) * n;        // l_{i,k}
         double* cn = colb + ((k + 1) & 1) * n;        // l_{i,k+1}, written now
+        const bool wide = n - k - 2 >= kWideBulkRows;
+        const int nbulk = wide ? 7 * 32 : 6 * 32;
+        const int bt = wide ? bt7 : bt6;
+        const bool bulk = bt >= 0;
         if (warp == 0) {
             // column p = k + 1, rows i = p .. n-1 in slots of 32: u_i = H_ip -
             // l_ik H_pk (the pivot is u_p), then every lane forms 1 / u_p

@@ -415,32 +415,32 @@ __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
             if (c0 >= nvalid) continue;     // chunk past the last valid pixel of the tile
 #pragma unroll
             for (int bb = 0; bb < kBatches; ++bb) {
-                // phase 1: q = M p, nearest pixel (packed (v << 16) | u, or -1
-                // when dropped: sides are at most 32767), bounds
+                // phase 1: q = M p, nearest pixel, bounds
                 float2 qxy[kBatch];
                 float qz[kBatch];
-                int pk[kBatch];
+                int iu[kBatch], iv[kBatch];
+                bool ok[kBatch];
 #pragma unroll
                 for (int k = 0; k < kBatch; ++k) {
                     const int s = c0 + (bb * kBatch + k) * 32 + lane;
-                    const float4 p = sp[s];
-                    int iu, iv;
-                    const bool ok = assoc_project(K, p.x, p.y, p.z, qxy[k], qz[k], iu, iv) && s < nvalid;
-                    pk[k] = ok ? (iv << 16) | iu : -1;
+                    const float4 p = sp[BT_CHECK_IDX(s < kTile, kChkSourceTile, a.ctrl) ? s : 0];
+                    ok[k] = assoc_project(K, p.x, p.y, p.z, qxy[k], qz[k], iu[k], iv[k]) && s < nvalid &&
+                            BT_CHECK_IDX((unsigned)iu[k] < (unsigned)K.W && (unsigned)iv[k] < (unsigned)K.H,
+                                         kChkGather, a.ctrl);
                 }
                 // phase 2: the gathers of the batch in flight together
                 float4 t[kBatch];
 #pragma unroll
                 for (int k = 0; k < kBatch; ++k)
-                    t[k] = pk[k] >= 0 ? load_target<P>(tgt, (size_t)(pk[k] >> 16) * K.W + (pk[k] & 0xffff), zref)
-                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+                    t[k] = ok[k] ? load_target<P>(tgt, (size_t)iv[k] * K.W + iu[k], zref)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
                 // phase 3: gates, residual, Jacobian, Huber, accumulation
 #pragma unroll
                 for (int k = 0; k < kBatch; ++k) {
-                    if (!(pk[k] >= 0 && t[k].x > 0.f)) continue;
+                    if (!(ok[k] && t[k].x > 0.f)) continue;
                     float2 txy, dxy;
                     float dz;
-                    if (!assoc_distance(K, pk[k] & 0xffff, pk[k] >> 16, t[k].x, qxy[k], qz[k], dmax2, txy, dxy, dz))
+                    if (!assoc_distance(K, iu[k], iv[k], t[k].x, qxy[k], qz[k], dmax2, txy, dxy, dz))
                         continue;
                     const float4 n = sn[c0 + (bb * kBatch + k) * 32 + lane];
                     float2 nxy;
@@ -466,7 +466,8 @@ __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
                 }
             }
         }
-        float* slot = red + ((size_t)jj * kW + warp) * kDenseVals;
+        float* slot = red + ((size_t)(BT_CHECK_IDX(jj < M1 && warp < kW, kChkRedSlot, a.ctrl) ? jj : 0) * kW + warp) *
+                                kDenseVals;
         if constexpr (kFull) {
             slot[lane] = warp_transpose_reduce(acc, lane);
         } else {
@@ -502,7 +503,8 @@ __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
                 s = t2;
             }
         }
-        a.dpart[((size_t)tile * M1 + jj) * kDenseVals + v] = s;
+        if (BT_CHECK_IDX(tile < a.n_tiles && jj < M1, kChkOutput, a.ctrl))
+            a.dpart[((size_t)tile * M1 + jj) * kDenseVals + v] = s;
     }
 }
 
@@ -577,6 +579,7 @@ __device__ void sparse_edge(const SolveArgs& a, int e)
     __syncthreads();
     for (int k = threadIdx.x; k < kSparseVals; k += blockDim.x) {   // blocks of 32 threads too
         if (!kFull && k < 37) continue;
+        if (!BT_CHECK_IDX(e < a.n_edges, kChkOutput, a.ctrl)) continue;
         float s = 0.f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sred[w][k];
         a.spart[(size_t)e * kSparseVals + k] = s;

@@ -377,6 +377,40 @@ int bt_warmstart_set_params(bt_warmstart* ws, const float* params, int32_t mem_k
     return BT_OK;
 }
 
+int bt_warmstart_get_adam(const bt_warmstart* ws, float* m, float* v, int32_t* step, int32_t mem_kind)
+{
+    last_error().clear();
+    int st = check_ready(ws, "bt_warmstart_get_adam");
+    if (st != BT_OK) return st;
+    if (!m || !v || !step) return fail(BT_ERR_INVALID, "bt_warmstart_get_adam: NULL argument");
+    if (mem_kind != BT_HOST && mem_kind != BT_DEVICE) return fail(BT_ERR_INVALID, "bt_warmstart_get_adam: mem_kind");
+    const cudaMemcpyKind kind = mem_kind == BT_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    BT_CUDA(cudaMemcpyAsync(m, ws->m.p, sizeof(float) * W::kNumParams, kind, ws->stream), "read moments");
+    BT_CUDA(cudaMemcpyAsync(v, ws->v.p, sizeof(float) * W::kNumParams, kind, ws->stream), "read moments");
+    BT_CUDA(cudaStreamSynchronize(ws->stream), "bt_warmstart_get_adam: synchronize");
+    *step = ws->adam_t;
+    return BT_OK;
+}
+
+int bt_warmstart_set_adam(bt_warmstart* ws, const float* m, const float* v, int32_t step, int32_t mem_kind)
+{
+    last_error().clear();
+    int st = check_ready(ws, "bt_warmstart_set_adam");
+    if (st != BT_OK) return st;
+    if (!m || !v || step < 0) return fail(BT_ERR_INVALID, "bt_warmstart_set_adam: NULL argument or negative step");
+    if (mem_kind != BT_HOST && mem_kind != BT_DEVICE) return fail(BT_ERR_INVALID, "bt_warmstart_set_adam: mem_kind");
+    if (mem_kind == BT_HOST)
+        for (int k = 0; k < W::kNumParams; ++k)
+            if (!std::isfinite(m[k]) || !(v[k] >= 0.f) || !std::isfinite(v[k]))
+                return fail(BT_ERR_INVALID, "bt_warmstart_set_adam: non-finite moment or negative second moment");
+    const cudaMemcpyKind kind = mem_kind == BT_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    BT_CUDA(cudaMemcpyAsync(ws->m.p, m, sizeof(float) * W::kNumParams, kind, ws->stream), "upload moments");
+    BT_CUDA(cudaMemcpyAsync(ws->v.p, v, sizeof(float) * W::kNumParams, kind, ws->stream), "upload moments");
+    BT_CUDA(cudaStreamSynchronize(ws->stream), "bt_warmstart_set_adam: synchronize");
+    ws->adam_t = step;
+    return BT_OK;
+}
+
 int bt_warmstart_get_params(const bt_warmstart* ws, float* params, int32_t mem_kind)
 {
     last_error().clear();

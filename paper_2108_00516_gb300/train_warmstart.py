@@ -97,6 +97,9 @@ def main(argv=None):
     ap.add_argument("--init-seed", type=int, default=0)
     ap.add_argument("--workers", type=int, default=0)
     ap.add_argument("--out", type=str, default=str(DEFAULT_OUT))
+    ap.add_argument("--checkpoint", type=str, default="",
+                    help="after every epoch, save parameters, Adam state, epoch, step and RNG state here")
+    ap.add_argument("--resume", type=str, default="", help="continue from a --checkpoint file")
     a = ap.parse_args(argv)
     log = lambda m: print(m, flush=True)
 
@@ -126,7 +129,16 @@ def main(argv=None):
     log(f"held-out edge error before training: {before}")
     t0 = time.time()
     step = 0
-    for ep in range(a.epochs):
+    first_epoch = 0
+    if a.resume:
+        ck = np.load(a.resume)
+        ws.set_params(ck["params"])
+        ws.set_adam(ck["adam_m"], ck["adam_v"], int(ck["adam_t"]))
+        first_epoch, step = int(ck["epoch"]), int(ck["step"])
+        rng.bit_generator.state = json.loads(str(ck["rng"]))
+        history = json.loads(str(ck["history"]))
+        log(f"resumed from {a.resume}: epoch {first_epoch}, step {step}")
+    for ep in range(first_epoch, a.epochs):
         perm = rng.permutation(n_tr).astype(np.int32)
         run = 0.0
         for s in range(steps_per_epoch):
@@ -138,6 +150,10 @@ def main(argv=None):
             step += 1
         val = mean_loss(ws, ho_ids) if n_ho else float("nan")
         history.append(dict(epoch=ep + 1, train_loss=run, heldout_loss=val, seconds=time.time() - t0))
+        if a.checkpoint:
+            m, v, adam_t = ws.get_adam()
+            np.savez(a.checkpoint, params=ws.get_params(), adam_m=m, adam_v=v, adam_t=adam_t, epoch=ep + 1,
+                     step=step, rng=json.dumps(rng.bit_generator.state), history=json.dumps(history))
         log(f"epoch {ep + 1}: train {run:.4f}  held-out {val:.4f}  ({time.time() - t0:.1f} s)")
     t_train = time.time() - t0
     after = edge_errors(ws, ho_ids) if n_ho else {}

@@ -286,3 +286,44 @@ def test_largest_graph_solve_and_average(bt):
     ws.close()
     for h in (pg, pb, pw):
         h.close()
+
+
+def test_training_resumes_from_checkpoint(bt):
+    """Parameters + Adam state saved after 20 steps and loaded into a fresh
+    warm start continue exactly as the uninterrupted run (bit for bit); a
+    warm start given the parameters alone (moments cleared) takes different
+    steps."""
+    graphs = [S.training_graph(k) for k in range(12)]
+
+    def fresh(params):
+        ws = bt.WarmStart(params)
+        for g in graphs:
+            pg = bt.graph_from_synth(g)
+            ws.add_graph(pg, g.pose_init, g.pose_true)
+            pg.close()
+        return ws
+
+    rng = np.random.default_rng(3)
+    a = fresh(S.warmstart_init(2))
+    n = a.num_samples()
+    batches = [rng.choice(n, 16, replace=False) for _ in range(40)]
+    for ids in batches[:20]:
+        a.train_step(ids, 1e-3)
+    params, (m, v, t) = a.get_params(), a.get_adam()
+    assert t == 20 and np.abs(m).max() > 0 and v.min() >= 0
+    for ids in batches[20:]:
+        a.train_step(ids, 1e-3)
+    b = fresh(params)
+    b.set_adam(m, v, t)
+    for ids in batches[20:]:
+        b.train_step(ids, 1e-3)
+    assert np.array_equal(a.get_params(), b.get_params())
+    assert b.get_adam()[2] == 40
+    c = fresh(params)                      # moments cleared by set_params
+    for ids in batches[20:]:
+        c.train_step(ids, 1e-3)
+    assert not np.array_equal(a.get_params(), c.get_params())
+    with pytest.raises(bt.BTError):
+        c.set_adam(m, -np.abs(v) - 1.0, 5)
+    for w in (a, b, c):
+        w.close()
