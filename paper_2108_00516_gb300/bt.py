@@ -81,11 +81,13 @@ SIGNATURES = {
     "bt_set_matches": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
                                  C.c_int32]),
     "bt_remove_frame": (C.c_int, [C.c_void_p, C.c_int32]),
-    "bt_set_active": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32]),
+    # the per-solve calls take raw addresses (c_void_p also accepts ctypes
+    # pointers): converting an array with data_as costs more than the call
+    "bt_set_active": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "bt_num_active": (C.c_int, [C.c_void_p]),
-    "bt_set_poses": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "bt_set_poses": (C.c_int, [C.c_void_p, C.c_void_p]),
     "bt_get_poses": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
-    "bt_solve": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(bt_solve_report)]),
+    "bt_solve": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "bt_eval_cost": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "bt_batch_create": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
     "bt_batch_destroy": (None, [C.c_void_p]),
@@ -223,6 +225,13 @@ class PoseGraph:
         self._stream = stream
         _check(L.bt_graph_create(C.byref(cfg), _stream_handle(stream), C.byref(self._h)), "bt_graph_create")
         self.config = cfg
+        # per-solve buffers reused across calls (their addresses taken once)
+        self._lib = L
+        self._rep = bt_solve_report()
+        self._rep_addr = C.addressof(self._rep)
+        self._cpi = np.ctypeslib.as_array(self._rep.cost_per_iter)
+        self._pout = np.zeros(16 * BT_MAX_NODES)
+        self._pout_addr = self._pout.ctypes.data
 
     def close(self):
         if self._h:
@@ -279,12 +288,11 @@ class PoseGraph:
 
     def set_active(self, ids):
         arr = np.ascontiguousarray(ids, np.int32)
-        _check(load().bt_set_active(self._h, arr.ctypes.data_as(C.POINTER(C.c_int32)), len(arr)),
-               "bt_set_active")
+        _check(self._lib.bt_set_active(self._h, arr.ctypes.data, len(arr)), "bt_set_active")
 
     @property
     def num_active(self) -> int:
-        n = load().bt_num_active(self._h)
+        n = self._lib.bt_num_active(self._h)
         _check(min(n, 0), "bt_num_active")
         return n
 
@@ -292,7 +300,7 @@ class PoseGraph:
         P = np.ascontiguousarray(poses, np.float64).reshape(-1)
         if P.size != 16 * self.num_active:
             raise ValueError("poses must be (n_active, 4, 4)")
-        _check(load().bt_set_poses(self._h, P.ctypes.data_as(C.POINTER(C.c_double))), "bt_set_poses")
+        _check(self._lib.bt_set_poses(self._h, P.ctypes.data), "bt_set_poses")
 
     def get_poses(self) -> np.ndarray:
         out = np.zeros((self.num_active, 4, 4))
@@ -301,16 +309,20 @@ class PoseGraph:
 
     def solve(self, iters: int, raise_on_error: bool = True):
         """Returns (poses (N,4,4), report dict)."""
-        out = np.zeros((self.num_active, 4, 4))
-        rep = bt_solve_report()
-        st = load().bt_solve(self._h, int(iters), out.ctypes.data_as(C.POINTER(C.c_double)), C.byref(rep))
+        n = self.num_active
+        C.memset(self._rep_addr, 0, C.sizeof(bt_solve_report))
+        st = self._lib.bt_solve(self._h, int(iters), self._pout_addr, self._rep_addr)
         if raise_on_error:
             _check(st, "bt_solve")
-        r = dict(status=st, iters_run=rep.iters_run, cost_init=rep.cost_init, cost_final=rep.cost_final,
+        if st != BT_OK:
+            self._pout[:16 * n] = 0.0    # the poses are not written on failure
+        rep = self._rep
+        k = rep.iters_run
+        r = dict(status=st, iters_run=k, cost_init=rep.cost_init, cost_final=rep.cost_final,
                  dense_cost_final=rep.dense_cost_final, sparse_cost_final=rep.sparse_cost_final,
-                 cost_per_iter=np.array(rep.cost_per_iter[:rep.iters_run]),
-                 dense_inliers=rep.dense_inliers, dense_pixel_pairs=rep.dense_pixel_pairs)
-        return out, r
+                 cost_per_iter=self._cpi[:k].copy(), dense_inliers=rep.dense_inliers,
+                 dense_pixel_pairs=rep.dense_pixel_pairs)
+        return self._pout[:16 * n].reshape(n, 4, 4).copy(), r
 
     def ransac_init(self, hypotheses: int = 256, seed: int = 0, inlier_dist: float = 0.005, refine: bool = False):
         """bt_ransac_init: the paper's coarse initialisation of the free nodes."""

@@ -217,9 +217,9 @@ std::vector<ActiveEdge> bthost::active_edges(const bt_graph* g)
 
 int bthost::resolve_pending(bt_graph* g)
 {
-    bool any = false;
-    for (auto& kv : g->frames) any |= kv.second.pending;
-    if (!any) return BT_OK;
+    // every pending frame holds one read-back slot: none is pending when all
+    // slots are free (no scan over the stored frames on every solve)
+    if ((int)g->free_slots.size() >= g->pin_cap) return BT_OK;
     BT_CUDA(cudaStreamSynchronize(g->stream), "read back frame preparation");
     for (auto& kv : g->frames) {
         Frame& f = kv.second;
@@ -244,6 +244,11 @@ int bthost::build_topology(bt_graph* g, int tile)
     if (N > BT_MAX_NODES) return fail(BT_ERR_INVALID, "solve: more than BT_MAX_NODES active nodes");
     std::vector<bt::NodeDev> nodes(N);
     std::vector<int> tile_node;
+    {
+        size_t nt = 0;
+        for (int k = 0; k < N; ++k) nt += (size_t)(g->frames.at(g->active[k]).M + tile - 1) / tile;
+        tile_node.reserve(nt);
+    }
     int nfree = 0;
     int64_t px = 0;
     for (int k = 0; k < N; ++k) {

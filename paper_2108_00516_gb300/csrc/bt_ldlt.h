@@ -55,9 +55,19 @@ struct LdltScratch {
 // (shared memory, zero on entry) is set when a pivot is not positive; x is
 // then meaningless, and the caller reads *fail after the call (the call ends
 // with a barrier).  t_mid: every thread's clock after the factorisation and
-// D w = z.  All threads of the CTA (blockDim.x == 256) must call it.
+// D w = z.  idle(warp): called once by each of warps 1-7 while warp 0 alone
+// runs the first block of the back substitution (work the caller has for
+// otherwise idle warps; it must not touch H, y or the scratch, and is not
+// called when a pivot failed).  All threads of the CTA (blockDim.x == 256)
+// must call it.
+struct LdltNoIdle {
+    __device__ void operator()(int) const {}
+};
+
+template <typename Idle = LdltNoIdle>
 __device__ __forceinline__ void ldlt_solve(double* __restrict__ H, int ld, int n, double* __restrict__ y,
-                                           const LdltScratch& sc, int* fail, unsigned long long& t_mid)
+                                           const LdltScratch& sc, int* fail, unsigned long long& t_mid,
+                                           const Idle& idle = Idle())
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
     double* rD = sc.rD;
@@ -172,6 +182,7 @@ __device__ __forceinline__ void ldlt_solve(double* __restrict__ H, int ld, int n
     for (int i = tid; i < n; i += nt) y[i] *= rD[i];   // D w = z
     __syncthreads();
     t_mid = clock64();
+    const bool failed = *fail != 0;
     // L^T x = w, unit diagonal (L_ki is stored at (i, k)), in blocks of 32
     // unknowns from the last block up.  Warp 0 runs the chain of one block
     // with the block's values in registers, lane l holding row r0 + l: x_k
@@ -208,6 +219,8 @@ __device__ __forceinline__ void ldlt_solve(double* __restrict__ H, int ld, int n
                 if (i < k) wv = fma(-hk, xk, wv);
             }
             if (i < r1) y[i] = wv;
+        } else if (r0 + 32 >= n && !failed) {
+            idle(warp);
         }
         __syncthreads();
         if (r0 == 0) break;

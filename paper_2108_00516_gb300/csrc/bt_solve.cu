@@ -334,43 +334,51 @@ __device__ void reduce_upair(const SolveArgs& a, int u, double* sm)
     }
 }
 
-// Entry (r, c) of the SE(3) exponential of xi = (v, w) as a 3x4 matrix:
-// R = I + A W + B W^2, t = (I + B W + C W^2) v with W = [w]x, W^2 = w w^T -
-// th^2 I, A = sin(th)/th, B = (1 - cos th)/th^2, C = (th - sin th)/th^3.  One
-// thread per entry: a warp-wide FP64 instruction costs its sub-partition
-// ~64 cycles whatever the number of active lanes, so the twelve entries of
-// each node are spread over lanes instead of running one node per lane.
-// Below th = 0.1 the coefficients come from their Taylor series through th^8
-// (truncation < 3e-18), which keeps the FP64 chain short; above it from sincos.
-__device__ double se3_exp_entry(const double* xi, int r, int c)
+// The SE(3) exponential of xi = (v, w) as a 3x4 matrix:
+// R = I + A W + B W^2, t = (I + B W + C W^2) v = v + B (w x v) + C (w (w.v) -
+// th^2 v), with W = [w]x, W^2 = w w^T - th^2 I, A = sin(th)/th,
+// B = (1 - cos th)/th^2, C = (th - sin th)/th^3.  Below th = 0.1 the
+// coefficients come from their Taylor series through th^8 (truncation
+// < 3e-18), which keeps FP64 sincos off the critical path; above it from
+// sincos.  which: 0 = A, 1 = B, 2 = C.
+__device__ double se3_exp_coef(const double* xi, int which)
 {
-    const double w[3] = {xi[3], xi[4], xi[5]};
-    const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-    double A, B, C;
+    const double th2 = fma(xi[5], xi[5], fma(xi[4], xi[4], xi[3] * xi[3]));
     if (th2 < 0.01) {
-        A = 1.0 + th2 * (-1.0 / 6.0 + th2 * (1.0 / 120.0 + th2 * (-1.0 / 5040.0 + th2 * (1.0 / 362880.0))));
-        B = 0.5 + th2 * (-1.0 / 24.0 + th2 * (1.0 / 720.0 + th2 * (-1.0 / 40320.0 + th2 * (1.0 / 3628800.0))));
-        C = 1.0 / 6.0 + th2 * (-1.0 / 120.0 + th2 * (1.0 / 5040.0 + th2 * (-1.0 / 362880.0 + th2 * (1.0 / 39916800.0))));
-    } else {
-        const double th = sqrt(th2);
-        double sn, cs;
-        sincos(th, &sn, &cs);
-        A = sn / th;
-        B = (1.0 - cs) / th2;
-        C = (th - sn) / (th2 * th);
+        if (which == 0)
+            return 1.0 + th2 * (-1.0 / 6.0 + th2 * (1.0 / 120.0 + th2 * (-1.0 / 5040.0 + th2 * (1.0 / 362880.0))));
+        if (which == 1)
+            return 0.5 + th2 * (-1.0 / 24.0 + th2 * (1.0 / 720.0 + th2 * (-1.0 / 40320.0 + th2 * (1.0 / 3628800.0))));
+        return 1.0 / 6.0 + th2 * (-1.0 / 120.0 + th2 * (1.0 / 5040.0 + th2 * (-1.0 / 362880.0 + th2 * (1.0 / 39916800.0))));
     }
-    auto Wm = [&](int i, int j) -> double {      // [w]x
-        if (i == j) return 0.0;
-        const int k = 3 - i - j;
-        const bool plus = (i + 1) % 3 == j;        // (0,1), (1,2), (2,0): -w_k
-        return plus ? -w[k] : w[k];
-    };
-    auto W2m = [&](int i, int j) -> double { return w[i] * w[j] - (i == j ? th2 : 0.0); };
-    if (c < 3) return (r == c ? 1.0 : 0.0) + A * Wm(r, c) + B * W2m(r, c);
-    double t = 0.0;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) t += ((r == k ? 1.0 : 0.0) + B * Wm(r, k) + C * W2m(r, k)) * xi[k];
-    return t;
+    const double th = sqrt(th2);
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    if (which == 0) return sn / th;
+    if (which == 1) return (1.0 - cs) / th2;
+    return (th - sn) / (th2 * th);
+}
+
+// Entry (r, c) of exp(xi); cf = (th^2, A, B, C).  One thread per entry: a
+// warp-wide FP64 instruction costs its sub-partition ~64 cycles whatever the
+// number of active lanes, so the entries are spread over lanes.
+__device__ double se3_exp_entry(const double* xi, const double* cf, int r, int c)
+{
+    const double th2 = cf[0], A = cf[1], B = cf[2], C = cf[3];
+    const double* w = xi + 3;
+    if (c < 3) {
+        // [w]x (r, c): 0 on the diagonal, -w_k for (0,1), (1,2), (2,0), +w_k
+        // for the transposed positions, k the third index
+        const int k = 3 - r - c;
+        const double Wrc = r == c ? 0.0 : ((r + 1) % 3 == c ? -w[k] : w[k]);
+        const double W2rc = fma(w[r], w[c], r == c ? -th2 : 0.0);
+        return fma(B, W2rc, fma(A, Wrc, r == c ? 1.0 : 0.0));
+    }
+    const int r1 = (r + 1) % 3, r2 = (r + 2) % 3;
+    const double cross = fma(w[r1], xi[r2], -(w[r2] * xi[r1]));     // (w x v)_r
+    const double wv = fma(w[2], xi[2], fma(w[1], xi[1], w[0] * xi[0]));
+    const double inner = fma(w[r], wv, -(th2 * xi[r]));              // (W^2 v)_r
+    return fma(C, inner, fma(B, cross, xi[r]));
 }
 
 // Last CTA: energies, then (full) assembly of H and g over the free nodes,
@@ -432,27 +440,31 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
     }
     for (int q = tid; q < 12 * N; q += nt) ps[q] = a.pose[q];
     if (tid == 0) s_fail = 0;
-    {   // pair blocks to shared memory, eight independent loads in flight per thread
+    {   // pair blocks to shared memory, up to twelve independent loads in
+        // flight per thread (one round for ten nodes: each round costs an
+        // L2 round trip)
         const double2* src = reinterpret_cast<const double2*>(a.upairblk);
         double2* dst = reinterpret_cast<double2*>(stage);
         const int n2 = (int)(stage_len / 2);
-        for (int q0 = tid; q0 < n2; q0 += 8 * nt) {
-            double2 v[8];
+        for (int q0 = tid; q0 < n2; q0 += 12 * nt) {
+            double2 v[12];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
+            for (int k = 0; k < 12; ++k) {
                 const int q = q0 + k * nt;
                 if (q < n2) v[k] = __ldcg(src + q);
             }
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
+            for (int k = 0; k < 12; ++k) {
                 const int q = q0 + k * nt;
                 if (q < n2) dst[q] = v[k];
             }
         }
     }
     __syncthreads();
-    // the last warp (one diagonal block at most) adds up the energies
-    if (staged_costs && warp == (nt >> 5) - 1) write_costs(stage, true);
+    // (with staged blocks the energies are added up during the update, by a
+    // warp that has no other work there: here their FP64 adds would hold
+    // one sub-partition's DP unit beside its share of the diagonal sums)
+    const int cost_warp = (nt >> 5) - 1;
     const bool staged = a.stage_blocks != 0;
     auto blk = [&](size_t q) { return staged ? stage[q] : __ldcg(a.upairblk + q); };
     // diagonal blocks and gradient: one thread per (free node, value), values
@@ -482,9 +494,12 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
     const int nob = nf * (nf - 1) / 2;
     for (int q = tid; q < nob * 36; q += nt) {
         const int b = q / 36, e = q % 36, rr = e / 6, cc = e % 6;
-        int fa = 1, rem = b;
-        while (rem >= fa) { rem -= fa; ++fa; }
-        const int fb = rem;
+        // b = fa (fa - 1) / 2 + fb with fb < fa: fa from the square root,
+        // corrected by one step either way (b < 253, exact in FP32)
+        int fa = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)b)) * 0.5f);
+        if (fa * (fa - 1) / 2 > b) --fa;
+        if (fa * (fa + 1) / 2 <= b) ++fa;
+        const int fb = b - fa * (fa - 1) / 2;
         const int A = node_of[fa], B = node_of[fb];
         const int u = A < B ? upair_index(A, B, N) : upair_index(B, A, N);
         H[(6 * fa + rr) * ld + 6 * fb + cc] = blk((size_t)u * kUPairBlk + 42 + (A < B ? rr * 6 + cc : cc * 6 + rr));
@@ -498,6 +513,7 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
             a.ne_out[q] = r >= c ? H[r * ld + c] : H[c * ld + r];
         }
         for (int q = tid; q < n; q += nt) a.ne_out[n * n + q] = -y[q];
+        if (staged_costs && warp == cost_warp) write_costs(stage, true);
         return;
     }
     unsigned long long t1 = clock64();
@@ -581,6 +597,7 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
         }
         if (s_fail) {
             if (tid == 0) a.ctrl->status = -4;
+            if (staged_costs && warp == cost_warp) write_costs(stage, true);
             return;
         }
         for (int i = tid; i < n; i += nt) y[i] = xv[i];
@@ -594,22 +611,52 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
     sc.colb = colb;
     sc.tab = reinterpret_cast<int*>(colb + 2 * n);
     sc.part = reinterpret_cast<double*>(node_of + kMaxNodes);
-    ldlt_solve(H, ld, n, y, sc, &s_fail, t2);
+    // the energies are added up by the last warp while warp 0 runs the
+    // first block of the back substitution alone
+    ldlt_solve(H, ld, n, y, sc, &s_fail, t2, [&](int w) {
+        if (staged_costs && w == cost_warp) write_costs(stage, true);
+    });
     if (s_fail) {
         if (tid == 0) a.ctrl->status = -4;
+        if (staged_costs && warp == cost_warp) write_costs(stage, true);
         return;
     }
     __syncthreads();
     t3 = clock64();
     }
-    // T_A <- T_A exp(dx_A): one thread per entry of exp(dx_A), then one per
-    // entry of the product (the look-ahead columns and tinv are free now)
+    // T_A <- T_A exp(dx_A) in three steps: the coefficients of exp per node
+    // (warps 0-2, one coefficient each, so the three FP64 chains run on
+    // three sub-partitions), the entries of exp(dx_A) (one thread each), the
+    // products T_A exp(dx_A) (one thread each).  The look-ahead columns, rD
+    // and tinv are free now (after PCG the last warp adds up the energies
+    // meanwhile; the Cholesky path has done so during its back substitution).
     {
+        double* cf = rD;       // [nf][4]: th^2, A, B, C
         double* E = colb;      // [nf][12]
         double* P = tinv;      // [nf][12]
+        if (warp < 3 && lane < nf) {
+            const double* xi = y + 6 * lane;
+            const double c = se3_exp_coef(xi, warp);
+            cf[4 * lane + 1 + warp] = c;
+            if (warp == 0) cf[4 * lane] = fma(xi[5], xi[5], fma(xi[4], xi[4], xi[3] * xi[3]));
+        }
+        if (a.solver == 1 && staged_costs && warp == cost_warp) write_costs(stage, true);
+        __syncthreads();
         for (int q = tid; q < 12 * nf; q += nt) {
-            const int e = q % 12;
-            E[q] = se3_exp_entry(y + 6 * (q / 12), e >> 2, e & 3);
+            // rotation entries (f, r, c < 3) first, then the translations
+            int f, r, c;
+            if (q < 9 * nf) {
+                f = q / 9;
+                const int e = q - 9 * f;
+                r = e / 3;
+                c = e - 3 * r;
+            } else {
+                const int e = q - 9 * nf;
+                f = e / 3;
+                r = e - 3 * f;
+                c = 3;
+            }
+            E[f * 12 + r * 4 + c] = se3_exp_entry(y + 6 * f, cf + 4 * f, r, c);
         }
         __syncthreads();
         for (int q = tid; q < 12 * nf; q += nt) {
