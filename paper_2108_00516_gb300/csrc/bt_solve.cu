@@ -275,22 +275,26 @@ __device__ void reduce_upair(const SolveArgs& a, int u, double* sm)
         K[tid] = tot[d * 32 + sym_idx(r, cc)];
     }
     __syncthreads();
+    // the 6-term products as two independent 3-term FMA chains (a dependent
+    // FP64 operation costs ~100 cycles on the critical path)
     if (tid < 72) {
         const int d = tid / 36, q = tid % 36, r = q / 6, cc = q % 6;
-        double x = 0.0;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) x += K[d * 36 + r * 6 + k] * Ad[d * 36 + k * 6 + cc];
-        KA[tid] = x;
+        const double* Kr = K + d * 36 + r * 6;
+        const double* Ac = Ad + d * 36 + cc;
+        const double x0 = fma(Kr[2], Ac[12], fma(Kr[1], Ac[6], Kr[0] * Ac[0]));
+        const double x1 = fma(Kr[5], Ac[30], fma(Kr[4], Ac[24], Kr[3] * Ac[18]));
+        KA[tid] = x0 + x1;
     }
     __syncthreads();
     // K'_d = Ad_d^T K_d Ad_d and g'_d = Ad_d^T g_d per direction (threads
     // 0-83), and the three sparse blocks (threads 128-235), side by side
     if (tid < 72) {
         const int d = tid / 36, q = tid % 36, r = q / 6, cc = q % 6;
-        double x = 0.0;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) x += Ad[d * 36 + k * 6 + r] * KA[d * 36 + k * 6 + cc];
-        K[tid] = x;
+        const double* Ar = Ad + d * 36 + r;
+        const double* Bc = KA + d * 36 + cc;
+        const double x0 = fma(Ar[12], Bc[12], fma(Ar[6], Bc[6], Ar[0] * Bc[0]));
+        const double x1 = fma(Ar[30], Bc[30], fma(Ar[24], Bc[24], Ar[18] * Bc[18]));
+        K[tid] = x0 + x1;
     } else if (tid < 84) {
         const int d = (tid - 72) / 6, r = (tid - 72) % 6;
         double g = 0.0;
@@ -385,13 +389,40 @@ __device__ double se3_exp_entry(const double* xi, const double* cf, int r, int c
 // the FP64 solve of H dx = -g (square-root-free Cholesky with a one-column
 // look-ahead, bt_ldlt.h; or PCG, the paper's inner solver), and finally
 // T <- T exp(dx).
+// The first global reads of the last CTA, issued by every CTA of the reduce
+// kernel before its pair stage: the last CTA is only known after the
+// hand-off, and these values (the sticky status of earlier iterations, the
+// nodes' free indices, the poses) do not change within the kernel, so their
+// L2 round trip overlaps the pair stage instead of following the hand-off.
+// Thread t holds pose entries t and t + blockDim.x (12 N <= 2 * 256) and the
+// free index of node t.
+static_assert(12 * kMaxNodes <= 2 * kThreads && kMaxNodes <= kThreads, "final_prefetch: two pose entries a thread");
+struct FinalPrefetch {
+    int status;
+    int free_idx;
+    double pose0, pose1;
+};
+
 template <bool kFull>
-__device__ void final_phase(const SolveArgs& a, int iter, double* sm)
+__device__ __forceinline__ FinalPrefetch final_prefetch(const SolveArgs& a)
+{
+    FinalPrefetch pf{0, -1, 0.0, 0.0};
+    if (!kFull) return pf;
+    const int tid = threadIdx.x, nt = blockDim.x, N = a.N;
+    pf.status = __ldcg(&a.ctrl->status);
+    if (tid < N) pf.free_idx = __ldcg(&a.nodes[tid].free_idx);
+    if (tid < 12 * N) pf.pose0 = __ldcg(a.pose + tid);
+    if (tid + nt < 12 * N) pf.pose1 = __ldcg(a.pose + tid + nt);
+    return pf;
+}
+
+template <bool kFull>
+__device__ void final_phase(const SolveArgs& a, int iter, double* sm, const FinalPrefetch& pf)
 {
     const int N = a.N, U = a.n_upairs;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
     const int nf = a.n_free, n = 6 * nf;
-    const int status0 = kFull ? *(volatile int*)&a.ctrl->status : 0;
+    const int status0 = kFull ? pf.status : 0;
     // energies of the iteration: from the staged pair blocks when a full
     // solve stages them, else straight from global memory
     const bool staged_costs = kFull && n > 0 && status0 == 0 && a.stage_blocks != 0;
@@ -434,11 +465,9 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm)
     const size_t stage_len = a.stage_blocks ? (size_t)U * kUPairBlk : 0;
     int* node_of = reinterpret_cast<int*>(stage + stage_len);
     __shared__ int s_fail;
-    for (int k = tid; k < N; k += nt) {
-        const int f = a.nodes[k].free_idx;
-        if (f >= 0) node_of[f] = k;
-    }
-    for (int q = tid; q < 12 * N; q += nt) ps[q] = a.pose[q];
+    if (tid < N && pf.free_idx >= 0) node_of[pf.free_idx] = tid;
+    if (tid < 12 * N) ps[tid] = pf.pose0;
+    if (tid + nt < 12 * N) ps[tid + nt] = pf.pose1;
     if (tid == 0) s_fail = 0;
     {   // pair blocks to shared memory, up to twelve independent loads in
         // flight per thread (one round for ten nodes: each round costs an
@@ -689,6 +718,7 @@ __global__ void __launch_bounds__(kThreads, 1) reduce_kernel(SolveArgs a, int it
     extern __shared__ double sm[];
     __shared__ int s_last;
     const int b = blockIdx.x;
+    const FinalPrefetch pf = final_prefetch<kFull>(a);
     if (b < a.n_upairs) reduce_upair<kFull>(a, b, sm);
     __threadfence();
     __syncthreads();
@@ -700,7 +730,7 @@ __global__ void __launch_bounds__(kThreads, 1) reduce_kernel(SolveArgs a, int it
     if (!s_last) return;
     __threadfence();
     if (threadIdx.x == 0) a.ctrl->counter = 0u;
-    final_phase<kFull>(a, iter, sm);
+    final_phase<kFull>(a, iter, sm, pf);
 }
 
 static size_t reduce_smem_bytes_for(int n_free, int N, bool stage)
@@ -773,7 +803,7 @@ __global__ void __launch_bounds__(kThreads, 1) batch_solve_kernel(const SolveArg
     __shared__ SolveArgs sa;
     if (threadIdx.x == 0) sa = args[blockIdx.x];
     __syncthreads();
-    final_phase<kFull>(sa, iter, smd);
+    final_phase<kFull>(sa, iter, smd, final_prefetch<kFull>(sa));
 }
 
 cudaError_t launch_batch_xforms(const SolveArgs* args_dev, int n_graphs, cudaStream_t s)
