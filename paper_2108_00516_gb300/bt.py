@@ -232,6 +232,7 @@ class PoseGraph:
         self._cpi = np.ctypeslib.as_array(self._rep.cost_per_iter)
         self._pout = np.zeros(16 * BT_MAX_NODES)
         self._pout_addr = self._pout.ctypes.data
+        self._n_active = None   # cached count; every method that changes the active set resets it
 
     def close(self):
         if self._h:
@@ -252,6 +253,7 @@ class PoseGraph:
 
     def add_frame(self, depth, normals, mask, intrinsics, pose, fixed=False, matches=()):
         """matches: iterable of (other_frame_id, pts_self (n,3), pts_other (n,3))."""
+        self._n_active = None
         L = load()
         d, kd, mk = _ptr(depth, np.float32)
         n, kn, mk2 = _ptr(normals, np.float32)
@@ -284,16 +286,22 @@ class PoseGraph:
                "bt_set_matches")
 
     def remove_frame(self, frame_id):
+        self._n_active = None
         _check(load().bt_remove_frame(self._h, int(frame_id)), "bt_remove_frame")
 
     def set_active(self, ids):
         arr = np.ascontiguousarray(ids, np.int32)
+        self._n_active = None
         _check(self._lib.bt_set_active(self._h, arr.ctypes.data, len(arr)), "bt_set_active")
+        self._n_active = len(arr)
 
     @property
     def num_active(self) -> int:
+        if self._n_active is not None:
+            return self._n_active
         n = self._lib.bt_num_active(self._h)
         _check(min(n, 0), "bt_num_active")
+        self._n_active = n
         return n
 
     def set_poses(self, poses):

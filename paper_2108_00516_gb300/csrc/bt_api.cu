@@ -313,8 +313,6 @@ int bthost::build_topology(bt_graph* g, int tile)
     }
     BT_CUDA(g->d_tab.ensure(tab_bytes), "alloc tables");
     BT_CUDA(g->d_state.ensure(StateLayout(N).bytes), "alloc solve state");
-    BT_CUDA(g->d_xf.ensure(sizeof(float) * 12 * N * N), "alloc xf");
-    BT_CUDA(g->d_xinv.ensure(sizeof(float) * 12 * N), "alloc xinv");
     BT_CUDA(g->d_dpart.ensure(sizeof(float) * bt::kDenseVals * (size_t)std::max(T, 1) * std::max(N - 1, 1)),
             "alloc dpart");
     BT_CUDA(g->d_spart.ensure(sizeof(float) * bt::kSparseVals * std::max(E, 1)), "alloc spart");
@@ -352,8 +350,8 @@ int bthost::build_topology(bt_graph* g, int tile)
     a.ctrl = reinterpret_cast<bt::Control*>(state);
     a.pose = reinterpret_cast<double*>(state + L.pose);
     a.costs = reinterpret_cast<double*>(state + L.costs);
-    a.xf = g->d_xf.as<float>();
-    a.xinv = g->d_xinv.as<float>();
+    a.xf = reinterpret_cast<float*>(state + L.xf);
+    a.xinv = reinterpret_cast<float*>(state + L.xinv);
     a.dpart = g->d_dpart.as<float>();
     a.spart = g->d_spart.as<float>();
     a.upairblk = g->d_upairblk.as<double>();
@@ -367,25 +365,56 @@ int bthost::build_topology(bt_graph* g, int tile)
     return BT_OK;
 }
 
-void bthost::stage_state(const bt_graph* g, char* blk)
+void bthost::stage_state(const bt_graph* g, char* blk, bool xforms)
 {
     const int N = (int)g->active.size();
     const StateLayout L(N);
     std::memset(blk, 0, sizeof(bt::Control));
     double* pose = reinterpret_cast<double*>(blk + L.pose);
     for (int k = 0; k < N; ++k) std::memcpy(pose + 12 * (size_t)k, g->frames.at(g->active[k]).pose, sizeof(double) * 12);
+    if (!xforms) return;
+    // the transforms the solve kernel forms after each update (write_xforms),
+    // with the same operations in the same order (std::fma is the correctly
+    // rounded fused operation, as on the device): T_i^-1 in FP64, then
+    // M = T_j T_i^-1 in FP64, each entry rounded once to single precision
+    float* xf = reinterpret_cast<float*>(blk + L.xf);
+    float* xinv = reinterpret_cast<float*>(blk + L.xinv);
+    std::vector<double> inv(12 * (size_t)N);
+    for (int i = 0; i < N; ++i) {
+        const double* T = pose + 12 * (size_t)i;
+        for (int r = 0; r < 3; ++r) {
+            for (int c = 0; c < 3; ++c) inv[12 * i + r * 4 + c] = T[c * 4 + r];
+            inv[12 * i + r * 4 + 3] = -std::fma(T[2 * 4 + r], T[11], std::fma(T[1 * 4 + r], T[7], T[0 * 4 + r] * T[3]));
+        }
+        for (int e = 0; e < 12; ++e) xinv[12 * i + e] = (float)inv[12 * i + e];
+    }
+    for (int i = 0; i < N; ++i) {
+        const double* B = inv.data() + 12 * (size_t)i;
+        for (int j = 0; j < N; ++j) {
+            if (j == i) continue;
+            const double* A = pose + 12 * (size_t)j;
+            float* m = xf + ((size_t)i * N + j) * 12;
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 4; ++c) {
+                    double s = std::fma(A[r * 4 + 2], B[2 * 4 + c],
+                                        std::fma(A[r * 4 + 1], B[1 * 4 + c], A[r * 4 + 0] * B[0 * 4 + c]));
+                    if (c == 3) s += A[r * 4 + 3];
+                    m[r * 4 + c] = (float)s;
+                }
+        }
+    }
 }
 
 int bthost::upload_poses(bt_graph* g)
 {
     const StateLayout L((int)g->active.size());
     BT_CUDA(g->pin_state.acquire(L.bytes), "cudaHostAlloc(state staging)");
-    stage_state(g, g->pin_state.at<char>(0));
+    // the poses and the first pass's transforms in one copy (no transform
+    // kernel ahead of the first residual pass)
+    stage_state(g, g->pin_state.at<char>(0), true);
     BT_CUDA(cudaMemcpyAsync(g->d_state.p, g->pin_state.p, L.upload_bytes(), cudaMemcpyHostToDevice, g->stream),
             "upload poses");
     BT_CUDA(g->pin_state.mark(g->stream), "record state upload");
-    BT_CUDA(bt::launch_xforms(g->args, g->stream), "launch xform");
-    g->prof.xform_launches++;
     return BT_OK;
 }
 

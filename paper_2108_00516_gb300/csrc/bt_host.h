@@ -153,11 +153,16 @@ inline int order_streams(cudaStream_t from, cudaStream_t to)
 // uploads the leading `upload_bytes` (cleared control words and the starting
 // poses) in one copy and reads `readback_bytes(iters)` back in one copy.
 struct StateLayout {
-    size_t pose = 0, costs = 0, bytes = 0;
+    size_t pose = 0, xf = 0, xinv = 0, costs = 0, bytes = 0;
     explicit StateLayout(int N)
     {
         pose = align_up(sizeof(bt::Control), 64);
-        costs = align_up(pose + sizeof(double) * 12 * (size_t)N, 64);
+        // the single-precision pair transforms of the first pass, formed on
+        // the host and uploaded with the poses (later passes' are written by
+        // the solve kernel in place)
+        xf = align_up(pose + sizeof(double) * 12 * (size_t)N, 64);
+        xinv = align_up(xf + sizeof(float) * 12 * (size_t)N * N, 64);
+        costs = align_up(xinv + sizeof(float) * 12 * (size_t)N, 64);
         bytes = align_up(costs + sizeof(double) * 4 * (BT_MAX_REPORT_ITERS + 1), 256);
     }
     size_t upload_bytes() const { return costs; }
@@ -275,7 +280,7 @@ struct bt_graph {
     // per-solve state: the topology tables (nodes, edges, tile owners, node
     // pairs, pair -> edge) in one device block staged through pinned memory,
     // the solve state block (StateLayout) likewise, and the work buffers
-    bthost::DevBuf d_tab, d_state, d_xf, d_xinv, d_dpart, d_spart, d_upairblk;
+    bthost::DevBuf d_tab, d_state, d_dpart, d_spart, d_upairblk;
     bthost::DevBuf d_debug;             // outputs of the diagnostic calls
     bthost::PinBuf pin_tab, pin_state;
     bthost::PinBuf pin_match;           // staging of the correspondence sets given to bt_add_frame
@@ -303,7 +308,7 @@ struct bt_graph {
         pin_state.release();
         pin_match.release();
         for (cudaEvent_t e : events) cudaEventDestroy(e);
-        for (bthost::DevBuf* b : {&up_depth, &up_normals, &up_mask, &prep_blk, &d_tab, &d_state, &d_xf, &d_xinv,
+        for (bthost::DevBuf* b : {&up_depth, &up_normals, &up_mask, &prep_blk, &d_tab, &d_state,
                                   &d_dpart, &d_spart, &d_upairblk, &d_debug})
             b->release();
     }
@@ -371,7 +376,9 @@ int resolve_pending(bt_graph* g);
 int upload_poses(bt_graph* g);
 // Writes cleared control words and the stored poses of g's active nodes into
 // a state block at `blk` (host memory laid out as StateLayout).
-void stage_state(const bt_graph* g, char* blk);
+// Cleared control words and the graph's poses into the staging block `blk`;
+// with `xforms`, also the first pass's single-precision transforms.
+void stage_state(const bt_graph* g, char* blk, bool xforms = false);
 // Fills `rep` (when not NULL) from a state block read back after `iters`
 // iterations and returns the solve's status (BT_OK or BT_ERR_SINGULAR).
 int fill_report(bt_graph* g, const char* blk, int iters, bt_solve_report* rep);
