@@ -32,7 +32,10 @@ def nvcc() -> str:
 
 
 def _flags(ptxas_verbose: bool):
+    # -ffp-contract=off: host arithmetic is not fused, so the host reproduces
+    # the device's explicitly rounded operations bit for bit
     f = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
+         "-Xcompiler", "-ffp-contract=off",
          f"-I{INCLUDE}", f"-I{CSRC}", "--expt-relaxed-constexpr"]
     if ptxas_verbose:
         f += ["-Xptxas", "-v"]

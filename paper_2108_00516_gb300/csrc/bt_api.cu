@@ -7,6 +7,7 @@
 //   xform  ->  iters x [residual(full) -> reduce(full)]  ->  residual(cost) -> reduce(cost)
 // and then one device-to-host copy of poses, costs and status.
 #include "bt_host.h"
+#include "bt_xform.cuh"
 
 #include <cuda_runtime.h>
 
@@ -373,36 +374,22 @@ void bthost::stage_state(const bt_graph* g, char* blk, bool xforms)
     double* pose = reinterpret_cast<double*>(blk + L.pose);
     for (int k = 0; k < N; ++k) std::memcpy(pose + 12 * (size_t)k, g->frames.at(g->active[k]).pose, sizeof(double) * 12);
     if (!xforms) return;
-    // the transforms the solve kernel forms after each update (write_xforms),
-    // with the same operations in the same order (std::fma is the correctly
-    // rounded fused operation, as on the device): T_i^-1 in FP64, then
-    // M = T_j T_i^-1 in FP64, each entry rounded once to single precision
+    // the transforms the solve kernel forms after each update (write_xforms,
+    // bt_xform.cuh), with the same operations in the same order
     float* xf = reinterpret_cast<float*>(blk + L.xf);
     float* xinv = reinterpret_cast<float*>(blk + L.xinv);
-    std::vector<double> inv(12 * (size_t)N);
-    for (int i = 0; i < N; ++i) {
-        const double* T = pose + 12 * (size_t)i;
-        for (int r = 0; r < 3; ++r) {
-            for (int c = 0; c < 3; ++c) inv[12 * i + r * 4 + c] = T[c * 4 + r];
-            inv[12 * i + r * 4 + 3] = -std::fma(T[2 * 4 + r], T[11], std::fma(T[1 * 4 + r], T[7], T[0 * 4 + r] * T[3]));
-        }
-        for (int e = 0; e < 12; ++e) xinv[12 * i + e] = (float)inv[12 * i + e];
-    }
-    for (int i = 0; i < N; ++i) {
-        const double* B = inv.data() + 12 * (size_t)i;
+    std::vector<float> sp((size_t)bt::kXfSplit * N);
+    for (int i = 0; i < N; ++i)
+        for (int k = 0; k < 15; ++k) bt::xf_split_entry(pose + 12 * (size_t)i, k, sp.data() + bt::kXfSplit * i);
+    for (int i = 0; i < N; ++i)
+        for (int e = 0; e < 12; ++e) xinv[12 * i + e] = bt::xf_inv_entry(sp.data() + bt::kXfSplit * i, e);
+    for (int i = 0; i < N; ++i)
         for (int j = 0; j < N; ++j) {
             if (j == i) continue;
-            const double* A = pose + 12 * (size_t)j;
-            float* m = xf + ((size_t)i * N + j) * 12;
-            for (int r = 0; r < 3; ++r)
-                for (int c = 0; c < 4; ++c) {
-                    double s = std::fma(A[r * 4 + 2], B[2 * 4 + c],
-                                        std::fma(A[r * 4 + 1], B[1 * 4 + c], A[r * 4 + 0] * B[0 * 4 + c]));
-                    if (c == 3) s += A[r * 4 + 3];
-                    m[r * 4 + c] = (float)s;
-                }
+            for (int e = 0; e < 12; ++e)
+                xf[((size_t)i * N + j) * 12 + e] =
+                    bt::xf_pair_entry(sp.data() + bt::kXfSplit * j, sp.data() + bt::kXfSplit * i, e);
         }
-    }
 }
 
 int bthost::upload_poses(bt_graph* g)

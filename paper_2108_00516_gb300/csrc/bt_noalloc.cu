@@ -15,6 +15,7 @@
 // streams, or two host threads) race on it.
 #include "bt.h"
 #include "bt_assoc.cuh"
+#include "bt_xform.cuh"
 
 #include <cuda_runtime.h>
 
@@ -166,25 +167,16 @@ int fail(int code, const std::string& msg)
     return code;
 }
 
-// M = T_dst T_src^-1 in FP64 with fused multiply-adds in the library's fixed
-// order (std::fma is the correctly rounded fused operation, as on the
-// device), rounded once to single precision -- the same bits the solve
-// kernels derive on the device.
+// M = T_dst T_src^-1 as the solve kernels form it (bt_xform.cuh: double-float
+// arithmetic, the same operations in the same order) -- the same bits.
 void pair_transform(const double* Tsrc, const double* Tdst, float* m)
 {
-    double inv[12];
-    for (int r = 0; r < 3; ++r) {
-        for (int c = 0; c < 3; ++c) inv[r * 4 + c] = Tsrc[c * 4 + r];
-        inv[r * 4 + 3] = -std::fma(Tsrc[2 * 4 + r], Tsrc[11], std::fma(Tsrc[1 * 4 + r], Tsrc[7], Tsrc[0 * 4 + r] * Tsrc[3]));
+    float ss[bt::kXfSplit], sd[bt::kXfSplit];
+    for (int k = 0; k < 15; ++k) {
+        bt::xf_split_entry(Tsrc, k, ss);
+        bt::xf_split_entry(Tdst, k, sd);
     }
-    for (int r = 0; r < 3; ++r) {
-        for (int c = 0; c < 4; ++c) {
-            double v = std::fma(Tdst[r * 4 + 2], inv[2 * 4 + c],
-                                std::fma(Tdst[r * 4 + 1], inv[1 * 4 + c], Tdst[r * 4 + 0] * inv[0 * 4 + c]));
-            if (c == 3) v += Tdst[r * 4 + 3];
-            m[r * 4 + c] = (float)v;
-        }
-    }
+    for (int e = 0; e < 12; ++e) m[e] = bt::xf_pair_entry(sd, ss, e);
 }
 
 }  // namespace

@@ -14,6 +14,7 @@
 // bt_residual.cu for why every iterate equals the left-perturbation one).
 #include "bt_internal.h"
 #include "bt_ldlt.h"
+#include "bt_xform.cuh"
 
 #include <cuda_runtime.h>
 #include <math.h>
@@ -22,50 +23,41 @@
 namespace bt {
 
 // ---------------------------------------------------------------------------
-// Single-precision transforms of the FP64 poses.  M = T_j T_i^-1 is formed in
-// FP64 with fused multiply-adds in a fixed order (fma(a2, b2, fma(a1, b1,
-// a0 * b0)), plus the translation) and rounded once to single precision, so
-// its bits are reproducible (the no-alloc call forms the same bits on the
-// host with std::fma).
+// Single-precision transforms of the FP64 poses (bt_xform.cuh: double-float
+// arithmetic on the FP32 pipes, the same bits the host forms for the first
+// pass of a solve and for the no-alloc call).
 // ---------------------------------------------------------------------------
 
-// Writes xf[i*N+j] = float(T_j T_i^-1) (i != j) and xinv[i] = float(T_i^-1) with the
-// threads of one CTA, one matrix entry per thread (the FP64 inverse first, then
-// the products).  `tinv` is shared scratch of 12 * N doubles.
-__device__ void write_xforms(const SolveArgs& a, double* __restrict__ tinv, const double* __restrict__ pose)
+// Writes xf[i*N+j] = T_j T_i^-1 (i != j) and xinv[i] = T_i^-1 in single
+// precision with the threads of one CTA: the splits of every pose first,
+// then one matrix entry per thread.  `sf` is shared scratch of
+// kXfSplit * N floats.
+__device__ void write_xforms(const SolveArgs& a, float* __restrict__ sf, const double* __restrict__ pose)
 {
     const int N = a.N, tid = threadIdx.x, nt = blockDim.x;
-    for (int id = tid; id < N * 12; id += nt) {
-        const int i = id / 12, e = id % 12, r = e / 4, c = e % 4;
-        const double* T = pose + i * 12;
-        double v;
-        if (c < 3) {
-            v = T[c * 4 + r];
-        } else {
-            v = -fma(T[2 * 4 + r], T[11], fma(T[1 * 4 + r], T[7], T[0 * 4 + r] * T[3]));
-        }
-        tinv[id] = v;
-        a.xinv[id] = __double2float_rn(v);
+    for (int id = tid; id < N * 15; id += nt) {
+        const int i = id / 15;
+        xf_split_entry(pose + i * 12, id - 15 * i, sf + kXfSplit * i);
     }
     __syncthreads();
+    for (int id = tid; id < N * 12; id += nt) {
+        const int i = id / 12;
+        a.xinv[id] = xf_inv_entry(sf + kXfSplit * i, id - 12 * i);
+    }
     // pairs i != j only (the residual pass never reads xf[i*N+i])
     const int M = N > 1 ? N - 1 : 0;
     for (int id = tid; id < N * M * 12; id += nt) {
-        const int pr = id / 12, e = id % 12, r = e / 4, c = e % 4;
+        const int pr = id / 12, e = id % 12;
         const int i = pr / M, jj = pr % M, j = jj < i ? jj : jj + 1;
-        const double* A = pose + j * 12;     // T_j
-        const double* B = tinv + i * 12;     // T_i^-1
-        double s = fma(A[r * 4 + 2], B[2 * 4 + c], fma(A[r * 4 + 1], B[1 * 4 + c], A[r * 4 + 0] * B[0 * 4 + c]));
-        if (c == 3) s += A[r * 4 + 3];
-        a.xf[(i * N + j) * 12 + e] = __double2float_rn(s);
+        a.xf[(i * N + j) * 12 + e] = xf_pair_entry(sf + kXfSplit * j, sf + kXfSplit * i, e);
     }
 }
 
 __global__ void xform_kernel(SolveArgs a)
 {
     pdl_wait_and_release();
-    __shared__ double tinv[12 * kMaxNodes];
-    write_xforms(a, tinv, a.pose);
+    __shared__ float sf[kXfSplit * kMaxNodes];
+    write_xforms(a, sf, a.pose);
 }
 
 cudaError_t launch_xforms(const SolveArgs& a, cudaStream_t s)
@@ -701,7 +693,9 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm, const Fina
     }
     __syncthreads();
     for (int q = tid; q < 12 * N; q += nt) a.pose[q] = ps[q];
-    write_xforms(a, tinv, ps);
+    // split scratch from tinv on (32 N floats: tinv, the look-ahead columns,
+    // the triangle table and the staged blocks are free now)
+    write_xforms(a, reinterpret_cast<float*>(tinv), ps);
     if (tid == 0) {
         unsigned long long t4 = clock64();
         a.ctrl->clk[0] += t1 - t0;
@@ -775,11 +769,11 @@ cudaError_t launch_reduce(const SolveArgs& a, bool full, int iter, cudaStream_t 
 __global__ void batch_xform_kernel(const SolveArgs* __restrict__ args)
 {
     pdl_wait_and_release();
-    __shared__ double tinv[12 * kMaxNodes];
+    __shared__ float sf[kXfSplit * kMaxNodes];
     __shared__ SolveArgs sa;
     if (threadIdx.x == 0) sa = args[blockIdx.x];
     __syncthreads();
-    write_xforms(sa, tinv, sa.pose);
+    write_xforms(sa, sf, sa.pose);
 }
 
 template <bool kFull>
