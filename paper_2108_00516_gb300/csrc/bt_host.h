@@ -15,6 +15,7 @@
 #include <map>
 #include <string>
 #include <utility>
+#include <unordered_map>
 #include <vector>
 
 namespace bthost {
@@ -249,6 +250,13 @@ struct MatchSet {
     bool owned = true;      // pa, pb are pool blocks of their own; else inside a frame's mblock
 };
 
+struct FramePairHash {
+    size_t operator()(const std::pair<int, int>& p) const
+    {
+        return std::hash<uint64_t>()(((uint64_t)(uint32_t)p.first << 32) | (uint32_t)p.second);
+    }
+};
+
 
 inline bool finite_pose(const double* T)
 {
@@ -264,8 +272,10 @@ struct bt_graph {
     bt_config cfg{};
     cudaStream_t stream = nullptr;
     int next_id = 0;
-    std::map<int, bthost::Frame> frames;
-    std::map<std::pair<int, int>, bthost::MatchSet> matches;
+    std::unordered_map<int, bthost::Frame> frames;   // by frame id (looked up per node on every solve)
+    // keyed by the frame pair (a < b); looked up for every node pair of each
+    // solve's graph, so hashed rather than ordered
+    std::unordered_map<std::pair<int, int>, bthost::MatchSet, bthost::FramePairHash> matches;
     std::map<int, std::vector<int>> partners;   // frame -> frames it has a correspondence set with
     std::vector<int> active;
     bool topo_dirty = true;
