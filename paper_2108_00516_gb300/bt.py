@@ -76,7 +76,7 @@ SIGNATURES = {
     "bt_graph_create": (C.c_int, [C.POINTER(bt_config), C.c_void_p, C.POINTER(C.c_void_p)]),
     "bt_graph_destroy": (None, [C.c_void_p]),
     "bt_add_frame": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(bt_intrinsics),
-                               C.POINTER(C.c_double), C.c_int32, C.POINTER(bt_matches), C.c_int32, C.c_int32,
+                               C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int32,
                                C.POINTER(C.c_int32)]),
     "bt_set_matches": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
                                  C.c_int32]),
@@ -183,8 +183,20 @@ def _is_torch(x) -> bool:
     return type(x).__module__.startswith("torch")
 
 
+def _addr(a) -> int:
+    """Address of the first element of a C-contiguous numpy array.  Through
+    the buffer protocol when the array is writable (~0.35 us), else numpy's
+    ctypes interface (~0.9 us): the per-frame calls pass up to ~20 arrays."""
+    try:
+        return C.addressof(C.c_char.from_buffer(a))
+    except (TypeError, ValueError, BufferError):
+        return a.ctypes.data
+
+
 def _ptr(x, dtype, shape_check=None):
     """(pointer, keepalive, mem_kind) for a numpy array or a CUDA tensor."""
+    if type(x) is np.ndarray and x.dtype == dtype and x.flags.c_contiguous:
+        return _addr(x), x, BT_HOST
     if _is_torch(x):
         if not x.is_cuda:
             x = x.contiguous().numpy()
@@ -192,7 +204,13 @@ def _ptr(x, dtype, shape_check=None):
             x = x.contiguous()
             return C.c_void_p(x.data_ptr()), x, BT_DEVICE
     a = np.ascontiguousarray(x, dtype=dtype)
-    return C.c_void_p(a.ctypes.data), a, BT_HOST
+    return _addr(a), a, BT_HOST
+
+
+# numpy image of bt_matches (int32, int32, void*, void*): a frame's
+# correspondence sets are passed as one array built column by column
+_MATCHES_DT = np.dtype([("other_frame", "<i4"), ("count", "<i4"), ("pts_self", "<u8"), ("pts_other", "<u8")])
+assert _MATCHES_DT.itemsize == C.sizeof(bt_matches)
 
 
 def config_default() -> bt_config:
@@ -264,17 +282,27 @@ class PoseGraph:
         K = bt_intrinsics(fx, fy, cx, cy, w, h)
         P = np.ascontiguousarray(pose, np.float64).reshape(16)
         keep = [kd, kn, km]
-        ms = (bt_matches * max(1, len(matches)))()
-        for k, (other, ps, po) in enumerate(matches):
-            a, ka, mka = _ptr(ps, np.float32)
-            b, kb, mkb = _ptr(po, np.float32)
-            if not (mka == mkb == mk):
-                raise ValueError("matches must use the same memory kind as the frame")
-            keep += [ka, kb]
-            ms[k] = bt_matches(int(other), int(len(ps)), a, b)
+        nm = len(matches)
+        ms = np.zeros(max(1, nm), _MATCHES_DT)
+        if nm:
+            others, counts, pa, pb = [], [], [], []
+            for other, ps, po in matches:
+                a, ka, mka = _ptr(ps, np.float32)
+                b, kb, mkb = _ptr(po, np.float32)
+                if not (mka == mkb == mk):
+                    raise ValueError("matches must use the same memory kind as the frame")
+                keep += [ka, kb]
+                others.append(int(other))
+                counts.append(len(ps))
+                pa.append(a.value if isinstance(a, C.c_void_p) else a)
+                pb.append(b.value if isinstance(b, C.c_void_p) else b)
+            ms["other_frame"][:nm] = others
+            ms["count"][:nm] = counts
+            ms["pts_self"][:nm] = pa
+            ms["pts_other"][:nm] = pb
         fid = C.c_int32(-1)
-        _check(L.bt_add_frame(self._h, d, n, m, C.byref(K), P.ctypes.data_as(C.POINTER(C.c_double)),
-                              int(bool(fixed)), ms, len(matches), mk, C.byref(fid)), "bt_add_frame")
+        _check(L.bt_add_frame(self._h, d, n, m, C.byref(K), _addr(P), int(bool(fixed)), ms.ctypes.data, nm, mk,
+                              C.byref(fid)), "bt_add_frame")
         return fid.value
 
     def set_matches(self, frame_a, frame_b, pts_a, pts_b):

@@ -581,10 +581,17 @@ int bt_add_frame(bt_graph* g, const float* depth, const float* normals, const ui
         int* np = nullptr;
         BT_CUDA(alloc_should_fail() ? cudaErrorMemoryAllocation
                                     : cudaHostAlloc(reinterpret_cast<void**>(&np), sizeof(int) * 2 * (size_t)cap,
-                                                    cudaHostAllocDefault),
+                                                    cudaHostAllocMapped),
                 "cudaHostAlloc(read-back slots)");
+        int* npd = nullptr;
+        const cudaError_t em = cudaHostGetDevicePointer(reinterpret_cast<void**>(&npd), np, 0);
+        if (em != cudaSuccess) {
+            cudaFreeHost(np);
+            return cuda_fail(em, "cudaHostGetDevicePointer(read-back slots)");
+        }
         if (g->pin_m2) cudaFreeHost(g->pin_m2);
         g->pin_m2 = np;
+        g->pin_m2_dev = npd;
         for (int k = cap - 1; k >= g->pin_cap; --k) g->free_slots.push_back(k);
         g->pin_cap = cap;
     }
@@ -601,20 +608,21 @@ int bt_add_frame(bt_graph* g, const float* depth, const float* normals, const ui
     f.src_n = sn;
     f.dev_m2 = static_cast<int*>(m2);
     const float ifx = 1.0f / K->fx, ify = 1.0f / K->fy;
-    if (e == cudaSuccess)
-        e = bt::launch_prep(d_depth, d_normals, d_mask, W, H, K->cx, K->cy, ifx, ify, P, f.tgt, f.src_p, f.src_n,
-                            g->prep_blk.p, f.dev_m2, s);
-    g->prof.prep_launches += 3;
+    // (M, zref) land in a mapped pinned slot, written by the preparation's
+    // scan kernel itself (no separate read-back copy), read at the next
+    // topology build after a stream synchronisation
     if (e == cudaSuccess) {
         f.slot = g->free_slots.back();
         g->free_slots.pop_back();
-        e = cudaMemcpyAsync(g->pin_m2 + 2 * f.slot, f.dev_m2, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+        e = bt::launch_prep(d_depth, d_normals, d_mask, W, H, K->cx, K->cy, ifx, ify, P, f.tgt, f.src_p, f.src_n,
+                            g->prep_blk.p, f.dev_m2, g->pin_m2_dev + 2 * f.slot, s);
         f.pending = true;
         if (e != cudaSuccess) {
             g->free_slots.push_back(f.slot);
             f.slot = -1;
         }
     }
+    g->prof.prep_launches += 3;
     if (e != cudaSuccess) {
         g->pool.put(f.tgt, f.tgt_bytes);
         g->pool.put(f.src_p, f.src_bytes);

@@ -284,6 +284,7 @@ struct bt_graph {
     bthost::DevBuf up_depth, up_normals, up_mask, prep_blk;
     bthost::DevPool pool;               // frame maps, source lists, correspondence sets
     int* pin_m2 = nullptr;              // pinned host slots [cap][2] for (M, zref) read-backs
+    int* pin_m2_dev = nullptr;          // the same slots as the device writes them (mapped)
     int pin_cap = 0;
     std::vector<int> free_slots;
 

@@ -178,7 +178,7 @@ inline size_t pixel_bytes(int precision) { return precision == 0 ? 16 : 8; }
 cudaError_t launch_prep(const float* depth, const float* normals, const uint8_t* mask,
                         int W, int H, float cx, float cy, float ifx, float ify, int precision,
                         void* tgt, void* src_p, void* src_n, void* block_scratch,
-                        int* out2, cudaStream_t s);
+                        int* out2, int* host_out2, cudaStream_t s);
 
 // Float transforms for the current FP64 poses (start of a solve).
 cudaError_t launch_xforms(const SolveArgs& a, cudaStream_t s);

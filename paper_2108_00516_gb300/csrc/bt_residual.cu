@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kThreads) prep_count_kernel(
 // Exclusive scan of the block counts; M and the reference depth (mean valid
 // depth, used by the 16-bit encodings).
 __global__ void prep_scan_kernel(int* __restrict__ blockcnt, const double* __restrict__ blocksum, int nblk,
-                                 int* __restrict__ out2)
+                                 int* __restrict__ out2, int* __restrict__ host_out2)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         int s = 0;
@@ -160,6 +160,10 @@ __global__ void prep_scan_kernel(int* __restrict__ blockcnt, const double* __res
         }
         out2[0] = s;
         out2[1] = __float_as_int(s > 0 ? (float)(z / s) : 0.f);
+        if (host_out2) {      // the host's read-back slot (mapped pinned memory)
+            host_out2[0] = out2[0];
+            host_out2[1] = out2[1];
+        }
     }
 }
 
@@ -222,7 +226,7 @@ __global__ void __launch_bounds__(kThreads) prep_write_kernel(
 
 cudaError_t launch_prep(const float* depth, const float* normals, const uint8_t* mask, int W, int H, float cx,
                         float cy, float ifx, float ify, int precision, void* tgt, void* src_p, void* src_n,
-                        void* block_scratch, int* out2, cudaStream_t s)
+                        void* block_scratch, int* out2, int* host_out2, cudaStream_t s)
 {
     const int HW = W * H;
     const int nblk = (HW + kPrepPix - 1) / kPrepPix;
@@ -230,7 +234,7 @@ cudaError_t launch_prep(const float* depth, const float* normals, const uint8_t*
     double* blocksum = reinterpret_cast<double*>(
         (reinterpret_cast<uintptr_t>(blockcnt + nblk + 1) + 15) & ~static_cast<uintptr_t>(15));
     prep_count_kernel<<<nblk, kThreads, 0, s>>>(depth, normals, mask, HW, blockcnt, blocksum);
-    prep_scan_kernel<<<1, 32, 0, s>>>(blockcnt, blocksum, nblk, out2);
+    prep_scan_kernel<<<1, 32, 0, s>>>(blockcnt, blocksum, nblk, out2, host_out2);
     if (precision == 1)
         prep_write_kernel<1><<<nblk, kThreads, 0, s>>>(depth, normals, mask, W, HW, cx, cy, ifx, ify, blockcnt, out2,
                                                        tgt, src_p, src_n);
