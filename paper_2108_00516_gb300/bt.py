@@ -320,7 +320,7 @@ class PoseGraph:
     def set_active(self, ids):
         arr = np.ascontiguousarray(ids, np.int32)
         self._n_active = None
-        _check(self._lib.bt_set_active(self._h, arr.ctypes.data, len(arr)), "bt_set_active")
+        _check(self._lib.bt_set_active(self._h, _addr(arr), len(arr)), "bt_set_active")
         self._n_active = len(arr)
 
     @property
@@ -336,7 +336,7 @@ class PoseGraph:
         P = np.ascontiguousarray(poses, np.float64).reshape(-1)
         if P.size != 16 * self.num_active:
             raise ValueError("poses must be (n_active, 4, 4)")
-        _check(self._lib.bt_set_poses(self._h, P.ctypes.data), "bt_set_poses")
+        _check(self._lib.bt_set_poses(self._h, _addr(P)), "bt_set_poses")
 
     def get_poses(self) -> np.ndarray:
         out = np.zeros((self.num_active, 4, 4))
