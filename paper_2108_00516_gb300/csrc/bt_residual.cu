@@ -359,6 +359,10 @@ __device__ __forceinline__ void accumulate_pair(float (&acc)[kDenseVals], float2
 #endif
 constexpr int residual_batch(int P) { return P == 0 ? BT_RES_BATCH_F32 : 4; }
 constexpr int residual_threads_per_sm(int P) { return P == 0 ? BT_RES_THREADS_F32 : 640; }
+// The FP32 cost-only pass (no Jacobian, two sums a pixel) fits in 64
+// registers without spills: 1024 resident threads a SM, more warps to hide
+// the gathers (the 16-bit decodes would spill there).
+constexpr int residual_threads_per_sm(int P, bool full) { return full || P != 0 ? residual_threads_per_sm(P) : 1024; }
 
 // One tile of kT x kB source pixels of node i against every other node j.
 // The work of the tile is (N-1) x kW units -- unit (jj, c) = target jj, chunk
@@ -592,7 +596,7 @@ __device__ void sparse_edge(const SolveArgs& a, int e)
 
 
 template <bool kFull, int kT, int kB, int P>
-__global__ void __launch_bounds__(kT, residual_threads_per_sm(P) / kT) residual_kernel(SolveArgs a)
+__global__ void __launch_bounds__(kT, residual_threads_per_sm(P, kFull) / kT) residual_kernel(SolveArgs a)
 {
     pdl_wait_and_release();
     extern __shared__ __align__(16) unsigned char dsm[];
@@ -604,7 +608,7 @@ __global__ void __launch_bounds__(kT, residual_threads_per_sm(P) / kT) residual_
 
 // Batched residual pass: CTA b takes work item work[b] = (graph, item).
 template <bool kFull, int kT, int kB, int P>
-__global__ void __launch_bounds__(kT, residual_threads_per_sm(P) / kT) batch_residual_kernel(const SolveArgs* __restrict__ args,
+__global__ void __launch_bounds__(kT, residual_threads_per_sm(P, kFull) / kT) batch_residual_kernel(const SolveArgs* __restrict__ args,
                                                                        const int2* __restrict__ work)
 {
     pdl_wait_and_release();
