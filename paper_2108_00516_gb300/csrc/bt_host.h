@@ -276,7 +276,7 @@ struct bt_graph {
     // keyed by the frame pair (a < b); looked up for every node pair of each
     // solve's graph, so hashed rather than ordered
     std::unordered_map<std::pair<int, int>, bthost::MatchSet, bthost::FramePairHash> matches;
-    std::map<int, std::vector<int>> partners;   // frame -> frames it has a correspondence set with
+    std::unordered_map<int, std::vector<int>> partners;   // frame -> frames it has a correspondence set with
     std::vector<int> active;
     bool topo_dirty = true;
 
