@@ -143,7 +143,11 @@ __device__ __forceinline__ bool index_check(bool ok, unsigned bit, Control* ctrl
 // launch latency of every kernel overlaps the tail of the previous one --
 // for the reduce kernel, its single-CTA solve stage.  The wait covers the
 // predecessor's completion and memory, and each predecessor waited for its
-// own, so every earlier kernel of the chain is complete as well.
+// own, so every earlier kernel of the chain is complete as well.  Work that
+// reads only what earlier kernels (not the predecessor) wrote may run before
+// the wait: the residual pass stages its source tiles (frame data) there, and
+// the reduce kernel reads the poses and status of the previous update, so
+// that their latency overlaps the predecessor's tail.
 #ifdef __CUDACC__
 __device__ __forceinline__ void pdl_wait_and_release()
 {

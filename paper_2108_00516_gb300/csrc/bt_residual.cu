@@ -402,6 +402,9 @@ __device__ void dense_tile(const SolveArgs& a, int tile, unsigned char* dsm)
         sp[s] = pp;
         sn[s] = nn;
     }
+    // the source tile is frame data; the transforms below were written by
+    // the predecessor (the previous update), so the wait goes here
+    pdl_wait_and_release();
     if (threadIdx.x < N && threadIdx.x != i) fill_pair_const(a, i, threadIdx.x, pc[threadIdx.x]);
     __syncthreads();
     const float dmax2 = a.dmax2, cmin = a.cmin, hub = a.huber_dense;
@@ -598,12 +601,13 @@ __device__ void sparse_edge(const SolveArgs& a, int e)
 template <bool kFull, int kT, int kB, int P>
 __global__ void __launch_bounds__(kT, residual_threads_per_sm(P, kFull) / kT) residual_kernel(SolveArgs a)
 {
-    pdl_wait_and_release();
     extern __shared__ __align__(16) unsigned char dsm[];
-    if ((int)blockIdx.x < a.n_edges)
+    if ((int)blockIdx.x < a.n_edges) {
+        pdl_wait_and_release();
         sparse_edge<kFull>(a, blockIdx.x);
-    else
-        dense_tile<kFull, kT, kB, P>(a, blockIdx.x - a.n_edges, dsm);
+    } else {
+        dense_tile<kFull, kT, kB, P>(a, blockIdx.x - a.n_edges, dsm);   // waits after staging its tile
+    }
 }
 
 // Batched residual pass: CTA b takes work item work[b] = (graph, item).
@@ -611,15 +615,15 @@ template <bool kFull, int kT, int kB, int P>
 __global__ void __launch_bounds__(kT, residual_threads_per_sm(P, kFull) / kT) batch_residual_kernel(const SolveArgs* __restrict__ args,
                                                                        const int2* __restrict__ work)
 {
-    pdl_wait_and_release();
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ SolveArgs sa;
-    const int2 w = work[blockIdx.x];
+    const int2 w = work[blockIdx.x];     // the work list and arguments: written before the solve
     if (threadIdx.x == 0) sa = args[w.x];
     __syncthreads();
-    if (w.y < sa.n_edges)
+    if (w.y < sa.n_edges) {
+        pdl_wait_and_release();
         sparse_edge<kFull>(sa, w.y);
-    else
+    } else
         dense_tile<kFull, kT, kB, P>(sa, w.y - sa.n_edges, dsm);
 }
 

@@ -708,11 +708,13 @@ __device__ void final_phase(const SolveArgs& a, int iter, double* sm, const Fina
 template <bool kFull>
 __global__ void __launch_bounds__(kThreads, 1) reduce_kernel(SolveArgs a, int iter)
 {
-    pdl_wait_and_release();
     extern __shared__ double sm[];
     __shared__ int s_last;
     const int b = blockIdx.x;
+    // the previous update's poses and status: written before the residual
+    // pass this kernel waits for, so read ahead of the wait
     const FinalPrefetch pf = final_prefetch<kFull>(a);
+    pdl_wait_and_release();
     if (b < a.n_upairs) reduce_upair<kFull>(a, b, sm);
     __threadfence();
     __syncthreads();
