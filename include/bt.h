@@ -475,7 +475,10 @@ int32_t bt_debug_fail_allocations(int32_t n);
  * below cover the same timed launches. */
 typedef struct {
     int64_t prep_launches;      /* frame-preparation kernels (3 per frame) */
-    int64_t xform_launches;
+    int64_t xform_launches;     /* transform kernels: always 0 (a solve's first
+                                 * transforms are formed on the host, the later
+                                 * ones by the update in the reduce kernel);
+                                 * kept so that the layout does not change */
     int64_t residual_launches;  /* residual pass launches (dense + sparse) */
     int64_t reduce_launches;    /* reduce / assemble / solve launches */
     double residual_ms;         /* summed event time of timed residual launches */

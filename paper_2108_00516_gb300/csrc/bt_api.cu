@@ -3,8 +3,9 @@
 // A bt_graph owns the device copies of its frames (target map + compacted
 // source pixels, built on the GPU by the prep kernels), the correspondence
 // sets, and the per-solve work buffers (grow-only, so repeated solves do not
-// allocate).  bt_solve enqueues, on the graph's stream:
-//   xform  ->  iters x [residual(full) -> reduce(full)]  ->  residual(cost) -> reduce(cost)
+// allocate).  bt_solve uploads the poses with the single-precision
+// transforms formed from them on the host, enqueues on the graph's stream
+//   iters x [residual(full) -> reduce(full)]  ->  residual(cost) -> reduce(cost)
 // and then one device-to-host copy of poses, costs and status.
 #include "bt_host.h"
 #include "bt_xform.cuh"

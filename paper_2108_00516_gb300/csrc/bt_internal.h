@@ -135,7 +135,8 @@ __device__ __forceinline__ bool index_check(bool ok, unsigned bit, Control* ctrl
 #endif
 
 // Programmatic dependent launch.  The kernels of a solve form one chain per
-// stream (transforms -> residual -> reduce -> residual -> ...).  Each is
+// stream (residual -> reduce -> residual -> ...; the batched solver's chain
+// starts with its transform kernel).  Each is
 // launched with programmatic stream serialisation: it may be scheduled
 // while its predecessor is still running, waits (griddepcontrol.wait) before
 // touching anything the predecessor writes, and at once allows its own
@@ -183,9 +184,6 @@ cudaError_t launch_prep(const float* depth, const float* normals, const uint8_t*
                         int W, int H, float cx, float cy, float ifx, float ify, int precision,
                         void* tgt, void* src_p, void* src_n, void* block_scratch,
                         int* out2, int* host_out2, cudaStream_t s);
-
-// Float transforms for the current FP64 poses (start of a solve).
-cudaError_t launch_xforms(const SolveArgs& a, cudaStream_t s);
 
 // One residual pass (dense tiles + sparse edges) and one reduce/solve pass.
 // full = true: Gauss-Newton iteration `iter` (records E before the update);

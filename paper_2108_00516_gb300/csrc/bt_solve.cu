@@ -53,18 +53,6 @@ __device__ void write_xforms(const SolveArgs& a, float* __restrict__ sf, const d
     }
 }
 
-__global__ void xform_kernel(SolveArgs a)
-{
-    pdl_wait_and_release();
-    __shared__ float sf[kXfSplit * kMaxNodes];
-    write_xforms(a, sf, a.pose);
-}
-
-cudaError_t launch_xforms(const SolveArgs& a, cudaStream_t s)
-{
-    return launch_chained(xform_kernel, dim3(1), dim3(kThreads), 0, s, a);
-}
-
 // ---------------------------------------------------------------------------
 // Reduce / assemble / solve / update
 // ---------------------------------------------------------------------------
