@@ -338,8 +338,15 @@ int bt_warmstart_clear_samples(bt_warmstart* ws);
  * pointer may be NULL.  Errors: BT_ERR_INVALID, BT_ERR_CUDA. */
 int bt_warmstart_get_sample(const bt_warmstart* ws, int32_t id, float* centre, float* label);
 
-/* Network outputs (n x 6 floats, host) for samples ids[0..n) (host array).
- * Errors: BT_ERR_INVALID (id out of range), BT_ERR_STATE, BT_ERR_CUDA. */
+/* The calls below that run the network report BT_ERR_TIMEOUT when one of
+ * the forward pass's bounded waits on the tensor cores ran out (1 s, see
+ * bt_debug_tensor_wait_ns); the outputs of that pass are discarded and the
+ * CUDA context stays usable.  bt_warmstart_train_step without loss_out does
+ * not synchronise: such a timeout is reported by the next call that does.
+ *
+ * Network outputs (n x 6 floats, host) for samples ids[0..n) (host array).
+ * Errors: BT_ERR_INVALID (id out of range), BT_ERR_STATE, BT_ERR_TIMEOUT,
+ * BT_ERR_CUDA. */
 int bt_warmstart_predict(bt_warmstart* ws, const int32_t* ids, int32_t n, float* y_out);
 /* Gradient (BT_WS_NUM_PARAMS floats, host; may be NULL) and value (may be
  * NULL) of the mean loss over samples ids[0..n), without an update. */
@@ -351,7 +358,8 @@ int bt_warmstart_train_step(bt_warmstart* ws, const int32_t* ids, int32_t n, flo
 /* Replaces the stored poses of g's free active nodes by the warm start
  * computed from its correspondence sets at its stored poses (fixed nodes are
  * kept).  Errors: BT_ERR_INVALID, BT_ERR_STATE, BT_ERR_SINGULAR (a free node
- * without correspondences; poses unchanged), BT_ERR_CUDA, BT_ERR_OOM. */
+ * without correspondences; poses unchanged), BT_ERR_TIMEOUT (poses
+ * unchanged), BT_ERR_CUDA, BT_ERR_OOM. */
 int bt_warmstart_apply(bt_warmstart* ws, bt_graph* g);
 /* The same for every graph of a batch, in one launch per kernel; status_out:
  * NULL or bt_batch_size() statuses.  Graphs that fail keep their poses. */
@@ -370,7 +378,8 @@ int bt_warmstart_apply_batch(bt_warmstart* ws, bt_batch* b, int32_t* status_out)
  *     not converged (with iters == 0 only failures fall back).
  * reps: NULL or bt_batch_size() reports with used_warmstart / fell_back set.
  * Synchronises the batch stream.
- * Errors: BT_ERR_INVALID, BT_ERR_STATE, BT_ERR_SINGULAR, BT_ERR_CUDA, BT_ERR_OOM. */
+ * Errors: BT_ERR_INVALID, BT_ERR_STATE, BT_ERR_SINGULAR, BT_ERR_TIMEOUT (every
+ * graph keeps the poses it had before the call), BT_ERR_CUDA, BT_ERR_OOM. */
 int bt_batch_solve_warm(bt_batch* b, bt_warmstart* ws, int32_t iters, int32_t fallback_iters,
                         const double* ref_costs, double tol, bt_solve_report* reps);
 
@@ -466,6 +475,14 @@ int bt_debug_normal_equations(bt_graph* g, double* H_out, double* g_out, int32_t
  * that were still pending.  Allocations the device-memory cache can serve
  * from idle blocks are not allocations and do not consume one. */
 int32_t bt_debug_fail_allocations(int32_t n);
+
+/* Sets the bound (nanoseconds of the GPU's global timer) of the warm-start
+ * forward pass's waits for its tensor-core contractions, for the launches
+ * that follow; ns < 0 restores the default of 1 s, and ns = 0 makes the first
+ * wait give up at once, so that a caller can exercise the BT_ERR_TIMEOUT
+ * path (the kernel still lets the contraction in flight finish before it
+ * frees its tensor memory).  Process wide.  Returns the previous bound. */
+int64_t bt_debug_tensor_wait_ns(int64_t ns);
 
 /* Profiling counters of one graph (the tracing facility; no paper
  * counterpart).  Launch counts are always kept; kernel durations are summed

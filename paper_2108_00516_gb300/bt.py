@@ -130,6 +130,7 @@ SIGNATURES = {
     "bt_debug_normal_equations": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int32,
                                             C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
     "bt_debug_fail_allocations": (C.c_int32, [C.c_int32]),
+    "bt_debug_tensor_wait_ns": (C.c_int64, [C.c_int64]),
     "bt_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "bt_profile_read": (C.c_int, [C.c_void_p, C.POINTER(bt_profile)]),
     "bt_device_cache_bytes": (C.c_int64, []),
@@ -519,6 +520,13 @@ def debug_fail_allocations(n: int) -> int:
     """bt_debug_fail_allocations: the library's next n device or pinned host
     allocations fail as out of memory (0 cancels); returns the pending count."""
     return int(load().bt_debug_fail_allocations(int(n)))
+
+
+def debug_tensor_wait_ns(ns: int) -> int:
+    """bt_debug_tensor_wait_ns: bound of the warm-start forward pass's waits on
+    the tensor cores for the launches that follow (ns < 0: default 1 s, 0:
+    give up at once); returns the previous bound."""
+    return int(load().bt_debug_tensor_wait_ns(int(ns)))
 
 
 def device_cache_bytes() -> int:

@@ -3,13 +3,21 @@
 // reduction, Adam, and the FP64 relative-pose averaging solve that turns the
 // predicted edge increments into node poses for Gauss-Newton (Sec. IV-D).
 //
-// Forward pass: a persistent CTA per SM keeps the BF16 W2 (padded rows, for
-// conflict-free ldmatrix) and W3 in shared memory and walks its sets in
-// chunks of 64 points: layer 1 (K = 6) on the FP32 pipes, rounded to BF16
-// into shared memory; the 64 x 256 x 128 contraction of layer 2 on the tensor
-// cores (mma.sync m16n8k16, BF16 in, FP32 accumulate, 8 warps of 32 x 64
-// tiles); bias, ReLU and a running per-channel maximum (with the row that
-// holds it, first row on ties) in registers; then the 256 -> 128 -> 6 head.
+// Forward pass: a persistent CTA per SM keeps the BF16 W2 (in the tensor
+// cores' core-matrix layout) and W3 in shared memory and walks its sets in
+// chunks of 128 points.  Layer 1 (K = 6) runs on the FP32 pipes and is
+// rounded to BF16 into one of two shared-memory tiles; the 128 x 256 x 128
+// contraction of layer 2 runs on the fifth-generation tensor cores
+// (tcgen05.mma, BF16 in, FP32 accumulators in tensor memory, issued by one
+// thread, completion signalled on an mbarrier).  While the tensor cores work
+// on chunk c, the CUDA cores compute layer 1 of chunk c+1 into the other
+// tile, and then read chunk c's accumulators (tcgen05.ld) for bias, ReLU and
+// a running per-channel maximum (with the row that holds it, first row on
+// ties); two accumulators in tensor memory let chunk c+1's contraction run
+// during that read-out.  Then the 256 -> 128 -> 6 head.  Every wait on the
+// tensor cores is bounded (globaltimer); a wait that runs out sets the
+// network's fault word, drains the contraction in flight, frees the tensor
+// memory and ends the kernel, and the host reports BT_ERR_TIMEOUT.
 // Backward pass: only the rows that hold a channel's maximum receive
 // gradient, so layer 1 and layer 2 gradients are outer products over at most
 // 256 rows, recomputed from the inputs with the forward pass's arithmetic.
@@ -27,8 +35,7 @@ namespace ws {
 namespace {
 
 constexpr int kFwdThreads = 256;
-constexpr int kChunk = 64;      // points per layer-2 tile
-constexpr int kLd = 136;        // padded row length (BF16) of W2 and the h1 tile in shared memory
+constexpr int kChunk = 128;     // points per layer-2 tile: the M of one tensor-core contraction
 constexpr int kLd3 = 258;       // padded row length (BF16) of the layer-3 weights (odd word stride)
 
 __device__ __forceinline__ float bf2f(__nv_bfloat16 b) { return __bfloat162float(b); }
@@ -108,28 +115,141 @@ __device__ __forceinline__ float z1_unit(const float* w, float b, const float x[
     return a;
 }
 
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* ptr)
+// ---------------------------------------------------------------------------
+// Fifth-generation tensor cores (PTX ISA: tcgen05 instructions, shared-memory
+// matrix descriptors, instruction descriptor of kind::f16)
+// ---------------------------------------------------------------------------
+
+// Both operands of the layer-2 contraction are K-major BF16 with K = 128,
+// stored without swizzling as core matrices of 8 rows x 16 bytes (8 values of
+// K): element (row, k) at core_off(row, k).  In the matrix descriptor the
+// leading-dimension offset is the distance between core matrices that follow
+// each other along K, the stride-dimension offset the distance between
+// neighbouring groups of 8 rows.
+constexpr uint32_t kCoreK = 128;                    // bytes from one core matrix to the next along K
+constexpr uint32_t kCoreRows = (kH1 / 8) * kCoreK;  // 2048: bytes from one group of 8 rows to the next
+constexpr uint32_t kH1TileBytes = kChunk * kH1 * 2; // one BF16 [128][128] tile of layer-1 outputs
+__host__ __device__ constexpr uint32_t core_off(int row, int k)
 {
-    const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(ptr));
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(a));
+    return (uint32_t)(row >> 3) * kCoreRows + (uint32_t)(k >> 3) * kCoreK + (uint32_t)(row & 7) * 16u +
+           (uint32_t)(k & 7) * 2u;
 }
 
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+// Matrix descriptor: start address >> 4 (bits 0-13), leading-dimension byte
+// offset >> 4 (16-29), stride-dimension byte offset >> 4 (32-45), the fixed
+// value 1 in bits 46-48, base offset 0, no swizzling.
+__device__ __forceinline__ uint64_t mat_desc(uint32_t saddr)
+{
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(kCoreK >> 4) << 16) |
+           ((uint64_t)(kCoreRows >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor: FP32 accumulator (bits 4-5 = 1), A and B BF16
+// (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in bits
+// 17-22, M >> 4 in bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kH2 >> 3) << 17) |
+                            ((uint32_t)(kChunk >> 4) << 24);
+static_assert(kChunk == 128 && kH2 % 16 == 0 && kH2 <= 256, "shape of one kind::f16 contraction (M = 128)");
+
+constexpr int kTmemCols = 2 * kH2;                 // two FP32 [128][256] accumulators
+constexpr long long kTensorWaitNs = 1000000000LL;  // default bound of a wait on the tensor cores (1 s)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// D[128][256] (tensor memory at d_tmem) = A[128][128] . B[256][128]^T, A and B
+// K-major in shared memory: eight K = 16 steps, the first overwriting D; the
+// completion of all eight arrives on the mbarrier at `bar`.  One thread.
+__device__ __forceinline__ void issue_layer2(uint32_t d_tmem, uint32_t a_saddr, uint32_t b_saddr, uint32_t bar)
+{
+#pragma unroll
+    for (int k = 0; k < kH1 / 16; ++k) {
+        const uint64_t ad = mat_desc(a_saddr + 2 * kCoreK * k), bd = mat_desc(b_saddr + 2 * kCoreK * k);
+        asm volatile(
+            "{\n\t.reg .pred acc;\n\tsetp.ne.b32 acc, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, acc;\n\t}"
+            ::"r"(d_tmem), "l"(ad), "l"(bd), "r"(kIdesc), "r"((uint32_t)(k > 0))
+            : "memory");
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+// Waits until phase `parity` of the mbarrier at `bar` has completed, for at
+// most limit_ns of the global timer; limit_ns <= 0 gives up without polling.
+__device__ __forceinline__ bool wait_tensor(uint32_t bar, uint32_t parity, long long limit_ns)
+{
+    if (limit_ns <= 0) return false;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((long long)(global_ns() - t0) > limit_ns) return false;
+    }
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Eight 16-lane x 256-bit blocks of tensor memory from taddr on (columns
+// taddr + 8j .. + 8j + 7 for block j), waited for: lane l of the warp gets
+// v[4j], v[4j+1] = row (l / 4), columns 8j + 2 (l % 4) + {0, 1}, and
+// v[4j+2], v[4j+3] = row (l / 4) + 8, the same columns.
+__device__ __forceinline__ void tmem_load_16x256b_x8(uint32_t taddr, uint32_t (&v)[32])
 {
     asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+        "tcgen05.ld.sync.aligned.16x256b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr)
+        : "memory");
+}
+
+// Layer 1 of one row of a chunk, 64 of the 128 units (half 0 or 1): ReLU,
+// rounded to BF16, written as eight 16-byte core-matrix rows of the tile.
+__device__ __forceinline__ void layer1_half_row(unsigned char* tile, const float* sW1, const float x[6], int row,
+                                                int half)
+{
+    unsigned char* dst = tile + core_off(row, half * 64);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        uint32_t w[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int u = half * 64 + 8 * j + 2 * e;
+            const float h0 = fmaxf(z1_unit8(sW1 + w1_at(u), x), 0.f);
+            const float h1 = fmaxf(z1_unit8(sW1 + w1_at(u + 1), x), 0.f);
+            __nv_bfloat162 b = __floats2bfloat162_rn(h0, h1);
+            w[e] = *reinterpret_cast<uint32_t*>(&b);
+        }
+        *reinterpret_cast<uint4*>(dst + j * kCoreK) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
 }
 
 // Shared-memory layout of the forward kernel (byte offsets).
 struct Fwd {
-    static constexpr size_t W2 = 0;                                          // bf16 [256][kLd]
-    static constexpr size_t H1 = W2 + 2 * (size_t)kH2 * kLd;                 // bf16 [64][kLd]
-    static constexpr size_t W3 = H1 + 2 * (size_t)kChunk * kLd;              // bf16 [128][kLd3]
+    static constexpr size_t W2 = 0;                                          // bf16 [256][128], core_off layout
+    static constexpr size_t H1 = W2 + 2 * (size_t)kH2 * kH1;                 // 2 x bf16 [128][128], core_off layout
+    static constexpr size_t W3 = H1 + 2 * (size_t)kH1TileBytes;              // bf16 [128][kLd3]
     static constexpr size_t W1 = W3 + ((2 * (size_t)kH3 * kLd3 + 15) / 16) * 16;   // float [128][8] + skew (w1_at)
     static constexpr size_t B2 = W1 + 4 * ((size_t)kH1 * 8 + 16);            // float [256]
     static constexpr size_t B3 = B2 + 4 * (size_t)kH2;                       // float [128]
@@ -137,24 +257,27 @@ struct Fwd {
     static constexpr size_t B4 = W4 + 4 * (size_t)kOut * kH3;                // float [8]
     static constexpr size_t G = B4 + 32;                                     // float [256]
     static constexpr size_t R = G + 4 * (size_t)kH2;                         // int [256]
-    static constexpr size_t RV = R + 4 * (size_t)kH2;                        // float [2][256]
-    static constexpr size_t RI = RV + 8 * (size_t)kH2;                       // int [2][256]
-    static constexpr size_t H3 = RI + 8 * (size_t)kH2;                       // float [128]
+    static constexpr size_t RV = R + 4 * (size_t)kH2;                        // float [4][256]
+    static constexpr size_t RI = RV + 16 * (size_t)kH2;                      // int [4][256]
+    static constexpr size_t H3 = RI + 16 * (size_t)kH2;                      // float [128]
     static constexpr size_t Z3 = H3 + 4 * (size_t)kH3;                       // float [128]
     static constexpr size_t MC = Z3 + 4 * (size_t)kH3;                       // float [16]: m[12], c[3]
-    static constexpr size_t Total = MC + 64;
+    static constexpr size_t BAR = MC + 64;                                   // two mbarriers (u64)
+    static constexpr size_t TM = BAR + 16;                                   // tensor-memory base address
+    static constexpr size_t Total = TM + 16;
 };
-static_assert(Fwd::H1 % 16 == 0 && Fwd::W3 % 16 == 0 && Fwd::W1 % 16 == 0, "alignment");
+static_assert(Fwd::H1 % 16 == 0 && Fwd::W3 % 16 == 0 && Fwd::W1 % 16 == 0 && Fwd::BAR % 8 == 0, "alignment");
+static_assert(Fwd::Total <= 227 * 1024, "shared memory of one CTA");
+static_assert(Fwd::Total > 114 * 1024, "one CTA per SM: the two accumulators take all of its tensor memory");
 static_assert(kFwdThreads == 2 * kH3 && kFwdThreads == kH2, "head mapping: two threads per layer-3 unit");
+static_assert(kFwdThreads == 2 * kChunk, "layer 1: two threads per row of a chunk");
 
 template <bool kTrain>
 __global__ void __launch_bounds__(kFwdThreads, 1)
     forward_kernel(Net net, const Sample* __restrict__ smp, const int* __restrict__ ids, int n_sets,
                    float* __restrict__ y_out, Cache* __restrict__ cache)
 {
-    extern __shared__ __align__(16) unsigned char sm[];
-    __nv_bfloat16* sW2 = reinterpret_cast<__nv_bfloat16*>(sm + Fwd::W2);
-    __nv_bfloat16* sH1 = reinterpret_cast<__nv_bfloat16*>(sm + Fwd::H1);
+    extern __shared__ __align__(1024) unsigned char sm[];
     __nv_bfloat16* sW3 = reinterpret_cast<__nv_bfloat16*>(sm + Fwd::W3);    // layer 3: [unit][kLd3]
     float* sW1 = reinterpret_cast<float*>(sm + Fwd::W1);     // unit u at w1_at(u): weights [0..5], bias [6]
     float* sB2 = reinterpret_cast<float*>(sm + Fwd::B2);
@@ -170,11 +293,11 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     float* sMC = reinterpret_cast<float*>(sm + Fwd::MC);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // stage the weights once per CTA
+    // stage the weights once per CTA; W2 as 16-byte core-matrix rows
     for (int k = tid; k < kH2 * kH1 / 8; k += kFwdThreads) {
-        const int row = k >> 4, c8 = (k & 15) * 8;
-        *reinterpret_cast<uint4*>(sW2 + row * kLd + c8) =
-            *reinterpret_cast<const uint4*>(net.wb + bW2 + row * kH1 + c8);
+        const int row = k >> 4, k8 = (k & 15) * 8;
+        *reinterpret_cast<uint4*>(sm + Fwd::W2 + core_off(row, k8)) =
+            *reinterpret_cast<const uint4*>(net.wb + bW2 + row * kH1 + k8);
     }
     for (int k = tid; k < kH3 * kH2 / 2; k += kFwdThreads) {   // bf16 pairs, rows padded to kLd3
         const int o = k / (kH2 / 2), c2 = (k % (kH2 / 2)) * 2;
@@ -190,13 +313,37 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     for (int k = tid; k < kH3; k += kFwdThreads) sB3[k] = net.master[ob3 + k];
     if (tid < kOut) sB4[tid] = net.master[ob4 + tid];
 
-    const int wm = warp & 1, wn = warp >> 1;     // warp tile: rows wm*32 .. +32, columns wn*64 .. +64
+    const uint32_t bar0 = smem_u32(sm + Fwd::BAR);    // mbarrier of accumulator b at bar0 + 8 b
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(sm + Fwd::TM)),
+                     "r"((uint32_t)kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // the tensor cores read W2 and the layer-1 tiles through the async proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
     __syncthreads();
-    float b2[16];                                // layer-2 bias of the thread's 16 columns
+    tc_fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + Fwd::TM);
+    const uint32_t w2_s = smem_u32(sm + Fwd::W2), h1_s = smem_u32(sm + Fwd::H1);
+    unsigned char* const h1_tile = sm + Fwd::H1;
+
+    // read-out: warp w takes the tensor-memory lanes (rows of a chunk)
+    // 32 (w % 4) .. + 31 and the columns 128 (w / 4) .. + 127; a lane holds
+    // 32 of those columns (idx: column 128 cw + 8 (idx / 2) + 2 (lane % 4) + idx % 2)
+    const int qr = warp & 3, cw = warp >> 2;
+    float b2[32];
 #pragma unroll
-    for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-        for (int e = 0; e < 2; ++e) b2[2 * nt + e] = sB2[wn * 64 + nt * 8 + 2 * (lane & 3) + e];
+    for (int k = 0; k < 32; ++k) b2[k] = sB2[128 * cw + 8 * (k >> 1) + 2 * (lane & 3) + (k & 1)];
+    const int lrow = tid >> 1, lhalf = tid & 1;   // layer 1: thread = (row of the chunk, half of the 128 units)
+    uint32_t cc = 0;                              // chunks this CTA has contracted so far
+    bool fault = false;
     for (int s = blockIdx.x; s < n_sets; s += gridDim.x) {
         const int sid = ids ? ids[s] : s;
         const Sample* S = smp + sid;
@@ -210,113 +357,129 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         }
         const float* P = S->p;
         const float* Q = S->q;
-        float best[16];
-        int bestr[16];
+        // running maxima of the thread's 32 columns (ReLU outputs are >= 0);
+        // training also keeps the row that holds each (first row on ties)
+        float best[32];
+        int bestr[32];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            best[k] = -1.f;
+        for (int k = 0; k < 32; ++k) {
+            best[k] = kTrain ? -1.f : 0.f;
             bestr[k] = 0;
         }
-        const int lrow = tid >> 2, q4 = tid & 3;  // layer 1: thread = (row, quarter of the 128 units)
-        float pq[6];                             // the point pair of this thread's row of the chunk
+        const int nch = (n + kChunk - 1) / kChunk;
+        float pq[6];                             // the point pair of this thread's row of a chunk
         load_pair(P, Q, lrow, n, pq);
-        for (int r0 = 0; r0 < n; r0 += kChunk) {
-            {
-                const int gr = r0 + lrow;
+        {
+            float x[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (lrow < n) features_from(pq, sMC, sMC + 12, x);
+            layer1_half_row(h1_tile + (cc & 1) * kH1TileBytes, sW1, x, lrow, lhalf);
+        }
+        load_pair(P, Q, kChunk + lrow, n, pq);   // in flight during the first contraction
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) issue_layer2(tmem + (cc & 1) * kH2, h1_s + (cc & 1) * kH1TileBytes, w2_s, bar0 + 8 * (cc & 1));
+        for (int c = 0; c < nch; ++c, ++cc) {
+            const uint32_t b = cc & 1;
+            if (c + 1 < nch) {   // layer 1 of the next chunk while the tensor cores work on this one
+                const int gr = (c + 1) * kChunk + lrow;
                 float x[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 if (gr < n) features_from(pq, sMC, sMC + 12, x);
-                uint32_t packed[16];
-#pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    const int u = q4 * 32 + 2 * k;
-                    const float h0 = fmaxf(z1_unit8(sW1 + w1_at(u), x), 0.f);
-                    const float h1 = fmaxf(z1_unit8(sW1 + w1_at(u + 1), x), 0.f);
-                    __nv_bfloat162 b2 = __floats2bfloat162_rn(h0, h1);
-                    packed[k] = *reinterpret_cast<uint32_t*>(&b2);
-                }
-                uint4* dst = reinterpret_cast<uint4*>(sH1 + lrow * kLd + q4 * 32);
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    dst[k] = make_uint4(packed[4 * k], packed[4 * k + 1], packed[4 * k + 2], packed[4 * k + 3]);
+                layer1_half_row(h1_tile + (b ^ 1) * kH1TileBytes, sW1, x, lrow, lhalf);
+                load_pair(P, Q, (c + 2) * kChunk + lrow, n, pq);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             }
-            __syncthreads();
-            // the next chunk's point pair: the loads are in flight during layer 2
-            load_pair(P, Q, r0 + kChunk + lrow, n, pq);
-            float acc[2][8][4];
-#pragma unroll
-            for (int a = 0; a < 2; ++a)
-#pragma unroll
-                for (int b = 0; b < 8; ++b)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
-#pragma unroll
-            for (int k0 = 0; k0 < kH1; k0 += 16) {
-                uint32_t a[2][4];
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt)
-                    ldsm_x4(a[mt], sH1 + (wm * 32 + mt * 16 + (lane & 15)) * kLd + k0 + (lane >> 4) * 8);
-#pragma unroll
-                for (int np = 0; np < 4; ++np) {
-                    uint32_t b[4];
-                    ldsm_x4(b, sW2 + (wn * 64 + np * 16 + (lane & 7) + ((lane >> 4) << 3)) * kLd + k0 +
-                                   ((lane >> 3) & 1) * 8);
-#pragma unroll
-                    for (int mt = 0; mt < 2; ++mt) {
-                        mma_bf16(acc[mt][2 * np], a[mt], b[0], b[1]);
-                        mma_bf16(acc[mt][2 * np + 1], a[mt], b[2], b[3]);
-                    }
-                }
+            const bool done = wait_tensor(bar0 + 8 * b, (cc >> 1) & 1, net.wait_ns);
+            tc_fence_before();
+            if (__syncthreads_or(!done)) {
+                // give the contraction in flight time to finish before the
+                // tensor memory is freed, then end the kernel
+                wait_tensor(bar0 + 8 * b, (cc >> 1) & 1, kTensorWaitNs);
+                fault = true;
+                break;
             }
-            // bias, ReLU, running maximum; rows visited in increasing order
+            tc_fence_after();
+            if (c + 1 < nch && tid == 0)
+                issue_layer2(tmem + (b ^ 1) * kH2, h1_s + (b ^ 1) * kH1TileBytes, w2_s, bar0 + 8 * (b ^ 1));
+            // bias, ReLU and the running maximum of chunk c; rows in increasing order
+            const uint32_t tacc = tmem + b * kH2 + 128 * cw;
 #pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
+            for (int lh = 0; lh < 2; ++lh) {
+                const int rb = c * kChunk + 32 * qr + 16 * lh;
+                if (rb >= n) break;   // the same for the whole warp
+                const int ra = rb + (lane >> 2), rc = ra + 8;
+                const bool va = ra < n, vc = rc < n;
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int row = r0 + wm * 32 + mt * 16 + (lane >> 2) + 8 * h;
-                    if (row < n) {
+                for (int cq = 0; cq < 2; ++cq) {
+                    uint32_t v[32];
+                    tmem_load_16x256b_x8(tacc + ((uint32_t)(32 * qr + 16 * lh) << 16) + 64 * cq, v);
 #pragma unroll
-                        for (int nt = 0; nt < 8; ++nt)
+                    for (int g = 0; g < 8; ++g)
 #pragma unroll
-                            for (int e = 0; e < 2; ++e) {
-                                const float v = fmaxf(acc[mt][nt][2 * h + e] + b2[2 * nt + e], 0.f);
-                                if (v > best[2 * nt + e]) {
-                                    best[2 * nt + e] = v;
-                                    bestr[2 * nt + e] = row;
+                        for (int e = 0; e < 2; ++e) {
+                            const int k = 2 * (8 * cq + g) + e;
+                            if constexpr (kTrain) {
+                                const float za = fmaxf(__uint_as_float(v[4 * g + e]) + b2[k], 0.f);
+                                if (va && za > best[k]) {
+                                    best[k] = za;
+                                    bestr[k] = ra;
                                 }
+                                const float zc = fmaxf(__uint_as_float(v[4 * g + 2 + e]) + b2[k], 0.f);
+                                if (vc && zc > best[k]) {
+                                    best[k] = zc;
+                                    bestr[k] = rc;
+                                }
+                            } else {   // max(0, max_rows z) = max_rows relu(z): one maximum an element
+                                if (va) best[k] = fmaxf(best[k], __uint_as_float(v[4 * g + e]) + b2[k]);
+                                if (vc) best[k] = fmaxf(best[k], __uint_as_float(v[4 * g + 2 + e]) + b2[k]);
                             }
-                    }
+                        }
                 }
-            __syncthreads();   // the next chunk overwrites sH1
+            }
+            tc_fence_before();
         }
-        // combine the 8 lanes of each column, then the two row halves
+        if (fault) break;
+        // combine the 8 lanes of each column, then the four row quarters
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
+        for (int k = 0; k < 32; ++k) {
             float v = best[k];
             int r = bestr[k];
 #pragma unroll
             for (int off = 4; off < 32; off <<= 1) {
                 const float ov = __shfl_xor_sync(0xffffffffu, v, off);
-                const int orr = __shfl_xor_sync(0xffffffffu, r, off);
-                if (ov > v || (ov == v && orr < r)) {
-                    v = ov;
-                    r = orr;
+                if constexpr (kTrain) {
+                    const int orr = __shfl_xor_sync(0xffffffffu, r, off);
+                    if (ov > v || (ov == v && orr < r)) {
+                        v = ov;
+                        r = orr;
+                    }
+                } else {
+                    v = fmaxf(v, ov);
                 }
             }
             if (lane < 4) {
-                const int col = wn * 64 + (k >> 1) * 8 + 2 * lane + (k & 1);
-                sRV[wm * kH2 + col] = v;
-                sRI[wm * kH2 + col] = r;
+                const int col = 128 * cw + 8 * (k >> 1) + 2 * lane + (k & 1);
+                sRV[qr * kH2 + col] = v;
+                if (kTrain) sRI[qr * kH2 + col] = r;
             }
         }
         __syncthreads();
         {
             float v = sRV[tid];
-            int r = sRI[tid];
-            const float v1 = sRV[kH2 + tid];
-            const int r1 = sRI[kH2 + tid];
-            if (v1 > v || (v1 == v && r1 < r)) {
-                v = v1;
-                r = r1;
+            int r = kTrain ? sRI[tid] : 0;
+#pragma unroll
+            for (int q = 1; q < 4; ++q) {
+                const float v1 = sRV[q * kH2 + tid];
+                if constexpr (kTrain) {
+                    const int r1 = sRI[q * kH2 + tid];
+                    if (v1 > v || (v1 == v && r1 < r)) {
+                        v = v1;
+                        r = r1;
+                    }
+                } else {
+                    v = fmaxf(v, v1);
+                }
             }
             sG[tid] = v;
             sR[tid] = r;
@@ -356,6 +519,17 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
             cache[s].r[tid] = sR[tid];
             if (tid < kH3) cache[s].z3[tid] = sZ3[tid];
         }
+    }
+    if (fault && tid == 0) {
+        *reinterpret_cast<volatile int*>(net.fault) = 1;
+        __threadfence_system();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)kTmemCols)
+                     : "memory");
     }
 }
 

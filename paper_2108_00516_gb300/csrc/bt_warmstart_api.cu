@@ -7,12 +7,19 @@
 #include "bt_ws.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <new>
 #include <vector>
 
 using namespace bthost;
 namespace W = bt::ws;
+
+namespace {
+// bound of the forward pass's waits on the tensor cores (bt_debug_tensor_wait_ns)
+constexpr long long kDefaultTensorWaitNs = 1000000000LL;
+std::atomic<long long> g_tensor_wait_ns{kDefaultTensorWaitNs};
+}  // namespace
 
 struct bt_warmstart {
     cudaStream_t stream = nullptr;
@@ -28,6 +35,10 @@ struct bt_warmstart {
     DevBuf ids, y, cache, G, loss_per, grad, loss;
     DevBuf app_samples, app_y, app_graphs, app_scratch, app_status, app_items;
     PinBuf pin_app, pin_status;   // staging of the apply tables and the per-graph status
+    // fault word of the forward pass (mapped pinned host memory: the kernel
+    // writes it, the host reads it after the call's synchronisation)
+    int* fault_host = nullptr;
+    int* fault_dev = nullptr;
     // the apply tables on the device were built for this batch build (0:
     // none); a warm-started batched solve of an unchanged batch reuses them
     uint64_t app_build = 0;
@@ -35,7 +46,8 @@ struct bt_warmstart {
 
     W::Net net() const
     {
-        return W::Net{master.as<float>(), wb.as<__nv_bfloat16>(), m.as<float>(), v.as<float>()};
+        return W::Net{master.as<float>(), wb.as<__nv_bfloat16>(), m.as<float>(), v.as<float>(), fault_dev,
+                      g_tensor_wait_ns.load(std::memory_order_relaxed)};
     }
 
     ~bt_warmstart()
@@ -47,6 +59,7 @@ struct bt_warmstart {
             b->release();
         pin_app.release();
         pin_status.release();
+        if (fault_host) cudaFreeHost(fault_host);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
@@ -95,6 +108,19 @@ int reserve(bt_warmstart* ws, int64_t add_pts, int add_sets)
         ws->cap_samples = cap;
     }
     return BT_OK;
+}
+
+// BT_ERR_TIMEOUT when a forward pass since the last check gave up waiting on
+// the tensor cores (its outputs are not valid); clears the fault word.  Call
+// after the stream has been synchronised.
+int take_fault(bt_warmstart* ws, const char* who)
+{
+    volatile int* f = ws->fault_host;
+    if (*f == 0) return BT_OK;
+    *f = 0;
+    return fail(BT_ERR_TIMEOUT, std::string(who) +
+                                    ": a wait of the network's forward pass on the tensor cores ran out; "
+                                    "its outputs were discarded");
 }
 
 int check_ready(const bt_warmstart* ws, const char* who)
@@ -299,10 +325,16 @@ int apply_graphs(bt_warmstart* ws, bt_graph* const* gs, int n_graphs, int* statu
     if (st != BT_OK) return st;
     BT_CUDA(cudaStreamSynchronize(s), "warm start: synchronize");
     ws->pin_status.busy = false;
+    for (int k = 0; k < n_graphs; ++k) gs[k]->pin_state.busy = false;
+    st = take_fault(ws, "warm start");
+    if (st != BT_OK) {     // no graph's poses are stored
+        if (status_out)
+            for (int k = 0; k < n_graphs; ++k) status_out[k] = st;
+        return st;
+    }
     int worst = BT_OK;
     for (int k = 0; k < n_graphs; ++k) {
         bt_graph* g = gs[k];
-        g->pin_state.busy = false;
         const int bad = ws->pin_status.at<int>(0)[k];
         if (status_out) status_out[k] = bad ? BT_ERR_SINGULAR : BT_OK;
         if (bad) {
@@ -344,6 +376,14 @@ int bt_warmstart_create(void* cuda_stream, bt_warmstart** out)
         if (e == cudaSuccess) e = b->ensure(sizeof(float) * W::kNumParams);
     }
     if (e == cudaSuccess) e = ws->wb.ensure(sizeof(__nv_bfloat16) * W::kNumBf16);
+    if (e == cudaSuccess)
+        e = alloc_should_fail() ? cudaErrorMemoryAllocation
+                                : cudaHostAlloc(reinterpret_cast<void**>(&ws->fault_host), sizeof(int),
+                                                cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+        *ws->fault_host = 0;
+        e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&ws->fault_dev), ws->fault_host, 0);
+    }
     if (e != cudaSuccess) {
         delete ws;
         return cuda_fail(e, "bt_warmstart_create: parameters");
@@ -560,7 +600,7 @@ int bt_warmstart_predict(bt_warmstart* ws, const int32_t* ids, int32_t n, float*
     BT_CUDA(cudaMemcpyAsync(y_out, ws->y.p, sizeof(float) * W::kOut * (size_t)n, cudaMemcpyDeviceToHost, ws->stream),
             "read outputs");
     BT_CUDA(cudaStreamSynchronize(ws->stream), "bt_warmstart_predict: synchronize");
-    return BT_OK;
+    return take_fault(ws, "bt_warmstart_predict");
 }
 
 int bt_warmstart_get_sample(const bt_warmstart* ws, int32_t id, float* centre, float* label)
@@ -593,7 +633,7 @@ int bt_warmstart_gradient(bt_warmstart* ws, const int32_t* ids, int32_t n, float
     if (loss_out)
         BT_CUDA(cudaMemcpyAsync(loss_out, ws->loss.p, sizeof(double), cudaMemcpyDeviceToHost, ws->stream), "read loss");
     BT_CUDA(cudaStreamSynchronize(ws->stream), "bt_warmstart_gradient: synchronize");
-    return BT_OK;
+    return take_fault(ws, "bt_warmstart_gradient");
 }
 
 int bt_warmstart_train_step(bt_warmstart* ws, const int32_t* ids, int32_t n, float lr, double* loss_out)
@@ -604,6 +644,8 @@ int bt_warmstart_train_step(bt_warmstart* ws, const int32_t* ids, int32_t n, flo
     if (st != BT_OK) return st;
     if (n <= 0 || !ids || !std::isfinite(lr) || lr < 0.f)
         return fail(BT_ERR_INVALID, "bt_warmstart_train_step: bad arguments");
+    st = take_fault(ws, "bt_warmstart_train_step (an earlier step)");
+    if (st != BT_OK) return st;
     st = gradient_pass(ws, ids, n);
     if (st != BT_OK) return st;
     const double b1 = 0.9, b2 = 0.999;
@@ -615,6 +657,7 @@ int bt_warmstart_train_step(bt_warmstart* ws, const int32_t* ids, int32_t n, flo
     if (loss_out) {
         BT_CUDA(cudaMemcpyAsync(loss_out, ws->loss.p, sizeof(double), cudaMemcpyDeviceToHost, ws->stream), "read loss");
         BT_CUDA(cudaStreamSynchronize(ws->stream), "bt_warmstart_train_step: synchronize");
+        return take_fault(ws, "bt_warmstart_train_step");
     }
     return BT_OK;
 }
@@ -692,6 +735,8 @@ int bt_batch_solve_warm(bt_batch* b, bt_warmstart* ws, int32_t iters, int32_t fa
     BT_CUDA(cudaStreamSynchronize(s), "bt_batch_solve_warm: synchronize");
     b->pin_state.busy = false;
     ws->pin_status.busy = false;
+    st = take_fault(ws, "bt_batch_solve_warm");
+    if (st != BT_OK) return st;     // before any graph's poses are stored
     std::vector<int> ws_status(G, BT_OK);
     for (size_t k = 0; k < G; ++k) ws_status[k] = ws->pin_status.at<int>(0)[k] ? BT_ERR_SINGULAR : BT_OK;
     std::vector<bt_solve_report> r(G);
@@ -724,6 +769,12 @@ int bt_batch_solve_warm(bt_batch* b, bt_warmstart* ws, int32_t iters, int32_t fa
         for (size_t k = 0; k < G; ++k) reps[k] = r[k];
     if (worst != BT_OK) return fail(worst, "bt_batch_solve_warm: some graphs were singular; their poses are unchanged");
     return BT_OK;
+}
+
+int64_t bt_debug_tensor_wait_ns(int64_t ns)
+{
+    const long long v = ns < 0 ? kDefaultTensorWaitNs : (long long)ns;
+    return (int64_t)g_tensor_wait_ns.exchange(v);
 }
 
 }  // extern "C"

@@ -64,6 +64,8 @@ struct Net {
     __nv_bfloat16* wb;          // [kNumBf16]
     float* m;                   // Adam first moments
     float* v;                   // Adam second moments
+    int* fault;                 // set to 1 when a bounded wait of the forward pass ran out (mapped host word)
+    long long wait_ns;          // bound of the forward pass's waits on the tensor cores (<= 0: give up at once)
 };
 
 // What the backward pass needs of one set's forward pass.

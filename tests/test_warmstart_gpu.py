@@ -60,7 +60,8 @@ def _params(seed):
     return (P + rng.normal(scale=0.01, size=P.shape)).astype(np.float32)
 
 
-SIZES = [1, 7, 63, 64, 65, 130, 257, 800]
+# set sizes around the 128-point chunks of the forward pass
+SIZES = [1, 7, 63, 64, 65, 127, 128, 129, 130, 255, 256, 257, 800]
 
 
 def _loaded(bt, sets, params):
@@ -94,6 +95,24 @@ def test_forward_is_set_order_invariant(bt):
     ws = _loaded(bt, [(p, q, M0, M), (p[perm], q[perm], M0, M)], _params(2))
     y = ws.predict([0, 1])
     assert np.allclose(y[0], y[1], rtol=1e-5, atol=1e-6)
+
+
+def test_forward_wait_timeout_is_reported(bt):
+    """A forward pass whose bounded wait on the tensor cores runs out reports
+    BT_ERR_TIMEOUT (here the bound is 0: the first wait gives up at once) and
+    leaves the context usable: the next pass gives the same outputs."""
+    sets = _sets(3, [200, 333])
+    ws = _loaded(bt, sets, _params(3))
+    y0 = ws.predict([0, 1])
+    prev = bt.debug_tensor_wait_ns(0)
+    try:
+        with pytest.raises(bt.BTError) as e:
+            ws.predict([0, 1])
+        assert e.value.status == bt.BT_ERR_TIMEOUT
+    finally:
+        bt.debug_tensor_wait_ns(-1)
+    assert prev == 1_000_000_000
+    assert np.array_equal(ws.predict([0, 1]), y0)
 
 
 def _routing_gap(P, x):
