@@ -256,10 +256,11 @@ def cpu_model() -> str:
     return platform.processor() or platform.machine()
 
 
-def cpu_baseline(seq, graphs, inits, seconds: float, iters: int, tiny=None):
+def cpu_baseline(seq, graphs, inits, seconds: float, iters: int, tiny=None, batch=None):
     """The FP64 oracle, as it stands, on a bounded sample of the same graphs
     (all host threads over ordered pairs, then one thread on a shorter
-    sample), and on the whole tiny workload (100 graphs, 7 iterations)."""
+    sample), on the whole tiny workload (100 graphs, 7 iterations) and on a
+    bounded sample of the batched workload's graphs (all host threads)."""
     import oracle as O
     n_threads = os.cpu_count() or 1
     order = sample_order(len(graphs))
@@ -308,6 +309,24 @@ def cpu_baseline(seq, graphs, inits, seconds: float, iters: int, tiny=None):
         out["tiny_workload"] = {"graphs": len(tiny), "iters": 7, "unit": "solves/s",
                                 "value": res["threads"], "single_thread": res["single_thread"],
                                 "workload": "N=4, 160x120, 200 matches per pair (20% outliers)"}
+    if batch:
+        # graphs of uneven size: the pixel-pair rate is the comparable figure
+        order_b = sample_order(len(batch))
+        done_b, px_b, t0 = 0, 0, time.perf_counter()
+        while True:
+            g = batch[order_b[done_b % len(batch)]]
+            if O.solve(g, iters, n_threads=n_threads)["status"] != 0:
+                raise RuntimeError("oracle solve failed")
+            done_b += 1
+            px_b += pixel_pairs(g)
+            el_b = time.perf_counter() - t0
+            if el_b >= max(1.0, seconds / 3):
+                break
+        out["batched_workload"] = {
+            "graphs": done_b, "iters": iters, "unit": "solves/s", "value": round(done_b / el_b, 3),
+            "value_pixel_pairs_per_s": round(px_b / el_b, 1),
+            "sample": f"{done_b} of the {len(batch)} batched graphs (a stride through the batch), "
+                      f"{n_threads} threads over ordered pairs, {el_b:.1f} s"}
     return out
 
 
@@ -651,9 +670,12 @@ def run_ours(args):
 
     base = None
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
-        base = cpu_baseline(seq, graphs, inits, args.cpu_seconds, it, tiny)
+        base = cpu_baseline(seq, graphs, inits, args.cpu_seconds, it, tiny, graphs_b)
         if tiny_gpu and base.get("tiny_workload"):
             tiny_gpu["vs_oracle_all_threads"] = round(tiny_gpu["value"] / base["tiny_workload"]["value"], 1)
+        if batched and base.get("batched_workload"):
+            batched["batched_vs_oracle_pixel_pairs"] = round(
+                batched["pixel_pairs_per_s"] / base["batched_workload"]["value_pixel_pairs_per_s"], 1)
 
     if rank == 0:
         out = {"metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world,
