@@ -26,6 +26,7 @@ from __future__ import annotations
 import argparse
 import gc
 import hashlib
+import itertools
 import json
 import os
 import re
@@ -753,7 +754,13 @@ def run_e2e(bt, seq, graphs, pools, inits, stream, args, world):
         h2d = d2h = 0
         pg = bt.PoseGraph(stream=stream)
         ids = {}
-        have = set()
+        have = set()          # frame pairs (a < b) whose correspondence set the graph holds
+        partners = {}         # frame -> frames it shares a set with
+
+        def link(a, b):
+            have.add((a, b))
+            partners.setdefault(a, set()).add(b)
+            partners.setdefault(b, set()).add(a)
 
         def add(t, olds=()):
             # the new frame with its correspondence sets to earlier frames
@@ -762,19 +769,19 @@ def run_e2e(bt, seq, graphs, pools, inits, stream, args, world):
             sets = [(ids[a],) + matches_h[(a, t)][::-1] for a in olds]
             ids[t] = pg.add_frame(d, n, m, seq.cam.as_tuple(), seq.poses_true[t], fixed=(t == 0), matches=sets)
             h2d += d.nbytes + n.nbytes + m.nbytes + sum(x.nbytes + y.nbytes for _, x, y in sets)
-            have.update((a, t) for a in olds)
+            for a in olds:
+                link(a, t)
 
         add(0)
         for k, nodes in enumerate(graphs):
             t = nodes[-1]
             add(t, [a for a in nodes if a < t and (a, t) not in have])
-            for a in nodes:
-                for b in nodes:
-                    if a < b and (a, b) not in have:
-                        pa, pb = matches_h[(a, b)]
-                        pg.set_matches(ids[a], ids[b], pa, pb)
-                        have.add((a, b))
-                        h2d += pa.nbytes + pb.nbytes
+            for a, b in itertools.combinations(sorted(nodes), 2):
+                if (a, b) not in have:
+                    pa, pb = matches_h[(a, b)]
+                    pg.set_matches(ids[a], ids[b], pa, pb)
+                    link(a, b)
+                    h2d += pa.nbytes + pb.nbytes
             pg.set_active([ids[f] for f in nodes])
             P0 = np.stack(inits[k])
             pg.set_poses(P0)
@@ -782,10 +789,12 @@ def run_e2e(bt, seq, graphs, pools, inits, stream, args, world):
             P, rep = pg.solve(it)
             d2h += 96 * len(nodes) + 32 * (it + 1) + 16
             # memory pool (Sec. IV-E): pools[t] is the pool after frame t;
-            # a frame that did not join it is dropped
+            # a frame that did not join it is dropped with its sets
             if t not in pools[t]:
                 pg.remove_frame(ids[t])
-                have = {p for p in have if t not in p}
+                for o in partners.pop(t, ()):
+                    have.discard((min(o, t), max(o, t)))
+                    partners[o].discard(t)
         pg.close()
         return h2d, d2h
 
