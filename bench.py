@@ -800,6 +800,20 @@ def run_e2e(bt, seq, graphs, pools, inits, stream, args, world):
 
     e2e_step()                      # warm-up
     torch.cuda.synchronize()
+    # the host's pinned -> device copy rate for one frame's bytes (the copies
+    # of the end-to-end path move ~5 MB a solve; boxes differ here)
+    d0, n0, m0 = frames_h[0]
+    probe_h = torch.zeros(d0.nbytes + n0.nbytes + m0.nbytes, dtype=torch.uint8, pin_memory=True)
+    probe_d = torch.empty_like(probe_h, device="cuda")
+    for _ in range(5):
+        probe_d.copy_(probe_h, non_blocking=True)
+    torch.cuda.synchronize()
+    p0 = time.perf_counter()
+    for _ in range(50):
+        probe_d.copy_(probe_h, non_blocking=True)
+    torch.cuda.synchronize()
+    h2d_gbs = probe_h.numel() * 50 / (time.perf_counter() - p0) / 1e9
+    del probe_h, probe_d
     if world > 1:
         dist.barrier()
     gc_pause()
@@ -821,9 +835,11 @@ def run_e2e(bt, seq, graphs, pools, inits, stream, args, world):
             "steps": args.e2e_steps,
             "per_step_solves_per_s": {"median": round(statistics.median(rates), 2), "min": round(rates[0], 2),
                                       "max": round(rates[-1], 2)},
+            "h2d_copy_gbs": round(h2d_gbs, 1),
             "note": "pinned host buffers through bt_add_frame (with the new frame's correspondence sets) / "
                     "bt_set_matches / bt_solve; frames arrive one per solve; non-keyframes are removed after "
-                    "their solve"}
+                    "their solve; h2d_copy_gbs: one frame's bytes copied from pinned memory, measured before "
+                    "the timed steps"}
 
 
 # --------------------------------------------------------------------------- reference arm
