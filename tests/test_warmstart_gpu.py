@@ -115,6 +115,21 @@ def test_forward_wait_timeout_is_reported(bt):
     assert np.array_equal(ws.predict([0, 1]), y0)
 
 
+def test_training_and_inference_forward_agree(bt):
+    """The training forward pass (running maxima with the row of each) and
+    the inference pass (maxima only) pool the same values: the mean loss of
+    bt_warmstart_gradient, formed from the training pass's outputs, equals
+    the loss formed here from bt_warmstart_predict's outputs."""
+    sets = _sets(4, SIZES)
+    ws = _loaded(bt, sets, _params(4))
+    ids = list(range(len(sets)))
+    y = ws.predict(ids).astype(np.float64)
+    ystar = np.array([ws.sample(k)[1] for k in ids], np.float64)
+    loss_inf = float(np.mean(0.5 * np.sum((y - ystar) ** 2, axis=1)))
+    loss_train, _ = ws.gradient(ids)
+    assert abs(loss_train - loss_inf) <= 1e-6 * loss_inf, (loss_train, loss_inf)
+
+
 def _routing_gap(P, x):
     """Smallest gap, over channels with a positive maximum, between the
     maximum of h2 and the runner-up (FP64 oracle values)."""
