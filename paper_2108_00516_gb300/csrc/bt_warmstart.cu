@@ -881,7 +881,18 @@ __global__ void rebase_kernel(Sample* __restrict__ smp, int n, const float* old_
 // ---------------------------------------------------------------------------
 
 constexpr int kAvgThreads = 256;
-constexpr int kScr = 64;        // scratch doubles per edge: D [12], e [6], A [36]
+constexpr int kScr = kAvgScratch;   // scratch doubles per edge (bt_ws.h)
+constexpr int kScrP = 54;           // P = A^T W A, lower triangle (21)
+constexpr int kScrG = 75;           // A^T W e (6)
+static_assert(kScrG + 6 <= kScr, "averaging scratch per edge");
+
+// Row and column of entry q (0..20) of a 6x6 lower triangle, row by row.
+__device__ __forceinline__ void tri_rc(int q, int& r, int& c)
+{
+    r = 0;
+    while ((r + 1) * (r + 2) / 2 <= q) ++r;
+    c = q - r * (r + 1) / 2;
+}
 
 __global__ void __launch_bounds__(kAvgThreads) average_kernel(const AvgGraph* __restrict__ graphs)
 {
@@ -969,30 +980,57 @@ __global__ void __launch_bounds__(kAvgThreads) average_kernel(const AvgGraph* __
             }
     }
     __syncthreads();
-    // 3. normal equations over the free nodes (lower triangle) and right-hand side
+    // 3. normal equations over the free nodes (lower triangle) and right-hand
+    // side.  The edge (i, j) has Jacobians J_i = -A, J_j = I on its
+    // residual e (weights W): its i-side diagonal block A^T W A and its
+    // gradient term A^T W e are formed once per edge, with the lanes packed
+    // over (edge, entry) -- a warp's FP64 instruction takes its DP unit as
+    // long whether 6 or 32 lanes are active -- then summed per node.
+    for (int idx = tid; idx < E * 27; idx += kAvgThreads) {
+        const int e = idx / 27, q = idx % 27;
+        if (G.smp[e].n <= 0) continue;
+        double* scr = G.scratch + (size_t)e * kScr;
+        const double* A = scr + 18;
+        double v = 0.0;
+        if (q < 21) {
+            int al, be;
+            tri_rc(q, al, be);
+            for (int g = 0; g < 6; ++g) v += A[g * 6 + al] * Wd[g] * A[g * 6 + be];
+            scr[kScrP + q] = v;
+        } else {
+            const int al = q - 21;
+            for (int g = 0; g < 6; ++g) v += A[g * 6 + al] * Wd[g] * scr[12 + g];
+            scr[kScrG + al] = v;
+        }
+    }
+    __syncthreads();
+    // diagonal blocks: free node a's edges, A^T W A where a is the i side, W
+    // where it is the j side
+    for (int idx = tid; idx < nf * 21; idx += kAvgThreads) {
+        const int f = idx / 21;
+        int al, be;
+        tri_rc(idx % 21, al, be);
+        const int a = freenode[f];
+        double v = 0.0;
+        for (int m = 0; m < N; ++m) {
+            const int e = m == a ? -1 : eof[a * N + m];
+            if (e < 0) continue;
+            if (G.edges[e].j == a) v += al == be ? Wd[al] : 0.0;
+            else v += G.scratch[(size_t)e * kScr + kScrP + idx % 21];
+        }
+        H[(6 * f + al) * ld + 6 * f + be] = v;
+    }
+    // off-diagonal blocks: -A^T W (a = i) or -W A (a = j) of the edge between
     for (int idx = tid; idx < n * n; idx += kAvgThreads) {
         const int r = idx / n, c = idx % n;
-        if (c > r) continue;
+        if (c > r || r / 6 == c / 6) continue;
         const int a = freenode[r / 6], al = r % 6, bn = freenode[c / 6], be = c % 6;
         double v = 0.0;
-        if (a == bn) {
-            for (int m = 0; m < N; ++m) {
-                const int e = m == a ? -1 : eof[a * N + m];
-                if (e < 0) continue;
-                if (G.edges[e].j == a) {
-                    v += al == be ? Wd[al] : 0.0;
-                } else {
-                    const double* A = G.scratch + (size_t)e * kScr + 18;
-                    for (int g = 0; g < 6; ++g) v += A[g * 6 + al] * Wd[g] * A[g * 6 + be];
-                }
-            }
-        } else {
-            const int e = eof[a * N + bn];
-            if (e >= 0) {
-                const double* A = G.scratch + (size_t)e * kScr + 18;
-                if (G.edges[e].i == a) v = -A[be * 6 + al] * Wd[be];      // J_a = -A, J_b = I
-                else v = -Wd[al] * A[al * 6 + be];                        // J_a = I, J_b = -A
-            }
+        const int e = eof[a * N + bn];
+        if (e >= 0) {
+            const double* A = G.scratch + (size_t)e * kScr + 18;
+            if (G.edges[e].i == a) v = -A[be * 6 + al] * Wd[be];      // J_a = -A, J_b = I
+            else v = -Wd[al] * A[al * 6 + be];                        // J_a = I, J_b = -A
         }
         H[r * ld + c] = v;
     }
@@ -1003,11 +1041,8 @@ __global__ void __launch_bounds__(kAvgThreads) average_kernel(const AvgGraph* __
             const int e = m == a ? -1 : eof[a * N + m];
             if (e < 0) continue;
             const double* scr = G.scratch + (size_t)e * kScr;
-            if (G.edges[e].j == a) {
-                v += Wd[al] * scr[12 + al];
-            } else {
-                for (int g = 0; g < 6; ++g) v -= scr[18 + g * 6 + al] * Wd[g] * scr[12 + g];
-            }
+            if (G.edges[e].j == a) v += Wd[al] * scr[12 + al];
+            else v -= scr[kScrG + al];
         }
         b[r] = v;
     }

@@ -228,7 +228,7 @@ int enqueue_apply(bt_warmstart* ws, bt_graph* const* gs, int n_graphs, double* c
     BT_CUDA(ws->app_samples.ensure(sizeof(W::Sample) * (size_t)std::max(S, 1)), "alloc samples");
     BT_CUDA(ws->app_items.ensure(sizeof(W::PrepItem) * (size_t)std::max(S, 1)), "alloc items");
     BT_CUDA(ws->app_y.ensure(sizeof(float) * W::kOut * (size_t)std::max(S, 1)), "alloc outputs");
-    BT_CUDA(ws->app_scratch.ensure(sizeof(double) * 64 * (size_t)std::max(S, 1)), "alloc scratch");
+    BT_CUDA(ws->app_scratch.ensure(sizeof(double) * W::kAvgScratch * (size_t)std::max(S, 1)), "alloc scratch");
     BT_CUDA(ws->app_graphs.ensure(sizeof(W::AvgGraph) * (size_t)n_graphs), "alloc graphs");
     BT_CUDA(ws->app_status.ensure(sizeof(int) * (size_t)n_graphs), "alloc status");
     for (int k = 0; k < n_graphs; ++k) {
@@ -242,7 +242,7 @@ int enqueue_apply(bt_warmstart* ws, bt_graph* const* gs, int n_graphs, double* c
         a.y = ws->app_y.as<float>() + (size_t)first[k] * W::kOut;
         a.smp = ws->app_samples.as<W::Sample>() + first[k];
         a.pose = pose[k];
-        a.scratch = ws->app_scratch.as<double>() + (size_t)first[k] * 64;
+        a.scratch = ws->app_scratch.as<double>() + (size_t)first[k] * W::kAvgScratch;
         a.status = ws->app_status.as<int>() + k;
         avg.push_back(a);
     }

@@ -85,7 +85,7 @@ struct AvgGraph {
     const float* y;             // [n_edges][6] network outputs
     const Sample* smp;          // [n_edges] (centres)
     double* pose;               // [N][12] in: initial poses, out: warm-start poses
-    double* scratch;            // [n_edges][48]
+    double* scratch;            // [n_edges][kAvgScratch]
     int* status;                // 0 ok, 1 singular (poses left unchanged)
 };
 
@@ -106,6 +106,10 @@ cudaError_t launch_reduce(const float* G, const float* loss_per, int n, float* g
 // Adam step: c1 = 1 / (1 - beta1^t), c2 = 1 / (1 - beta2^t).
 cudaError_t launch_adam(Net net, const float* grad, float lr, float beta1, float beta2, float eps, float c1,
                         float c2, cudaStream_t s);
+// Scratch doubles per edge of an averaging launch: the increment D [12], the
+// residual e [6], the adjoint A [36], P = A^T W A (lower triangle) [21],
+// A^T W e [6], padding.
+constexpr int kAvgScratch = 88;
 cudaError_t launch_average(const AvgGraph* graphs, int n_graphs, int max_free, cudaStream_t s);
 size_t average_smem_bytes(int max_free, int max_N);
 // Rebases sample point pointers after the point pool moved.
