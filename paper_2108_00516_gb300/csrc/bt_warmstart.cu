@@ -831,26 +831,56 @@ __global__ void prep_kernel(Sample* __restrict__ smp, const PrepItem* __restrict
     Sample* S = smp + it.sample;
     const int n = S->n;
     const float* q = S->q;
-    double sx = 0.0, sy = 0.0, sz = 0.0;
-    for (int k = lane; k < n; k += 32) {
-        sx += q[3 * k];
-        sy += q[3 * k + 1];
-        sz += q[3 * k + 2];
-    }
+    // the centre: compensated FP32 sums per lane, combined in FP64 (a warp's
+    // FP64 instruction, a conversion included, holds its DP unit as long as
+    // a full one whatever the active lanes, so the per-point work stays off it)
+    float s3[3] = {0.f, 0.f, 0.f}, k3[3] = {0.f, 0.f, 0.f};
+    for (int k = lane; k < n; k += 32)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float y = q[3 * k + d] - k3[d];
+            const float t = s3[d] + y;
+            k3[d] = (t - s3[d]) - y;
+            s3[d] = t;
+        }
+    double sx = (double)s3[0] - (double)k3[0], sy = (double)s3[1] - (double)k3[1],
+           sz = (double)s3[2] - (double)k3[2];
     for (int off = 16; off > 0; off >>= 1) {
         sx += __shfl_xor_sync(0xffffffffu, sx, off);
         sy += __shfl_xor_sync(0xffffffffu, sy, off);
         sz += __shfl_xor_sync(0xffffffffu, sz, off);
     }
-    if (lane != 0) return;
+    // M0 = T_j T_i^-1 one entry a lane (lanes 0-11, the operations of
+    // pose_inv and pose_mul), the centre on lanes 12-14
+    if (lane < 12) {
+        const int r = lane >> 2, cc = lane & 3;
+        const double* Ti = it.Ti0;
+        const double* Tj = it.Tj0;
+        double v;
+        if (cc < 3) {
+            v = Tj[r * 4 + 0] * Ti[cc * 4 + 0] + Tj[r * 4 + 1] * Ti[cc * 4 + 1] + Tj[r * 4 + 2] * Ti[cc * 4 + 2];
+        } else {
+            double iv[3];
+            for (int k = 0; k < 3; ++k) iv[k] = -(Ti[0 * 4 + k] * Ti[3] + Ti[1 * 4 + k] * Ti[7] + Ti[2 * 4 + k] * Ti[11]);
+            v = Tj[r * 4 + 0] * iv[0] + Tj[r * 4 + 1] * iv[1] + Tj[r * 4 + 2] * iv[2];
+            v += Tj[r * 4 + 3];
+        }
+        S->m[lane] = (float)v;
+    } else if (lane < 15) {
+        const double sd = lane == 12 ? sx : lane == 13 ? sy : sz;
+        S->c[lane - 12] = (float)(n > 0 ? sd / n : 0.0);
+    } else if (lane == 15) {
+        S->c[3] = 0.f;
+    } else if (lane < 22 && !it.Ti1) {
+        S->ystar[lane - 16] = 0.f;
+    }
+    if (lane != 0 || !it.Ti1) return;
+    // training label (one lane): the increment from M0 to the converged M
     const double c[3] = {n > 0 ? sx / n : 0.0, n > 0 ? sy / n : 0.0, n > 0 ? sz / n : 0.0};
     double inv[12], M0[12];
     pose_inv(it.Ti0, inv);
     pose_mul(it.Tj0, inv, M0);
-    for (int k = 0; k < 12; ++k) S->m[k] = (float)M0[k];
-    for (int k = 0; k < 3; ++k) S->c[k] = (float)c[k];
-    S->c[3] = 0.f;
-    if (it.Ti1) {
+    {
         double M[12], M0inv[12], D[12], w[3], th;
         pose_inv(it.Ti1, inv);
         pose_mul(it.Tj1, inv, M);
@@ -862,8 +892,6 @@ __global__ void prep_kernel(Sample* __restrict__ smp, const PrepItem* __restrict
             S->ystar[r] = (float)(w[r] / kSW);
             S->ystar[3 + r] = (float)((D[r * 4 + 3] + Rc - c[r]) / kSU);
         }
-    } else {
-        for (int k = 0; k < 6; ++k) S->ystar[k] = 0.f;
     }
 }
 
