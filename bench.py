@@ -737,6 +737,8 @@ def run_e2e(bt, seq, graphs, pools, inits, stream, args, world):
         out[...] = a
         return out
 
+    # each graph's starting poses as one (N, 4, 4) array, as a caller holds them
+    inits_h = [pinned(np.ascontiguousarray(np.stack(x))) for x in inits]
     frames_h = {}
     for t in sorted({f for g in graphs for f in g} | {0}):
         r = seq.frame(t)
@@ -783,8 +785,7 @@ def run_e2e(bt, seq, graphs, pools, inits, stream, args, world):
                     link(a, b)
                     h2d += pa.nbytes + pb.nbytes
             pg.set_active([ids[f] for f in nodes])
-            P0 = np.stack(inits[k])
-            pg.set_poses(P0)
+            pg.set_poses(inits_h[k])
             h2d += 96 * len(nodes)
             P, rep = pg.solve(it)
             d2h += 96 * len(nodes) + 32 * (it + 1) + 16
